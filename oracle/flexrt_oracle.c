@@ -1,0 +1,749 @@
+/*
+ * flexrt_oracle.c -- plain, slow, FP64 CPU oracle of the FlexRT adaptive
+ * ray-tracing radiative-transfer step (Cain & D'Aloisio, arXiv:2409.04521).
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or constant generator with the CUDA path; the two
+ * agree only because both follow the same reading of the paper.
+ *
+ * Everything here is double precision in physical cgs units, written in the
+ * order the paper states the method:
+ *   Sec. 3.1, Eq. 1  -- 12*4^l HEALPix rays cast from the centre of every
+ *                       source cell, NESTED pixel numbering, a fresh random
+ *                       rotation of each source's sphere every step;
+ *   Sec. 3.1         -- each ray moves exactly one cell width per step and is
+ *                       absorbed in every cell it crosses;
+ *   Sec. 3.2, Eq. 2-3 -- a level-l ray splits into (l+1, 4p+i), i=0..3, once
+ *                       its distance from the source reaches r_split(l);
+ *   Sec. 4.2, Eq. 13 and 17 -- tau = kappa*ds and the cell-averaged
+ *                       photo-ionisation rate for a finite mean free path
+ *                       (kappa = n_HI sigma + 1/lambda_mfp);
+ *   Sec. 4.1, Eq. 6-10 -- C2-Ray style time-dependent ionisation update;
+ *   Sec. 4.1, Eq. 12 -- temperature equation (static density, fixed z).
+ * Where the paper is silent the reading taken is stated at the spot
+ * (fixed-point geometry, termination, rotation sampler, rate fits ...).
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no FMA contraction:
+ * the HEALPix vectors and rotations must be the correctly rounded result of
+ * every written operation, in the written order).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_FRAC_BITS 21                     /* positions: 2^-21 cell units      */
+#define OR_S ((int64_t)1 << OR_FRAC_BITS)   /* one cell in fixed point          */
+#define OR_VQ_BITS 24                       /* pixel vectors / rotation entries */
+#define OR_MAXB 8                           /* max frequency bins               */
+#define OR_MAXL 13                          /* levels 0..12                     */
+
+static const double OR_PI = 3.141592653589793238462643383279502884;
+
+/* ------------------------------------------------------------------------- */
+/* integer helpers                                                            */
+/* ------------------------------------------------------------------------- */
+static int64_t floordiv64(int64_t a, int64_t b) /* b > 0 */
+{
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+/* round(X / 2^k) with ties to even, exact integer arithmetic */
+static int64_t rne_shift(int64_t X, int k)
+{
+    int64_t den = (int64_t)1 << k;
+    int64_t q = floordiv64(X, den);
+    int64_t r = X - q * den;           /* 0 <= r < den */
+    int64_t half = den >> 1;
+    if (r > half) q += 1;
+    else if (r == half && (q & 1)) q += 1;
+    return q;
+}
+
+/* ------------------------------------------------------------------------- */
+/* HEALPix NESTED pix2vec (Gorski et al. 2005, cited in Sec. 3.1)             */
+/* ------------------------------------------------------------------------- */
+
+/* sin and cos on [0, pi/4] by their Taylor series (through x^17 and x^18),
+ * nested so that only + - * / by exact integers appear. */
+static double taylor_sin(double x)
+{
+    double x2 = x * x, t = 1.0;
+    for (int j = 8; j >= 1; --j) {
+        double c = (double)((2 * j) * (2 * j + 1));
+        double a = x2 / c;
+        double b = a * t;
+        t = 1.0 - b;
+    }
+    return x * t;
+}
+static double taylor_cos(double x)
+{
+    double x2 = x * x, t = 1.0;
+    for (int j = 9; j >= 1; --j) {
+        double c = (double)((2 * j - 1) * (2 * j));
+        double a = x2 / c;
+        double b = a * t;
+        t = 1.0 - b;
+    }
+    return t;
+}
+
+/* cos(pi m / q), sin(pi m / q) for integers m, q > 0: exact integer quadrant
+ * reduction, then the series on an argument in [0, pi/4]. */
+static void sincos_pi_frac(int64_t m, int64_t q, double *co, double *si)
+{
+    int64_t M = m % (2 * q);
+    if (M < 0) M += 2 * q;                 /* angle pi*M/q in [0, 2pi)        */
+    int64_t k = (2 * M) / q;               /* quadrant 0..3                   */
+    int64_t r2 = 4 * M - 2 * k * q;        /* psi = pi*r2/(4q) in [0, pi/2)   */
+    double c, s;
+    if (r2 <= q) {
+        double x = ((double)r2 * OR_PI) / (double)(4 * q);
+        c = taylor_cos(x);
+        s = taylor_sin(x);
+    } else {
+        double x = ((double)(2 * q - r2) * OR_PI) / (double)(4 * q);
+        c = taylor_sin(x);
+        s = taylor_cos(x);
+    }
+    switch ((int)k) {
+    case 0: *co = c;  *si = s;  break;
+    case 1: *co = -s; *si = c;  break;
+    case 2: *co = -c; *si = -s; break;
+    default: *co = s; *si = -c; break;
+    }
+}
+
+static const int jrll[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
+static const int jpll[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
+
+static int64_t compact_even_bits(int64_t v)
+{
+    int64_t out = 0;
+    for (int i = 0; i < 31; ++i)
+        if (v & ((int64_t)1 << (2 * i))) out |= (int64_t)1 << i;
+    return out;
+}
+
+/* unit vector of NESTED pixel p at level l (nside = 2^l) */
+int or_pix2vec(int level, int64_t p, double v[3])
+{
+    if (level < 0 || level >= OR_MAXL) return -1;
+    int64_t nside = (int64_t)1 << level, npface = nside * nside;
+    if (p < 0 || p >= 12 * npface) return -1;
+    int64_t face = p / npface, ipf = p % npface;
+    int64_t ix = compact_even_bits(ipf), iy = compact_even_bits(ipf >> 1);
+    int64_t jr = jrll[face] * nside - ix - iy - 1;
+    int64_t nr, kshift;
+    double z;
+    if (jr < nside) {
+        nr = jr;
+        z = 1.0 - (double)(nr * nr) / (double)(3 * nside * nside);
+        kshift = 0;
+    } else if (jr > 3 * nside) {
+        nr = 4 * nside - jr;
+        z = (double)(nr * nr) / (double)(3 * nside * nside) - 1.0;
+        kshift = 0;
+    } else {
+        nr = nside;
+        z = (double)(2 * (2 * nside - jr)) / (double)(3 * nside);
+        kshift = (jr - nside) & 1;
+    }
+    int64_t jp = (jpll[face] * nr + ix - iy + 1 + kshift) / 2;
+    if (jp > 4 * nside) jp -= 4 * nside;
+    if (jp < 1) jp += 4 * nside;
+    /* phi = (jp - (kshift+1)/2) * pi / (2 nr) = pi * (2 jp - kshift - 1) / (4 nr) */
+    double cp, sp;
+    sincos_pi_frac(2 * jp - kshift - 1, 4 * nr, &cp, &sp);
+    double st = sqrt((1.0 - z) * (1.0 + z));
+    v[0] = st * cp;
+    v[1] = st * sp;
+    v[2] = z;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Random rotation of a source's HEALPix sphere (Sec. 3.1).                   */
+/* Reading: one uniform rotation per (seed, emitter, step).  Uniforms come    */
+/* from SplitMix64 (Steele, Lea & Flood 2014) used as a counter-based stream; */
+/* the rotation is Marsaglia's (1972) uniform point on S^3 read as a unit     */
+/* quaternion.                                                                */
+/* ------------------------------------------------------------------------- */
+static const uint64_t SM_GAMMA = 0x9E3779B97F4A7C15ULL;
+static uint64_t sm_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+static uint64_t rot_key(uint64_t seed, int64_t e, int64_t s)
+{
+    uint64_t h = sm_mix(seed + SM_GAMMA);
+    h = sm_mix(h + SM_GAMMA * (uint64_t)(e + 1));
+    h = sm_mix(h + SM_GAMMA * (uint64_t)(s + 1));
+    return h;
+}
+static double rot_uniform(uint64_t key, int i) /* i-th draw, in [0,1) */
+{
+    uint64_t u = sm_mix(key + SM_GAMMA * (uint64_t)(i + 1));
+    return (double)(u >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* raw 64-bit draw i of the stream keyed by `key` (exposed for tests) */
+uint64_t or_sm_draw(uint64_t key, int32_t i) { return sm_mix(key + SM_GAMMA * (uint64_t)(i + 1)); }
+uint64_t or_rot_key(uint64_t seed, int64_t e, int64_t s) { return rot_key(seed, e, s); }
+
+/* rotation matrix R (row major) and its 2^24 fixed-point copy */
+void or_rotation(uint64_t seed, int64_t e, int64_t s, int rotate, double R[9], int32_t Rq[9])
+{
+    double w = 1.0, x = 0.0, y = 0.0, z = 0.0;
+    if (rotate) {
+        uint64_t key = rot_key(seed, e, s);
+        int draw = 0, ok1 = 0, ok2 = 0;
+        double a = 0, b = 0, s1 = 0, c = 0, d = 0, s2 = 0;
+        for (int t = 0; t < 64 && !ok1; ++t) {
+            a = 2.0 * rot_uniform(key, draw++) - 1.0;
+            b = 2.0 * rot_uniform(key, draw++) - 1.0;
+            s1 = a * a + b * b;
+            ok1 = s1 < 1.0;
+        }
+        for (int t = 0; t < 64 && ok1 && !ok2; ++t) {
+            c = 2.0 * rot_uniform(key, draw++) - 1.0;
+            d = 2.0 * rot_uniform(key, draw++) - 1.0;
+            s2 = c * c + d * d;
+            ok2 = (s2 < 1.0) && (s2 > 0.0);
+        }
+        if (ok1 && ok2) {
+            double f = sqrt((1.0 - s1) / s2);
+            w = a; x = b; y = c * f; z = d * f;
+        }
+    }
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+    for (int i = 0; i < 9; ++i) Rq[i] = (int32_t)nearbyint(R[i] * 16777216.0);
+}
+
+/* Fixed-point direction of pixel (l,p) under rotation Rq:
+ * vq = round(v * 2^24), d = round(Rq . vq / 2^27), |d| <= 2^21 per axis. */
+int or_direction(int level, int64_t p, const int32_t Rq[9], int32_t d[3])
+{
+    double v[3];
+    if (or_pix2vec(level, p, v)) return -1;
+    int64_t vq[3];
+    for (int j = 0; j < 3; ++j) vq[j] = (int64_t)nearbyint(v[j] * 16777216.0);
+    for (int a = 0; a < 3; ++a) {
+        int64_t acc = 0;
+        for (int j = 0; j < 3; ++j) acc += (int64_t)Rq[3 * a + j] * vq[j];
+        d[a] = (int32_t)rne_shift(acc, 2 * OR_VQ_BITS - OR_FRAC_BITS);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Split radius table (Sec. 3.2, Eq. 2) in whole steps:                       */
+/* K[l] = smallest integer k >= 1 with k >= 2^l sqrt(3/(pi N_min)).           */
+/* The ray has travelled (age+1) cells after its march; it splits while       */
+/* age+1 >= K[l].                                                             */
+/* ------------------------------------------------------------------------- */
+void or_split_table(double n_min, int32_t K[OR_MAXL])
+{
+    double f = sqrt(3.0 / (OR_PI * n_min));
+    for (int l = 0; l < OR_MAXL; ++l) {
+        double r = ldexp(f, l);
+        int64_t k = (int64_t)ceil(r);
+        if (k < 1) k = 1;
+        K[l] = (int32_t)k;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cell traversal of one step (Sec. 3.1): the segment from p0 to p0 + d.      */
+/* Reading: the crossed cells are those of the exact straight segment; a ray  */
+/* sitting on a face belongs to the cell it moves into; simultaneous face     */
+/* crossings step all those axes at once (no zero-length segment); the step   */
+/* ends at t = 1 and a face reached exactly at t = 1 is crossed next step.    */
+/* t runs over [0,1] and one step is one cell width, so ds = dt in cells.     */
+/* Returns the number of in-box segments; *escaped = 1 if the ray left the    */
+/* box [0,n)^3 (open boundaries).                                             */
+/* ------------------------------------------------------------------------- */
+int or_traverse(const int64_t p0[3], const int32_t d[3], const int32_t n[3],
+                int32_t cells[4][3], double ds[4], int *escaped)
+{
+    int64_t cell[3], D[3], ad[3];
+    int sg[3];
+    for (int a = 0; a < 3; ++a) {
+        ad[a] = d[a] < 0 ? -(int64_t)d[a] : (int64_t)d[a];
+        sg[a] = d[a] > 0 ? 1 : (d[a] < 0 ? -1 : 0);
+        if (d[a] > 0) {
+            cell[a] = floordiv64(p0[a], OR_S);
+            D[a] = (cell[a] + 1) * OR_S - p0[a];
+        } else if (d[a] < 0) {
+            cell[a] = floordiv64(p0[a] - 1, OR_S);
+            D[a] = p0[a] - cell[a] * OR_S;
+        } else {
+            cell[a] = floordiv64(p0[a], OR_S);
+            D[a] = 0;
+        }
+    }
+    int64_t tn = 0, td = 1; /* start of the current segment, t = tn/td */
+    int nseg = 0;
+    *escaped = 0;
+    for (;;) {
+        for (int a = 0; a < 3; ++a)
+            if (cell[a] < 0 || cell[a] >= n[a]) { *escaped = 1; return nseg; }
+        int amin = -1;
+        for (int a = 0; a < 3; ++a) {
+            if (sg[a] == 0 || D[a] >= ad[a]) continue;  /* no crossing before t=1 */
+            if (amin < 0 || D[a] * ad[amin] < D[amin] * ad[a]) amin = a;
+        }
+        int64_t un, ud;
+        if (amin < 0) { un = 1; ud = 1; }
+        else { un = D[amin]; ud = ad[amin]; }
+        /* ds = un/ud - tn/td, numerator exact in int64 */
+        int64_t num = un * td - tn * ud, den = ud * td;
+        if (nseg >= 4) return -1; /* cannot happen for |d_a| <= 2^21 */
+        cells[nseg][0] = (int32_t)cell[0];
+        cells[nseg][1] = (int32_t)cell[1];
+        cells[nseg][2] = (int32_t)cell[2];
+        ds[nseg] = (double)num / (double)den;
+        nseg++;
+        if (amin < 0) return nseg;
+        int64_t Dm = D[amin], am = ad[amin];
+        for (int a = 0; a < 3; ++a) {
+            if (sg[a] == 0 || D[a] >= ad[a]) continue;
+            if (D[a] * am == Dm * ad[a]) { cell[a] += sg[a]; D[a] += OR_S; }
+        }
+        tn = Dm; td = am;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Rate coefficients.                                                         */
+/* Sec. 4.1 cites Hui & Gnedin (1997) for the thermal solution; their fits    */
+/* (their Appendix, lambda = 2*157807 K / T) are used for alpha_B, case-B     */
+/* recombination cooling and collisional ionisation; collisional excitation   */
+/* and free-free cooling follow Cen (1992); Compton cooling off the CMB is    */
+/* written from physical constants.                                           */
+/* ------------------------------------------------------------------------- */
+static const double KB = 1.380649e-16;       /* erg/K */
+static const double T_HI = 157807.0;         /* K     */
+static const double EV = 1.602176634e-12;    /* erg   */
+
+double or_alpha_B(double T)
+{
+    double lam = 2.0 * T_HI / T;
+    return 2.753e-14 * pow(lam, 1.5) / pow(1.0 + pow(lam / 2.740, 0.407), 2.242);
+}
+double or_coll_ion(double T)
+{
+    double lam = 2.0 * T_HI / T;
+    return 21.11 * pow(T, -1.5) * exp(-lam / 2.0) * pow(lam, -1.089) /
+           pow(1.0 + pow(lam / 0.354, 0.874), 1.101);
+}
+/* net cooling rate Lambda (erg s^-1 cm^-3) */
+double or_cooling(double T, double ne, double nHI, double nHII, double z)
+{
+    double lam = 2.0 * T_HI / T;
+    double rec = 3.435e-30 * T * pow(lam, 1.970) / pow(1.0 + pow(lam / 2.250, 0.376), 3.720);
+    double cion = 13.6 * EV * or_coll_ion(T);
+    double cexc = 7.5e-19 * exp(-118348.0 / T) / (1.0 + sqrt(T / 1.0e5));
+    double lt = log10(T);
+    double gff = 1.1 + 0.34 * exp(-(5.5 - lt) * (5.5 - lt) / 3.0);
+    double ff = 1.42e-27 * gff * sqrt(T);
+    /* Compton: 4 k_B sigma_T a T_cmb^4 (T - T_cmb) n_e / (m_e c) */
+    const double sigma_T = 6.6524587e-25, a_rad = 7.5657e-15, m_e = 9.1093837e-28, c = 2.99792458e10;
+    double Tc = 2.7255 * (1.0 + z);
+    double comp = 4.0 * KB * sigma_T * a_rad * Tc * Tc * Tc * Tc / (m_e * c) * (T - Tc);
+    return rec * ne * nHII + cion * ne * nHI + cexc * ne * nHI + ff * ne * nHII + comp * ne;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One cell's ionisation update (Sec. 4.1, Eq. 6-10) at fixed Gamma:          */
+/* x(t) = x_eq + (x0 - x_eq) exp(-t/t_i), <x> its average over dt, with n_e   */
+/* re-evaluated from <x> `iters` times.  Written for the neutral fraction     */
+/* y = 1 - x: y_eq = alpha n_e / (Gamma + C n_e + alpha n_e).                 */
+/* ------------------------------------------------------------------------- */
+void or_chem_cell(double nH, double G, double alpha, double C, double dt, int iters,
+                  double y0, double *y1_out, double *ybar_out)
+{
+    double ybar = y0, y1 = y0;
+    for (int it = 0; it < iters; ++it) {
+        double ne = nH * (1.0 - ybar);
+        double a = G + C * ne, b = alpha * ne;
+        double sum = a + b;
+        if (!(sum > 0.0)) { y1 = y0; ybar = y0; break; }
+        double yeq = b / sum;
+        double r = dt * sum; /* dt / t_i */
+        y1 = yeq + (y0 - yeq) * exp(-r);
+        ybar = yeq + (y0 - yeq) * (-expm1(-r)) / r;
+    }
+    *y1_out = y1;
+    *ybar_out = ybar;
+}
+
+/* Temperature update (Sec. 4.1, Eq. 12 with H(z) = 0 and static density):
+ * the particle-number term first, T n_tot conserved over the step; then the
+ * radiative term 2/(3 k n_tot) (H - Lambda) by explicit sub-steps of at most
+ * 5% of T, at most 1000 of them. */
+double or_temperature(double T, double nH, double x0, double x1, double xbar,
+                      double heat, double z, double dt)
+{
+    T = T * (1.0 + x0) / (1.0 + x1);
+    double ne = nH * xbar, nHII = nH * xbar, nHI = nH * (1.0 - xbar), ntot = nH * (1.0 + xbar);
+    double left = dt;
+    for (int k = 0; k < 1000 && left > 0.0; ++k) {
+        double dTdt = 2.0 / (3.0 * KB * ntot) * (heat - or_cooling(T, ne, nHI, nHII, z));
+        double h = left;
+        if (k < 999 && dTdt != 0.0) {
+            double lim = 0.05 * T / fabs(dTdt);
+            if (lim < h) h = lim;
+        }
+        T += dTdt * h;
+        left -= h;
+    }
+    return T;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Simulation state                                                           */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t l;       /* HEALPix level                */
+    int64_t p;       /* NESTED pixel                 */
+    int32_t e;       /* emitter (source cell)        */
+    int32_t b;       /* birth step                   */
+    int32_t d[3];    /* fixed-point direction        */
+    double N[OR_MAXB]; /* photons per bin            */
+} or_ray;
+
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx;          /* physical cell size, cm      */
+    double z;           /* redshift (fixed)            */
+    int32_t nb;
+    double frac[OR_MAXB], sigma[OR_MAXB], eheat[OR_MAXB];
+    int32_t mfp_mode;   /* 0 none, 1 constant lambda, 2 power law in ionised cells */
+    double lambda0_c, delta_exp, gamma_ref, gamma_exp, gamma_floor, xion_thr, nH_mean;
+    int32_t l_src, l_max;
+    double n_min, eps_term;
+    uint64_t seed;
+    int32_t rotate, isothermal, rates, chem_iters;
+    double alpha_const, x_init, T_init;
+} or_config;
+
+typedef struct {
+    or_config c;
+    int64_t ncell;
+    double *nH, *y, *T, *gamma, *kap_sub;  /* per cell state; kap_sub in cm^-1 */
+    double *ion, *heat, *absd;            /* per step accumulators           */
+    int32_t *segcnt;                      /* segments per cell, last step    */
+    int32_t K[OR_MAXL];
+    /* emitters */
+    int32_t ne, ecap;
+    int32_t *ecell;                       /* 3 per emitter                   */
+    double *endot;
+    /* rays */
+    or_ray *rays;
+    int64_t nray, rcap;
+    int64_t step;
+    double emitted, absorbed, escaped, in_flight;
+    int64_t segments_total, segments_last, near_threshold;
+} or_sim;
+
+static int grow_rays(or_ray **buf, int64_t *cap, int64_t need)
+{
+    if (need <= *cap) return 0;
+    int64_t nc = *cap ? *cap : 1024;
+    while (nc < need) nc *= 2;
+    or_ray *nb = (or_ray *)realloc(*buf, (size_t)nc * sizeof(or_ray));
+    if (!nb) return -1;
+    *buf = nb;
+    *cap = nc;
+    return 0;
+}
+
+static void update_kappa_sub(or_sim *S, int64_t i)
+{
+    const or_config *c = &S->c;
+    double k = 0.0;
+    if (c->mfp_mode == 1) {
+        k = (1.0 + c->z) / c->lambda0_c;
+    } else if (c->mfp_mode == 2) {
+        if (1.0 - S->y[i] >= c->xion_thr) {
+            double delta = S->nH[i] / c->nH_mean;
+            double g = S->gamma[i] > c->gamma_floor ? S->gamma[i] : c->gamma_floor;
+            double lam_c = c->lambda0_c * pow(delta, -c->delta_exp) * pow(g / c->gamma_ref, c->gamma_exp);
+            k = (1.0 + c->z) / lam_c;
+        }
+    }
+    S->kap_sub[i] = k;
+}
+
+or_sim *or_create(const or_config *cfg, const double *nH)
+{
+    or_sim *S = (or_sim *)calloc(1, sizeof(or_sim));
+    if (!S) return NULL;
+    S->c = *cfg;
+    S->ncell = (int64_t)cfg->nx * cfg->ny * cfg->nz;
+    int64_t n = S->ncell;
+    S->nH = malloc(n * sizeof(double));
+    S->y = malloc(n * sizeof(double));
+    S->T = malloc(n * sizeof(double));
+    S->gamma = calloc(n, sizeof(double));
+    S->kap_sub = calloc(n, sizeof(double));
+    S->ion = calloc(n, sizeof(double));
+    S->heat = calloc(n, sizeof(double));
+    S->absd = calloc(n, sizeof(double));
+    S->segcnt = calloc(n, sizeof(int32_t));
+    if (!S->nH || !S->y || !S->T || !S->gamma || !S->kap_sub || !S->ion || !S->heat || !S->absd || !S->segcnt)
+        return NULL;
+    if (S->c.nH_mean <= 0.0) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += nH[i];
+        S->c.nH_mean = s / (double)n;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        S->nH[i] = nH[i];
+        S->y[i] = 1.0 - cfg->x_init;
+        S->T[i] = cfg->T_init;
+        update_kappa_sub(S, i);
+    }
+    or_split_table(cfg->n_min, S->K);
+    return S;
+}
+
+void or_destroy(or_sim *S)
+{
+    if (!S) return;
+    free(S->nH); free(S->y); free(S->T); free(S->gamma); free(S->kap_sub);
+    free(S->ion); free(S->heat); free(S->absd); free(S->segcnt);
+    free(S->ecell); free(S->endot); free(S->rays);
+    free(S);
+}
+
+/* Sources in one cell form one emitter (Sec. 3.1: rays are cast from each
+ * cell that contains sources); emitters are numbered in order of the first
+ * source seen in their cell, and their rates add. */
+int or_add_sources(or_sim *S, int32_t n, const int32_t *ijk, const double *ndot)
+{
+    for (int32_t s = 0; s < n; ++s) {
+        const int32_t *q = ijk + 3 * s;
+        if (q[0] < 0 || q[0] >= S->c.nx || q[1] < 0 || q[1] >= S->c.ny || q[2] < 0 || q[2] >= S->c.nz)
+            return -1;
+        int found = -1;
+        for (int32_t e = 0; e < S->ne; ++e)
+            if (S->ecell[3 * e] == q[0] && S->ecell[3 * e + 1] == q[1] && S->ecell[3 * e + 2] == q[2]) { found = e; break; }
+        if (found >= 0) { S->endot[found] += ndot[s]; continue; }
+        if (S->ne == S->ecap) {
+            int32_t nc = S->ecap ? 2 * S->ecap : 16;
+            int32_t *c2 = realloc(S->ecell, (size_t)nc * 3 * sizeof(int32_t));
+            double *n2 = realloc(S->endot, (size_t)nc * sizeof(double));
+            if (!c2 || !n2) return -2;
+            S->ecell = c2; S->endot = n2; S->ecap = nc;
+        }
+        S->ecell[3 * S->ne] = q[0];
+        S->ecell[3 * S->ne + 1] = q[1];
+        S->ecell[3 * S->ne + 2] = q[2];
+        S->endot[S->ne] = ndot[s];
+        S->ne++;
+    }
+    return 0;
+}
+
+/* Deposit the photons a ray still carries into `cell` as if the ray stayed
+ * there for ever (termination; reading of Sec. 2.1's "rays disappear when
+ * tau >> 1": the leftover is absorbed where the ray stops). */
+static void deposit_all(or_sim *S, int64_t cell, const double *N, const double *kap)
+{
+    const or_config *c = &S->c;
+    for (int b = 0; b < c->nb; ++b) {
+        S->absd[cell] += N[b];
+        S->absorbed += N[b];
+        if (kap[b] > 0.0) {
+            S->ion[cell] += c->sigma[b] * N[b] / kap[b];
+            S->heat[cell] += c->eheat[b] * c->sigma[b] * N[b] / kap[b];
+        }
+    }
+}
+
+int or_step(or_sim *S, double dt)
+{
+    const or_config *c = &S->c;
+    const int32_t n3[3] = {c->nx, c->ny, c->nz};
+    const int64_t ncast = 12LL << (2 * c->l_src);
+    const double V = c->dx * c->dx * c->dx;
+    const int64_t s = S->step;
+
+    /* 1. emission (Sec. 3.1, Eq. 1): new rays march in this same step */
+    if (grow_rays(&S->rays, &S->rcap, S->nray + (int64_t)S->ne * ncast)) return -2;
+    for (int32_t e = 0; e < S->ne; ++e) {
+        double R[9];
+        int32_t Rq[9];
+        or_rotation(c->seed, e, s, c->rotate, R, Rq);
+        double N0 = S->endot[e] * dt / (double)ncast;
+        for (int64_t p = 0; p < ncast; ++p) {
+            or_ray *r = &S->rays[S->nray++];
+            r->l = c->l_src; r->p = p; r->e = e; r->b = (int32_t)s;
+            or_direction(c->l_src, p, Rq, r->d);
+            for (int b = 0; b < c->nb; ++b) {
+                r->N[b] = c->frac[b] * N0;
+                S->emitted += r->N[b];
+            }
+        }
+    }
+
+    for (int64_t i = 0; i < S->ncell; ++i) { S->ion[i] = 0.0; S->heat[i] = 0.0; S->absd[i] = 0.0; S->segcnt[i] = 0; }
+
+    /* 2. march every ray one cell width (Sec. 3.1) with absorption (Eq. 13, 17) */
+    or_ray *out = NULL;
+    int64_t nout = 0, ocap = 0;
+    int64_t segs = 0;
+    for (int64_t ir = 0; ir < S->nray; ++ir) {
+        or_ray r = S->rays[ir];
+        int64_t age = s - r.b;
+        int64_t p0[3];
+        const int32_t *ec = S->ecell + 3 * r.e;
+        for (int a = 0; a < 3; ++a) p0[a] = (2 * (int64_t)ec[a] + 1) * (OR_S / 2) + age * (int64_t)r.d[a];
+        int32_t cells[4][3];
+        double ds[4];
+        int esc;
+        int ns = or_traverse(p0, r.d, n3, cells, ds, &esc);
+        if (ns < 0) return -3;
+        int64_t last = -1;
+        double kap[OR_MAXB];
+        for (int k = 0; k < ns; ++k) {
+            int64_t ci = ((int64_t)cells[k][2] * c->ny + cells[k][1]) * c->nx + cells[k][0];
+            double nHI = S->nH[ci] * S->y[ci];
+            double dsp = ds[k] * c->dx; /* path length, cm */
+            for (int b = 0; b < c->nb; ++b) {
+                kap[b] = nHI * c->sigma[b] + S->kap_sub[ci];
+                double tau = kap[b] * dsp;
+                double absb = -r.N[b] * expm1(-tau); /* N (1 - e^-tau) */
+                /* Eq. 17: N (1 - e^{-ds/lambda}) sigma lambda, lambda = 1/kappa */
+                double ion = kap[b] > 0.0 ? c->sigma[b] * absb / kap[b] : c->sigma[b] * r.N[b] * dsp;
+                S->ion[ci] += ion;
+                S->heat[ci] += c->eheat[b] * ion;
+                S->absd[ci] += absb;
+                S->absorbed += absb;
+                r.N[b] = r.N[b] * exp(-tau);
+            }
+            S->segcnt[ci] += 1;
+            last = ci;
+        }
+        segs += ns;
+        if (esc) {
+            for (int b = 0; b < c->nb; ++b) S->escaped += r.N[b];
+            continue;
+        }
+        /* termination: below eps of the ray's unattenuated content */
+        double tot = 0.0;
+        for (int b = 0; b < c->nb; ++b) tot += r.N[b];
+        double N0 = S->endot[r.e] * dt / (double)ncast;
+        double thr = c->eps_term * N0 * ldexp(1.0, -2 * (r.l - c->l_src));
+        if (fabs(tot - thr) <= 1e-5 * thr) S->near_threshold++;
+        if (tot < thr) {
+            deposit_all(S, last, r.N, kap);
+            continue;
+        }
+        /* splitting (Sec. 3.2, Eq. 2-3): the ray has travelled age+1 cells */
+        int m = 0;
+        while (r.l + m < c->l_max && age + 1 >= S->K[r.l + m]) m++;
+        int64_t nchild = (int64_t)1 << (2 * m);
+        if (grow_rays(&out, &ocap, nout + nchild)) return -2;
+        if (m == 0) { out[nout++] = r; continue; }
+        double R[9];
+        int32_t Rq[9];
+        or_rotation(c->seed, r.e, r.b, c->rotate, R, Rq);
+        for (int64_t j = 0; j < nchild; ++j) {
+            or_ray ch = r;
+            ch.l = r.l + m;
+            ch.p = r.p * nchild + j;
+            or_direction(ch.l, ch.p, Rq, ch.d);
+            for (int b = 0; b < c->nb; ++b) ch.N[b] = r.N[b] / (double)nchild;
+            out[nout++] = ch;
+        }
+    }
+    free(S->rays);
+    S->rays = out; S->nray = nout; S->rcap = ocap;
+    S->segments_last = segs;
+    S->segments_total += segs;
+    S->in_flight = 0.0;
+    for (int64_t i = 0; i < S->nray; ++i)
+        for (int b = 0; b < c->nb; ++b) S->in_flight += S->rays[i].N[b];
+
+    /* 3. chemistry and temperature per cell (Sec. 4.1) */
+    for (int64_t i = 0; i < S->ncell; ++i) {
+        double G = S->ion[i] / (V * dt);     /* Eq. 17 */
+        double Hn = S->heat[i] / (V * dt);   /* sum_nu E_nu Gamma_nu */
+        double T0 = S->T[i];
+        double alpha = c->rates ? or_alpha_B(T0) : c->alpha_const;
+        double C = c->rates ? or_coll_ion(T0) : 0.0;
+        double y0 = S->y[i], y1, ybar;
+        or_chem_cell(S->nH[i], G, alpha, C, dt, c->chem_iters, y0, &y1, &ybar);
+        if (!c->isothermal) {
+            double heat = S->nH[i] * ybar * Hn;
+            S->T[i] = or_temperature(T0, S->nH[i], 1.0 - y0, 1.0 - y1, 1.0 - ybar, heat, c->z, dt);
+        }
+        S->y[i] = y1;
+        S->gamma[i] = G;
+        update_kappa_sub(S, i);
+    }
+    S->step++;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* accessors                                                                  */
+/* ------------------------------------------------------------------------- */
+void or_get_fields(const or_sim *S, double *gamma, double *xHII, double *T, double *nHI)
+{
+    for (int64_t i = 0; i < S->ncell; ++i) {
+        if (gamma) gamma[i] = S->gamma[i];
+        if (xHII) xHII[i] = 1.0 - S->y[i];
+        if (T) T[i] = S->T[i];
+        if (nHI) nHI[i] = S->nH[i] * S->y[i];
+    }
+}
+void or_get_budget(const or_sim *S, double out[4])
+{
+    out[0] = S->emitted; out[1] = S->absorbed; out[2] = S->escaped; out[3] = S->in_flight;
+}
+void or_get_counts(const or_sim *S, int64_t out[5])
+{
+    out[0] = S->nray; out[1] = S->segments_last; out[2] = S->segments_total;
+    out[3] = S->step; out[4] = S->near_threshold;
+}
+void or_get_segcount(const or_sim *S, int32_t *out)
+{
+    memcpy(out, S->segcnt, (size_t)S->ncell * sizeof(int32_t));
+}
+void or_get_deposits(const or_sim *S, double *absd, double *ion)
+{
+    for (int64_t i = 0; i < S->ncell; ++i) { if (absd) absd[i] = S->absd[i]; if (ion) ion[i] = S->ion[i]; }
+}
+/* live rays: level, pixel, emitter, birth, direction, photons */
+int64_t or_get_rays(const or_sim *S, int32_t *lv, int64_t *pix, int32_t *em, int32_t *birth,
+                    int32_t *dir, double *N, int64_t cap)
+{
+    int64_t n = S->nray < cap ? S->nray : cap;
+    for (int64_t i = 0; i < n; ++i) {
+        const or_ray *r = &S->rays[i];
+        lv[i] = r->l; pix[i] = r->p; em[i] = r->e; birth[i] = r->b;
+        for (int a = 0; a < 3; ++a) dir[3 * i + a] = r->d[a];
+        for (int b = 0; b < S->c.nb; ++b) N[(int64_t)S->c.nb * i + b] = r->N[b];
+    }
+    return S->nray;
+}
+int32_t or_num_emitters(const or_sim *S) { return S->ne; }
+int64_t or_config_size(void) { return (int64_t)sizeof(or_config); }
