@@ -1,0 +1,355 @@
+"""Throughput of the GB300 adaptive ray-tracing RT step.
+
+One bench step = one complete simulation of the 16-source cosmological
+workload: 128^3 lognormal density (sigma_ln = 1, P(k) ~ k^-2) in a 0.5 Mpc/h
+box at z = 9, 16 sources in the densest cells (log-uniform 1e51..1e52 /s),
+a 4-bin 1e5 K blackbody, temperature evolution, 100 RT steps of 0.1 Myr.
+Every RT step runs emission, the fused march/deposit/split kernel and the
+chemistry kernel.
+
+value  : ray-cell segments per second with the density and sources already
+         resident on the device (CUDA events on the simulation's stream).
+e2e    : the same metric through the C-ABI from host buffers: create (H2D of
+         the density), sources, 100 steps, fields back to the host (D2H).
+roofline: the march kernel's algorithmic bytes per launch over its average
+         CUDA-event duration, against the measured HBM copy bandwidth.
+cpu_baseline / --impl reference: the FP64 C oracle on the host cores on a
+         bounded sample of the same workload (its first RT steps).
+
+Multi-GPU (torchrun): independent replicas, one simulation per rank per step
+("replicas only": the simulations do not exchange data); value = segments of
+all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ray-cell segments/s"
+UNIT = "segments/s"
+DEFAULT_PEAK_GBS = 6800.0
+WORKLOAD_DESC = ("cosmo16: 128^3 lognormal (sigma_ln=1, P~k^-2) 0.5 Mpc/h z=9, 16 sources 1e51-1e52/s, "
+                 "4-bin 1e5 K blackbody, T evolution, 100 RT steps x 0.1 Myr (one simulation per step)")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Dist:
+    """Barrier and max-reduction across replicas (gloo on CPU, nccl on GPU)."""
+
+    def __init__(self, backend=None):
+        self.ws, self.rank, self.local = dist_env()
+        self.pg = None
+        if self.ws > 1:
+            import torch.distributed as td
+            td.init_process_group(backend=backend or "nccl")
+            self.td = td
+
+    def barrier(self):
+        if self.ws > 1:
+            self.td.barrier()
+
+    def max(self, x: float) -> float:
+        if self.ws == 1:
+            return x
+        import torch
+        dev = "cuda" if self.td.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.td.all_reduce(t, op=self.td.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if self.ws == 1:
+            return x
+        import torch
+        dev = "cuda" if self.td.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.td.all_reduce(t, op=self.td.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.ws > 1:
+            self.td.destroy_process_group()
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return DEFAULT_PEAK_GBS, "fallback"
+
+
+def committed_traffic():
+    """DRAM bytes per march launch from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", "march_cosmo16_traffic.txt")
+    try:
+        for line in open(p):
+            if line.startswith("bytes_per_launch_scaled"):
+                return float(line.split("=")[1].split()[0])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+def problem(args):
+    import workloads as W
+    return W.cosmo16(n=args.grid, nsteps=args.rt_steps)
+
+
+def run_oracle_sample(prob, budget_s):
+    """Oracle on the first RT steps of the workload until `budget_s` seconds
+    of CPU work; returns (segments, seconds, steps)."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.OracleSim(prob)
+    steps = 0
+    while steps < prob.nsteps:
+        o.step(prob.dt)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    seg = o.counts()["segments_total"]
+    o.close()
+    return seg, dt, steps
+
+
+def impl_reference(args, dist):
+    if dist.rank != 0:
+        return
+    prob = problem(args)
+    for _ in range(args.warmup):
+        run_oracle_sample(prob, args.ref_budget)
+    segs, secs, steps = 0, 0.0, []
+    for _ in range(args.steps):
+        s, t, k = run_oracle_sample(prob, args.ref_budget)
+        segs += s
+        secs += t
+        steps.append(k)
+    v = segs / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {min(steps)}-{max(steps)} RT steps of the workload per step "
+                                       f"(about {args.ref_budget:.0f} s of single-thread FP64 C each)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def impl_gpu(args, dist):
+    import torch
+    import paper_2409_04521_gb300 as F
+
+    torch.cuda.set_device(dist.local)
+    dev_index = torch.cuda.current_device()
+    prob = problem(args)
+    stream = torch.cuda.Stream()
+    ncell = prob.ncell
+    nb = prob.spectrum.nbins
+
+    # device-resident runs
+    sim = F.Simulation(prob, ray_capacity=args.capacity, stream=stream.cuda_stream)
+    max_rays = 0
+
+    def one_sim():
+        nonlocal max_rays
+        sim.reset()
+        for _ in range(prob.nsteps):
+            sim.step(prob.dt)
+
+    for _ in range(args.warmup):
+        one_sim()
+        sim.sync()
+        max_rays = max(max_rays, sim.counts()["rays"])
+    torch.cuda.synchronize()
+    sim.profile(True)
+    clocks = ClockSampler(dev_index)
+    seg0 = 0
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    segs = 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_sim()
+        c = sim.counts()   # synchronises; reads this simulation's segment total
+        segs += c["segments_total"] - seg0
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    kms, klaunch, krays = sim.kernel_times()
+    sim.profile(False)
+    sim.close()
+
+    t_max = dist.max(ms)
+    segs_all = dist.sum(float(segs))
+    value = segs_all / (t_max * 1e-3)
+
+    # algorithmic bytes of the march kernel (per launch): rays read
+    # (pixlev, emitter, birth, dir, photons) and photons written, plus the
+    # compulsory cell traffic (kappa read, deposits read and written).
+    ray_read = 24 + 4 * nb
+    ray_write = 4 * nb
+    b_cell = 8 + 24
+    march_launches = max(int(klaunch["march"]), 1)
+    alg_bytes = krays * (ray_read + ray_write) + march_launches * ncell * b_cell
+    per_launch_bytes = alg_bytes / march_launches
+    per_launch_s = kms["march"] * 1e-3 / march_launches
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    peak, peak_src = measured_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": committed_traffic(), "kernel": "k_march (fused march+deposit+split+compact)",
+                "peak_source": peak_src, "algorithmic_bytes_per_launch": per_launch_bytes,
+                "avg_launch_ms": per_launch_s * 1e3,
+                "kernel_ms": {k: float(v) for k, v in kms.items()},
+                "kernel_share": {k: float(v / max(sum(kms.values()), 1e-30)) for k, v in kms.items()}}
+
+    # end to end through the C-ABI from host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e_segs, e2e_t = 0, 0.0
+        h2d = d2h = 0
+        for _ in range(max(1, min(args.steps, 2))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = F.Simulation(prob, ray_capacity=args.capacity)
+            for _ in range(prob.nsteps):
+                s2.step(prob.dt)
+            f = s2.fields()
+            t1 = time.perf_counter()
+            e2e_segs += s2.counts()["segments_total"]
+            e2e_t += t1 - t0
+            s2.close()
+            h2d = ncell * 8 + len(prob.source_ndot) * (12 + 8) + 3 * nb * 8
+            d2h = ncell * (8 + 8 + 4 + 4)
+            del f
+        e2e = {"value": dist.sum(e2e_segs) / dist.max(e2e_t), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "create+sources+100 RT steps+fields per step, host wall clock"}
+
+    # oracle baseline on the host cores (rank 0 only, N=1 only)
+    cpu = None
+    if dist.rank == 0 and dist.ws == 1 and not args.no_cpu:
+        s, t, k = run_oracle_sample(prob, args.ref_budget)
+        cpu = {"value": s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {k} of {prob.nsteps} RT steps of the same workload, single-thread FP64 C "
+                         f"({t:.1f} s)"}
+
+    launches_per_sim = 1 + prob.nsteps * (3 + (1 if len(prob.source_ndot) else 0))
+    if dist.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD_DESC, "grid": args.grid, "rt_steps": prob.nsteps,
+                           "ray_capacity": args.capacity, "max_live_rays": max_rays,
+                           "parallelism": f"replicas x{dist.ws}",
+                           "l2": "working set larger than L2 (ray queues of several GB)",
+                           "precision": "rays/deposits fp32, ionisation update fp64, temperature fp32"},
+                "sims_per_hour": 3600.0 / (t_max * 1e-3 / args.steps) * dist.ws,
+                "segments_per_sim": segs_all / args.steps / dist.ws,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches_per_sim * args.steps}
+        print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="flexrt", choices=["flexrt", "reference"])
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--rt-steps", type=int, default=100)
+    ap.add_argument("--capacity", type=int, default=400_000_000)
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        dist = Dist(backend="gloo")
+        impl_reference(args, dist)
+    else:
+        dist = Dist()
+        impl_gpu(args, dist)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * flexrt.h -- C ABI of libflexrt: the adaptive ray-tracing radiative-transfer
+ * step of FlexRT (Cain & D'Aloisio, arXiv:2409.04521) on one GB300 GPU.
+ *
+ * One call to flexrt_step() advances a simulation by one RT step, in the
+ * order the paper states it:
+ *   1. emission:  every source cell casts 12*4^l_src rays from its centre along
+ *                 the NESTED HEALPix pixel centres of a sphere that is randomly
+ *                 rotated each step (Sec. 3.1, Eq. 1);
+ *   2. march:     every ray moves exactly one cell width and is attenuated by
+ *                 exp(-tau), tau = kappa * ds, kappa = n_HI sigma_nu + 1/lambda_mfp
+ *                 (Sec. 3.1; Sec. 4.2, Eq. 13);
+ *   3. deposit:   absorbed photons go to the crossed cells as the finite-mfp
+ *                 photo-ionisation rate of Sec. 4.2, Eq. 17 (which reduces to
+ *                 Eq. 5 when lambda = 1/(n_HI sigma));
+ *   4. split:     a level-l ray that has travelled r_split(l) (Sec. 3.2, Eq. 2)
+ *                 becomes the four rays (l+1, 4p+i) (Eq. 3);
+ *   5. chemistry: per cell, the time-dependent ionisation update of Sec. 4.1,
+ *                 Eq. 7-10, and the temperature equation Eq. 12.
+ *
+ * Conventions for every entry point:
+ *   - host pointers are read during the call and never kept; output buffers
+ *     are caller-owned host memory;
+ *   - no C++ exception crosses the ABI; every call returns flexrt_status and
+ *     the context keeps a message for flexrt_last_error();
+ *   - a context is used by one host thread at a time; its device work runs on
+ *     the CUDA stream given in flexrt_options.cuda_stream (0 = a stream the
+ *     library creates);
+ *   - flexrt_step() only enqueues work.  Device-side failures (ray-queue
+ *     overflow) are latched: the failed step leaves the state of the last good
+ *     step, later steps do nothing, and the status is returned by the next
+ *     flexrt_step() or flexrt_sync() that sees it; the getters keep returning
+ *     the state of the last good step.
+ *   - device memory is allocated by flexrt_create (cells, ray queues) and by
+ *     flexrt_add_sources (emitter tables, when they grow), and freed by
+ *     flexrt_destroy; the probes allocate and free their own scratch.
+ */
+#ifndef FLEXRT_H
+#define FLEXRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FLEXRT_OK = 0,
+    FLEXRT_E_INVALID = 1,   /* bad argument                                  */
+    FLEXRT_E_OOM = 2,       /* device or host allocation failed              */
+    FLEXRT_E_CAPACITY = 3,  /* ray queue, emitter or cell arena full         */
+    FLEXRT_E_CUDA = 4,      /* CUDA runtime error                            */
+    FLEXRT_E_TIMEOUT = 5,   /* a bounded device wait expired                 */
+    FLEXRT_E_STATE = 6      /* call not valid in the current state           */
+} flexrt_status;
+
+#define FLEXRT_MAX_BINS 8
+#define FLEXRT_MAX_LEVEL 12
+
+typedef struct flexrt_ctx flexrt_ctx;
+typedef struct flexrt_batch flexrt_batch;
+
+/* Uniform Cartesian grid of cubic RT cells, x fastest in every cell array. */
+typedef struct { int32_t nx, ny, nz; } flexrt_grid;
+
+/* Box: comoving length of the x side in cm and the (fixed) redshift.  The
+ * physical cell width is box_cm_comoving / nx / (1 + redshift). */
+typedef struct { double box_cm_comoving; double redshift; } flexrt_box;
+
+/* Spectrum in nbins frequency bins (Sec. 4.1, Eq. 5 sums over them):
+ * frac[b]      fraction of a source's photons in bin b (sum 1),
+ * sigma_cm2[b] HI photo-ionisation cross-section of bin b,
+ * eheat_erg[b] mean energy above 13.6 eV given to the gas per ionisation. */
+typedef struct {
+    int32_t nbins;
+    const double *frac, *sigma_cm2, *eheat_erg;
+} flexrt_spectrum;
+
+/* Sub-grid opacity, the 1/lambda_mfp term of kappa (Sec. 4.2, Eq. 13, 15):
+ * mode 0: none; mode 1: constant comoving lambda0 everywhere;
+ * mode 2: in cells with x_HII >= xion_threshold,
+ *   lambda = lambda0 * Delta^-delta_exp * (max(Gamma, gamma_floor)/gamma_ref)^gamma_exp
+ *   with Delta = n_H / nH_mean (nH_mean = 0: mean of the grid) and Gamma the
+ *   previous step's rate. */
+typedef struct {
+    int32_t mode;
+    double lambda0_cm_comoving, delta_exp, gamma_ref, gamma_exp, gamma_floor,
+        xion_threshold, nH_mean;
+} flexrt_mfp;
+
+typedef struct {
+    int32_t l_src;          /* HEALPix level of emission (Eq. 1)                */
+    int32_t l_max;          /* deepest split level, <= FLEXRT_MAX_LEVEL         */
+    double n_ray_min;       /* N_ray^min of Eq. 2                              */
+    double eps_term;        /* ray dropped below eps * its unattenuated content */
+    uint64_t seed;          /* seed of the per-step sphere rotations            */
+    int32_t rotate;         /* 1: rotate each sphere each step (Sec. 3.1)       */
+    int32_t isothermal;     /* 1: T fixed; 0: Eq. 12                            */
+    int32_t rates;          /* 0: constant alpha_B, no collisional ionisation;
+                               1: temperature-dependent rate fits               */
+    int32_t chem_iters;     /* n_e re-evaluations of Eq. 7-10 per step          */
+    double alpha_B_const;   /* cm^3/s, used when rates == 0                     */
+    double x_init, T_init;  /* initial ionised fraction and temperature (K)     */
+    int64_t ray_capacity;   /* rays per queue; 0 = sized from free memory       */
+    int32_t keep_diagnostics; /* 1: keep per-cell segment counts of each step   */
+    void *cuda_stream;      /* cudaStream_t, 0 = library-owned stream           */
+} flexrt_options;
+
+/* Fill *o with defaults (l_src 0, l_max 12, N_min 3, eps 1e-10, seed 1,
+ * rotate 1, isothermal 1, rates 0, 5 iterations, alpha_B 2.59e-13,
+ * x_init 1.2e-3, T_init 1e4, automatic capacity, library stream). */
+void flexrt_default_options(flexrt_options *o);
+
+/* Create one simulation.  n_H: host, nx*ny*nz doubles, physical cm^-3,
+ * x fastest.  Copies every input to the device.  *out receives the context. */
+flexrt_status flexrt_create(const flexrt_grid *grid, const flexrt_box *box,
+                            const double *n_H, const flexrt_mfp *mfp,
+                            const flexrt_spectrum *spectrum,
+                            const flexrt_options *opt, flexrt_ctx **out);
+
+/* Add n point sources: cell_ijk host int32[3n] (i,j,k), ndot host double[n]
+ * photons/s.  Sources sharing a cell form one emitter (Sec. 3.1: rays are cast
+ * from each cell that holds sources) whose rate is their sum; emitters are
+ * numbered in order of first appearance. */
+flexrt_status flexrt_add_sources(flexrt_ctx *ctx, int32_t n, const int32_t *cell_ijk,
+                                 const double *ndot);
+
+/* Enqueue one RT step of length dt_s seconds (asynchronous). */
+flexrt_status flexrt_step(flexrt_ctx *ctx, double dt_s);
+
+/* Wait for all enqueued work; returns a latched device error if any. */
+flexrt_status flexrt_sync(flexrt_ctx *ctx);
+
+/* Restore the state right after flexrt_create + flexrt_add_sources (fields,
+ * rays, step counter, photon budget) without touching host memory. */
+flexrt_status flexrt_reset(flexrt_ctx *ctx);
+
+/* Per-cell fields after the last step, host doubles (NULL = skip):
+ * gamma_HI (1/s, Eq. 17), x_HII, T (K), n_HI (cm^-3). Synchronises. */
+typedef struct { double *gamma_HI, *x_HII, *T, *n_HI; } flexrt_fields;
+flexrt_status flexrt_get_fields(flexrt_ctx *ctx, flexrt_fields *f);
+
+/* Photon budget in photons: out[0] emitted, out[1] absorbed (sum over cells
+ * of deposited photons), out[2] escaped through the box faces, out[3] in
+ * flight in live rays.  emitted = absorbed + escaped + in flight. */
+flexrt_status flexrt_get_budget(flexrt_ctx *ctx, double out[4]);
+
+/* Counters: out[0] live rays, out[1] ray-cell segments of the last step,
+ * out[2] segments since creation/reset, out[3] steps taken, out[4] queue
+ * capacity, out[5] rays marched in the last step. */
+flexrt_status flexrt_get_counts(flexrt_ctx *ctx, int64_t out[6]);
+
+/* Diagnostics (need keep_diagnostics = 1): ray-cell segments per cell in
+ * the last step, host int32[ncell]. */
+flexrt_status flexrt_get_segment_counts(flexrt_ctx *ctx, int32_t *out);
+
+/* Diagnostics: copy up to cap live rays to host arrays (NULL = skip):
+ * level, pixel (NESTED), emitter, birth step, direction int32[3] (2^-21 cell
+ * per step), photons double[nbins] (photons, physical).  *n gets the count. */
+flexrt_status flexrt_get_rays(flexrt_ctx *ctx, int64_t cap, int32_t *level, int64_t *pixel,
+                              int32_t *emitter, int32_t *birth, int32_t *dir, double *photons,
+                              int64_t *n);
+
+/* Per-kernel device time accumulated since the last call (CUDA events on
+ * the context stream): names "emit", "march", "chem"; ms[k], launches[k].
+ * Timing is only recorded when enabled by flexrt_profile(ctx, 1). */
+flexrt_status flexrt_profile(flexrt_ctx *ctx, int32_t enable);
+flexrt_status flexrt_get_kernel_times(flexrt_ctx *ctx, double ms[3], int64_t launches[3],
+                                      int64_t march_rays[1]);
+
+const char *flexrt_last_error(const flexrt_ctx *ctx);
+void flexrt_destroy(flexrt_ctx *ctx);
+
+/* ----------------------------------------------------------------------- */
+/* Device-function probes.  Each runs the very device function the step    */
+/* kernels use, on host inputs, and returns host outputs.  Synchronous.     */
+/* ----------------------------------------------------------------------- */
+
+/* Fixed-point NESTED HEALPix vectors (Sec. 3.1): for pixels p0..p0+n-1 of
+ * `level`, out int32[3n] = round(v * 2^24). */
+flexrt_status flexrt_probe_pixvec(int32_t level, int64_t p0, int64_t n, int32_t *out);
+
+/* Rotation of (seed, emitter, step) quantised to 2^24: out int32[9]. */
+flexrt_status flexrt_probe_rotation(uint64_t seed, int64_t emitter, int64_t step,
+                                    int32_t rotate, int32_t *out);
+
+/* Rotated fixed-point directions of pixels p0..p0+n-1 at `level`:
+ * round(Rq . vq / 2^27), out int32[3n]; Rq int32[9]. */
+flexrt_status flexrt_probe_direction(int32_t level, int64_t p0, int64_t n,
+                                     const int32_t *Rq, int32_t *out);
+
+/* One-step cell traversal (Sec. 3.1) of n rays from p0 (int64[3n], 2^-21
+ * cell) along d (int32[3n]) in grid g: cells int32[n*4*3], ds float[n*4]
+ * (cells), nseg int32[n], escaped int32[n]. */
+flexrt_status flexrt_probe_traverse(int64_t n, const int64_t *p0, const int32_t *d,
+                                    const flexrt_grid *g, int32_t *cells, float *ds,
+                                    int32_t *nseg, int32_t *escaped);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -651,7 +651,7 @@ int or_step(or_sim *S, double dt)
         for (int b = 0; b < c->nb; ++b) tot += r.N[b];
         double N0 = S->endot[r.e] * dt / (double)ncast;
         double thr = c->eps_term * N0 * ldexp(1.0, -2 * (r.l - c->l_src));
-        if (fabs(tot - thr) <= 1e-5 * thr) S->near_threshold++;
+        if (fabs(tot - thr) <= 1e-4 * thr) S->near_threshold++;
         if (tot < thr) {
             deposit_all(S, last, r.N, kap);
             continue;

@@ -1,0 +1,318 @@
+// frt_device.cuh -- device functions of the RT step.
+//
+// The HEALPix vectors and sphere rotations are computed in double precision
+// with explicitly rounded intrinsics (no FMA contraction), so their 2^-24
+// fixed-point copies are the same integers on every IEEE-754 machine that
+// evaluates the same expressions in the same order.  Everything that decides
+// an integer (directions, crossed cells, splits) is integer arithmetic.
+#pragma once
+#include <cstdint>
+#include "frt_types.h"
+
+namespace frt {
+
+constexpr unsigned FULL = 0xffffffffu;
+__device__ __constant__ static const double DPI = 3.141592653589793238462643383279502884;
+
+// ---------------------------------------------------------------------------
+// NESTED HEALPix pixel centres (Gorski et al. 2005; Sec. 3.1, Eq. 1)
+// ---------------------------------------------------------------------------
+// sin x, cos x for x in [0, pi/4]: Taylor series through x^17 / x^18,
+// nested so that only exactly rounded + - * / appear.
+__device__ __forceinline__ double series_sin(double x) {
+    double x2 = __dmul_rn(x, x), t = 1.0;
+#pragma unroll
+    for (int j = 8; j >= 1; --j) {
+        double c = (double)((2 * j) * (2 * j + 1));
+        t = __dsub_rn(1.0, __dmul_rn(__ddiv_rn(x2, c), t));
+    }
+    return __dmul_rn(x, t);
+}
+__device__ __forceinline__ double series_cos(double x) {
+    double x2 = __dmul_rn(x, x), t = 1.0;
+#pragma unroll
+    for (int j = 9; j >= 1; --j) {
+        double c = (double)((2 * j - 1) * (2 * j));
+        t = __dsub_rn(1.0, __dmul_rn(__ddiv_rn(x2, c), t));
+    }
+    return t;
+}
+// cos(pi m/q), sin(pi m/q) with exact integer reduction to [0, pi/4]
+__device__ __forceinline__ void sincos_pi_ratio(long long m, long long q, double &co, double &si) {
+    long long M = m % (2 * q);
+    if (M < 0) M += 2 * q;
+    long long k = (2 * M) / q;
+    long long r2 = 4 * M - 2 * k * q;
+    double c, s;
+    if (r2 <= q) {
+        double x = __ddiv_rn(__dmul_rn((double)r2, DPI), (double)(4 * q));
+        c = series_cos(x);
+        s = series_sin(x);
+    } else {
+        double x = __ddiv_rn(__dmul_rn((double)(2 * q - r2), DPI), (double)(4 * q));
+        c = series_sin(x);
+        s = series_cos(x);
+    }
+    switch ((int)k) {
+        case 0: co = c; si = s; break;
+        case 1: co = -s; si = c; break;
+        case 2: co = -c; si = -s; break;
+        default: co = s; si = -c; break;
+    }
+}
+
+__device__ __forceinline__ long long even_bits(long long v) {
+    long long o = 0;
+    for (int i = 0; i < 31; ++i)
+        if (v & (1LL << (2 * i))) o |= 1LL << i;
+    return o;
+}
+
+// ring and longitude offsets of the 12 base faces
+__device__ __constant__ static const int HP_JR0[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
+__device__ __constant__ static const int HP_JP0[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
+
+// unit vector of NESTED pixel p at `level`, as round(v * 2^24)
+__device__ inline int4 healpix_vq(int level, long long p) {
+    const int *jr0 = HP_JR0, *jp0 = HP_JP0;
+    long long ns = 1LL << level, npf = ns * ns;
+    long long face = p / npf, ipf = p % npf;
+    long long ix = even_bits(ipf), iy = even_bits(ipf >> 1);
+    long long jr = jr0[face] * ns - ix - iy - 1;
+    long long nr, sh;
+    double z;
+    if (jr < ns) {
+        nr = jr;
+        z = __dsub_rn(1.0, __ddiv_rn((double)(nr * nr), (double)(3 * ns * ns)));
+        sh = 0;
+    } else if (jr > 3 * ns) {
+        nr = 4 * ns - jr;
+        z = __dsub_rn(__ddiv_rn((double)(nr * nr), (double)(3 * ns * ns)), 1.0);
+        sh = 0;
+    } else {
+        nr = ns;
+        z = __ddiv_rn((double)(2 * (2 * ns - jr)), (double)(3 * ns));
+        sh = (jr - ns) & 1;
+    }
+    long long jp = (jp0[face] * nr + ix - iy + 1 + sh) / 2;
+    if (jp > 4 * ns) jp -= 4 * ns;
+    if (jp < 1) jp += 4 * ns;
+    double cp, sp;
+    sincos_pi_ratio(2 * jp - sh - 1, 4 * nr, cp, sp);
+    double st = __dsqrt_rn(__dmul_rn(__dsub_rn(1.0, z), __dadd_rn(1.0, z)));
+    const double Q = 16777216.0;
+    return make_int4(__double2int_rn(__dmul_rn(__dmul_rn(st, cp), Q)),
+                     __double2int_rn(__dmul_rn(__dmul_rn(st, sp), Q)),
+                     __double2int_rn(__dmul_rn(z, Q)), 0);
+}
+
+__host__ __device__ __forceinline__ long long level_offset(int l) {  // sum_{j<l} 12*4^j
+    return 4LL * ((1LL << (2 * l)) - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Per-(emitter, step) random rotation (Sec. 3.1).  SplitMix64 (Steele, Lea &
+// Flood 2014) as a counter-based stream; Marsaglia (1972) uniform unit
+// quaternion.  Rows returned as round(R * 2^24).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t sm64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+constexpr uint64_t GOLD = 0x9E3779B97F4A7C15ULL;
+
+__device__ inline void rotation_rows(uint64_t seed, long long e, long long s, int rotate, int4 rows[3]) {
+    double w = 1.0, x = 0.0, y = 0.0, zz = 0.0;
+    if (rotate) {
+        uint64_t h = sm64(seed + GOLD);
+        h = sm64(h + GOLD * (uint64_t)(e + 1));
+        h = sm64(h + GOLD * (uint64_t)(s + 1));
+        int draw = 0;
+        auto uni = [&](void) -> double {
+            uint64_t u = sm64(h + GOLD * (uint64_t)(draw + 1));
+            ++draw;
+            return __dmul_rn(__ull2double_rn(u >> 11), 1.0 / 9007199254740992.0);
+        };
+        double a = 0, b = 0, s1 = 0, c = 0, d = 0, s2 = 0;
+        bool ok1 = false, ok2 = false;
+        for (int t = 0; t < 64 && !ok1; ++t) {
+            a = __dsub_rn(__dmul_rn(2.0, uni()), 1.0);
+            b = __dsub_rn(__dmul_rn(2.0, uni()), 1.0);
+            s1 = __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+            ok1 = s1 < 1.0;
+        }
+        for (int t = 0; t < 64 && ok1 && !ok2; ++t) {
+            c = __dsub_rn(__dmul_rn(2.0, uni()), 1.0);
+            d = __dsub_rn(__dmul_rn(2.0, uni()), 1.0);
+            s2 = __dadd_rn(__dmul_rn(c, c), __dmul_rn(d, d));
+            ok2 = (s2 < 1.0) && (s2 > 0.0);
+        }
+        if (ok1 && ok2) {
+            double f = __dsqrt_rn(__ddiv_rn(__dsub_rn(1.0, s1), s2));
+            w = a; x = b; y = __dmul_rn(c, f); zz = __dmul_rn(d, f);
+        }
+    }
+    double R[9];
+    R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(zz, zz))));
+    R[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, zz)));
+    R[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, zz), __dmul_rn(w, y)));
+    R[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, zz)));
+    R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(zz, zz))));
+    R[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(y, zz), __dmul_rn(w, x)));
+    R[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, zz), __dmul_rn(w, y)));
+    R[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, zz), __dmul_rn(w, x)));
+    R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
+    const double Q = 16777216.0;
+    for (int r = 0; r < 3; ++r)
+        rows[r] = make_int4(__double2int_rn(__dmul_rn(R[3 * r], Q)), __double2int_rn(__dmul_rn(R[3 * r + 1], Q)),
+                            __double2int_rn(__dmul_rn(R[3 * r + 2], Q)), 0);
+}
+
+// round(X / 2^27), ties to even (X = Rq . vq, 2^48 scale -> 2^21 scale)
+__device__ __forceinline__ int32_t rne_shift27(long long X) {
+    long long q = X >> 27;                 // arithmetic shift = floor
+    long long r = X - (q << 27);
+    const long long half = 1LL << 26;
+    q += (r > half) | ((r == half) & (q & 1));
+    return (int32_t)q;
+}
+__device__ __forceinline__ void rotate_dir(const int4 rows[3], int4 v, int32_t &dx, int32_t &dy, int32_t &dz) {
+    dx = rne_shift27((long long)rows[0].x * v.x + (long long)rows[0].y * v.y + (long long)rows[0].z * v.z);
+    dy = rne_shift27((long long)rows[1].x * v.x + (long long)rows[1].y * v.y + (long long)rows[1].z * v.z);
+    dz = rne_shift27((long long)rows[2].x * v.x + (long long)rows[2].y * v.y + (long long)rows[2].z * v.z);
+}
+
+// ---------------------------------------------------------------------------
+// One-step traversal (Sec. 3.1): the segment p0 -> p0 + d through unit cells.
+// Integer state; a ray on a face belongs to the cell it moves into; tied face
+// crossings step together; crossings are compared as exact fractions.
+// ---------------------------------------------------------------------------
+struct Walk {
+    int cx, cy, cz;          // current cell
+    int Dx, Dy, Dz;          // distance along each axis to the next face ahead
+    int ax, ay, az;          // |d|
+    int sx, sy, sz;          // sign of d
+    long long tn, td;        // segment start, t = tn/td
+};
+
+__device__ __forceinline__ void axis_init(long long p, int d, int &c, int &D, int &a, int &s) {
+    if (d > 0) {
+        long long cc = p >> FRAC_BITS;
+        c = (int)cc; D = (int)(((cc + 1) << FRAC_BITS) - p); a = d; s = 1;
+    } else if (d < 0) {
+        long long cc = (p - 1) >> FRAC_BITS;
+        c = (int)cc; D = (int)(p - (cc << FRAC_BITS)); a = -d; s = -1;
+    } else {
+        c = (int)(p >> FRAC_BITS); D = 0; a = 0; s = 0;
+    }
+}
+__device__ __forceinline__ void walk_init(Walk &w, long long px, long long py, long long pz, int dx, int dy, int dz) {
+    axis_init(px, dx, w.cx, w.Dx, w.ax, w.sx);
+    axis_init(py, dy, w.cy, w.Dy, w.ay, w.sy);
+    axis_init(pz, dz, w.cz, w.Dz, w.az, w.sz);
+    w.tn = 0; w.td = 1;
+}
+__device__ __forceinline__ bool walk_outside(const Walk &w, int nx, int ny, int nz) {
+    return (unsigned)w.cx >= (unsigned)nx || (unsigned)w.cy >= (unsigned)ny || (unsigned)w.cz >= (unsigned)nz;
+}
+// Emit the segment in the current (inside) cell: its length ds (cells) and
+// whether the ray goes on to another cell in this step.  Advances the walk.
+__device__ __forceinline__ bool walk_segment(Walk &w, float &ds) {
+    bool crx = w.sx != 0 && w.Dx < w.ax;
+    bool cry = w.sy != 0 && w.Dy < w.ay;
+    bool crz = w.sz != 0 && w.Dz < w.az;
+    long long un = 1, ud = 1;
+    bool cross = false;
+    if (crx) { un = w.Dx; ud = w.ax; cross = true; }
+    if (cry && (!cross || (long long)w.Dy * ud < un * w.ay)) { un = w.Dy; ud = w.ay; cross = true; }
+    if (crz && (!cross || (long long)w.Dz * ud < un * w.az)) { un = w.Dz; ud = w.az; cross = true; }
+    long long num = un * w.td - w.tn * ud;
+    long long den = ud * w.td;
+    ds = __fdividef(__ll2float_rn(num), __ll2float_rn(den));
+    if (cross) {
+        if (crx && (long long)w.Dx * ud == un * w.ax) { w.cx += w.sx; w.Dx += (int)ONE_CELL; }
+        if (cry && (long long)w.Dy * ud == un * w.ay) { w.cy += w.sy; w.Dy += (int)ONE_CELL; }
+        if (crz && (long long)w.Dz * ud == un * w.az) { w.cz += w.sz; w.Dz += (int)ONE_CELL; }
+        w.tn = un; w.td = ud;
+    }
+    return cross;
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Sum NV values over the lanes of each peer group (lanes with the same key);
+// the lowest lane of each group ends with the group sum.  Pairwise tree over
+// the ranks within each group: log2(group size) rounds.
+template <int NV>
+__device__ __forceinline__ void peer_sum(unsigned peers, float (&v)[NV]) {
+    const int lane = lane_id();
+    const unsigned below = (1u << lane) - 1u;
+    unsigned above = lane == 31 ? 0u : (peers & (0xffffffffu << (lane + 1)));
+    int rank = __popc(peers & below);
+    bool alive = true;
+    while (__any_sync(FULL, alive && above != 0u)) {
+        int src = above ? (__ffs(above) - 1) : lane;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            float t = __shfl_sync(FULL, v[k], src);
+            if (alive && !(rank & 1) && above) v[k] += t;
+        }
+        unsigned odd = __ballot_sync(FULL, alive && (rank & 1));
+        if (rank & 1) alive = false;
+        above &= ~odd;
+        rank >>= 1;
+    }
+}
+
+// Warp-inclusive prefix sum of an int.
+__device__ __forceinline__ int warp_incl_scan(int x) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Rate coefficients in single precision (temperature-dependent fits cited by
+// Sec. 4.1: Hui & Gnedin 1997 for case-B recombination, recombination cooling
+// and collisional ionisation; Cen 1992 for collisional excitation and
+// free-free cooling; Compton cooling from physical constants).
+// ---------------------------------------------------------------------------
+constexpr float KB_F = 1.380649e-16f;
+constexpr float T_HI_F = 157807.0f;
+
+__device__ __forceinline__ float alphaB_f(float T) {
+    float lam = 2.0f * T_HI_F / T;
+    return 2.753e-14f * powf(lam, 1.5f) / powf(1.0f + powf(lam * (1.0f / 2.740f), 0.407f), 2.242f);
+}
+__device__ __forceinline__ float collion_f(float T) {
+    float lam = 2.0f * T_HI_F / T;
+    return 21.11f * powf(T, -1.5f) * expf(-0.5f * lam) * powf(lam, -1.089f) /
+           powf(1.0f + powf(lam * (1.0f / 0.354f), 0.874f), 1.101f);
+}
+// Lambda in erg s^-1 cm^-3 divided by n_H^2 is not used: densities are small
+// but positive; computed directly in float (values ~1e-30 fit in range).
+__device__ __forceinline__ float cooling_f(float T, float ne, float nHI, float nHII, float compton_c, float Tcmb) {
+    float lam = 2.0f * T_HI_F / T;
+    float rec = 3.435e-30f * T * powf(lam, 1.970f) / powf(1.0f + powf(lam * (1.0f / 2.250f), 0.376f), 3.720f);
+    float cion = 2.1789874e-11f * collion_f(T);      // 13.6 eV in erg
+    float cexc = 7.5e-19f * expf(-118348.0f / T) / (1.0f + sqrtf(T * 1.0e-5f));
+    float lt = log10f(T);
+    float gff = 1.1f + 0.34f * expf(-(5.5f - lt) * (5.5f - lt) * (1.0f / 3.0f));
+    float ff = 1.42e-27f * gff * sqrtf(T);
+    return (rec + ff) * ne * nHII + (cion + cexc) * ne * nHI + compton_c * (T - Tcmb) * ne;
+}
+
+}  // namespace frt

@@ -1,0 +1,582 @@
+// frt_kernels.cu -- the GPU kernels of one RT step and their launchers.
+//
+//   k_emit   : per active emitter, the step's random sphere rotation and the
+//              12*4^l_src new rays at the emitter's cell centre
+//              (Sec. 3.1, Eq. 1);
+//   k_march  : per ray, the one-cell march with exp(-tau) attenuation, the
+//              Eq. 17 deposit (warp-aggregated vector reductions into the
+//              per-cell buffers), escape, termination, the Eq. 2-3 split and
+//              the compacted write of survivors and children;
+//   k_chem   : per cell, Gamma from the deposits, the ionisation update of
+//              Sec. 4.1 Eq. 7-10 (double precision), the temperature update
+//              of Eq. 12 (single precision) and kappa for the next step;
+//   k_end    : per simulation, commit of the step's photon budget.
+// All launches are sized on the host from capacities only; counts are read
+// from device memory, so the same launches can be replayed in a CUDA graph.
+#include <cstdio>
+#include "frt_device.cuh"
+#include "frt_launch.h"
+
+namespace frt {
+
+// ---------------------------------------------------------------------------
+// fixed-point pixel vector table, levels 0..L
+// ---------------------------------------------------------------------------
+__global__ void k_pixtab(int4 *tab, int L) {
+    long long n = level_offset(L + 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (level_offset(l + 1) <= i) ++l;
+        tab[i] = healpix_vq(l, i - level_offset(l));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kappa of a cell for the next step (Sec. 4.2, Eq. 13 and the sub-grid law)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cell_kappa(const SimDev &S, double nH, double y, double x, double G) {
+    float kx = (float)(nH * y * S.sigma_ref * S.dx_phys);
+    float ks = 0.0f;
+    if (S.mfp_mode == 1) {
+        ks = (float)(S.dx_com / S.lambda0_c);
+    } else if (S.mfp_mode == 2 && x >= S.xion_thr) {
+        double g = G > S.gamma_floor ? G : S.gamma_floor;
+        float f = powf((float)(nH / S.nH_mean), (float)(-S.delta_exp)) * powf((float)(g / S.gamma_ref), (float)S.gamma_exp);
+        ks = (float)(S.dx_com / S.lambda0_c) / f;
+    }
+    return make_float2(kx, ks);
+}
+
+__global__ void k_init_cells(const SimDev *sims, int sim, Cells c) {
+    const SimDev &S = sims[sim];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.ncell; i += (long long)gridDim.x * blockDim.x) {
+        long long g = S.cell_off + i;
+        double y = 1.0 - S.x_init;
+        c.y[g] = y;
+        c.T[g] = (float)S.T_init;
+        c.gamma[g] = 0.0f;
+        c.dep[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c.segcnt) c.segcnt[g] = 0;
+        c.kap[g] = cell_kappa(S, c.nH[g], y, S.x_init, 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// emission
+// ---------------------------------------------------------------------------
+__global__ void k_emit(EmitArgs A) {
+    Ctl *C = A.ctl;
+    if (C->err) return;
+    const int par = C->par;
+    const long long base = C->cnt[par];
+    const long long total = C->emit_total;
+    if (base + total > A.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&C->err, 1);
+        return;
+    }
+    const Queue q = A.q[par];
+    const int n = C->n_act_emit;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int e = A.em.act[j];
+        const long long off = base + A.em.act_off[j];
+        const int4 cell = A.em.cell[e];
+        const SimDev &S = A.sims[cell.w];
+        const int s = S.step;
+        int4 rows[3];
+        rotation_rows(S.seed, A.em.local[e], s, S.rotate, rows);
+        int4 *ring = A.em.ring + ((long long)e * A.em.ring_w + (s % A.em.ring_w)) * 3;
+        ring[0] = rows[0]; ring[1] = rows[1]; ring[2] = rows[2];
+        const float n0 = (float)(A.em.ndot[e] * S.dt * S.inv_ncast / S.nref);
+        A.em.n0[e] = n0;
+        float ph[MAXB];
+        double tot = 0.0;
+#pragma unroll
+        for (int b = 0; b < MAXB; ++b) {
+            ph[b] = b < S.nb ? S.frac[b] * n0 : 0.0f;
+            tot += (double)ph[b];
+        }
+        const int l = S.l_src;
+        const long long ncast = 12LL << (2 * l);
+        const int4 *vt = A.pixtab + level_offset(l <= A.ltab ? l : 0);
+        for (long long p = 0; p < ncast; ++p) {
+            int32_t dx, dy, dz;
+            rotate_dir(rows, l <= A.ltab ? vt[p] : healpix_vq(l, p), dx, dy, dz);
+            long long o = off + p;
+            q.pl[o] = ((uint32_t)l << LEVEL_SHIFT) | (uint32_t)p;
+            q.em[o] = (uint32_t)e;
+            q.bi[o] = s;
+            q.dx[o] = dx; q.dy[o] = dy; q.dz[o] = dz;
+            for (int b = 0; b < A.nb; ++b) q.ph[b][o] = ph[b];
+        }
+        atomicAdd(&A.acc[cell.w].p_emit, tot * (double)ncast);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// march + deposit + terminate + split + compact
+// ---------------------------------------------------------------------------
+constexpr int NACC = 6;  // in, escaped, out, segments, rays in, rays out
+
+template <int NB>
+__global__ void __launch_bounds__(256) k_march(MarchArgs A) {
+    extern __shared__ double sh_acc[];
+    for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) sh_acc[i] = 0.0;
+    __syncthreads();
+    Ctl *C = A.ctl;
+    const int lane = lane_id();
+    if (C->err == 0) {
+        const int par = C->par;
+        const Queue qi = A.q[par], qo = A.q[par ^ 1];
+        unsigned long long *out_cnt = (unsigned long long *)&C->cnt[par ^ 1];
+        const long long n = C->cnt[par] + C->emit_total;
+        const long long nr = (n + 31) & ~31LL;
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += stride) {
+            bool valid = i < n;
+            uint32_t pl = 0, e = 0;
+            int bi = 0, dx = 0, dy = 0, dz = 0, sim = -1;
+            float ph[NB];
+            int4 ec = make_int4(0, 0, 0, 0);
+            if (valid) {
+                pl = qi.pl[i]; e = qi.em[i]; bi = qi.bi[i];
+                dx = qi.dx[i]; dy = qi.dy[i]; dz = qi.dz[i];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) ph[b] = qi.ph[b][i];
+                ec = __ldg(&A.em.cell[e]);
+                sim = ec.w;
+                if (!A.sims[sim].active) valid = false;
+            } else {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) ph[b] = 0.0f;
+            }
+            const SimDev *S = A.sims + (sim < 0 ? 0 : sim);
+            const int step = S->step;
+            const int age = step - bi;
+            if (valid && (age < 0 || age >= A.em.ring_w)) {
+                atomicOr(&C->err, 2);
+                valid = false;
+            }
+            float sig[NB], sige[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) { sig[b] = S->sig[b]; sige[b] = S->sige[b]; }
+            const int nx = S->nx, ny = S->ny, nz = S->nz;
+            const long long coff = S->cell_off;
+
+            float s_in = 0.0f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) s_in += ph[b];
+
+            Walk w;
+            {
+                long long px = ((2LL * ec.x + 1) << (FRAC_BITS - 1)) + (long long)age * dx;
+                long long py = ((2LL * ec.y + 1) << (FRAC_BITS - 1)) + (long long)age * dy;
+                long long pz = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + (long long)age * dz;
+                walk_init(w, px, py, pz, dx, dy, dz);
+            }
+            bool live = valid, esc = false;
+            if (live && walk_outside(w, nx, ny, nz)) { esc = true; live = false; }
+            long long last = -1;
+            float2 lastk = make_float2(0.f, 0.f);
+            int nseg = 0;
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                int key = -1;
+                float v[4] = {0.f, 0.f, 0.f, 1.0f};
+                if (live) {
+                    const long long gc = coff + ((long long)w.cz * ny + w.cy) * nx + w.cx;
+                    float ds;
+                    const bool more = walk_segment(w, ds);
+                    const float2 k = __ldg(&A.cells.kap[gc]);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const float kb = fmaf(k.x, sig[b], k.y);
+                        const float tau = kb * ds;
+                        float tr, ab;
+                        if (tau < 0.5f) {
+                            const float em1 = expm1f(-tau);
+                            ab = -em1; tr = 1.0f + em1;
+                        } else {
+                            tr = expf(-tau); ab = 1.0f - tr;
+                        }
+                        const float a = ph[b] * ab;
+                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds;
+                        ph[b] *= tr;
+                        v[0] += a;
+                        v[1] = fmaf(sig[b], phin, v[1]);
+                        v[2] = fmaf(sige[b], phin, v[2]);
+                    }
+                    key = (int)gc;
+                    last = gc; lastk = k;
+                    ++nseg;
+                    if (!more) live = false;
+                    else if (walk_outside(w, nx, ny, nz)) { esc = true; live = false; }
+                }
+                if (__ballot_sync(FULL, key >= 0) == 0u) break;
+                const unsigned peers = __match_any_sync(FULL, key);
+                if (__any_sync(FULL, key >= 0 && __popc(peers) > 1)) peer_sum<4>(peers, v);
+                if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0u)
+                    red_add_v4(A.cells.dep + key, v[0], v[1], v[2], v[3]);
+            }
+            if (live) {  // more than four segments: impossible for |d| <= 2^21
+                atomicOr(&C->err, 4);
+                live = false;
+            }
+            float s_end = 0.0f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) s_end += ph[b];
+            int nout = 0, m = 0;
+            const int lev = (int)(pl >> LEVEL_SHIFT);
+            if (valid && !esc) {
+                const float thr = S->eps_term * A.em.n0[e] * ldexpf(1.0f, -2 * (lev - S->l_src));
+                if (s_end < thr) {
+                    // termination: the ray's last photons stay in its last cell
+                    float g = 0.f, h = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const float kb = fmaf(lastk.x, sig[b], lastk.y);
+                        if (kb > 0.0f) {
+                            const float q = __fdividef(ph[b], kb);
+                            g = fmaf(sig[b], q, g);
+                            h = fmaf(sige[b], q, h);
+                        }
+                    }
+                    red_add_v4(A.cells.dep + last, s_end, g, h, 0.0f);
+                } else {
+                    while (lev + m < S->l_max && age + 1 >= S->K[lev + m]) ++m;
+                    nout = 1 << (2 * m);
+                }
+            }
+            // per-simulation tallies
+            {
+                float v[NACC] = {s_in, esc ? s_end : 0.0f, nout ? s_end : 0.0f, (float)nseg,
+                                 valid ? 1.0f : 0.0f, (float)nout};
+                const int key = valid ? sim : -1;
+                const unsigned peers = __match_any_sync(FULL, key);
+                if (__any_sync(FULL, __popc(peers) > 1)) peer_sum<NACC>(peers, v);
+                if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0u) {
+#pragma unroll
+                    for (int k = 0; k < NACC; ++k) atomicAdd(&sh_acc[key * NACC + k], (double)v[k]);
+                }
+            }
+            // compacted output
+            const int incl = warp_incl_scan(nout);
+            const int tot = __shfl_sync(FULL, incl, 31);
+            if (tot > 0) {
+                unsigned long long base = 0;
+                if (lane == 31) base = atomicAdd(out_cnt, (unsigned long long)tot);
+                base = __shfl_sync(FULL, base, 31);
+                if ((long long)base + tot > A.cap) {
+                    if (lane == 0) atomicOr(&C->err, 1);
+                } else if (nout > 0) {
+                    const long long o = (long long)base + incl - nout;
+                    if (nout == 1) {
+                        qo.pl[o] = pl; qo.em[o] = e; qo.bi[o] = bi;
+                        qo.dx[o] = dx; qo.dy[o] = dy; qo.dz[o] = dz;
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) qo.ph[b][o] = ph[b];
+                    } else {
+                        const int L = lev + m;
+                        const uint32_t pix0 = (pl & PIX_MASK) << (2 * m);
+                        const int4 *rg = A.em.ring + ((long long)e * A.em.ring_w + (bi % A.em.ring_w)) * 3;
+                        int4 rows[3] = {rg[0], rg[1], rg[2]};
+                        const float scale = ldexpf(1.0f, -2 * m);
+                        float cph[NB];
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) cph[b] = ph[b] * scale;
+                        for (int c = 0; c < nout; ++c) {
+                            const uint32_t pix = pix0 + (uint32_t)c;
+                            const int4 vq = L <= A.ltab ? __ldg(&A.pixtab[level_offset(L) + pix]) : healpix_vq(L, pix);
+                            int32_t cx, cy, cz;
+                            rotate_dir(rows, vq, cx, cy, cz);
+                            const long long oc = o + c;
+                            qo.pl[oc] = ((uint32_t)L << LEVEL_SHIFT) | pix;
+                            qo.em[oc] = e; qo.bi[oc] = bi;
+                            qo.dx[oc] = cx; qo.dy[oc] = cy; qo.dz[oc] = cz;
+#pragma unroll
+                            for (int b = 0; b < NB; ++b) qo.ph[b][oc] = cph[b];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) {
+        const double v = sh_acc[i];
+        if (v != 0.0) {
+            SimAcc &a = A.acc[i / NACC];
+            double *dst = nullptr;
+            switch (i % NACC) {
+                case 0: dst = &a.p_in; break;
+                case 1: dst = &a.p_esc; break;
+                case 2: dst = &a.p_out; break;
+                case 3: dst = &a.p_seg; break;
+                case 4: dst = &a.p_rays_in; break;
+                default: dst = &a.p_rays_out; break;
+            }
+            atomicAdd(dst, v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// chemistry
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
+    extern __shared__ double sh_abs[];
+    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) sh_abs[i] = 0.0;
+    __syncthreads();
+    const Ctl *C = A.ctl;
+    const bool err = C->err != 0;
+    const long long n = C->ncell_active;
+    const int nrng = C->n_ranges;
+    const long long nr = (n + 31) & ~31LL;
+    const int lane = lane_id();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += (long long)gridDim.x * blockDim.x) {
+        int sim = -1;
+        float a_abs = 0.0f;
+        if (i < n) {
+            int lo = 0, hi = nrng;  // largest r with pref[r] <= i
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (A.rg.pref[mid] <= i) lo = mid; else hi = mid;
+            }
+            sim = A.rg.sim[lo];
+            const long long g = A.rg.cell0[lo] + (i - A.rg.pref[lo]);
+            const float4 d = A.cells.dep[g];
+            A.cells.dep[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (A.cells.segcnt) A.cells.segcnt[g] = (int)d.w;
+            if (!err) {
+                a_abs = d.x;
+                const SimDev &S = A.sims[sim];
+                const double G = (double)d.y * S.gscale;            // Eq. 17, 1/s
+                const double nH = A.cells.nH[g];
+                const double y0 = A.cells.y[g];
+                const float T0 = A.cells.T[g];
+                const double alpha = S.rates ? (double)alphaB_f(T0) : S.alpha_const;
+                const double Cc = S.rates ? (double)collion_f(T0) : 0.0;
+                // Eq. 7-10 for the neutral fraction, n_e re-evaluated from <x>
+                double yb = y0, y1 = y0;
+                for (int it = 0; it < S.chem_iters; ++it) {
+                    const double ne = nH * (1.0 - yb);
+                    const double sum = G + (Cc + alpha) * ne;
+                    if (!(sum > 0.0)) { y1 = y0; yb = y0; break; }
+                    const double inv = 1.0 / sum;
+                    const double yeq = alpha * ne * inv;
+                    const double r = S.dt * sum;
+                    const float rf = (float)r;
+                    const double ex = (double)expf(-rf);
+                    const double q = r < 1e-4 ? 1.0 - 0.5 * r + r * r / 6.0 : (double)(-expm1f(-rf)) / r;
+                    const double ybn = yeq + (y0 - yeq) * q;
+                    y1 = yeq + (y0 - yeq) * ex;
+                    const bool conv = fabs(ybn - yb) <= 1e-13 * yb;
+                    yb = ybn;
+                    if (conv) break;
+                }
+                const double x1 = 1.0 - y1;
+                float T = T0;
+                if (!S.isothermal) {
+                    // Eq. 12 with static density: particle-number term, then
+                    // sub-stepped heating minus cooling (per n_H^2)
+                    const float x0 = (float)(1.0 - y0), xb = (float)(1.0 - yb);
+                    T = T0 * (1.0f + x0) / (1.0f + (float)x1);
+                    const float nHf = (float)nH;
+                    const float heat = (float)((double)d.z * S.gscale * 1.602176634e-12 * yb / nH);
+                    const float pref = 2.0f * nHf / (3.0f * KB_F * (1.0f + xb));
+                    const float cc = S.compton_c / nHf;
+                    float left = (float)S.dt;
+                    for (int k = 0; k < 1000 && left > 0.0f; ++k) {
+                        const float lam = cooling_f(T, xb, 1.0f - xb, xb, cc, S.Tcmb);
+                        const float dTdt = pref * (heat - lam);
+                        float h = left;
+                        if (k < 999 && dTdt != 0.0f) h = fminf(h, 0.05f * T / fabsf(dTdt));
+                        T += dTdt * h;
+                        left -= h;
+                    }
+                }
+                A.cells.y[g] = y1;
+                A.cells.T[g] = T;
+                A.cells.gamma[g] = (float)G;
+                A.cells.kap[g] = cell_kappa(S, nH, y1, x1, G);
+            }
+        }
+        const unsigned peers = __match_any_sync(FULL, sim);
+        float v[1] = {a_abs};
+        if (__any_sync(FULL, __popc(peers) > 1)) peer_sum<1>(peers, v);
+        if (sim >= 0 && (peers & ((1u << lane) - 1u)) == 0u && v[0] != 0.0f) atomicAdd(&sh_abs[sim], (double)v[0]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x)
+        if (sh_abs[i] != 0.0) atomicAdd(&A.acc[i].p_abs, sh_abs[i]);
+}
+
+// ---------------------------------------------------------------------------
+// end of step
+// ---------------------------------------------------------------------------
+__global__ void k_end(Ctl *C, SimDev *sims, SimAcc *acc, int nsims) {
+    const bool err = C->err != 0;
+    for (int j = threadIdx.x; j < nsims; j += blockDim.x) {
+        SimAcc &a = acc[j];
+        if (!err && sims[j].active) {
+            a.emitted += a.p_emit;
+            a.absorbed += a.p_abs;
+            a.escaped += a.p_esc;
+            a.in_flight = a.p_out;
+            a.seg_last = a.p_seg;
+            a.seg_total += a.p_seg;
+            a.rays_live = a.p_rays_out;
+            a.rays_in_last = a.p_rays_in;
+            a.rays_in_total += a.p_rays_in;
+            sims[j].step += 1;
+        }
+        a.p_emit = a.p_abs = a.p_esc = a.p_out = a.p_in = 0.0;
+        a.p_seg = a.p_rays_in = a.p_rays_out = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int par = C->par;
+        if (!err) { C->cnt[par] = 0; C->par = par ^ 1; }
+        else C->cnt[par ^ 1] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// probes: the same device functions on host-given inputs
+// ---------------------------------------------------------------------------
+__global__ void k_probe_pixvec(int level, long long p0, long long n, int32_t *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int4 v = healpix_vq(level, p0 + i);
+        out[3 * i] = v.x; out[3 * i + 1] = v.y; out[3 * i + 2] = v.z;
+    }
+}
+__global__ void k_probe_rotation(uint64_t seed, long long e, long long s, int rotate, int32_t *out) {
+    int4 r[3];
+    rotation_rows(seed, e, s, rotate, r);
+    for (int k = 0; k < 3; ++k) { out[3 * k] = r[k].x; out[3 * k + 1] = r[k].y; out[3 * k + 2] = r[k].z; }
+}
+__global__ void k_probe_direction(int level, long long p0, long long n, const int32_t *Rq, const int4 *tab, int ltab,
+                                  int32_t *out) {
+    int4 rows[3];
+    for (int k = 0; k < 3; ++k) rows[k] = make_int4(Rq[3 * k], Rq[3 * k + 1], Rq[3 * k + 2], 0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        long long p = p0 + i;
+        int4 v = level <= ltab ? tab[level_offset(level) + p] : healpix_vq(level, p);
+        int32_t dx, dy, dz;
+        rotate_dir(rows, v, dx, dy, dz);
+        out[3 * i] = dx; out[3 * i + 1] = dy; out[3 * i + 2] = dz;
+    }
+}
+__global__ void k_probe_traverse(long long n, const long long *p0, const int32_t *d, int gx, int gy, int gz,
+                                 int32_t *cells, float *ds, int32_t *nseg, int32_t *esc) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        Walk w;
+        walk_init(w, p0[3 * i], p0[3 * i + 1], p0[3 * i + 2], d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+        int k = 0, e = 0;
+        bool live = true;
+        if (walk_outside(w, gx, gy, gz)) { e = 1; live = false; }
+        while (live && k < 4) {
+            cells[12 * i + 3 * k] = w.cx; cells[12 * i + 3 * k + 1] = w.cy; cells[12 * i + 3 * k + 2] = w.cz;
+            float s;
+            bool more = walk_segment(w, s);
+            ds[4 * i + k] = s;
+            ++k;
+            if (!more) live = false;
+            else if (walk_outside(w, gx, gy, gz)) { e = 1; live = false; }
+        }
+        nseg[i] = live ? -1 : k;
+        esc[i] = e;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_pixtab(int4 *tab, int L, cudaStream_t st) {
+    long long n = level_offset(L + 1);
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 65535) blocks = 65535;
+    k_pixtab<<<blocks, 256, 0, st>>>(tab, L);
+    return cudaGetLastError();
+}
+cudaError_t launch_init_cells(const SimDev *sims, int sim, Cells c, long long ncell, cudaStream_t st) {
+    int blocks = (int)((ncell + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_init_cells<<<blocks, 256, 0, st>>>(sims, sim, c);
+    return cudaGetLastError();
+}
+cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st) {
+    k_emit<<<blocks, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+template <int NB>
+static cudaError_t march_nb(const MarchArgs &a, int blocks, int threads, cudaStream_t st) {
+    size_t sh = (size_t)a.nsims * NACC * sizeof(double);
+    k_march<NB><<<blocks, threads, sh, st>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_march(const MarchArgs &a, int nb, int blocks, int threads, cudaStream_t st) {
+    switch (nb) {
+        case 1: return march_nb<1>(a, blocks, threads, st);
+        case 2: return march_nb<2>(a, blocks, threads, st);
+        case 3: return march_nb<3>(a, blocks, threads, st);
+        case 4: return march_nb<4>(a, blocks, threads, st);
+        case 5: return march_nb<5>(a, blocks, threads, st);
+        case 6: return march_nb<6>(a, blocks, threads, st);
+        case 7: return march_nb<7>(a, blocks, threads, st);
+        case 8: return march_nb<8>(a, blocks, threads, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+int march_max_blocks_per_sm(int nb, int threads, int nsims) {
+    int n = 0;
+    size_t sh = (size_t)nsims * NACC * sizeof(double);
+    switch (nb) {
+        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<1>, threads, sh); break;
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<2>, threads, sh); break;
+        case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<3>, threads, sh); break;
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<4>, threads, sh); break;
+        case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<5>, threads, sh); break;
+        case 6: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<6>, threads, sh); break;
+        case 7: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<7>, threads, sh); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<8>, threads, sh); break;
+    }
+    return n;
+}
+cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st) {
+    k_chem<<<blocks, 256, (size_t)a.nsims * sizeof(double), st>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_t st) {
+    k_end<<<1, 256, 0, st>>>(c, sims, acc, nsims);
+    return cudaGetLastError();
+}
+cudaError_t launch_probe_pixvec(int level, long long p0, long long n, int32_t *out, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_probe_pixvec<<<blocks, 256, 0, st>>>(level, p0, n, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_probe_rotation(uint64_t seed, long long e, long long s, int rotate, int32_t *out, cudaStream_t st) {
+    k_probe_rotation<<<1, 1, 0, st>>>(seed, e, s, rotate, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_probe_direction(int level, long long p0, long long n, const int32_t *Rq, const int4 *tab, int ltab,
+                                   int32_t *out, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_probe_direction<<<blocks, 256, 0, st>>>(level, p0, n, Rq, tab, ltab, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_probe_traverse(long long n, const long long *p0, const int32_t *d, int gx, int gy, int gz,
+                                  int32_t *cells, float *ds, int32_t *nseg, int32_t *esc, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_probe_traverse<<<blocks, 256, 0, st>>>(n, p0, d, gx, gy, gz, cells, ds, nseg, esc);
+    return cudaGetLastError();
+}
+
+}  // namespace frt

@@ -1,0 +1,55 @@
+// frt_launch.h -- kernel argument blocks and launchers (host side).
+#pragma once
+#include "frt_types.h"
+
+namespace frt {
+
+struct EmitArgs {
+    Ctl *ctl;
+    const SimDev *sims;
+    SimAcc *acc;
+    Queue q[2];
+    long long cap;
+    Emitters em;
+    const int4 *pixtab;
+    int ltab;
+    int nb;
+};
+
+struct MarchArgs {
+    Ctl *ctl;
+    const SimDev *sims;
+    SimAcc *acc;
+    int nsims;
+    Queue q[2];
+    long long cap;
+    Emitters em;
+    Cells cells;
+    const int4 *pixtab;
+    int ltab;
+};
+
+struct ChemArgs {
+    const Ctl *ctl;
+    const SimDev *sims;
+    SimAcc *acc;
+    int nsims;
+    Cells cells;
+    Ranges rg;
+};
+
+cudaError_t launch_pixtab(int4 *tab, int L, cudaStream_t st);
+cudaError_t launch_init_cells(const SimDev *sims, int sim, Cells c, long long ncell, cudaStream_t st);
+cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st);
+cudaError_t launch_march(const MarchArgs &a, int nb, int blocks, int threads, cudaStream_t st);
+int march_max_blocks_per_sm(int nb, int threads, int nsims);
+cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st);
+cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_t st);
+cudaError_t launch_probe_pixvec(int level, long long p0, long long n, int32_t *out, cudaStream_t st);
+cudaError_t launch_probe_rotation(uint64_t seed, long long e, long long s, int rotate, int32_t *out, cudaStream_t st);
+cudaError_t launch_probe_direction(int level, long long p0, long long n, const int32_t *Rq, const int4 *tab, int ltab,
+                                   int32_t *out, cudaStream_t st);
+cudaError_t launch_probe_traverse(long long n, const long long *p0, const int32_t *d, int gx, int gy, int gz,
+                                  int32_t *cells, float *ds, int32_t *nseg, int32_t *esc, cudaStream_t st);
+
+}  // namespace frt

@@ -1,0 +1,107 @@
+// frt_types.h -- data layout shared by the step kernels and the host engine.
+//
+// Units on the device ("code units"): lengths in cells, one step moves a ray
+// one cell (Sec. 3.1), positions and directions in 2^-21 cell fixed point,
+// photons in units of a per-simulation reference count nref, opacities as
+// optical depth per cell at the reference cross-section sigma_ref.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace frt {
+
+constexpr int FRAC_BITS = 21;                       // position fixed point
+constexpr int64_t ONE_CELL = int64_t(1) << FRAC_BITS;
+constexpr int VQ_BITS = 24;                         // pixel vectors / rotations
+constexpr int MAXB = 8;                             // frequency bins
+constexpr int MAXL = 13;                            // HEALPix levels 0..12
+constexpr int LEVEL_SHIFT = 28;                     // pixlev = level<<28 | pixel
+constexpr uint32_t PIX_MASK = (1u << LEVEL_SHIFT) - 1u;
+
+// Per-simulation constants and step state.
+struct SimDev {
+    int32_t nx, ny, nz, nb;
+    int64_t cell_off, ncell;
+    int32_t l_src, l_max;
+    int32_t K[16];          // split after (age+1) >= K[l] whole steps (Eq. 2)
+    int32_t active;         // takes part in steps
+    int32_t step;           // steps taken
+    int32_t ring_w;         // rotation ring length (> largest ray age)
+    int32_t rotate;
+    uint64_t seed;
+    float eps_term;
+    float sig[MAXB];        // sigma_b / sigma_ref
+    float sige[MAXB];       // sigma_b / sigma_ref * eheat_b / 1 eV
+    float frac[MAXB];       // photon fraction per bin
+    double dt;              // s
+    double gscale;          // Gamma per unit of the Gamma numerator: nref sigma_ref / (dx^2 dt)
+    float compton_c;        // Compton cooling coefficient at this redshift (erg s^-1 K^-1)
+    float Tcmb;             // K
+    double nref;            // photons per code photon
+    double sigma_ref;       // cm^2
+    double dx_phys;         // cm
+    double dx_com;          // cm comoving
+    double inv_ncast;       // 1 / (12 * 4^l_src)
+    double z;
+    double alpha_const;
+    int32_t rates, isothermal, chem_iters, mfp_mode;
+    double lambda0_c, delta_exp, gamma_ref, gamma_exp, gamma_floor, xion_thr, nH_mean;
+    double x_init, T_init;
+};
+
+// Per-simulation accumulators, code photons (double) and counters.
+struct SimAcc {
+    double emitted, absorbed, escaped, in_flight;     // committed
+    double p_emit, p_abs, p_esc, p_out, p_in;         // current step
+    double p_seg, p_rays_in, p_rays_out;              // current step
+    double seg_last, seg_total, rays_live, rays_in_last, rays_in_total;
+};
+
+// Global control words of one engine.
+struct Ctl {
+    long long cnt[2];        // rays in queue 0 / 1
+    int32_t par;             // queue holding the live rays
+    int32_t err;             // latched error (bit 0 capacity, bit 1 age, bit 2 level)
+    long long emit_total;    // rays emitted per step by the active emitters
+    int32_t n_act_emit;      // active emitters
+    int32_t n_ranges;        // active cell ranges
+    long long ncell_active;  // cells in active simulations
+};
+
+// Structure-of-arrays ray queue.
+struct Queue {
+    uint32_t *pl;            // level << 28 | NESTED pixel
+    uint32_t *em;            // emitter id
+    int32_t *bi;             // birth step
+    int32_t *dx, *dy, *dz;   // direction, 2^-21 cell per step
+    float *ph[MAXB];         // code photons per bin
+};
+
+struct Cells {
+    double *nH;              // cm^-3 physical
+    double *y;               // neutral fraction x_HI
+    float *T;                // K
+    float *gamma;            // Gamma_HI of the last step, 1/s
+    float2 *kap;             // (tau per cell at sigma_ref from HI, sub-grid tau per cell)
+    float4 *dep;             // (absorbed, Gamma numerator, heating numerator, segments)
+    int32_t *segcnt;         // segments of the last step (diagnostics) or null
+};
+
+struct Emitters {
+    int4 *cell;              // (i, j, k, sim)
+    int32_t *local;          // index within its simulation (rotation key)
+    double *ndot;            // photons / s
+    float *n0;               // this step's code photons per emitted ray
+    int4 *ring;              // [emitter][ring slot][3] rotation rows (2^24)
+    int32_t ring_w;          // slots per emitter (same for all)
+    int32_t *act;            // active emitter ids
+    long long *act_off;      // first emitted ray of each active emitter
+};
+
+struct Ranges {              // active cell ranges for the chemistry kernel
+    long long *pref;         // prefix of range sizes [n+1]
+    long long *cell0;        // first global cell
+    int32_t *sim;            // owning simulation
+};
+
+}  // namespace frt

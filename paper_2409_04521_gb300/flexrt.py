@@ -1,0 +1,267 @@
+"""ctypes binding of libflexrt (include/flexrt.h): argument marshalling only.
+
+Every step of the RT method runs in the library's CUDA kernels.  There is no
+CPU fallback: if the library cannot be loaded, or no CUDA device is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+FLEXRT_OK = 0
+STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CAPACITY", 4: "CUDA", 5: "TIMEOUT", 6: "STATE"}
+MAX_BINS = 8
+
+
+class FlexRTError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"flexrt status {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
+
+
+class Box(C.Structure):
+    _fields_ = [("box_cm_comoving", C.c_double), ("redshift", C.c_double)]
+
+
+class Spectrum(C.Structure):
+    _fields_ = [("nbins", C.c_int32), ("frac", C.POINTER(C.c_double)), ("sigma_cm2", C.POINTER(C.c_double)),
+                ("eheat_erg", C.POINTER(C.c_double))]
+
+
+class Mfp(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("lambda0_cm_comoving", C.c_double), ("delta_exp", C.c_double),
+                ("gamma_ref", C.c_double), ("gamma_exp", C.c_double), ("gamma_floor", C.c_double),
+                ("xion_threshold", C.c_double), ("nH_mean", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("l_src", C.c_int32), ("l_max", C.c_int32), ("n_ray_min", C.c_double), ("eps_term", C.c_double),
+                ("seed", C.c_uint64), ("rotate", C.c_int32), ("isothermal", C.c_int32), ("rates", C.c_int32),
+                ("chem_iters", C.c_int32), ("alpha_B_const", C.c_double), ("x_init", C.c_double),
+                ("T_init", C.c_double), ("ray_capacity", C.c_int64), ("keep_diagnostics", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
+class Fields(C.Structure):
+    _fields_ = [("gamma_HI", C.POINTER(C.c_double)), ("x_HII", C.POINTER(C.c_double)),
+                ("T", C.POINTER(C.c_double)), ("n_HI", C.POINTER(C.c_double))]
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def lib():
+    """Load libflexrt (building it if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            P = C.POINTER
+            vp = C.c_void_p
+            L.flexrt_default_options.argtypes = [P(Options)]
+            L.flexrt_create.argtypes = [P(Grid), P(Box), P(C.c_double), P(Mfp), P(Spectrum), P(Options), P(vp)]
+            L.flexrt_add_sources.argtypes = [vp, C.c_int32, P(C.c_int32), P(C.c_double)]
+            L.flexrt_step.argtypes = [vp, C.c_double]
+            L.flexrt_sync.argtypes = [vp]
+            L.flexrt_reset.argtypes = [vp]
+            L.flexrt_get_fields.argtypes = [vp, P(Fields)]
+            L.flexrt_get_budget.argtypes = [vp, P(C.c_double)]
+            L.flexrt_get_counts.argtypes = [vp, P(C.c_int64)]
+            L.flexrt_get_segment_counts.argtypes = [vp, P(C.c_int32)]
+            L.flexrt_get_rays.argtypes = [vp, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32), P(C.c_int32),
+                                          P(C.c_int32), P(C.c_double), P(C.c_int64)]
+            L.flexrt_profile.argtypes = [vp, C.c_int32]
+            L.flexrt_get_kernel_times.argtypes = [vp, P(C.c_double), P(C.c_int64), P(C.c_int64)]
+            L.flexrt_last_error.argtypes = [vp]
+            L.flexrt_last_error.restype = C.c_char_p
+            L.flexrt_destroy.argtypes = [vp]
+            L.flexrt_destroy.restype = None
+            L.flexrt_probe_pixvec.argtypes = [C.c_int32, C.c_int64, C.c_int64, P(C.c_int32)]
+            L.flexrt_probe_rotation.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int32, P(C.c_int32)]
+            L.flexrt_probe_direction.argtypes = [C.c_int32, C.c_int64, C.c_int64, P(C.c_int32), P(C.c_int32)]
+            L.flexrt_probe_traverse.argtypes = [C.c_int64, P(C.c_int64), P(C.c_int32), P(Grid), P(C.c_int32),
+                                                P(C.c_float), P(C.c_int32), P(C.c_int32)]
+            _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _check(status, ctx=None):
+    if status != FLEXRT_OK:
+        msg = ""
+        if ctx:
+            m = lib().flexrt_last_error(ctx)
+            msg = m.decode() if m else ""
+        raise FlexRTError(status, msg)
+
+
+def default_options() -> Options:
+    o = Options()
+    lib().flexrt_default_options(C.byref(o))
+    return o
+
+
+class Simulation:
+    """One simulation on the GPU, created from a problem description with the
+    attributes grid, box_cm_comoving, redshift, nH, spectrum (nbins, frac,
+    sigma_cm2, eheat_erg), mfp, options, source_cells, source_ndot."""
+
+    def __init__(self, prob, ray_capacity: int = 0, keep_diagnostics: bool = False, stream=None):
+        L = lib()
+        g = Grid(*[int(v) for v in prob.grid])
+        b = Box(float(prob.box_cm_comoving), float(prob.redshift))
+        sp = prob.spectrum
+        self._frac = np.ascontiguousarray(sp.frac, np.float64)
+        self._sig = np.ascontiguousarray(sp.sigma_cm2, np.float64)
+        self._eh = np.ascontiguousarray(sp.eheat_erg, np.float64)
+        s = Spectrum(int(sp.nbins), _p(self._frac, C.c_double), _p(self._sig, C.c_double), _p(self._eh, C.c_double))
+        m = prob.mfp
+        mf = Mfp(int(m.mode), m.lambda0_cm_comoving, m.delta_exp, m.gamma_ref, m.gamma_exp, m.gamma_floor,
+                 m.xion_threshold, m.nH_mean)
+        o = default_options()
+        po = prob.options
+        o.l_src, o.l_max = po.l_src, po.l_max
+        o.n_ray_min, o.eps_term = po.n_ray_min, po.eps_term
+        o.seed = po.seed
+        o.rotate, o.isothermal, o.rates, o.chem_iters = int(po.rotate), int(po.isothermal), int(po.rates), po.chem_iters
+        o.alpha_B_const, o.x_init, o.T_init = po.alpha_B_const, po.x_init, po.T_init
+        o.ray_capacity = int(ray_capacity)
+        o.keep_diagnostics = int(keep_diagnostics)
+        o.cuda_stream = stream
+        nH = np.ascontiguousarray(prob.nH, np.float64).reshape(-1)
+        self.ncell = nH.size
+        self.nb = int(sp.nbins)
+        h = C.c_void_p()
+        st = L.flexrt_create(C.byref(g), C.byref(b), _p(nH, C.c_double), C.byref(mf), C.byref(s), C.byref(o),
+                             C.byref(h))
+        if st != FLEXRT_OK:
+            raise FlexRTError(st, "flexrt_create failed")
+        self._h = h
+        if len(prob.source_ndot):
+            self.add_sources(prob.source_cells, prob.source_ndot)
+
+    def add_sources(self, cells, ndot):
+        cells = np.ascontiguousarray(np.asarray(cells, np.int32).reshape(-1, 3))
+        ndot = np.ascontiguousarray(np.asarray(ndot, np.float64).reshape(-1))
+        _check(lib().flexrt_add_sources(self._h, len(ndot), _p(cells, C.c_int32), _p(ndot, C.c_double)), self._h)
+
+    def step(self, dt: float):
+        _check(lib().flexrt_step(self._h, float(dt)), self._h)
+
+    def sync(self):
+        _check(lib().flexrt_sync(self._h), self._h)
+
+    def reset(self):
+        _check(lib().flexrt_reset(self._h), self._h)
+
+    def fields(self, which=("gamma_HI", "x_HII", "T", "n_HI")):
+        out = {k: np.zeros(self.ncell) for k in which}
+        f = Fields(*[(_p(out[k], C.c_double) if k in out else None) for k in ("gamma_HI", "x_HII", "T", "n_HI")])
+        _check(lib().flexrt_get_fields(self._h, C.byref(f)), self._h)
+        return out
+
+    def budget(self):
+        b = np.zeros(4)
+        _check(lib().flexrt_get_budget(self._h, _p(b, C.c_double)), self._h)
+        return b
+
+    def counts(self):
+        c = np.zeros(6, np.int64)
+        _check(lib().flexrt_get_counts(self._h, _p(c, C.c_int64)), self._h)
+        return dict(rays=int(c[0]), segments_last=int(c[1]), segments_total=int(c[2]), step=int(c[3]),
+                    capacity=int(c[4]), rays_marched_last=int(c[5]))
+
+    def segment_counts(self):
+        s = np.zeros(self.ncell, np.int32)
+        _check(lib().flexrt_get_segment_counts(self._h, _p(s, C.c_int32)), self._h)
+        return s
+
+    def rays(self, cap=None):
+        n = C.c_int64()
+        _check(lib().flexrt_get_rays(self._h, 0, None, None, None, None, None, None, C.byref(n)), self._h)
+        m = n.value if cap is None else min(cap, n.value)
+        lv = np.zeros(m, np.int32)
+        pix = np.zeros(m, np.int64)
+        em = np.zeros(m, np.int32)
+        bi = np.zeros(m, np.int32)
+        d = np.zeros((m, 3), np.int32)
+        N = np.zeros((m, self.nb))
+        _check(lib().flexrt_get_rays(self._h, m, _p(lv, C.c_int32), _p(pix, C.c_int64), _p(em, C.c_int32),
+                                     _p(bi, C.c_int32), _p(d, C.c_int32), _p(N, C.c_double), C.byref(n)), self._h)
+        return dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
+
+    def profile(self, enable=True):
+        _check(lib().flexrt_profile(self._h, int(enable)), self._h)
+
+    def kernel_times(self):
+        ms = np.zeros(3)
+        ln = np.zeros(3, np.int64)
+        rays = np.zeros(1, np.int64)
+        _check(lib().flexrt_get_kernel_times(self._h, _p(ms, C.c_double), _p(ln, C.c_int64), _p(rays, C.c_int64)),
+               self._h)
+        return dict(zip(("emit", "march", "chem"), ms)), dict(zip(("emit", "march", "chem"), ln)), int(rays[0])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().flexrt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# -------------------------------------------------------------------------
+# device-function probes
+# -------------------------------------------------------------------------
+def probe_pixvec(level: int, p0: int, n: int) -> np.ndarray:
+    out = np.zeros((n, 3), np.int32)
+    _check(lib().flexrt_probe_pixvec(level, p0, n, _p(out, C.c_int32)))
+    return out
+
+
+def probe_rotation(seed: int, emitter: int, step: int, rotate: bool = True) -> np.ndarray:
+    out = np.zeros(9, np.int32)
+    _check(lib().flexrt_probe_rotation(seed, emitter, step, int(rotate), _p(out, C.c_int32)))
+    return out.reshape(3, 3)
+
+
+def probe_direction(level: int, p0: int, n: int, Rq) -> np.ndarray:
+    Rq = np.ascontiguousarray(np.asarray(Rq, np.int32).reshape(9))
+    out = np.zeros((n, 3), np.int32)
+    _check(lib().flexrt_probe_direction(level, p0, n, _p(Rq, C.c_int32), _p(out, C.c_int32)))
+    return out
+
+
+def probe_traverse(p0, d, grid):
+    p0 = np.ascontiguousarray(np.asarray(p0, np.int64).reshape(-1, 3))
+    d = np.ascontiguousarray(np.asarray(d, np.int32).reshape(-1, 3))
+    n = len(p0)
+    cells = np.zeros((n, 4, 3), np.int32)
+    ds = np.zeros((n, 4), np.float32)
+    nseg = np.zeros(n, np.int32)
+    esc = np.zeros(n, np.int32)
+    g = Grid(*[int(v) for v in grid])
+    _check(lib().flexrt_probe_traverse(n, _p(p0, C.c_int64), _p(d, C.c_int32), C.byref(g), _p(cells, C.c_int32),
+                                       _p(ds, C.c_float), _p(nseg, C.c_int32), _p(esc, C.c_int32)))
+    return cells, ds, nseg, esc.astype(bool)

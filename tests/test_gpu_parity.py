@@ -1,0 +1,143 @@
+"""Whole-step parity of the CUDA path against the FP64 oracle on identical
+seeded inputs: live rays (ids and directions bit-exact, photons within
+FP32 accuracy), per-cell segment counts (exact), per-cell Gamma_HI
+(1e-4 relative), x_HII (1e-3 absolute), photon budgets, I-front radius."""
+import dataclasses as dc
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2409_04521_gb300 as F
+import workloads as W
+from parity_util import run_pair
+
+pytestmark = pytest.mark.gpu
+
+
+def test_stromgren_full_run():
+    prob = W.stromgren()
+    s = run_pair(prob, check_every=1)
+    assert s["straddles"] == 0
+    g = F.Simulation(prob, ray_capacity=1 << 20)
+    o = oracle.OracleSim(prob)
+    for _ in range(prob.nsteps):
+        g.step(prob.dt)
+        o.step(prob.dt)
+    Rg = oracle.ifront_radius_cells(g.fields()["x_HII"], prob.options.x_init)
+    Ro = oracle.ifront_radius_cells(o.fields()["x_HII"], prob.options.x_init)
+    assert abs(Rg - Ro) < 1.0
+    dx = prob.dx_phys_cm
+    rS = (3 * 3e48 / (4 * math.pi * 2.59e-13 * 1e-6)) ** (1 / 3) / dx
+    trec = 1 / (2.59e-13 * 1e-3)
+    t = prob.nsteps * prob.dt
+    R = 0.0
+    for _ in range(100):  # analytic law at the retarded time (c~ = 1 cell / step)
+        R = rS * (1 - math.exp(-max(t - R * prob.dt, 0) / trec)) ** (1 / 3)
+    assert abs(Rg - R) < 1.0
+
+
+def test_cosmological_16_sources_temperature():
+    prob = W.cosmo16(n=32, nsteps=12)
+    s = run_pair(prob, check_every=3, T_rtol=2e-3)
+    assert s["segments_total"] > 1e6
+
+
+def test_many_sources_subgrid_mfp():
+    prob = W.cosmo20k(n=40, nsteps=20, nsrc=200)
+    run_pair(prob, check_every=5)
+
+
+def test_batch_member_mfp_in_cells():
+    prob = W.batch_member(3, sizes=(32,), nsteps=20)
+    run_pair(prob, check_every=4)
+
+
+def test_edge_corner_source_and_ragged_grid():
+    prob = W.stromgren(n=16, nsteps=10)
+    prob.grid = (24, 16, 9)
+    prob.nH = np.full(24 * 16 * 9, 3e-4)
+    prob.source_cells = np.array([[0, 0, 0], [23, 15, 8], [11, 7, 4], [11, 7, 4]], np.int32)
+    prob.source_ndot = np.array([1e48, 2e48, 5e47, 5e47])
+    run_pair(prob)
+
+
+def test_edge_single_cell_grid():
+    prob = W.stromgren(n=1, nsteps=3)
+    prob.source_cells = np.array([[0, 0, 0]], np.int32)
+    run_pair(prob)
+
+
+def test_edge_unrotated_axis_aligned_ties():
+    # without rotation, level-0 pixels 4..7 point along +-x and +-y: rays run
+    # exactly on faces and edges and cross corners in ties
+    prob = W.stromgren(n=12, nsteps=8)
+    prob.options = dc.replace(prob.options, rotate=False)
+    prob.nH = np.full(12 ** 3, 1e-4)
+    run_pair(prob)
+
+
+def test_edge_deeper_source_level_and_fewer_rays_per_cell():
+    prob = W.stromgren(n=20, nsteps=10)
+    prob.options = dc.replace(prob.options, l_src=1, n_ray_min=2.0, l_max=4)
+    run_pair(prob)
+
+
+def test_edge_multi_level_split():
+    # large N_min: a fresh ray splits through several levels in one step
+    prob = W.stromgren(n=16, nsteps=6)
+    prob.options = dc.replace(prob.options, n_ray_min=60.0, l_max=5)
+    prob.nH = np.full(16 ** 3, 1e-4)
+    run_pair(prob)
+
+
+def test_edge_no_sources():
+    prob = W.stromgren(n=8, nsteps=3)
+    prob.source_cells = np.zeros((0, 3), np.int32)
+    prob.source_ndot = np.zeros(0)
+    g = F.Simulation(prob, ray_capacity=1024)
+    o = oracle.OracleSim(prob)
+    for _ in range(3):
+        g.step(prob.dt)
+        o.step(prob.dt)
+    assert g.counts()["rays"] == 0 and np.all(g.budget() == 0)
+    assert np.max(np.abs(g.fields()["x_HII"] - o.fields()["x_HII"])) < 1e-12
+
+
+def test_reset_reproduces_run():
+    prob = W.stromgren(n=16, nsteps=6)
+    g = F.Simulation(prob, ray_capacity=1 << 18)
+    for _ in range(6):
+        g.step(prob.dt)
+    f1, b1, c1 = g.fields(), g.budget(), g.counts()
+    g.reset()
+    assert g.counts()["step"] == 0 and g.counts()["rays"] == 0
+    for _ in range(6):
+        g.step(prob.dt)
+    f2, b2, c2 = g.fields(), g.budget(), g.counts()
+    assert c1 == c2
+    assert np.allclose(f1["gamma_HI"], f2["gamma_HI"], rtol=1e-5, atol=0)
+    assert np.allclose(b1, b2, rtol=1e-6)
+
+
+def test_capacity_overflow_keeps_last_good_step():
+    prob = W.stromgren(n=24, nsteps=12)
+    ref = F.Simulation(prob, ray_capacity=1 << 20)
+    small = F.Simulation(prob, ray_capacity=3000)
+    good = None
+    with pytest.raises(F.FlexRTError) as ei:
+        for s in range(12):
+            small.step(prob.dt)
+            small.sync()
+            good = s + 1
+    assert ei.value.status == 3
+    for _ in range(good):
+        ref.step(prob.dt)
+    assert small.counts()["step"] == good == ref.counts()["step"]
+    assert np.allclose(small.fields()["gamma_HI"], ref.fields()["gamma_HI"], rtol=1e-5, atol=0)
+    # further steps do nothing and keep reporting the error
+    with pytest.raises(F.FlexRTError):
+        small.step(prob.dt)
+        small.sync()
+    assert small.counts()["step"] == good
