@@ -497,7 +497,8 @@ extern "C" flexrt_status flexrt_reset(flexrt_ctx *c) {
     CK(c, cudaMemcpyAsync((char *)c->ctl + offsetof(Ctl, par), &zero, sizeof(zero), cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemcpyAsync((char *)c->ctl + offsetof(Ctl, err), &zero, sizeof(zero), cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemcpyAsync((char *)c->sims + offsetof(SimDev, step), &zero, sizeof(zero), cudaMemcpyHostToDevice, c->st));
-    CK(c, cudaMemsetAsync(c->acc, 0, sizeof(SimAcc), c->st));
+    // keep the monotonic marched-ray counter (last field) for profiling windows
+    CK(c, cudaMemsetAsync(c->acc, 0, offsetof(SimAcc, rays_in_total), c->st));
     CK(c, launch_init_cells(c->sims, 0, c->cells, c->ncell, c->st));
     CK(c, cudaStreamSynchronize(c->st));
     return FLEXRT_OK;

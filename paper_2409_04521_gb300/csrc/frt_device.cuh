@@ -188,6 +188,11 @@ __device__ __forceinline__ void rotate_dir(const int4 rows[3], int4 v, int32_t &
 // Integer state; a ray on a face belongs to the cell it moves into; tied face
 // crossings step together; crossings are compared as exact fractions.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float nonneg_ll_to_float(long long x) {
+    const unsigned hi = (unsigned)((unsigned long long)x >> 32), lo = (unsigned)x;
+    return fmaf((float)hi, 4294967296.0f, (float)lo);
+}
+
 struct Walk {
     int cx, cy, cz;          // current cell
     int Dx, Dy, Dz;          // distance along each axis to the next face ahead
@@ -227,9 +232,11 @@ __device__ __forceinline__ bool walk_segment(Walk &w, float &ds) {
     if (crx) { un = w.Dx; ud = w.ax; cross = true; }
     if (cry && (!cross || (long long)w.Dy * ud < un * w.ay)) { un = w.Dy; ud = w.ay; cross = true; }
     if (crz && (!cross || (long long)w.Dz * ud < un * w.az)) { un = w.Dz; ud = w.az; cross = true; }
-    long long num = un * w.td - w.tn * ud;
-    long long den = ud * w.td;
-    ds = __fdividef(__ll2float_rn(num), __ll2float_rn(den));
+    // ds = un/ud - tn/td as one exact integer fraction (both parts < 2^45),
+    // converted through 32-bit halves (no 64-bit conversion instructions)
+    const long long num = un * w.td - w.tn * ud;
+    const long long den = ud * w.td;
+    ds = __fdividef(nonneg_ll_to_float(num), nonneg_ll_to_float(den));
     if (cross) {
         if (crx && (long long)w.Dx * ud == un * w.ax) { w.cx += w.sx; w.Dx += (int)ONE_CELL; }
         if (cry && (long long)w.Dy * ud == un * w.ay) { w.cy += w.sy; w.Dy += (int)ONE_CELL; }
@@ -277,6 +284,46 @@ __device__ __forceinline__ int warp_incl_scan(int x) {
         if (lane >= o) x += t;
     }
     return x;
+}
+
+// Absorbed fraction a = 1 - e^-t and transmission e^-t of an optical depth
+// t >= 0 in single precision without cancellation: below t = 1/2 the Taylor
+// series of 1 - e^-t through t^10 (truncation < 1e-9 relative), above it
+// the hardware exponential.
+__device__ __forceinline__ void absorb_transmit(float t, float &a, float &tr) {
+    const float u = fminf(t, 0.5f);
+    float q = 1.0f / 3628800.0f;                 // 1/10!
+    q = fmaf(q, -u, 1.0f / 362880.0f);
+    q = fmaf(q, -u, 1.0f / 40320.0f);
+    q = fmaf(q, -u, 1.0f / 5040.0f);
+    q = fmaf(q, -u, 1.0f / 720.0f);
+    q = fmaf(q, -u, 1.0f / 120.0f);
+    q = fmaf(q, -u, 1.0f / 24.0f);
+    q = fmaf(q, -u, 1.0f / 6.0f);
+    q = fmaf(q, -u, 0.5f);
+    q = fmaf(q, -u, 1.0f);
+    const float series = q * u;                  // 1 - e^-u
+    const float ex = __expf(-t);
+    const bool small = t < 0.5f;
+    a = small ? series : 1.0f - ex;
+    tr = small ? 1.0f - series : ex;
+}
+
+// exact 2^-k for 0 <= k < 126
+__device__ __forceinline__ float pow2_neg(int k) { return __int_as_float((127 - k) << 23); }
+
+// v * 2^32 rounded to an unsigned 64-bit integer, for v >= 0 below 2^31;
+// built from the float's bits (no 64-bit conversion instruction)
+__device__ __forceinline__ unsigned long long fixed32(float v) {
+    const unsigned b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0 || (b >> 31)) return 0ull;
+    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+    const int sh = e - 118;                      // value * 2^32 = m * 2^(e - 150 + 32)
+    if (sh >= 0) return sh < 40 ? (m << sh) : 0xffffffffffffffffull;
+    const int r = -sh;
+    if (r > 24) return 0ull;
+    return (m + (1ull << (r - 1))) >> r;
 }
 
 __device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float c, float d) {

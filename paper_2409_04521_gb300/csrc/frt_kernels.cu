@@ -47,6 +47,23 @@ __device__ __forceinline__ float2 cell_kappa(const SimDev &S, double nH, double 
     return make_float2(kx, ks);
 }
 
+// e = e^-r, g = (1 - e^-r)/r and h = (1 - g)/r for r >= 0 in single
+// precision: Taylor series below r = 1/2, closed forms above.
+__device__ __forceinline__ void relax_factors(float r, float &e, float &g, float &h) {
+    const float u = fminf(fmaxf(r, 0.0f), 0.5f);
+    float sg = 1.0f / 39916800.0f, sh = 1.0f / 479001600.0f;     // 1/11!, 1/12!
+    const float cg[10] = {1.0f / 3628800.0f, 1.0f / 362880.0f, 1.0f / 40320.0f, 1.0f / 5040.0f, 1.0f / 720.0f,
+                          1.0f / 120.0f, 1.0f / 24.0f, 1.0f / 6.0f, 0.5f, 1.0f};
+    const float ch[10] = {1.0f / 39916800.0f, 1.0f / 3628800.0f, 1.0f / 362880.0f, 1.0f / 40320.0f, 1.0f / 5040.0f,
+                          1.0f / 720.0f, 1.0f / 120.0f, 1.0f / 24.0f, 1.0f / 6.0f, 0.5f};
+#pragma unroll
+    for (int k = 0; k < 10; ++k) { sg = fmaf(sg, -u, cg[k]); sh = fmaf(sh, -u, ch[k]); }
+    if (r < 0.5f) { g = sg; h = sh; e = 1.0f - r * sg; return; }
+    e = __expf(-r);
+    g = __fdividef(1.0f - e, r);
+    h = __fdividef(1.0f - g, r);
+}
+
 __global__ void k_init_cells(const SimDev *sims, int sim, Cells c) {
     const SimDev &S = sims[sim];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.ncell; i += (long long)gridDim.x * blockDim.x) {
@@ -118,9 +135,11 @@ __global__ void k_emit(EmitArgs A) {
 constexpr int NACC = 6;  // in, escaped, out, segments, rays in, rays out
 
 template <int NB>
-__global__ void __launch_bounds__(256) k_march(MarchArgs A) {
-    extern __shared__ double sh_acc[];
-    for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) sh_acc[i] = 0.0;
+__global__ void __launch_bounds__(256, 3) k_march(MarchArgs A) {
+    // per-simulation tallies of this block: photons in 2^-32 fixed point,
+    // counts as integers
+    extern __shared__ unsigned long long sh_acc[];
+    for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) sh_acc[i] = 0ull;
     __syncthreads();
     Ctl *C = A.ctl;
     const int lane = lane_id();
@@ -190,14 +209,8 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs A) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         const float kb = fmaf(k.x, sig[b], k.y);
-                        const float tau = kb * ds;
                         float tr, ab;
-                        if (tau < 0.5f) {
-                            const float em1 = expm1f(-tau);
-                            ab = -em1; tr = 1.0f + em1;
-                        } else {
-                            tr = expf(-tau); ab = 1.0f - tr;
-                        }
+                        absorb_transmit(kb * ds, ab, tr);
                         const float a = ph[b] * ab;
                         const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds;
                         ph[b] *= tr;
@@ -227,7 +240,7 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs A) {
             int nout = 0, m = 0;
             const int lev = (int)(pl >> LEVEL_SHIFT);
             if (valid && !esc) {
-                const float thr = S->eps_term * A.em.n0[e] * ldexpf(1.0f, -2 * (lev - S->l_src));
+                const float thr = S->eps_term * A.em.n0[e] * pow2_neg(2 * (lev - S->l_src));
                 if (s_end < thr) {
                     // termination: the ray's last photons stay in its last cell
                     float g = 0.f, h = 0.f;
@@ -254,8 +267,13 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs A) {
                 const unsigned peers = __match_any_sync(FULL, key);
                 if (__any_sync(FULL, __popc(peers) > 1)) peer_sum<NACC>(peers, v);
                 if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0u) {
-#pragma unroll
-                    for (int k = 0; k < NACC; ++k) atomicAdd(&sh_acc[key * NACC + k], (double)v[k]);
+                    unsigned long long *dst = sh_acc + key * NACC;
+                    atomicAdd(dst + 0, fixed32(v[0]));
+                    atomicAdd(dst + 1, fixed32(v[1]));
+                    atomicAdd(dst + 2, fixed32(v[2]));
+                    atomicAdd(dst + 3, (unsigned long long)(unsigned)__float2uint_rn(v[3]));
+                    atomicAdd(dst + 4, (unsigned long long)(unsigned)__float2uint_rn(v[4]));
+                    atomicAdd(dst + 5, (unsigned long long)(unsigned)__float2uint_rn(v[5]));
                 }
             }
             // compacted output
@@ -279,7 +297,7 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs A) {
                         const uint32_t pix0 = (pl & PIX_MASK) << (2 * m);
                         const int4 *rg = A.em.ring + ((long long)e * A.em.ring_w + (bi % A.em.ring_w)) * 3;
                         int4 rows[3] = {rg[0], rg[1], rg[2]};
-                        const float scale = ldexpf(1.0f, -2 * m);
+                        const float scale = pow2_neg(2 * m);
                         float cph[NB];
 #pragma unroll
                         for (int b = 0; b < NB; ++b) cph[b] = ph[b] * scale;
@@ -302,8 +320,9 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs A) {
     }
     __syncthreads();
     for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) {
-        const double v = sh_acc[i];
-        if (v != 0.0) {
+        const unsigned long long u = sh_acc[i];
+        const double v = (i % NACC) < 3 ? (double)u * 0x1p-32 : (double)u;
+        if (u != 0ull) {
             SimAcc &a = A.acc[i / NACC];
             double *dst = nullptr;
             switch (i % NACC) {
@@ -355,21 +374,22 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                 const float T0 = A.cells.T[g];
                 const double alpha = S.rates ? (double)alphaB_f(T0) : S.alpha_const;
                 const double Cc = S.rates ? (double)collion_f(T0) : 0.0;
-                // Eq. 7-10 for the neutral fraction, n_e re-evaluated from <x>
+                // Eq. 7-10 for the neutral fraction y = 1 - x with n_e
+                // re-evaluated from <x>.  With b = alpha n_e, r = dt (Gamma + C n_e
+                // + alpha n_e), g = (1 - e^-r)/r and h = (1 - g)/r:
+                //   y(dt) = y0 e^-r + b dt g,   <y> = y0 g + b dt h,
+                // the same solution as y_eq + (y0 - y_eq) e^-r and its time
+                // average, written with positive terms only and no division.
                 double yb = y0, y1 = y0;
                 for (int it = 0; it < S.chem_iters; ++it) {
                     const double ne = nH * (1.0 - yb);
-                    const double sum = G + (Cc + alpha) * ne;
-                    if (!(sum > 0.0)) { y1 = y0; yb = y0; break; }
-                    const double inv = 1.0 / sum;
-                    const double yeq = alpha * ne * inv;
-                    const double r = S.dt * sum;
-                    const float rf = (float)r;
-                    const double ex = (double)expf(-rf);
-                    const double q = r < 1e-4 ? 1.0 - 0.5 * r + r * r / 6.0 : (double)(-expm1f(-rf)) / r;
-                    const double ybn = yeq + (y0 - yeq) * q;
-                    y1 = yeq + (y0 - yeq) * ex;
-                    const bool conv = fabs(ybn - yb) <= 1e-13 * yb;
+                    const double bdt = alpha * ne * S.dt;
+                    const double r = S.dt * G + (Cc + alpha) * ne * S.dt;
+                    float ef, g, h;
+                    relax_factors((float)r, ef, g, h);
+                    y1 = y0 * (double)ef + bdt * (double)g;
+                    const double ybn = y0 * (double)g + bdt * (double)h;
+                    const bool conv = fabs(ybn - yb) <= 1e-9 * (1.0 - ybn) + 1e-300;
                     yb = ybn;
                     if (conv) break;
                 }
@@ -511,7 +531,7 @@ cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st) {
 }
 template <int NB>
 static cudaError_t march_nb(const MarchArgs &a, int blocks, int threads, cudaStream_t st) {
-    size_t sh = (size_t)a.nsims * NACC * sizeof(double);
+    size_t sh = (size_t)a.nsims * NACC * sizeof(unsigned long long);
     k_march<NB><<<blocks, threads, sh, st>>>(a);
     return cudaGetLastError();
 }
@@ -530,7 +550,7 @@ cudaError_t launch_march(const MarchArgs &a, int nb, int blocks, int threads, cu
 }
 int march_max_blocks_per_sm(int nb, int threads, int nsims) {
     int n = 0;
-    size_t sh = (size_t)nsims * NACC * sizeof(double);
+    size_t sh = (size_t)nsims * NACC * sizeof(unsigned long long);
     switch (nb) {
         case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<1>, threads, sh); break;
         case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<2>, threads, sh); break;
