@@ -168,6 +168,14 @@ flexrt_status flexrt_profile(flexrt_ctx *ctx, int32_t enable);
 flexrt_status flexrt_get_kernel_times(flexrt_ctx *ctx, double ms[3], int64_t launches[3],
                                       int64_t march_rays[1]);
 
+/* Launch configuration of the fused march kernel (chosen by the autotuner):
+ * agg: how lanes of a warp combine deposits into one cell before the
+ * vector reduction (0 none, 1 groups of equal cells, 2 runs of equal
+ * consecutive cells); minb: resident blocks per SM the register budget
+ * targets (2..4); blocks_per_sm: persistent blocks launched per SM
+ * (0 = occupancy limit).  FLEXRT_E_INVALID if the variant is not built. */
+flexrt_status flexrt_set_launch(flexrt_ctx *ctx, int32_t agg, int32_t minb, int32_t blocks_per_sm);
+
 const char *flexrt_last_error(const flexrt_ctx *ctx);
 void flexrt_destroy(flexrt_ctx *ctx);
 

@@ -86,6 +86,7 @@ struct flexrt_ctx {
     const int4 *pixtab = nullptr;
     int ltab = 0;
     int march_blocks = 0, march_threads = 256, chem_blocks = 0;
+    int march_agg = 1, march_minb = 3, sm_count = 1;
 
     SimDev h{};  // host copy of the simulation constants
     int ecap = 0;
@@ -321,7 +322,9 @@ extern "C" flexrt_status flexrt_create(const flexrt_grid *grid, const flexrt_box
 
     int dev_sms = 0;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
-    int per_sm = march_max_blocks_per_sm(c->nb, c->march_threads, 1);
+    c->sm_count = std::max(dev_sms, 1);
+    if (!march_variant_exists(c->nb, c->march_agg, c->march_minb)) { c->march_agg = 1; c->march_minb = 3; }
+    int per_sm = march_max_blocks_per_sm(c->nb, c->march_agg, c->march_minb, c->march_threads, 1);
     c->march_blocks = std::max(1, dev_sms * std::max(per_sm, 1));
     c->chem_blocks = std::max(1, (int)std::min<long long>((c->ncell + 255) / 256, (long long)dev_sms * 8));
     *out = c;
@@ -467,7 +470,7 @@ extern "C" flexrt_status flexrt_step(flexrt_ctx *c, double dt) {
         toc(0);
     }
     tic(1);
-    CK(c, launch_march(ma, c->nb, c->march_blocks, c->march_threads, c->st));
+    CK(c, launch_march(ma, c->nb, c->march_agg, c->march_minb, c->march_blocks, c->march_threads, c->st));
     toc(1);
     tic(2);
     CK(c, launch_chem(ca, c->chem_blocks, c->st));
@@ -639,6 +642,19 @@ extern "C" flexrt_status flexrt_get_kernel_times(flexrt_ctx *c, double ms[3], in
     if (s != FLEXRT_OK) return s;
     if (march_rays) march_rays[0] = (int64_t)(a.rays_in_total - c->rays_total_at_profile);
     c->rays_total_at_profile = a.rays_in_total;
+    return FLEXRT_OK;
+}
+
+extern "C" flexrt_status flexrt_set_launch(flexrt_ctx *c, int32_t agg, int32_t minb, int32_t blocks_per_sm) {
+    if (!c) return FLEXRT_E_INVALID;
+    if (!march_variant_exists(c->nb, agg, minb) || blocks_per_sm < 0 || blocks_per_sm > 32)
+        return c->fail(FLEXRT_E_INVALID, "march kernel variant not built");
+    int lim = march_max_blocks_per_sm(c->nb, agg, minb, c->march_threads, 1);
+    if (lim < 1) return c->fail(FLEXRT_E_INVALID, "variant cannot be resident");
+    int bps = blocks_per_sm == 0 ? lim : std::min(blocks_per_sm, lim);
+    c->march_agg = agg;
+    c->march_minb = minb;
+    c->march_blocks = c->sm_count * bps;
     return FLEXRT_OK;
 }
 

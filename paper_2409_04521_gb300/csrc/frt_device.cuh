@@ -275,6 +275,39 @@ __device__ __forceinline__ void peer_sum(unsigned peers, float (&v)[NV]) {
     }
 }
 
+// Sum NV values over runs of equal consecutive keys (segmented shuffle
+// tree); the first lane of each run ends with the run's sum.  Equal keys that
+// are not adjacent stay in separate runs.
+template <int NV>
+__device__ __forceinline__ bool run_sum(int key, float (&v)[NV]) {
+    const int lane = lane_id();
+    const int prev = __shfl_up_sync(FULL, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const unsigned above = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
+    const int run_end = above ? __ffs(above) - 1 : 32;
+    if (__all_sync(FULL, run_end == lane + 1)) return head;   // all runs of length 1
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float t = __shfl_down_sync(FULL, v[k], d);
+            if (lane + d < run_end) v[k] += t;
+        }
+    }
+    return head;
+}
+
+// Sum NV values over the whole warp (butterfly); every lane gets the sum.
+template <int NV>
+__device__ __forceinline__ void warp_sum(float (&v)[NV]) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(FULL, v[k], d);
+    }
+}
+
 // Warp-inclusive prefix sum of an int.
 __device__ __forceinline__ int warp_incl_scan(int x) {
     const int lane = lane_id();

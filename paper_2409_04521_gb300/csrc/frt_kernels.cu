@@ -134,8 +134,12 @@ __global__ void k_emit(EmitArgs A) {
 // ---------------------------------------------------------------------------
 constexpr int NACC = 6;  // in, escaped, out, segments, rays in, rays out
 
-template <int NB>
-__global__ void __launch_bounds__(256, 3) k_march(MarchArgs A) {
+// AGG selects how the lanes of a warp combine deposits into the same cell
+// before the vector reduction: 0 none, 1 peer groups of equal keys
+// (match_any + pairwise tree), 2 runs of equal consecutive keys.
+// MINB is the resident-block target per SM (register budget).
+template <int NB, int AGG, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
     // per-simulation tallies of this block: photons in 2^-32 fixed point,
     // counts as integers
     extern __shared__ unsigned long long sh_acc[];
@@ -225,10 +229,17 @@ __global__ void __launch_bounds__(256, 3) k_march(MarchArgs A) {
                     else if (walk_outside(w, nx, ny, nz)) { esc = true; live = false; }
                 }
                 if (__ballot_sync(FULL, key >= 0) == 0u) break;
-                const unsigned peers = __match_any_sync(FULL, key);
-                if (__any_sync(FULL, key >= 0 && __popc(peers) > 1)) peer_sum<4>(peers, v);
-                if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0u)
-                    red_add_v4(A.cells.dep + key, v[0], v[1], v[2], v[3]);
+                if (AGG == 0) {
+                    if (key >= 0) red_add_v4(A.cells.dep + key, v[0], v[1], v[2], v[3]);
+                } else if (AGG == 1) {
+                    const unsigned peers = __match_any_sync(FULL, key);
+                    if (__any_sync(FULL, key >= 0 && __popc(peers) > 1)) peer_sum<4>(peers, v);
+                    if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0u)
+                        red_add_v4(A.cells.dep + key, v[0], v[1], v[2], v[3]);
+                } else {
+                    const bool head = run_sum<4>(key, v);
+                    if (key >= 0 && head) red_add_v4(A.cells.dep + key, v[0], v[1], v[2], v[3]);
+                }
             }
             if (live) {  // more than four segments: impossible for |d| <= 2^21
                 atomicOr(&C->err, 4);
@@ -264,10 +275,20 @@ __global__ void __launch_bounds__(256, 3) k_march(MarchArgs A) {
                 float v[NACC] = {s_in, esc ? s_end : 0.0f, nout ? s_end : 0.0f, (float)nseg,
                                  valid ? 1.0f : 0.0f, (float)nout};
                 const int key = valid ? sim : -1;
-                const unsigned peers = __match_any_sync(FULL, key);
-                if (__any_sync(FULL, __popc(peers) > 1)) peer_sum<NACC>(peers, v);
-                if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0u) {
-                    unsigned long long *dst = sh_acc + key * NACC;
+                const int kref = __reduce_max_sync(FULL, key);
+                bool lead;
+                int kk = key;
+                if (__all_sync(FULL, key < 0 || key == kref)) {
+                    warp_sum<NACC>(v);               // invalid lanes carry zeros
+                    lead = lane == 0 && kref >= 0;
+                    kk = kref;
+                } else {
+                    const unsigned peers = __match_any_sync(FULL, key);
+                    peer_sum<NACC>(peers, v);
+                    lead = key >= 0 && (peers & ((1u << lane) - 1u)) == 0u;
+                }
+                if (lead) {
+                    unsigned long long *dst = sh_acc + kk * NACC;
                     atomicAdd(dst + 0, fixed32(v[0]));
                     atomicAdd(dst + 1, fixed32(v[1]));
                     atomicAdd(dst + 2, fixed32(v[2]));
@@ -529,38 +550,52 @@ cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st) {
     k_emit<<<blocks, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
-template <int NB>
-static cudaError_t march_nb(const MarchArgs &a, int blocks, int threads, cudaStream_t st) {
+// Kernel variants: every bin count with the default (AGG 1, 3 blocks/SM);
+// the bin counts of the standard spectra (1, 3, 4) with every aggregation
+// and register budget, for the autotuner.
+using MarchFn = void (*)(MarchArgs);
+static MarchFn march_fn(int nb, int agg, int minb) {
+#define FRT_V(NB)                                                                   \
+    if (nb == NB) {                                                                \
+        if (agg == 0 && minb == 2) return k_march<NB, 0, 2>;                       \
+        if (agg == 0 && minb == 3) return k_march<NB, 0, 3>;                       \
+        if (agg == 0 && minb == 4) return k_march<NB, 0, 4>;                       \
+        if (agg == 1 && minb == 2) return k_march<NB, 1, 2>;                       \
+        if (agg == 1 && minb == 3) return k_march<NB, 1, 3>;                       \
+        if (agg == 1 && minb == 4) return k_march<NB, 1, 4>;                       \
+        if (agg == 2 && minb == 2) return k_march<NB, 2, 2>;                       \
+        if (agg == 2 && minb == 3) return k_march<NB, 2, 3>;                       \
+        if (agg == 2 && minb == 4) return k_march<NB, 2, 4>;                       \
+        return nullptr;                                                            \
+    }
+    FRT_V(1)
+    FRT_V(3)
+    FRT_V(4)
+#undef FRT_V
+    if (agg != 1 || minb != 3) return nullptr;
+    switch (nb) {
+        case 2: return k_march<2, 1, 3>;
+        case 5: return k_march<5, 1, 3>;
+        case 6: return k_march<6, 1, 3>;
+        case 7: return k_march<7, 1, 3>;
+        case 8: return k_march<8, 1, 3>;
+        default: return nullptr;
+    }
+}
+bool march_variant_exists(int nb, int agg, int minb) { return march_fn(nb, agg, minb) != nullptr; }
+cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st) {
+    MarchFn f = march_fn(nb, agg, minb);
+    if (!f) return cudaErrorInvalidValue;
     size_t sh = (size_t)a.nsims * NACC * sizeof(unsigned long long);
-    k_march<NB><<<blocks, threads, sh, st>>>(a);
+    f<<<blocks, threads, sh, st>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_march(const MarchArgs &a, int nb, int blocks, int threads, cudaStream_t st) {
-    switch (nb) {
-        case 1: return march_nb<1>(a, blocks, threads, st);
-        case 2: return march_nb<2>(a, blocks, threads, st);
-        case 3: return march_nb<3>(a, blocks, threads, st);
-        case 4: return march_nb<4>(a, blocks, threads, st);
-        case 5: return march_nb<5>(a, blocks, threads, st);
-        case 6: return march_nb<6>(a, blocks, threads, st);
-        case 7: return march_nb<7>(a, blocks, threads, st);
-        case 8: return march_nb<8>(a, blocks, threads, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-int march_max_blocks_per_sm(int nb, int threads, int nsims) {
+int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims) {
+    MarchFn f = march_fn(nb, agg, minb);
+    if (!f) return 0;
     int n = 0;
     size_t sh = (size_t)nsims * NACC * sizeof(unsigned long long);
-    switch (nb) {
-        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<1>, threads, sh); break;
-        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<2>, threads, sh); break;
-        case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<3>, threads, sh); break;
-        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<4>, threads, sh); break;
-        case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<5>, threads, sh); break;
-        case 6: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<6>, threads, sh); break;
-        case 7: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<7>, threads, sh); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_march<8>, threads, sh); break;
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, sh);
     return n;
 }
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st) {

@@ -41,8 +41,9 @@ struct ChemArgs {
 cudaError_t launch_pixtab(int4 *tab, int L, cudaStream_t st);
 cudaError_t launch_init_cells(const SimDev *sims, int sim, Cells c, long long ncell, cudaStream_t st);
 cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st);
-cudaError_t launch_march(const MarchArgs &a, int nb, int blocks, int threads, cudaStream_t st);
-int march_max_blocks_per_sm(int nb, int threads, int nsims);
+bool march_variant_exists(int nb, int agg, int minb);
+cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st);
+int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims);
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st);
 cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_t st);
 cudaError_t launch_probe_pixvec(int level, long long p0, long long n, int32_t *out, cudaStream_t st);

@@ -87,6 +87,7 @@ def lib():
                                           P(C.c_int32), P(C.c_double), P(C.c_int64)]
             L.flexrt_profile.argtypes = [vp, C.c_int32]
             L.flexrt_get_kernel_times.argtypes = [vp, P(C.c_double), P(C.c_int64), P(C.c_int64)]
+            L.flexrt_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
             L.flexrt_last_error.argtypes = [vp]
             L.flexrt_last_error.restype = C.c_char_p
             L.flexrt_destroy.argtypes = [vp]
@@ -218,6 +219,9 @@ class Simulation:
         _check(lib().flexrt_get_kernel_times(self._h, _p(ms, C.c_double), _p(ln, C.c_int64), _p(rays, C.c_int64)),
                self._h)
         return dict(zip(("emit", "march", "chem"), ms)), dict(zip(("emit", "march", "chem"), ln)), int(rays[0])
+
+    def set_launch(self, agg: int, minb: int, blocks_per_sm: int = 0):
+        _check(lib().flexrt_set_launch(self._h, int(agg), int(minb), int(blocks_per_sm)), self._h)
 
     def close(self):
         if getattr(self, "_h", None):
