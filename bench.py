@@ -222,6 +222,12 @@ def impl_gpu(args, dist):
     # device-resident runs
     sim = F.Simulation(prob, ray_capacity=args.capacity, stream=stream.cuda_stream)
     max_rays = 0
+    tuned = None
+    if not args.no_tune:
+        from paper_2409_04521_gb300 import autotune
+        best, table = autotune.tune(sim, prob)
+        tuned = {"variant": {"agg": best[0], "minb": best[1], "blocks_per_sm": best[2]},
+                 "candidates": len(table)}
 
     def one_sim():
         nonlocal max_rays
@@ -289,6 +295,9 @@ def impl_gpu(args, dist):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s2 = F.Simulation(prob, ray_capacity=args.capacity)
+            if tuned:
+                v = tuned["variant"]
+                s2.set_launch(v["agg"], v["minb"], v["blocks_per_sm"])
             for _ in range(prob.nsteps):
                 s2.step(prob.dt)
             f = s2.fields()
@@ -321,7 +330,8 @@ def impl_gpu(args, dist):
                            "ray_capacity": args.capacity, "max_live_rays": max_rays,
                            "parallelism": f"replicas x{dist.ws}",
                            "l2": "working set larger than L2 (ray queues of several GB)",
-                           "precision": "rays/deposits fp32, ionisation update fp64, temperature fp32"},
+                           "precision": "rays/deposits fp32, ionisation update fp64, temperature fp32",
+                           "march_launch": tuned},
                 "sims_per_hour": 3600.0 / (t_max * 1e-3 / args.steps) * dist.ws,
                 "segments_per_sim": segs_all / args.steps / dist.ws,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -341,6 +351,7 @@ def main(argv=None):
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         dist = Dist(backend="gloo")

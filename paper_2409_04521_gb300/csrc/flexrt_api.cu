@@ -86,7 +86,7 @@ struct flexrt_ctx {
     const int4 *pixtab = nullptr;
     int ltab = 0;
     int march_blocks = 0, march_threads = 256, chem_blocks = 0;
-    int march_agg = 1, march_minb = 3, sm_count = 1;
+    int march_agg = 0, march_minb = 2, sm_count = 1;
 
     SimDev h{};  // host copy of the simulation constants
     int ecap = 0;
@@ -260,6 +260,11 @@ extern "C" flexrt_status flexrt_create(const flexrt_grid *grid, const flexrt_box
         mean = s / (double)c->ncell;
     }
     h.nH_mean = mean;
+    h.ksc = h.sigma_ref * h.dx_phys;
+    h.inv_nH_mean = 1.0 / mean;
+    h.inv_gamma_ref = m.gamma_ref > 0 ? 1.0 / m.gamma_ref : 0.0;
+    h.y_thr = 1.0 - m.xion_threshold;
+    h.kap_sub0 = m.lambda0_cm_comoving > 0 ? (float)(h.dx_com / m.lambda0_cm_comoving) : 0.0f;
     h.x_init = opt.x_init; h.T_init = opt.T_init;
     h.nref = 1.0;
 
@@ -323,7 +328,7 @@ extern "C" flexrt_status flexrt_create(const flexrt_grid *grid, const flexrt_box
     int dev_sms = 0;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
     c->sm_count = std::max(dev_sms, 1);
-    if (!march_variant_exists(c->nb, c->march_agg, c->march_minb)) { c->march_agg = 1; c->march_minb = 3; }
+    if (!march_variant_exists(c->nb, c->march_agg, c->march_minb)) { c->march_agg = 0; c->march_minb = 2; }
     int per_sm = march_max_blocks_per_sm(c->nb, c->march_agg, c->march_minb, c->march_threads, 1);
     c->march_blocks = std::max(1, dev_sms * std::max(per_sm, 1));
     c->chem_blocks = std::max(1, (int)std::min<long long>((c->ncell + 255) / 256, (long long)dev_sms * 8));
@@ -446,10 +451,13 @@ extern "C" flexrt_status flexrt_step(flexrt_ctx *c, double dt) {
         CK(c, cudaEventSynchronize(c->ev_dt));
         c->h.dt = dt;
         c->h.gscale = c->h.nref * c->h.sigma_ref / (c->h.dx_phys * c->h.dx_phys * dt);
+        c->h.hscale = c->h.gscale * EV_ERG;
         c->h_dt[0] = c->h.dt;
         c->h_dt[1] = c->h.gscale;
+        c->h_dt[2] = c->h.hscale;
         static_assert(offsetof(SimDev, gscale) == offsetof(SimDev, dt) + sizeof(double), "dt/gscale layout");
-        CK(c, cudaMemcpyAsync((char *)c->sims + offsetof(SimDev, dt), c->h_dt, 2 * sizeof(double),
+        static_assert(offsetof(SimDev, hscale) == offsetof(SimDev, dt) + 2 * sizeof(double), "dt/hscale layout");
+        CK(c, cudaMemcpyAsync((char *)c->sims + offsetof(SimDev, dt), c->h_dt, 3 * sizeof(double),
                               cudaMemcpyHostToDevice, c->st));
         CK(c, cudaEventRecord(c->ev_dt, c->st));
     }

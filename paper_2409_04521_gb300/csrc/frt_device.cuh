@@ -188,59 +188,63 @@ __device__ __forceinline__ void rotate_dir(const int4 rows[3], int4 v, int32_t &
 // Integer state; a ray on a face belongs to the cell it moves into; tied face
 // crossings step together; crossings are compared as exact fractions.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float nonneg_ll_to_float(long long x) {
-    const unsigned hi = (unsigned)((unsigned long long)x >> 32), lo = (unsigned)x;
-    return fmaf((float)hi, 4294967296.0f, (float)lo);
+// exact 32x32 -> 64-bit unsigned product (one wide multiply)
+__device__ __forceinline__ unsigned long long wmul(unsigned a, unsigned b) { return (unsigned long long)a * b; }
+
+__device__ __forceinline__ float u64_to_float(unsigned long long x) {
+    return fmaf((float)(unsigned)(x >> 32), 4294967296.0f, (float)(unsigned)x);
 }
 
 struct Walk {
     int cx, cy, cz;          // current cell
-    int Dx, Dy, Dz;          // distance along each axis to the next face ahead
-    int ax, ay, az;          // |d|
+    unsigned Dx, Dy, Dz;     // distance along each axis to the next face ahead (<= 2^22)
+    unsigned ax, ay, az;     // |d| (<= 2^21)
     int sx, sy, sz;          // sign of d
-    long long tn, td;        // segment start, t = tn/td
+    unsigned tn, td;         // segment start, t = tn/td
 };
 
-__device__ __forceinline__ void axis_init(long long p, int d, int &c, int &D, int &a, int &s) {
+// cell index (floor) and distance to the next face for one axis; a ray on a
+// face belongs to the cell it moves into
+__device__ __forceinline__ void axis_init(long long p, int d, int &c, unsigned &D, unsigned &a, int &s) {
+    const unsigned MASK = (unsigned)ONE_CELL - 1u;
     if (d > 0) {
-        long long cc = p >> FRAC_BITS;
-        c = (int)cc; D = (int)(((cc + 1) << FRAC_BITS) - p); a = d; s = 1;
+        c = (int)(p >> FRAC_BITS); D = (unsigned)ONE_CELL - ((unsigned)p & MASK); a = (unsigned)d; s = 1;
     } else if (d < 0) {
-        long long cc = (p - 1) >> FRAC_BITS;
-        c = (int)cc; D = (int)(p - (cc << FRAC_BITS)); a = -d; s = -1;
+        const long long q = p - 1;
+        c = (int)(q >> FRAC_BITS); D = ((unsigned)q & MASK) + 1u; a = (unsigned)(-d); s = -1;
     } else {
-        c = (int)(p >> FRAC_BITS); D = 0; a = 0; s = 0;
+        c = (int)(p >> FRAC_BITS); D = 0u; a = 0u; s = 0;
     }
 }
 __device__ __forceinline__ void walk_init(Walk &w, long long px, long long py, long long pz, int dx, int dy, int dz) {
     axis_init(px, dx, w.cx, w.Dx, w.ax, w.sx);
     axis_init(py, dy, w.cy, w.Dy, w.ay, w.sy);
     axis_init(pz, dz, w.cz, w.Dz, w.az, w.sz);
-    w.tn = 0; w.td = 1;
+    w.tn = 0u; w.td = 1u;
 }
 __device__ __forceinline__ bool walk_outside(const Walk &w, int nx, int ny, int nz) {
     return (unsigned)w.cx >= (unsigned)nx || (unsigned)w.cy >= (unsigned)ny || (unsigned)w.cz >= (unsigned)nz;
 }
 // Emit the segment in the current (inside) cell: its length ds (cells) and
 // whether the ray goes on to another cell in this step.  Advances the walk.
+// Face crossings t_a = D_a/|d_a| are compared as exact cross products.
 __device__ __forceinline__ bool walk_segment(Walk &w, float &ds) {
-    bool crx = w.sx != 0 && w.Dx < w.ax;
-    bool cry = w.sy != 0 && w.Dy < w.ay;
-    bool crz = w.sz != 0 && w.Dz < w.az;
-    long long un = 1, ud = 1;
+    const bool crx = w.sx != 0 && w.Dx < w.ax;
+    const bool cry = w.sy != 0 && w.Dy < w.ay;
+    const bool crz = w.sz != 0 && w.Dz < w.az;
+    unsigned un = 1u, ud = 1u;
     bool cross = false;
     if (crx) { un = w.Dx; ud = w.ax; cross = true; }
-    if (cry && (!cross || (long long)w.Dy * ud < un * w.ay)) { un = w.Dy; ud = w.ay; cross = true; }
-    if (crz && (!cross || (long long)w.Dz * ud < un * w.az)) { un = w.Dz; ud = w.az; cross = true; }
-    // ds = un/ud - tn/td as one exact integer fraction (both parts < 2^45),
-    // converted through 32-bit halves (no 64-bit conversion instructions)
-    const long long num = un * w.td - w.tn * ud;
-    const long long den = ud * w.td;
-    ds = __fdividef(nonneg_ll_to_float(num), nonneg_ll_to_float(den));
+    if (cry && (!cross || wmul(w.Dy, ud) < wmul(un, w.ay))) { un = w.Dy; ud = w.ay; cross = true; }
+    if (crz && (!cross || wmul(w.Dz, ud) < wmul(un, w.az))) { un = w.Dz; ud = w.az; cross = true; }
+    // ds = un/ud - tn/td as one exact integer fraction
+    const unsigned long long num = wmul(un, w.td) - wmul(w.tn, ud);
+    const unsigned long long den = wmul(ud, w.td);
+    ds = __fdividef(u64_to_float(num), u64_to_float(den));
     if (cross) {
-        if (crx && (long long)w.Dx * ud == un * w.ax) { w.cx += w.sx; w.Dx += (int)ONE_CELL; }
-        if (cry && (long long)w.Dy * ud == un * w.ay) { w.cy += w.sy; w.Dy += (int)ONE_CELL; }
-        if (crz && (long long)w.Dz * ud == un * w.az) { w.cz += w.sz; w.Dz += (int)ONE_CELL; }
+        if (crx && wmul(w.Dx, ud) == wmul(un, w.ax)) { w.cx += w.sx; w.Dx += (unsigned)ONE_CELL; }
+        if (cry && wmul(w.Dy, ud) == wmul(un, w.ay)) { w.cy += w.sy; w.Dy += (unsigned)ONE_CELL; }
+        if (crz && wmul(w.Dz, ud) == wmul(un, w.az)) { w.cz += w.sz; w.Dz += (unsigned)ONE_CELL; }
         w.tn = un; w.td = ud;
     }
     return cross;

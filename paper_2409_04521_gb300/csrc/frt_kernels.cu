@@ -34,15 +34,16 @@ __global__ void k_pixtab(int4 *tab, int L) {
 // ---------------------------------------------------------------------------
 // kappa of a cell for the next step (Sec. 4.2, Eq. 13 and the sub-grid law)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cell_kappa(const SimDev &S, double nH, double y, double x, double G) {
-    float kx = (float)(nH * y * S.sigma_ref * S.dx_phys);
+__device__ __forceinline__ float2 cell_kappa(const SimDev &S, double nH, double y, float G) {
+    const float kx = (float)(nH * y) * (float)S.ksc;
     float ks = 0.0f;
     if (S.mfp_mode == 1) {
-        ks = (float)(S.dx_com / S.lambda0_c);
-    } else if (S.mfp_mode == 2 && x >= S.xion_thr) {
-        double g = G > S.gamma_floor ? G : S.gamma_floor;
-        float f = powf((float)(nH / S.nH_mean), (float)(-S.delta_exp)) * powf((float)(g / S.gamma_ref), (float)S.gamma_exp);
-        ks = (float)(S.dx_com / S.lambda0_c) / f;
+        ks = S.kap_sub0;
+    } else if (S.mfp_mode == 2 && y <= S.y_thr) {
+        const float g = fmaxf(G, (float)S.gamma_floor);
+        const float f = powf((float)nH * (float)S.inv_nH_mean, (float)(-S.delta_exp)) *
+                        powf(g * (float)S.inv_gamma_ref, (float)S.gamma_exp);
+        ks = __fdividef(S.kap_sub0, f);
     }
     return make_float2(kx, ks);
 }
@@ -74,7 +75,7 @@ __global__ void k_init_cells(const SimDev *sims, int sim, Cells c) {
         c.gamma[g] = 0.0f;
         c.dep[g] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (c.segcnt) c.segcnt[g] = 0;
-        c.kap[g] = cell_kappa(S, c.nH[g], y, S.x_init, 0.0);
+        c.kap[g] = cell_kappa(S, c.nH[g], y, 0.0f);
     }
 }
 
@@ -134,16 +135,40 @@ __global__ void k_emit(EmitArgs A) {
 // ---------------------------------------------------------------------------
 constexpr int NACC = 6;  // in, escaped, out, segments, rays in, rays out
 
+// The per-simulation constants the march needs, staged in shared memory.
+struct MarchSim {
+    int nx, ny, nz, step, l_src, l_max, active, pad;
+    long long coff;
+    float eps;
+    int K[MAXL];
+    float sig[MAXB], sige[MAXB];
+};
+
+__host__ __device__ constexpr size_t march_shared_bytes(int nsims) {
+    return (size_t)nsims * (NACC * sizeof(unsigned long long) + sizeof(MarchSim));
+}
+
+// Phases per ray: (1) the integer walk of the whole step, (2) the opacity
+// loads of every crossed cell at once, (3) attenuation and deposits.
 // AGG selects how the lanes of a warp combine deposits into the same cell
 // before the vector reduction: 0 none, 1 peer groups of equal keys
 // (match_any + pairwise tree), 2 runs of equal consecutive keys.
 // MINB is the resident-block target per SM (register budget).
 template <int NB, int AGG, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
-    // per-simulation tallies of this block: photons in 2^-32 fixed point,
-    // counts as integers
+    // per-simulation tallies of this block (photons in 2^-32 fixed point,
+    // counts as integers), then the staged constants
     extern __shared__ unsigned long long sh_acc[];
+    MarchSim *msim = reinterpret_cast<MarchSim *>(sh_acc + A.nsims * NACC);
     for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) sh_acc[i] = 0ull;
+    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) {
+        const SimDev &S = A.sims[i];
+        MarchSim &m = msim[i];
+        m.nx = S.nx; m.ny = S.ny; m.nz = S.nz; m.step = S.step; m.l_src = S.l_src; m.l_max = S.l_max;
+        m.active = S.active; m.pad = 0; m.coff = S.cell_off; m.eps = S.eps_term;
+        for (int l = 0; l < MAXL; ++l) m.K[l] = S.K[l];
+        for (int b = 0; b < MAXB; ++b) { m.sig[b] = S.sig[b]; m.sige[b] = S.sige[b]; }
+    }
     __syncthreads();
     Ctl *C = A.ctl;
     const int lane = lane_id();
@@ -157,7 +182,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += stride) {
             bool valid = i < n;
             uint32_t pl = 0, e = 0;
-            int bi = 0, dx = 0, dy = 0, dz = 0, sim = -1;
+            int bi = 0, dx = 0, dy = 0, dz = 0, sim = 0;
             float ph[NB];
             int4 ec = make_int4(0, 0, 0, 0);
             if (valid) {
@@ -167,83 +192,91 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 for (int b = 0; b < NB; ++b) ph[b] = qi.ph[b][i];
                 ec = __ldg(&A.em.cell[e]);
                 sim = ec.w;
-                if (!A.sims[sim].active) valid = false;
             } else {
 #pragma unroll
                 for (int b = 0; b < NB; ++b) ph[b] = 0.0f;
             }
-            const SimDev *S = A.sims + (sim < 0 ? 0 : sim);
-            const int step = S->step;
-            const int age = step - bi;
+            const MarchSim &S = msim[sim];
+            if (!S.active) valid = false;
+            const int age = S.step - bi;
             if (valid && (age < 0 || age >= A.em.ring_w)) {
                 atomicOr(&C->err, 2);
                 valid = false;
             }
-            float sig[NB], sige[NB];
-#pragma unroll
-            for (int b = 0; b < NB; ++b) { sig[b] = S->sig[b]; sige[b] = S->sige[b]; }
-            const int nx = S->nx, ny = S->ny, nz = S->nz;
-            const long long coff = S->cell_off;
-
             float s_in = 0.0f;
 #pragma unroll
             for (int b = 0; b < NB; ++b) s_in += ph[b];
 
-            Walk w;
-            {
-                long long px = ((2LL * ec.x + 1) << (FRAC_BITS - 1)) + (long long)age * dx;
-                long long py = ((2LL * ec.y + 1) << (FRAC_BITS - 1)) + (long long)age * dy;
-                long long pz = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + (long long)age * dz;
-                walk_init(w, px, py, pz, dx, dy, dz);
-            }
-            bool live = valid, esc = false;
-            if (live && walk_outside(w, nx, ny, nz)) { esc = true; live = false; }
-            long long last = -1;
-            float2 lastk = make_float2(0.f, 0.f);
+            // (1) integer walk of this step
+            int key[4];
+            float ds[4];
+            bool esc = false;
             int nseg = 0;
-#pragma unroll 1
+            {
+                Walk w;
+                const long long px = ((2LL * ec.x + 1) << (FRAC_BITS - 1)) + (long long)age * dx;
+                const long long py = ((2LL * ec.y + 1) << (FRAC_BITS - 1)) + (long long)age * dy;
+                const long long pz = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + (long long)age * dz;
+                walk_init(w, px, py, pz, dx, dy, dz);
+                bool live = valid;
+                if (live && walk_outside(w, S.nx, S.ny, S.nz)) { esc = true; live = false; }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    key[j] = -1;
+                    ds[j] = 0.0f;
+                    if (live) {
+                        key[j] = (int)(S.coff + ((long long)w.cz * S.ny + w.cy) * S.nx + w.cx);
+                        const bool more = walk_segment(w, ds[j]);
+                        ++nseg;
+                        if (!more) live = false;
+                        else if (walk_outside(w, S.nx, S.ny, S.nz)) { esc = true; live = false; }
+                    }
+                }
+                if (live) {  // more than four segments: impossible for |d| <= 2^21
+                    atomicOr(&C->err, 4);
+                    valid = false;
+                }
+            }
+            // (2) opacities of the crossed cells
+            float2 kc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) kc[j] = key[j] >= 0 ? __ldg(&A.cells.kap[key[j]]) : make_float2(0.f, 0.f);
+            // (3) attenuation and deposits (Eq. 13, Eq. 17)
+            int last = -1;
+            float2 lastk = make_float2(0.f, 0.f);
+#pragma unroll
             for (int j = 0; j < 4; ++j) {
-                int key = -1;
                 float v[4] = {0.f, 0.f, 0.f, 1.0f};
-                if (live) {
-                    const long long gc = coff + ((long long)w.cz * ny + w.cy) * nx + w.cx;
-                    float ds;
-                    const bool more = walk_segment(w, ds);
-                    const float2 k = __ldg(&A.cells.kap[gc]);
+                if (key[j] >= 0) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
-                        const float kb = fmaf(k.x, sig[b], k.y);
+                        const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
                         float tr, ab;
-                        absorb_transmit(kb * ds, ab, tr);
+                        absorb_transmit(kb * ds[j], ab, tr);
                         const float a = ph[b] * ab;
-                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds;
+                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds[j];
                         ph[b] *= tr;
                         v[0] += a;
-                        v[1] = fmaf(sig[b], phin, v[1]);
-                        v[2] = fmaf(sige[b], phin, v[2]);
+                        v[1] = fmaf(S.sig[b], phin, v[1]);
+                        v[2] = fmaf(S.sige[b], phin, v[2]);
                     }
-                    key = (int)gc;
-                    last = gc; lastk = k;
-                    ++nseg;
-                    if (!more) live = false;
-                    else if (walk_outside(w, nx, ny, nz)) { esc = true; live = false; }
+                    last = key[j];
+                    lastk = kc[j];
                 }
-                if (__ballot_sync(FULL, key >= 0) == 0u) break;
                 if (AGG == 0) {
-                    if (key >= 0) red_add_v4(A.cells.dep + key, v[0], v[1], v[2], v[3]);
-                } else if (AGG == 1) {
-                    const unsigned peers = __match_any_sync(FULL, key);
-                    if (__any_sync(FULL, key >= 0 && __popc(peers) > 1)) peer_sum<4>(peers, v);
-                    if (key >= 0 && (peers & ((1u << lane) - 1u)) == 0u)
-                        red_add_v4(A.cells.dep + key, v[0], v[1], v[2], v[3]);
+                    if (key[j] >= 0) red_add_v4(A.cells.dep + key[j], v[0], v[1], v[2], v[3]);
                 } else {
-                    const bool head = run_sum<4>(key, v);
-                    if (key >= 0 && head) red_add_v4(A.cells.dep + key, v[0], v[1], v[2], v[3]);
+                    if (__ballot_sync(FULL, key[j] >= 0) == 0u) break;
+                    if (AGG == 1) {
+                        const unsigned peers = __match_any_sync(FULL, key[j]);
+                        if (__any_sync(FULL, key[j] >= 0 && __popc(peers) > 1)) peer_sum<4>(peers, v);
+                        if (key[j] >= 0 && (peers & ((1u << lane) - 1u)) == 0u)
+                            red_add_v4(A.cells.dep + key[j], v[0], v[1], v[2], v[3]);
+                    } else {
+                        const bool head = run_sum<4>(key[j], v);
+                        if (key[j] >= 0 && head) red_add_v4(A.cells.dep + key[j], v[0], v[1], v[2], v[3]);
+                    }
                 }
-            }
-            if (live) {  // more than four segments: impossible for |d| <= 2^21
-                atomicOr(&C->err, 4);
-                live = false;
             }
             float s_end = 0.0f;
 #pragma unroll
@@ -251,22 +284,22 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             int nout = 0, m = 0;
             const int lev = (int)(pl >> LEVEL_SHIFT);
             if (valid && !esc) {
-                const float thr = S->eps_term * A.em.n0[e] * pow2_neg(2 * (lev - S->l_src));
+                const float thr = S.eps * A.em.n0[e] * pow2_neg(2 * (lev - S.l_src));
                 if (s_end < thr) {
                     // termination: the ray's last photons stay in its last cell
                     float g = 0.f, h = 0.f;
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
-                        const float kb = fmaf(lastk.x, sig[b], lastk.y);
+                        const float kb = fmaf(lastk.x, S.sig[b], lastk.y);
                         if (kb > 0.0f) {
                             const float q = __fdividef(ph[b], kb);
-                            g = fmaf(sig[b], q, g);
-                            h = fmaf(sige[b], q, h);
+                            g = fmaf(S.sig[b], q, g);
+                            h = fmaf(S.sige[b], q, h);
                         }
                     }
                     red_add_v4(A.cells.dep + last, s_end, g, h, 0.0f);
                 } else {
-                    while (lev + m < S->l_max && age + 1 >= S->K[lev + m]) ++m;
+                    while (lev + m < S.l_max && age + 1 >= S.K[lev + m]) ++m;
                     nout = 1 << (2 * m);
                 }
             }
@@ -292,9 +325,9 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     atomicAdd(dst + 0, fixed32(v[0]));
                     atomicAdd(dst + 1, fixed32(v[1]));
                     atomicAdd(dst + 2, fixed32(v[2]));
-                    atomicAdd(dst + 3, (unsigned long long)(unsigned)__float2uint_rn(v[3]));
-                    atomicAdd(dst + 4, (unsigned long long)(unsigned)__float2uint_rn(v[4]));
-                    atomicAdd(dst + 5, (unsigned long long)(unsigned)__float2uint_rn(v[5]));
+                    atomicAdd(dst + 3, (unsigned long long)__float2uint_rn(v[3]));
+                    atomicAdd(dst + 4, (unsigned long long)__float2uint_rn(v[4]));
+                    atomicAdd(dst + 5, (unsigned long long)__float2uint_rn(v[5]));
                 }
             }
             // compacted output
@@ -393,39 +426,42 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                 const double nH = A.cells.nH[g];
                 const double y0 = A.cells.y[g];
                 const float T0 = A.cells.T[g];
-                const double alpha = S.rates ? (double)alphaB_f(T0) : S.alpha_const;
-                const double Cc = S.rates ? (double)collion_f(T0) : 0.0;
+                const float dtf = (float)S.dt;
+                const float alpha = S.rates ? alphaB_f(T0) : (float)S.alpha_const;
+                const float Cc = S.rates ? collion_f(T0) : 0.0f;
                 // Eq. 7-10 for the neutral fraction y = 1 - x with n_e
                 // re-evaluated from <x>.  With b = alpha n_e, r = dt (Gamma + C n_e
                 // + alpha n_e), g = (1 - e^-r)/r and h = (1 - g)/r:
                 //   y(dt) = y0 e^-r + b dt g,   <y> = y0 g + b dt h,
                 // the same solution as y_eq + (y0 - y_eq) e^-r and its time
                 // average, written with positive terms only and no division.
+                const double dtG = S.dt * G;
+                const double cad = (double)((Cc + alpha) * dtf);
+                const double adt = (double)(alpha * dtf);
                 double yb = y0, y1 = y0;
                 for (int it = 0; it < S.chem_iters; ++it) {
-                    const double ne = nH * (1.0 - yb);
-                    const double bdt = alpha * ne * S.dt;
-                    const double r = S.dt * G + (Cc + alpha) * ne * S.dt;
-                    float ef, g, h;
-                    relax_factors((float)r, ef, g, h);
-                    y1 = y0 * (double)ef + bdt * (double)g;
-                    const double ybn = y0 * (double)g + bdt * (double)h;
-                    const bool conv = fabs(ybn - yb) <= 1e-9 * (1.0 - ybn) + 1e-300;
+                    const double ne = fma(-nH, yb, nH);
+                    const double r = fma(cad, ne, dtG);
+                    const double bdt = adt * ne;
+                    float ef, gf, hf;
+                    relax_factors((float)r, ef, gf, hf);
+                    y1 = fma(y0, (double)ef, bdt * (double)gf);
+                    const double ybn = fma(y0, (double)gf, bdt * (double)hf);
+                    const float dy = (float)(ybn - yb);
                     yb = ybn;
-                    if (conv) break;
+                    if (fabsf(dy) <= 1e-9f * (1.0f - (float)ybn)) break;
                 }
-                const double x1 = 1.0 - y1;
                 float T = T0;
                 if (!S.isothermal) {
                     // Eq. 12 with static density: particle-number term, then
                     // sub-stepped heating minus cooling (per n_H^2)
-                    const float x0 = (float)(1.0 - y0), xb = (float)(1.0 - yb);
-                    T = T0 * (1.0f + x0) / (1.0f + (float)x1);
+                    const float x0 = (float)(1.0 - y0), x1 = (float)(1.0 - y1), xb = (float)(1.0 - yb);
+                    T = T0 * (1.0f + x0) / (1.0f + x1);
                     const float nHf = (float)nH;
-                    const float heat = (float)((double)d.z * S.gscale * 1.602176634e-12 * yb / nH);
+                    const float heat = d.z * (float)S.hscale * (float)yb / nHf;
                     const float pref = 2.0f * nHf / (3.0f * KB_F * (1.0f + xb));
                     const float cc = S.compton_c / nHf;
-                    float left = (float)S.dt;
+                    float left = dtf;
                     for (int k = 0; k < 1000 && left > 0.0f; ++k) {
                         const float lam = cooling_f(T, xb, 1.0f - xb, xb, cc, S.Tcmb);
                         const float dTdt = pref * (heat - lam);
@@ -438,7 +474,7 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                 A.cells.y[g] = y1;
                 A.cells.T[g] = T;
                 A.cells.gamma[g] = (float)G;
-                A.cells.kap[g] = cell_kappa(S, nH, y1, x1, G);
+                A.cells.kap[g] = cell_kappa(S, nH, y1, (float)G);
             }
         }
         const unsigned peers = __match_any_sync(FULL, sim);
@@ -550,7 +586,7 @@ cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st) {
     k_emit<<<blocks, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
-// Kernel variants: every bin count with the default (AGG 1, 3 blocks/SM);
+// Kernel variants: every bin count with the default (AGG 0, 2 blocks/SM);
 // the bin counts of the standard spectra (1, 3, 4) with every aggregation
 // and register budget, for the autotuner.
 using MarchFn = void (*)(MarchArgs);
@@ -572,13 +608,13 @@ static MarchFn march_fn(int nb, int agg, int minb) {
     FRT_V(3)
     FRT_V(4)
 #undef FRT_V
-    if (agg != 1 || minb != 3) return nullptr;
+    if (agg != 0 || minb != 2) return nullptr;
     switch (nb) {
-        case 2: return k_march<2, 1, 3>;
-        case 5: return k_march<5, 1, 3>;
-        case 6: return k_march<6, 1, 3>;
-        case 7: return k_march<7, 1, 3>;
-        case 8: return k_march<8, 1, 3>;
+        case 2: return k_march<2, 0, 2>;
+        case 5: return k_march<5, 0, 2>;
+        case 6: return k_march<6, 0, 2>;
+        case 7: return k_march<7, 0, 2>;
+        case 8: return k_march<8, 0, 2>;
         default: return nullptr;
     }
 }
@@ -586,16 +622,14 @@ bool march_variant_exists(int nb, int agg, int minb) { return march_fn(nb, agg, 
 cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st) {
     MarchFn f = march_fn(nb, agg, minb);
     if (!f) return cudaErrorInvalidValue;
-    size_t sh = (size_t)a.nsims * NACC * sizeof(unsigned long long);
-    f<<<blocks, threads, sh, st>>>(a);
+    f<<<blocks, threads, march_shared_bytes(a.nsims), st>>>(a);
     return cudaGetLastError();
 }
 int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims) {
     MarchFn f = march_fn(nb, agg, minb);
     if (!f) return 0;
     int n = 0;
-    size_t sh = (size_t)nsims * NACC * sizeof(unsigned long long);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, sh);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, march_shared_bytes(nsims));
     return n;
 }
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st) {
