@@ -589,10 +589,11 @@ extern "C" flexrt_status flexrt_get_rays(flexrt_ctx *c, int64_t cap, int32_t *le
     CK(c, cudaStreamSynchronize(c->st));
     Ctl hc;
     CK(c, cudaMemcpy(&hc, c->ctl, sizeof(hc), cudaMemcpyDeviceToHost));
-    long long cnt = hc.cnt[hc.par];
-    *n = cnt;
-    long long m = std::min<long long>(cnt, cap);
-    if (m == 0) return FLEXRT_OK;
+    SimAcc a;
+    CK(c, cudaMemcpy(&a, c->acc, sizeof(a), cudaMemcpyDeviceToHost));
+    *n = (int64_t)a.rays_live;
+    const long long m = hc.cnt[hc.par];  // queue slots, live or unused
+    if (m == 0 || cap == 0) return FLEXRT_OK;
     const Queue &q = c->q[hc.par];
     std::vector<uint32_t> pl(m), em(m);
     std::vector<int32_t> bi(m), d(3 * m);
@@ -602,19 +603,19 @@ extern "C" flexrt_status flexrt_get_rays(flexrt_ctx *c, int64_t cap, int32_t *le
     CK(c, cudaMemcpy(d.data(), q.dx, m * 4, cudaMemcpyDeviceToHost));
     CK(c, cudaMemcpy(d.data() + m, q.dy, m * 4, cudaMemcpyDeviceToHost));
     CK(c, cudaMemcpy(d.data() + 2 * m, q.dz, m * 4, cudaMemcpyDeviceToHost));
-    for (long long i = 0; i < m; ++i) {
-        if (level) level[i] = (int32_t)(pl[i] >> LEVEL_SHIFT);
-        if (pixel) pixel[i] = (int64_t)(pl[i] & PIX_MASK);
-        if (emitter) emitter[i] = (int32_t)em[i];
-        if (birth) birth[i] = bi[i];
-        if (dir) { dir[3 * i] = d[i]; dir[3 * i + 1] = d[m + i]; dir[3 * i + 2] = d[2 * m + i]; }
-    }
-    if (photons) {
-        std::vector<float> ph(m);
-        for (int b = 0; b < c->nb; ++b) {
-            CK(c, cudaMemcpy(ph.data(), q.ph[b], m * 4, cudaMemcpyDeviceToHost));
-            for (long long i = 0; i < m; ++i) photons[(size_t)c->nb * i + b] = (double)ph[i] * c->h.nref;
-        }
+    std::vector<std::vector<float>> ph(photons ? c->nb : 0, std::vector<float>(m));
+    for (int b = 0; b < (int)ph.size(); ++b)
+        CK(c, cudaMemcpy(ph[b].data(), q.ph[b], m * 4, cudaMemcpyDeviceToHost));
+    long long k = 0;  // live rays only: queue slots marked unused are skipped
+    for (long long i = 0; i < m && k < cap; ++i) {
+        if (pl[i] == DEAD_RAY) continue;
+        if (level) level[k] = (int32_t)(pl[i] >> LEVEL_SHIFT);
+        if (pixel) pixel[k] = (int64_t)(pl[i] & PIX_MASK);
+        if (emitter) emitter[k] = (int32_t)em[i];
+        if (birth) birth[k] = bi[i];
+        if (dir) { dir[3 * k] = d[i]; dir[3 * k + 1] = d[m + i]; dir[3 * k + 2] = d[2 * m + i]; }
+        for (int b = 0; b < (int)ph.size(); ++b) photons[(size_t)c->nb * k + b] = (double)ph[b][i] * c->h.nref;
+        ++k;
     }
     return FLEXRT_OK;
 }

@@ -179,22 +179,41 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         const long long n = C->cnt[par] + C->emit_total;
         const long long nr = (n + 31) & ~31LL;
         const long long stride = (long long)gridDim.x * blockDim.x;
+        // warp-private run of output slots [slab, slab + slab_left)
+        unsigned long long slab = 0;
+        int slab_left = 0;
+        // the next ray's words are loaded one iteration ahead
+        uint32_t npl = DEAD_RAY, ne_ = 0;
+        int nbi = 0, ndx = 0, ndy = 0, ndz = 0;
+        float nph[NB];
+        auto load_ray = [&](long long j) {
+            npl = DEAD_RAY;
+            if (j < n) npl = qi.pl[j];
+            if (npl != DEAD_RAY) {
+                ne_ = qi.em[j]; nbi = qi.bi[j];
+                ndx = qi.dx[j]; ndy = qi.dy[j]; ndz = qi.dz[j];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) nph[b] = qi.ph[b][j];
+            } else {
+                ne_ = 0; nbi = 0; ndx = ndy = ndz = 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) nph[b] = 0.0f;
+            }
+        };
+        load_ray(blockIdx.x * (long long)blockDim.x + threadIdx.x);
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += stride) {
-            bool valid = i < n;
-            uint32_t pl = 0, e = 0;
-            int bi = 0, dx = 0, dy = 0, dz = 0, sim = 0;
+            const uint32_t pl = npl, e = ne_;
+            const int bi = nbi, dx = ndx, dy = ndy, dz = ndz;
             float ph[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) ph[b] = nph[b];
+            load_ray(i + stride);
+            bool valid = pl != DEAD_RAY;
+            int sim = 0;
             int4 ec = make_int4(0, 0, 0, 0);
             if (valid) {
-                pl = qi.pl[i]; e = qi.em[i]; bi = qi.bi[i];
-                dx = qi.dx[i]; dy = qi.dy[i]; dz = qi.dz[i];
-#pragma unroll
-                for (int b = 0; b < NB; ++b) ph[b] = qi.ph[b][i];
                 ec = __ldg(&A.em.cell[e]);
                 sim = ec.w;
-            } else {
-#pragma unroll
-                for (int b = 0; b < NB; ++b) ph[b] = 0.0f;
             }
             const MarchSim &S = msim[sim];
             if (!S.active) valid = false;
@@ -284,7 +303,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             int nout = 0, m = 0;
             const int lev = (int)(pl >> LEVEL_SHIFT);
             if (valid && !esc) {
-                const float thr = S.eps * A.em.n0[e] * pow2_neg(2 * (lev - S.l_src));
+                const float thr = S.eps * __ldg(&A.em.n0[e]) * pow2_neg(2 * (lev - S.l_src));
                 if (s_end < thr) {
                     // termination: the ray's last photons stay in its last cell
                     float g = 0.f, h = 0.f;
@@ -330,16 +349,29 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     atomicAdd(dst + 5, (unsigned long long)__float2uint_rn(v[5]));
                 }
             }
-            // compacted output
+            // compacted output into the warp's slab
             const int incl = warp_incl_scan(nout);
             const int tot = __shfl_sync(FULL, incl, 31);
             if (tot > 0) {
-                unsigned long long base = 0;
-                if (lane == 31) base = atomicAdd(out_cnt, (unsigned long long)tot);
-                base = __shfl_sync(FULL, base, 31);
-                if ((long long)base + tot > A.cap) {
-                    if (lane == 0) atomicOr(&C->err, 1);
-                } else if (nout > 0) {
+                bool fits = true;
+                if (tot > slab_left) {
+                    for (int k = lane; k < slab_left; k += 32) qo.pl[slab + k] = DEAD_RAY;
+                    const int want = tot > OUT_SLAB ? tot : OUT_SLAB;
+                    unsigned long long nbase = 0;
+                    if (lane == 0) nbase = atomicAdd(out_cnt, (unsigned long long)want);
+                    nbase = __shfl_sync(FULL, nbase, 0);
+                    if ((long long)(nbase + want) > A.cap) {
+                        if (lane == 0) atomicOr(&C->err, 1);
+                        fits = false;
+                        slab_left = 0;
+                    } else {
+                        slab = nbase;
+                        slab_left = want;
+                    }
+                }
+                const unsigned long long base = slab;
+                if (fits) { slab += tot; slab_left -= tot; }
+                if (fits && nout > 0) {
                     const long long o = (long long)base + incl - nout;
                     if (nout == 1) {
                         qo.pl[o] = pl; qo.em[o] = e; qo.bi[o] = bi;
@@ -371,6 +403,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 }
             }
         }
+        for (int k = lane; k < slab_left; k += 32) qo.pl[slab + k] = DEAD_RAY;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) {

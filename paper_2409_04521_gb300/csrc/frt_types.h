@@ -17,6 +17,8 @@ constexpr int MAXB = 8;                             // frequency bins
 constexpr int MAXL = 13;                            // HEALPix levels 0..12
 constexpr int LEVEL_SHIFT = 28;                     // pixlev = level<<28 | pixel
 constexpr uint32_t PIX_MASK = (1u << LEVEL_SHIFT) - 1u;
+constexpr uint32_t DEAD_RAY = 0xffffffffu;         // unused queue slot (level 15 never occurs)
+constexpr int OUT_SLAB = 512;                       // queue slots a warp reserves at once
 
 // Per-simulation constants and step state.
 struct SimDev {
