@@ -306,7 +306,7 @@ def impl_gpu(args, dist):
             e2e_t += t1 - t0
             s2.close()
             h2d = ncell * 8 + len(prob.source_ndot) * (12 + 8) + 3 * nb * 8
-            d2h = ncell * (8 + 8 + 4 + 4)
+            d2h = ncell * (4 + 8 + 8 + 4 + 4)   # x, y and n_H (for n_HI), T, Gamma
             del f
         e2e = {"value": dist.sum(e2e_segs) / dist.max(e2e_t), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -86,7 +86,7 @@ struct flexrt_ctx {
     const int4 *pixtab = nullptr;
     int ltab = 0;
     int march_blocks = 0, march_threads = 256, chem_blocks = 0;
-    int march_agg = 0, march_minb = 2, sm_count = 1;
+    int march_agg = 0, march_minb = 3, sm_count = 1;
 
     SimDev h{};  // host copy of the simulation constants
     int ecap = 0;
@@ -126,7 +126,7 @@ struct flexrt_ctx {
 static void free_ctx(flexrt_ctx *c) {
     if (!c) return;
     cudaFree(c->ctl); cudaFree(c->sims); cudaFree(c->acc); cudaFree(c->qmem);
-    cudaFree(c->cells.nH); cudaFree(c->cells.y); cudaFree(c->cells.T); cudaFree(c->cells.gamma);
+    cudaFree(c->cells.nH); cudaFree(c->cells.y); cudaFree(c->cells.x); cudaFree(c->cells.T); cudaFree(c->cells.gamma);
     cudaFree(c->cells.kap); cudaFree(c->cells.dep); cudaFree(c->cells.segcnt);
     cudaFree(c->em.cell); cudaFree(c->em.local); cudaFree(c->em.ndot); cudaFree(c->em.n0);
     cudaFree(c->em.ring); cudaFree(c->em.act); cudaFree(c->em.act_off);
@@ -289,6 +289,7 @@ extern "C" flexrt_status flexrt_create(const flexrt_grid *grid, const flexrt_box
     ALLOC(c->acc, 1);
     ALLOC(c->cells.nH, c->ncell);
     ALLOC(c->cells.y, c->ncell);
+    ALLOC(c->cells.x, c->ncell);
     ALLOC(c->cells.T, c->ncell);
     ALLOC(c->cells.gamma, c->ncell);
     ALLOC(c->cells.kap, c->ncell);
@@ -523,18 +524,18 @@ extern "C" flexrt_status flexrt_get_fields(flexrt_ctx *c, flexrt_fields *f) {
     s = FLEXRT_OK;
     const size_t n = (size_t)c->ncell;
     std::vector<double> y;
-    if (f->x_HII || f->n_HI) {
+    std::vector<float> t;
+    if (f->T || f->gamma_HI || f->x_HII) t.resize(n);
+    if (f->n_HI) {
         y.resize(n);
         CK(c, cudaMemcpy(y.data(), c->cells.y, n * sizeof(double), cudaMemcpyDeviceToHost));
-    }
-    if (f->x_HII)
-        for (size_t i = 0; i < n; ++i) f->x_HII[i] = 1.0 - y[i];
-    if (f->n_HI) {
         CK(c, cudaMemcpy(f->n_HI, c->cells.nH, n * sizeof(double), cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < n; ++i) f->n_HI[i] *= y[i];
     }
-    std::vector<float> t;
-    if (f->T || f->gamma_HI) t.resize(n);
+    if (f->x_HII) {
+        CK(c, cudaMemcpy(t.data(), c->cells.x, n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) f->x_HII[i] = t[i];
+    }
     if (f->T) {
         CK(c, cudaMemcpy(t.data(), c->cells.T, n * sizeof(float), cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < n; ++i) f->T[i] = t[i];

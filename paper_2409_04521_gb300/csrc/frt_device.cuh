@@ -377,26 +377,30 @@ __device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float
 constexpr float KB_F = 1.380649e-16f;
 constexpr float T_HI_F = 157807.0f;
 
+// x^p for x > 0 through the hardware log2/exp2 (relative error ~1e-6)
+__device__ __forceinline__ float fpow(float x, float p) { return exp2f(p * __log2f(x)); }
+
 __device__ __forceinline__ float alphaB_f(float T) {
-    float lam = 2.0f * T_HI_F / T;
-    return 2.753e-14f * powf(lam, 1.5f) / powf(1.0f + powf(lam * (1.0f / 2.740f), 0.407f), 2.242f);
+    const float lam = 2.0f * T_HI_F / T;
+    return 2.753e-14f * fpow(lam, 1.5f) / fpow(1.0f + fpow(lam * (1.0f / 2.740f), 0.407f), 2.242f);
 }
 __device__ __forceinline__ float collion_f(float T) {
-    float lam = 2.0f * T_HI_F / T;
-    return 21.11f * powf(T, -1.5f) * expf(-0.5f * lam) * powf(lam, -1.089f) /
-           powf(1.0f + powf(lam * (1.0f / 0.354f), 0.874f), 1.101f);
+    const float lam = 2.0f * T_HI_F / T;
+    if (lam > 180.0f) return 0.0f;                    // exp(-lam/2) below the float range
+    return 21.11f * fpow(T, -1.5f) * __expf(-0.5f * lam) * fpow(lam, -1.089f) /
+           fpow(1.0f + fpow(lam * (1.0f / 0.354f), 0.874f), 1.101f);
 }
-// Lambda in erg s^-1 cm^-3 divided by n_H^2 is not used: densities are small
-// but positive; computed directly in float (values ~1e-30 fit in range).
-__device__ __forceinline__ float cooling_f(float T, float ne, float nHI, float nHII, float compton_c, float Tcmb) {
-    float lam = 2.0f * T_HI_F / T;
-    float rec = 3.435e-30f * T * powf(lam, 1.970f) / powf(1.0f + powf(lam * (1.0f / 2.250f), 0.376f), 3.720f);
-    float cion = 2.1789874e-11f * collion_f(T);      // 13.6 eV in erg
-    float cexc = 7.5e-19f * expf(-118348.0f / T) / (1.0f + sqrtf(T * 1.0e-5f));
-    float lt = log10f(T);
-    float gff = 1.1f + 0.34f * expf(-(5.5f - lt) * (5.5f - lt) * (1.0f / 3.0f));
-    float ff = 1.42e-27f * gff * sqrtf(T);
-    return (rec + ff) * ne * nHII + (cion + cexc) * ne * nHI + compton_c * (T - Tcmb) * ne;
+// net cooling rate per n_H^2 (erg cm^3 s^-1) for electron, HI and HII
+// fractions xe, xHI, xHII; compton_c already divided by n_H
+__device__ __forceinline__ float cooling_f(float T, float xe, float xHI, float xHII, float compton_c, float Tcmb) {
+    const float lam = 2.0f * T_HI_F / T;
+    const float rec = 3.435e-30f * T * fpow(lam, 1.970f) / fpow(1.0f + fpow(lam * (1.0f / 2.250f), 0.376f), 3.720f);
+    const float cion = 2.1789874e-11f * collion_f(T);      // 13.6 eV in erg
+    const float cexc = 7.5e-19f * __expf(-118348.0f / T) / (1.0f + sqrtf(T * 1.0e-5f));
+    const float lt = __log10f(T);
+    const float gff = 1.1f + 0.34f * __expf(-(5.5f - lt) * (5.5f - lt) * (1.0f / 3.0f));
+    const float ff = 1.42e-27f * gff * sqrtf(T);
+    return (rec + ff) * xe * xHII + (cion + cexc) * xe * xHI + compton_c * (T - Tcmb) * xe;
 }
 
 }  // namespace frt

@@ -71,6 +71,7 @@ __global__ void k_init_cells(const SimDev *sims, int sim, Cells c) {
         long long g = S.cell_off + i;
         double y = 1.0 - S.x_init;
         c.y[g] = y;
+        c.x[g] = (float)S.x_init;
         c.T[g] = (float)S.T_init;
         c.gamma[g] = 0.0f;
         c.dep[g] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -455,48 +456,47 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
             if (!err) {
                 a_abs = d.x;
                 const SimDev &S = A.sims[sim];
-                const double G = (double)d.y * S.gscale;            // Eq. 17, 1/s
+                const float Gf = d.y * (float)S.gscale;               // Eq. 17, 1/s
                 const double nH = A.cells.nH[g];
+                const float nHf = (float)nH;
                 const double y0 = A.cells.y[g];
+                const float y0f = (float)y0, x0f = A.cells.x[g];
                 const float T0 = A.cells.T[g];
                 const float dtf = (float)S.dt;
                 const float alpha = S.rates ? alphaB_f(T0) : (float)S.alpha_const;
                 const float Cc = S.rates ? collion_f(T0) : 0.0f;
-                // Eq. 7-10 for the neutral fraction y = 1 - x with n_e
-                // re-evaluated from <x>.  With b = alpha n_e, r = dt (Gamma + C n_e
-                // + alpha n_e), g = (1 - e^-r)/r and h = (1 - g)/r:
-                //   y(dt) = y0 e^-r + b dt g,   <y> = y0 g + b dt h,
-                // the same solution as y_eq + (y0 - y_eq) e^-r and its time
-                // average, written with positive terms only and no division.
-                const double dtG = S.dt * G;
-                const double cad = (double)((Cc + alpha) * dtf);
-                const double adt = (double)(alpha * dtf);
-                double yb = y0, y1 = y0;
+                // Eq. 7-10 with n_e re-evaluated from <x>.  With i = Gamma + C n_e,
+                // b = alpha n_e, r = dt (i + b), e = e^-r, g = (1 - e)/r and
+                // h = (1 - g)/r, the solution x(t) = x_eq + (x0 - x_eq) e^{-t/t_i}
+                // and its time average are, for y = 1 - x,
+                //   x1 = x0 e + g i dt,  y1 = y0 e + g b dt,
+                //   <x> = x0 g + h i dt, <y> = y0 g + h b dt:
+                // sums of positive terms, accurate however small x or y is.
+                float xb = x0f, yb = y0f, ef = 1.0f, gf = 0.0f, hf = 0.0f, idt = 0.0f, bdt = 0.0f;
                 for (int it = 0; it < S.chem_iters; ++it) {
-                    const double ne = fma(-nH, yb, nH);
-                    const double r = fma(cad, ne, dtG);
-                    const double bdt = adt * ne;
-                    float ef, gf, hf;
-                    relax_factors((float)r, ef, gf, hf);
-                    y1 = fma(y0, (double)ef, bdt * (double)gf);
-                    const double ybn = fma(y0, (double)gf, bdt * (double)hf);
-                    const float dy = (float)(ybn - yb);
-                    yb = ybn;
-                    if (fabsf(dy) <= 1e-9f * (1.0f - (float)ybn)) break;
+                    const float ne = nHf * xb;
+                    idt = (Gf + Cc * ne) * dtf;
+                    bdt = alpha * ne * dtf;
+                    relax_factors(idt + bdt, ef, gf, hf);
+                    const float xbn = fmaf(x0f, gf, hf * idt);
+                    yb = fmaf(y0f, gf, hf * bdt);
+                    const bool conv = fabsf(xbn - xb) <= 1e-7f * xbn;
+                    xb = xbn;
+                    if (conv) break;
                 }
+                const float x1 = fmaf(x0f, ef, gf * idt);
+                const double y1 = fma(y0, (double)ef, (double)(gf * bdt));   // neutral fraction kept in FP64
                 float T = T0;
                 if (!S.isothermal) {
                     // Eq. 12 with static density: particle-number term, then
                     // sub-stepped heating minus cooling (per n_H^2)
-                    const float x0 = (float)(1.0 - y0), x1 = (float)(1.0 - y1), xb = (float)(1.0 - yb);
-                    T = T0 * (1.0f + x0) / (1.0f + x1);
-                    const float nHf = (float)nH;
-                    const float heat = d.z * (float)S.hscale * (float)yb / nHf;
+                    T = T0 * (1.0f + x0f) / (1.0f + x1);
+                    const float heat = d.z * (float)S.hscale * yb / nHf;
                     const float pref = 2.0f * nHf / (3.0f * KB_F * (1.0f + xb));
                     const float cc = S.compton_c / nHf;
                     float left = dtf;
                     for (int k = 0; k < 1000 && left > 0.0f; ++k) {
-                        const float lam = cooling_f(T, xb, 1.0f - xb, xb, cc, S.Tcmb);
+                        const float lam = cooling_f(T, xb, yb, xb, cc, S.Tcmb);
                         const float dTdt = pref * (heat - lam);
                         float h = left;
                         if (k < 999 && dTdt != 0.0f) h = fminf(h, 0.05f * T / fabsf(dTdt));
@@ -505,9 +505,10 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                     }
                 }
                 A.cells.y[g] = y1;
+                A.cells.x[g] = x1;
                 A.cells.T[g] = T;
-                A.cells.gamma[g] = (float)G;
-                A.cells.kap[g] = cell_kappa(S, nH, y1, (float)G);
+                A.cells.gamma[g] = Gf;
+                A.cells.kap[g] = cell_kappa(S, nH, y1, Gf);
             }
         }
         const unsigned peers = __match_any_sync(FULL, sim);

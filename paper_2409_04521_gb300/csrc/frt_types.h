@@ -86,6 +86,7 @@ struct Queue {
 struct Cells {
     double *nH;              // cm^-3 physical
     double *y;               // neutral fraction x_HI
+    float *x;                // ionised fraction x_HII (kept separately: accurate when small)
     float *T;                // K
     float *gamma;            // Gamma_HI of the last step, 1/s
     float2 *kap;             // (tau per cell at sigma_ref from HI, sub-grid tau per cell)
