@@ -176,6 +176,8 @@ flexrt_status flexrt_get_kernel_times(flexrt_ctx *ctx, double ms[3], int64_t lau
  * (0 = occupancy limit).  FLEXRT_E_INVALID if the variant is not built. */
 flexrt_status flexrt_set_launch(flexrt_ctx *ctx, int32_t agg, int32_t minb, int32_t blocks_per_sm);
 
+/* Message of the context's last failure; with ctx == NULL, of the last failed
+ * call without a context (probes) on this host thread. */
 const char *flexrt_last_error(const flexrt_ctx *ctx);
 void flexrt_destroy(flexrt_ctx *ctx);
 
@@ -203,6 +205,28 @@ flexrt_status flexrt_probe_direction(int32_t level, int64_t p0, int64_t n,
 flexrt_status flexrt_probe_traverse(int64_t n, const int64_t *p0, const int32_t *d,
                                     const flexrt_grid *g, int32_t *cells, float *ds,
                                     int32_t *nseg, int32_t *escaped);
+
+/* Largest batch of flexrt_probe_traverse_static, in rays. */
+#define FLEXRT_STATIC_MAX_RAYS 32768
+
+/* flexrt_probe_traverse without any device allocation.  The paper has no
+ * counterpart: this is a deployment facility.  It is for callers that must
+ * not call cudaMalloc/cudaFree: programs whose device memory is owned by
+ * another allocator that has reserved the device (a framework's caching
+ * allocator, a fixed memory budget), and latency-sensitive loops that cannot
+ * take the implicit device synchronisation of cudaFree.
+ * Same arguments, results and kernel as flexrt_probe_traverse.  Its device
+ * staging is one fixed array inside the library of about 3.5 MB
+ * (FLEXRT_STATIC_MAX_RAYS rays), present on every GPU that loads the library
+ * until the process exits.  n > FLEXRT_STATIC_MAX_RAYS returns
+ * FLEXRT_E_CAPACITY with a message in flexrt_last_error(NULL).  The first call
+ * on each device looks up the array's device address; make that first call
+ * before any stream capture.  Every call reuses the same array: calls that
+ * overlap on the GPU (e.g. from two host threads) race, so serialise them.
+ * Synchronous; runs on the legacy default stream; allocates nothing. */
+flexrt_status flexrt_probe_traverse_static(int64_t n, const int64_t *p0, const int32_t *d,
+                                           const flexrt_grid *g, int32_t *cells, float *ds,
+                                           int32_t *nseg, int32_t *escaped);
 
 #ifdef __cplusplus
 }

@@ -668,8 +668,13 @@ extern "C" flexrt_status flexrt_set_launch(flexrt_ctx *c, int32_t agg, int32_t m
     return FLEXRT_OK;
 }
 
+namespace frt {
+static thread_local std::string g_free_err;
+void set_free_error(const std::string &msg) { g_free_err = msg; }
+}  // namespace frt
+
 extern "C" const char *flexrt_last_error(const flexrt_ctx *c) {
-    return c ? c->err.c_str() : "null context";
+    return c ? c->err.c_str() : frt::g_free_err.c_str();
 }
 
 extern "C" void flexrt_destroy(flexrt_ctx *c) {

@@ -1,5 +1,6 @@
 // frt_launch.h -- kernel argument blocks and launchers (host side).
 #pragma once
+#include <string>
 #include "frt_types.h"
 
 namespace frt {
@@ -37,6 +38,9 @@ struct ChemArgs {
     Cells cells;
     Ranges rg;
 };
+
+// message of the last failed call that has no context (this host thread)
+void set_free_error(const std::string &msg);
 
 cudaError_t launch_pixtab(int4 *tab, int L, cudaStream_t st);
 cudaError_t launch_init_cells(const SimDev *sims, int sim, Cells c, long long ncell, cudaStream_t st);

@@ -97,6 +97,7 @@ def lib():
             L.flexrt_probe_direction.argtypes = [C.c_int32, C.c_int64, C.c_int64, P(C.c_int32), P(C.c_int32)]
             L.flexrt_probe_traverse.argtypes = [C.c_int64, P(C.c_int64), P(C.c_int32), P(Grid), P(C.c_int32),
                                                 P(C.c_float), P(C.c_int32), P(C.c_int32)]
+            L.flexrt_probe_traverse_static.argtypes = L.flexrt_probe_traverse.argtypes
             _lib = L
     return _lib
 
@@ -107,11 +108,8 @@ def _p(a, ct):
 
 def _check(status, ctx=None):
     if status != FLEXRT_OK:
-        msg = ""
-        if ctx:
-            m = lib().flexrt_last_error(ctx)
-            msg = m.decode() if m else ""
-        raise FlexRTError(status, msg)
+        m = lib().flexrt_last_error(ctx)
+        raise FlexRTError(status, m.decode() if m else "")
 
 
 def default_options() -> Options:
@@ -257,7 +255,16 @@ def probe_direction(level: int, p0: int, n: int, Rq) -> np.ndarray:
     return out
 
 
-def probe_traverse(p0, d, grid):
+STATIC_MAX_RAYS = 32768
+
+
+def probe_traverse_static(p0, d, grid):
+    """probe_traverse through the entry point that allocates no device
+    memory (at most STATIC_MAX_RAYS rays per call)."""
+    return probe_traverse(p0, d, grid, _entry="flexrt_probe_traverse_static")
+
+
+def probe_traverse(p0, d, grid, _entry="flexrt_probe_traverse"):
     p0 = np.ascontiguousarray(np.asarray(p0, np.int64).reshape(-1, 3))
     d = np.ascontiguousarray(np.asarray(d, np.int32).reshape(-1, 3))
     n = len(p0)
@@ -266,6 +273,7 @@ def probe_traverse(p0, d, grid):
     nseg = np.zeros(n, np.int32)
     esc = np.zeros(n, np.int32)
     g = Grid(*[int(v) for v in grid])
-    _check(lib().flexrt_probe_traverse(n, _p(p0, C.c_int64), _p(d, C.c_int32), C.byref(g), _p(cells, C.c_int32),
-                                       _p(ds, C.c_float), _p(nseg, C.c_int32), _p(esc, C.c_int32)))
+    fn = getattr(lib(), _entry)
+    _check(fn(n, _p(p0, C.c_int64), _p(d, C.c_int32), C.byref(g), _p(cells, C.c_int32),
+              _p(ds, C.c_float), _p(nseg, C.c_int32), _p(esc, C.c_int32)))
     return cells, ds, nseg, esc.astype(bool)
