@@ -98,16 +98,30 @@ def measured_peak():
         return DEFAULT_PEAK_GBS, "fallback"
 
 
+def kernel_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("frt_kernels.cu", "frt_device.cuh", "frt_types.h"):
+        with open(os.path.join(ROOT, "paper_2409_04521_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def committed_traffic():
-    """DRAM bytes per march launch from the committed ncu summary, if any."""
+    """DRAM bytes per march launch from the committed ncu summary, or None
+    when the kernel sources have changed since those counters were taken."""
     p = os.path.join(ROOT, "profiles", "march_cosmo16_traffic.txt")
     try:
+        vals = {}
         for line in open(p):
-            if line.startswith("bytes_per_launch_scaled"):
-                return float(line.split("=")[1].split()[0])
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                vals[k.strip()] = v.strip().split()[0]
+        if vals.get("kernel_sources_sha1") != kernel_sources_sha1():
+            return None
+        return float(vals["bytes_per_launch_scaled"])
     except Exception:
-        pass
-    return None
+        return None
 
 
 class ClockSampler:
