@@ -206,6 +206,63 @@ flexrt_status flexrt_probe_traverse(int64_t n, const int64_t *p0, const int32_t 
                                     const flexrt_grid *g, int32_t *cells, float *ds,
                                     int32_t *nseg, int32_t *escaped);
 
+/* ----------------------------------------------------------------------- */
+/* Batch: many independent simulations of different sizes advanced by one  */
+/* set of kernel launches per RT step (replayed from a CUDA graph).  Each   */
+/* member follows exactly the single-simulation step above; the batch only  */
+/* shares the launches, the ray queue and the device arenas.  Members can   */
+/* be added and retired between steps (continuous batching).                */
+/* ----------------------------------------------------------------------- */
+typedef struct {
+    int32_t max_sims;        /* simulation slots                               */
+    int32_t max_grid;        /* largest grid edge of any member                */
+    int32_t nbins;           /* frequency bins of the ray layout (members may use fewer) */
+    double n_ray_min;        /* N_min used to size the pixel table (members choose their own) */
+    int64_t ray_capacity;    /* rays per queue, shared by all members; 0 = sized from free memory */
+    int64_t cell_capacity;   /* cells of all members together                  */
+    int32_t emitter_capacity;/* emitters of all members together               */
+    int32_t keep_diagnostics;
+    int32_t use_graph;       /* 1: replay each step from a CUDA graph          */
+    void *cuda_stream;       /* 0 = library-owned stream                       */
+} flexrt_batch_config;
+
+void flexrt_default_batch_config(flexrt_batch_config *c);
+
+/* Allocates every device arena of the batch; later calls allocate nothing. */
+flexrt_status flexrt_batch_create(const flexrt_batch_config *c, flexrt_batch **out);
+
+/* Admit one simulation (same parameters as flexrt_create plus its sources and
+ * step length): host inputs are copied; *slot receives its slot.
+ * FLEXRT_E_CAPACITY when no slot, cells or emitters are free. */
+flexrt_status flexrt_batch_add(flexrt_batch *b, const flexrt_grid *grid, const flexrt_box *box,
+                               const double *n_H, const flexrt_mfp *mfp, const flexrt_spectrum *spectrum,
+                               const flexrt_options *opt, int32_t n_sources, const int32_t *cell_ijk,
+                               const double *ndot, double dt_s, int32_t *slot);
+
+/* Enqueue one RT step of every active member (asynchronous; errors latched
+ * as for flexrt_step). */
+flexrt_status flexrt_batch_step(flexrt_batch *b);
+flexrt_status flexrt_batch_sync(flexrt_batch *b);
+
+/* Remove a member between steps; its cells are reusable at once, its slot
+ * and emitters after the next step. */
+flexrt_status flexrt_batch_retire(flexrt_batch *b, int32_t slot);
+
+/* Per-member read-back, as the single-simulation getters. */
+flexrt_status flexrt_batch_get_fields(flexrt_batch *b, int32_t slot, flexrt_fields *f);
+flexrt_status flexrt_batch_get_budget(flexrt_batch *b, int32_t slot, double out[4]);
+flexrt_status flexrt_batch_get_counts(flexrt_batch *b, int32_t slot, int64_t out[6]);
+flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *level,
+                                    int64_t *pixel, int32_t *emitter, int32_t *birth, int32_t *dir,
+                                    double *photons, int64_t *n);
+
+/* out[0] active members, out[1] free cells, out[2] free emitters,
+ * out[3] ray capacity. */
+flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[4]);
+flexrt_status flexrt_batch_set_launch(flexrt_batch *b, int32_t agg, int32_t minb, int32_t blocks_per_sm);
+const char *flexrt_batch_last_error(const flexrt_batch *b);
+void flexrt_batch_destroy(flexrt_batch *b);
+
 /* Largest batch of flexrt_probe_traverse_static, in rays. */
 #define FLEXRT_STATIC_MAX_RAYS 32768
 

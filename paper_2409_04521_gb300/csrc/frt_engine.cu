@@ -1,0 +1,785 @@
+// frt_engine.cu -- host engine: device arenas, simulation slots, step launch
+// (direct or replayed from a CUDA graph), accounting and read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+
+#include "frt_engine.h"
+
+namespace frt {
+
+namespace {
+
+constexpr double EV_ERG = 1.602176634e-12;
+constexpr double MYR_S = 3.15576e13;
+
+// process-wide fixed-point pixel vector tables, one per device, grown on demand
+struct PixTable {
+    int4 *ptr = nullptr;
+    int level = -1;
+};
+std::mutex g_tab_mu;
+std::map<int, PixTable> g_tabs;
+
+void split_table(double nmin, int32_t *K) {
+    const double f = std::sqrt(3.0 / (M_PI * nmin));
+    for (int l = 0; l < 16; ++l) {
+        long long k = (long long)std::ceil(std::ldexp(f, l));
+        if (k < 1) k = 1;
+        if (k > (1LL << 30)) k = 1LL << 30;
+        K[l] = (int32_t)k;
+    }
+}
+
+int ring_length(int n) { return (int)std::ceil(std::sqrt(3.0) * n) + 4; }
+
+size_t ray_bytes(int nb) { return 6 * sizeof(int32_t) + (size_t)nb * sizeof(float); }
+
+}  // namespace
+
+cudaError_t get_pixtab(int device, int level, cudaStream_t st, const int4 **out) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    PixTable &t = g_tabs[device];
+    if (t.level < level) {
+        int4 *p = nullptr;
+        const size_t bytes = (size_t)(4LL * ((1LL << (2 * (level + 1))) - 1)) * sizeof(int4);
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return e;
+        e = launch_pixtab(p, level, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { cudaFree(p); return e; }
+        if (t.ptr) cudaFree(t.ptr);
+        t.ptr = p;
+        t.level = level;
+    }
+    *out = t.ptr;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+void RangeAllocator::reset(long long capacity) {
+    cap_ = capacity;
+    used_ = 0;
+    free_.clear();
+    if (capacity > 0) free_.push_back({0, capacity});
+}
+long long RangeAllocator::alloc(long long n) {
+    if (n <= 0) return -1;
+    for (size_t i = 0; i < free_.size(); ++i) {
+        if (free_[i].n >= n) {
+            const long long s = free_[i].start;
+            free_[i].start += n;
+            free_[i].n -= n;
+            if (free_[i].n == 0) free_.erase(free_.begin() + (long)i);
+            used_ += n;
+            return s;
+        }
+    }
+    return -1;
+}
+void RangeAllocator::release(long long start, long long n) {
+    if (n <= 0) return;
+    used_ -= n;
+    auto it = std::lower_bound(free_.begin(), free_.end(), start,
+                               [](const Free &f, long long v) { return f.start < v; });
+    it = free_.insert(it, {start, n});
+    // merge with neighbours
+    size_t i = (size_t)(it - free_.begin());
+    if (i + 1 < free_.size() && free_[i].start + free_[i].n == free_[i + 1].start) {
+        free_[i].n += free_[i + 1].n;
+        free_.erase(free_.begin() + (long)i + 1);
+    }
+    if (i > 0 && free_[i - 1].start + free_[i - 1].n == free_[i].start) {
+        free_[i - 1].n += free_[i].n;
+        free_.erase(free_.begin() + (long)i);
+    }
+}
+
+// ---------------------------------------------------------------------------
+flexrt_status Engine::cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return FLEXRT_OK;
+    err_ = std::string(what) + ": " + cudaGetErrorString(e);
+    return FLEXRT_E_CUDA;
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e__ = (call);                         \
+        if (e__ != cudaSuccess) return cuda(e__, #call);  \
+    } while (0)
+
+Engine::~Engine() {
+    if (st_) cudaStreamSynchronize(st_);
+    if (graph_) cudaGraphExecDestroy(graph_);
+    cudaFree(ctl_); cudaFree(sims_); cudaFree(acc_); cudaFree(qmem_);
+    cudaFree(cells_.nH); cudaFree(cells_.y); cudaFree(cells_.x); cudaFree(cells_.T); cudaFree(cells_.gamma);
+    cudaFree(cells_.kap); cudaFree(cells_.dep); cudaFree(cells_.segcnt);
+    cudaFree(em_.cell); cudaFree(em_.local); cudaFree(em_.ndot); cudaFree(em_.n0);
+    cudaFree(em_.ring); cudaFree(em_.act); cudaFree(em_.act_off);
+    cudaFree(rg_.pref); cudaFree(rg_.cell0); cudaFree(rg_.sim);
+    if (h_err_) cudaFreeHost(h_err_);
+    if (h_stage_) cudaFreeHost(h_stage_);
+    if (ev_err_) cudaEventDestroy(ev_err_);
+    if (ev_stage_) cudaEventDestroy(ev_stage_);
+    for (auto e : ev_pool_) cudaEventDestroy(e);
+    for (auto &v : ev_k_)
+        for (auto &p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    if (own_stream_ && st_) cudaStreamDestroy(st_);
+}
+
+flexrt_status Engine::init(const EngineConfig &cfg) {
+    cfg_ = cfg;
+    if (cfg_.nb < 1 || cfg_.nb > MAXB || cfg_.max_sims < 1 || cfg_.max_sims > 1024 || cfg_.cell_capacity < 1 ||
+        cfg_.max_grid < 1 || cfg_.max_grid > 1000)
+        return fail(FLEXRT_E_INVALID, "bad engine configuration");
+    CK(cudaGetDevice(&device_));
+    if (cfg_.stream) st_ = (cudaStream_t)cfg_.stream;
+    else {
+        CK(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+        own_stream_ = true;
+    }
+    em_.ring_w = ring_length(cfg_.max_grid);
+    int32_t K[16];
+    split_table(cfg_.n_ray_min, K);
+    int L = 0;
+    while (L < cfg_.l_max && K[L] <= em_.ring_w) ++L;
+    ltab_ = std::min(L, 11);
+
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    long long cap = cfg_.ray_capacity;
+    if (cap <= 0) cap = (long long)(0.3 * (double)freeb / (2.0 * ray_bytes(cfg_.nb)));
+    cfg_.ray_capacity = cap = std::max(cap, 1024LL);
+
+    // ray queues: one allocation, structure of arrays, two buffers
+    {
+        const size_t a = (size_t)cap * 4, per = ray_bytes(cfg_.nb) * (size_t)cap;
+        char *base = nullptr;
+        if (cudaMalloc(&base, 2 * per + 256) != cudaSuccess) return fail(FLEXRT_E_OOM, "ray queue allocation failed");
+        qmem_ = base;
+        for (int k = 0; k < 2; ++k) {
+            char *p = base + k * per;
+            q_[k].pl = (uint32_t *)p; p += a;
+            q_[k].em = (uint32_t *)p; p += a;
+            q_[k].bi = (int32_t *)p; p += a;
+            q_[k].dx = (int32_t *)p; p += a;
+            q_[k].dy = (int32_t *)p; p += a;
+            q_[k].dz = (int32_t *)p; p += a;
+            for (int b = 0; b < MAXB; ++b) {
+                q_[k].ph[b] = b < cfg_.nb ? (float *)p : nullptr;
+                if (b < cfg_.nb) p += a;
+            }
+        }
+    }
+    const long long nc = cfg_.cell_capacity;
+    const int ms = cfg_.max_sims;
+#define ALLOC(ptr, n)                                                          \
+    if (cudaMalloc(&(ptr), (size_t)(n) * sizeof(*(ptr))) != cudaSuccess)       \
+        return fail(FLEXRT_E_OOM, "device allocation failed: " #ptr)
+    ALLOC(ctl_, 1);
+    ALLOC(sims_, ms);
+    ALLOC(acc_, ms);
+    ALLOC(cells_.nH, nc);
+    ALLOC(cells_.y, nc);
+    ALLOC(cells_.x, nc);
+    ALLOC(cells_.T, nc);
+    ALLOC(cells_.gamma, nc);
+    ALLOC(cells_.kap, nc);
+    ALLOC(cells_.dep, nc);
+    if (cfg_.keep_diagnostics) ALLOC(cells_.segcnt, nc);
+    ALLOC(rg_.pref, ms + 1);
+    ALLOC(rg_.cell0, ms);
+    ALLOC(rg_.sim, ms);
+#undef ALLOC
+    if (cudaMallocHost(&h_err_, 64) != cudaSuccess) return fail(FLEXRT_E_OOM, "pinned allocation failed");
+    if (cudaMallocHost(&h_stage_, (size_t)(ms + 1) * 4 * sizeof(double)) != cudaSuccess)
+        return fail(FLEXRT_E_OOM, "pinned allocation failed");
+    CK(cudaEventCreateWithFlags(&ev_err_, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_stage_, cudaEventDisableTiming));
+    cell_alloc_.reset(nc);
+    em_cap_ = 0;
+    flexrt_status s = grow_emitters(std::max(cfg_.emitter_capacity, 16));
+    if (s != FLEXRT_OK) return s;
+    em_alloc_.reset(em_cap_);
+    slots_.assign(ms, Slot());
+
+    CK(cudaMemsetAsync(ctl_, 0, sizeof(Ctl), st_));
+    CK(cudaMemsetAsync(sims_, 0, (size_t)ms * sizeof(SimDev), st_));
+    CK(cudaMemsetAsync(acc_, 0, (size_t)ms * sizeof(SimAcc), st_));
+    cudaError_t e = get_pixtab(device_, ltab_, st_, &pixtab_);
+    if (e != cudaSuccess) return cuda(e, "pixel table");
+
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device_);
+    sm_count_ = std::max(sms, 1);
+    if (!march_variant_exists(cfg_.nb, march_agg_, march_minb_)) { march_agg_ = 0; march_minb_ = 2; }
+    const int per_sm = march_max_blocks_per_sm(cfg_.nb, march_agg_, march_minb_, march_threads_, ms);
+    march_blocks_ = sm_count_ * std::max(per_sm, 1);
+    chem_blocks_ = (int)std::max<long long>(1, std::min<long long>((nc + 255) / 256, (long long)sm_count_ * 8));
+    CK(cudaStreamSynchronize(st_));
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::grow_emitters(int need) {
+    if (need <= em_cap_) return FLEXRT_OK;
+    if (em_cap_ > 0 && cfg_.emitter_capacity > 0)
+        return fail(FLEXRT_E_CAPACITY, "emitter table full");
+    const int cap = std::max(need, std::max(16, 2 * em_cap_));
+    Emitters ne{};
+    ne.ring_w = em_.ring_w;
+    if (cudaMalloc(&ne.cell, cap * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&ne.local, cap * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&ne.ndot, cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ne.n0, cap * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&ne.ring, (size_t)cap * ne.ring_w * 3 * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&ne.act, cap * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&ne.act_off, cap * sizeof(long long)) != cudaSuccess) {
+        cudaFree(ne.cell); cudaFree(ne.local); cudaFree(ne.ndot); cudaFree(ne.n0);
+        cudaFree(ne.ring); cudaFree(ne.act); cudaFree(ne.act_off);
+        return fail(FLEXRT_E_OOM, "emitter table allocation failed");
+    }
+    if (em_cap_ > 0) {
+        CK(cudaStreamSynchronize(st_));
+        CK(cudaMemcpy(ne.cell, em_.cell, em_cap_ * sizeof(int4), cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(ne.local, em_.local, em_cap_ * sizeof(int32_t), cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(ne.ndot, em_.ndot, em_cap_ * sizeof(double), cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(ne.n0, em_.n0, em_cap_ * sizeof(float), cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(ne.ring, em_.ring, (size_t)em_cap_ * ne.ring_w * 3 * sizeof(int4), cudaMemcpyDeviceToDevice));
+    }
+    cudaFree(em_.cell); cudaFree(em_.local); cudaFree(em_.ndot); cudaFree(em_.n0);
+    cudaFree(em_.ring); cudaFree(em_.act); cudaFree(em_.act_off);
+    em_ = ne;
+    em_cap_ = cap;
+    emit_blocks_ = std::max(1, std::min((em_cap_ + 127) / 128, 1024));
+    graph_dirty_ = true;
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::make_sim(const flexrt_grid *grid, const flexrt_box *box, const double *n_H,
+                               const flexrt_mfp *mfp, const flexrt_spectrum *sp, const flexrt_options *opt_in,
+                               SimDev &h, std::string &err) {
+    if (!grid || !box || !n_H || !sp) { err = "null argument"; return FLEXRT_E_INVALID; }
+    flexrt_options opt;
+    if (opt_in) opt = *opt_in; else flexrt_default_options(&opt);
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 1000 || grid->ny > 1000 || grid->nz > 1000) {
+        err = "grid must be 1..1000 cells per axis"; return FLEXRT_E_INVALID;
+    }
+    if (sp->nbins < 1 || sp->nbins > FLEXRT_MAX_BINS || !sp->frac || !sp->sigma_cm2 || !sp->eheat_erg) {
+        err = "bad spectrum"; return FLEXRT_E_INVALID;
+    }
+    if (opt.l_src < 0 || opt.l_max < opt.l_src || opt.l_max > FLEXRT_MAX_LEVEL || !(opt.n_ray_min > 0) ||
+        opt.chem_iters < 1 || !(box->box_cm_comoving > 0) || box->redshift <= -1.0) {
+        err = "bad options or box"; return FLEXRT_E_INVALID;
+    }
+    std::memset(&h, 0, sizeof(h));
+    h.nx = grid->nx; h.ny = grid->ny; h.nz = grid->nz; h.nb = sp->nbins;
+    h.ncell = (long long)grid->nx * grid->ny * grid->nz;
+    h.l_src = opt.l_src; h.l_max = opt.l_max;
+    split_table(opt.n_ray_min, h.K);
+    h.active = 1;
+    h.rotate = opt.rotate ? 1 : 0;
+    h.seed = opt.seed;
+    h.eps_term = (float)opt.eps_term;
+    h.sigma_ref = sp->sigma_cm2[0];
+    if (!(h.sigma_ref > 0)) { err = "sigma of bin 0 must be positive"; return FLEXRT_E_INVALID; }
+    for (int b = 0; b < sp->nbins; ++b) {
+        h.sig[b] = (float)(sp->sigma_cm2[b] / h.sigma_ref);
+        h.sige[b] = (float)(sp->sigma_cm2[b] / h.sigma_ref * sp->eheat_erg[b] / EV_ERG);
+        h.frac[b] = (float)sp->frac[b];
+    }
+    h.dx_com = box->box_cm_comoving / grid->nx;
+    h.dx_phys = h.dx_com / (1.0 + box->redshift);
+    h.inv_ncast = 1.0 / (double)(12LL << (2 * opt.l_src));
+    h.z = box->redshift;
+    {
+        const double kB = 1.380649e-16, sT = 6.6524587e-25, a = 7.5657e-15, me = 9.1093837e-28, cl = 2.99792458e10;
+        const double Tc = 2.7255 * (1.0 + box->redshift);
+        h.Tcmb = (float)Tc;
+        h.compton_c = (float)(4.0 * kB * sT * a * Tc * Tc * Tc * Tc / (me * cl));
+    }
+    h.alpha_const = opt.alpha_B_const;
+    h.rates = opt.rates; h.isothermal = opt.isothermal ? 1 : 0; h.chem_iters = opt.chem_iters;
+    flexrt_mfp m{};
+    if (mfp) m = *mfp;
+    h.mfp_mode = m.mode;
+    h.lambda0_c = m.lambda0_cm_comoving; h.delta_exp = m.delta_exp; h.gamma_ref = m.gamma_ref;
+    h.gamma_exp = m.gamma_exp; h.gamma_floor = m.gamma_floor; h.xion_thr = m.xion_threshold;
+    if ((m.mode == 1 || m.mode == 2) && !(m.lambda0_cm_comoving > 0)) { err = "lambda0 must be positive"; return FLEXRT_E_INVALID; }
+    if (m.mode == 2 && !(m.gamma_ref > 0)) { err = "gamma_ref must be positive"; return FLEXRT_E_INVALID; }
+    double mean = m.nH_mean;
+    if (!(mean > 0)) {
+        double s = 0.0;
+        for (long long i = 0; i < h.ncell; ++i) s += n_H[i];
+        mean = s / (double)h.ncell;
+    }
+    h.nH_mean = mean;
+    h.ksc = h.sigma_ref * h.dx_phys;
+    h.inv_nH_mean = mean > 0 ? 1.0 / mean : 0.0;
+    h.inv_gamma_ref = m.gamma_ref > 0 ? 1.0 / m.gamma_ref : 0.0;
+    h.y_thr = 1.0 - m.xion_threshold;
+    h.kap_sub0 = m.lambda0_cm_comoving > 0 ? (float)(h.dx_com / m.lambda0_cm_comoving) : 0.0f;
+    h.x_init = opt.x_init; h.T_init = opt.T_init;
+    h.nref = 1.0;
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::add_sim(const SimDev &proto, const double *n_H, int *slot_out) {
+    const int ms = (int)slots_.size();
+    int s = -1;
+    for (int i = 0; i < ms; ++i)
+        if (!slots_[i].used) { s = i; break; }
+    if (s < 0) return fail(FLEXRT_E_CAPACITY, "no free simulation slot");
+    const int edge = std::max(proto.nx, std::max(proto.ny, proto.nz));
+    if (edge > cfg_.max_grid) return fail(FLEXRT_E_INVALID, "grid larger than the engine's max_grid");
+    if (proto.nb > cfg_.nb) return fail(FLEXRT_E_INVALID, "more frequency bins than the engine's layout");
+    const long long c0 = cell_alloc_.alloc(proto.ncell);
+    if (c0 < 0) return fail(FLEXRT_E_CAPACITY, "cell arena full");
+    CK(cudaStreamSynchronize(st_));
+    Slot &sl = slots_[s];
+    sl = Slot();
+    sl.used = true;
+    sl.active = true;
+    sl.h = proto;
+    sl.h.cell_off = c0;
+    sl.h.ring_w = em_.ring_w;
+    sl.h.step = 0;
+    sl.h.active = 1;
+    sl.cell0 = c0;
+    CK(cudaMemcpy(sims_ + s, &sl.h, sizeof(SimDev), cudaMemcpyHostToDevice));
+    CK(cudaMemset(acc_ + s, 0, sizeof(SimAcc)));
+    CK(cudaMemcpy(cells_.nH + c0, n_H, (size_t)proto.ncell * sizeof(double), cudaMemcpyHostToDevice));
+    CK(launch_init_cells(sims_, s, cells_, proto.ncell, st_));
+    CK(cudaStreamSynchronize(st_));
+    flexrt_status r = upload_lists();
+    if (r != FLEXRT_OK) return r;
+    *slot_out = s;
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::add_sources(int s, int32_t n, const int32_t *ijk, const double *ndot) {
+    if (s < 0 || s >= (int)slots_.size() || !slots_[s].active) return fail(FLEXRT_E_INVALID, "bad slot");
+    if (n < 0 || (n > 0 && (!ijk || !ndot))) return fail(FLEXRT_E_INVALID, "bad source arrays");
+    Slot &sl = slots_[s];
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t *q = ijk + 3 * i;
+        if (q[0] < 0 || q[0] >= sl.h.nx || q[1] < 0 || q[1] >= sl.h.ny || q[2] < 0 || q[2] >= sl.h.nz ||
+            !(ndot[i] >= 0.0))
+            return fail(FLEXRT_E_INVALID, "source outside the grid or negative rate");
+    }
+    std::vector<int4> cell = sl.ecell;
+    std::vector<double> rate = sl.endot;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t *q = ijk + 3 * i;
+        size_t f = cell.size();
+        for (size_t k = 0; k < cell.size(); ++k)
+            if (cell[k].x == q[0] && cell[k].y == q[1] && cell[k].z == q[2]) { f = k; break; }
+        if (f < cell.size()) rate[f] += ndot[i];
+        else { cell.push_back(make_int4(q[0], q[1], q[2], s)); rate.push_back(ndot[i]); }
+    }
+    const int ne = (int)cell.size();
+    CK(cudaStreamSynchronize(st_));
+    if (ne > sl.em_n) {
+        if (sl.em0 >= 0 && sl.em_n > 0) {
+            // grow in place: only the single-simulation engine owns the whole table
+            if (slots_.size() != 1 || sl.em0 != 0) return fail(FLEXRT_E_STATE, "sources of a batch member are fixed");
+            flexrt_status r = grow_emitters(ne);
+            if (r != FLEXRT_OK) return r;
+            em_alloc_.reset(em_cap_);
+            em_alloc_.alloc(ne);
+        } else {
+            if (slots_.size() == 1) {
+                flexrt_status r = grow_emitters(ne);
+                if (r != FLEXRT_OK) return r;
+                em_alloc_.reset(em_cap_);
+            }
+            const long long e0 = em_alloc_.alloc(ne);
+            if (e0 < 0) return fail(FLEXRT_E_CAPACITY, "emitter table full");
+            sl.em0 = e0;
+        }
+        sl.em_n = ne;
+    }
+    sl.ecell = cell;
+    sl.endot = rate;
+    if (!sl.nref_set && ne > 0) {
+        const double mx = *std::max_element(rate.begin(), rate.end());
+        if (mx > 0) {
+            sl.h.nref = std::ldexp(1.0, (int)std::lround(std::log2(mx * MYR_S * sl.h.inv_ncast)));
+            sl.nref_set = true;
+            CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, nref), &sl.h.nref, sizeof(double),
+                          cudaMemcpyHostToDevice));
+            if (sl.h.dt > 0) {
+                const double dt = sl.h.dt;
+                sl.h.dt = 0.0;
+                flexrt_status r = set_dt(s, dt);
+                if (r != FLEXRT_OK) return r;
+                CK(cudaStreamSynchronize(st_));
+            }
+        }
+    }
+    std::vector<int32_t> local(ne);
+    for (int k = 0; k < ne; ++k) local[k] = k;
+    CK(cudaMemcpy(em_.cell + sl.em0, cell.data(), ne * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(em_.ndot + sl.em0, rate.data(), ne * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(em_.local + sl.em0, local.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return upload_lists();
+}
+
+flexrt_status Engine::upload_lists() {
+    std::vector<int32_t> act;
+    std::vector<long long> off;
+    std::vector<long long> pref(1, 0), cell0;
+    std::vector<int32_t> sim;
+    long long run = 0;
+    for (int s = 0; s < (int)slots_.size(); ++s) {
+        const Slot &sl = slots_[s];
+        if (!sl.active) continue;
+        const long long ncast = 12LL << (2 * sl.h.l_src);
+        for (int k = 0; k < sl.em_n; ++k) {
+            act.push_back((int32_t)(sl.em0 + k));
+            off.push_back(run);
+            run += ncast;
+        }
+        pref.push_back(pref.back() + sl.h.ncell);
+        cell0.push_back(sl.cell0);
+        sim.push_back(s);
+    }
+    if ((long long)act.size() > em_cap_) return fail(FLEXRT_E_CAPACITY, "emitter list");
+    CK(cudaStreamSynchronize(st_));
+    if (!act.empty()) {
+        CK(cudaMemcpy(em_.act, act.data(), act.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(em_.act_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    }
+    if (!sim.empty()) {
+        CK(cudaMemcpy(rg_.pref, pref.data(), pref.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(rg_.cell0, cell0.data(), cell0.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(rg_.sim, sim.data(), sim.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    const long long et = run;
+    const int32_t na = (int32_t)act.size(), nr = (int32_t)sim.size();
+    const long long nca = pref.back();
+    CK(cudaMemcpy((char *)ctl_ + offsetof(Ctl, emit_total), &et, sizeof(et), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((char *)ctl_ + offsetof(Ctl, n_act_emit), &na, sizeof(na), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((char *)ctl_ + offsetof(Ctl, n_ranges), &nr, sizeof(nr), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((char *)ctl_ + offsetof(Ctl, ncell_active), &nca, sizeof(nca), cudaMemcpyHostToDevice));
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::set_dt(int s, double dt) {
+    if (s < 0 || s >= (int)slots_.size() || !slots_[s].used) return fail(FLEXRT_E_INVALID, "bad slot");
+    if (!(dt > 0.0)) return fail(FLEXRT_E_INVALID, "dt must be positive");
+    SimDev &h = slots_[s].h;
+    if (dt == h.dt) return FLEXRT_OK;
+    CK(cudaEventSynchronize(ev_stage_));  // the staging slot's previous upload has been consumed
+    h.dt = dt;
+    h.gscale = h.nref * h.sigma_ref / (h.dx_phys * h.dx_phys * dt);
+    h.hscale = h.gscale * EV_ERG;
+    double *st = h_stage_ + 4 * s;
+    st[0] = h.dt; st[1] = h.gscale; st[2] = h.hscale;
+    static_assert(offsetof(SimDev, gscale) == offsetof(SimDev, dt) + sizeof(double), "dt/gscale layout");
+    static_assert(offsetof(SimDev, hscale) == offsetof(SimDev, dt) + 2 * sizeof(double), "dt/hscale layout");
+    CK(cudaMemcpyAsync((char *)(sims_ + s) + offsetof(SimDev, dt), st, 3 * sizeof(double), cudaMemcpyHostToDevice,
+                       st_));
+    CK(cudaEventRecord(ev_stage_, st_));
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::poll(bool wait) {
+    if (latched_ != FLEXRT_OK) return latched_;
+    if (!err_pending_) return FLEXRT_OK;
+    if (wait) {
+        cudaError_t e = cudaEventSynchronize(ev_err_);
+        if (e != cudaSuccess) return cuda(e, "step");
+    } else if (cudaEventQuery(ev_err_) != cudaSuccess) {
+        return FLEXRT_OK;
+    }
+    err_pending_ = false;
+    const int32_t v = *h_err_;
+    if (v) {
+        latched_ = FLEXRT_E_CAPACITY;
+        if (v & 1) err_ = "ray queue capacity exceeded; state kept at the last complete step";
+        else if (v & 2) err_ = "ray older than the rotation ring (internal bound)";
+        else err_ = "ray crossed more than four cells in one step (internal bound)";
+    }
+    return latched_;
+}
+
+static cudaEvent_t take_event(std::vector<cudaEvent_t> &pool) {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+flexrt_status Engine::launch_step() {
+    const int ms = (int)slots_.size();
+    EmitArgs ea{ctl_, sims_, acc_, {q_[0], q_[1]}, cfg_.ray_capacity, em_, pixtab_, ltab_, cfg_.nb};
+    MarchArgs ma{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, cfg_.ray_capacity, em_, cells_, pixtab_, ltab_};
+    ChemArgs ca{ctl_, sims_, acc_, ms, cells_, rg_};
+    const bool prof = profiling_ && !cfg_.use_graph;
+    cudaEvent_t e0 = nullptr;
+    auto tic = [&]() {
+        if (prof) { e0 = take_event(ev_pool_); cudaEventRecord(e0, st_); }
+    };
+    auto toc = [&](int k) {
+        if (prof) { cudaEvent_t e1 = take_event(ev_pool_); cudaEventRecord(e1, st_); ev_k_[k].push_back({e0, e1}); }
+    };
+    tic();
+    CK(launch_emit(ea, emit_blocks_, st_));
+    toc(0);
+    tic();
+    CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_));
+    toc(1);
+    tic();
+    CK(launch_chem(ca, chem_blocks_, st_));
+    toc(2);
+    CK(launch_end(ctl_, sims_, acc_, ms, st_));
+    return FLEXRT_OK;
+}
+
+void Engine::free_retired() {
+    for (auto &sl : slots_) {
+        if (sl.used && !sl.active && sl.release_after >= 0 && steps_taken_ > sl.release_after) {
+            if (sl.em0 >= 0 && sl.em_n > 0) em_alloc_.release(sl.em0, sl.em_n);
+            sl = Slot();
+        }
+    }
+}
+
+flexrt_status Engine::step() {
+    flexrt_status s = poll(false);
+    if (s != FLEXRT_OK) return s;
+    free_retired();
+    if (cfg_.use_graph) {
+        if (graph_dirty_) {
+            if (graph_) { cudaGraphExecDestroy(graph_); graph_ = nullptr; }
+            CK(cudaStreamSynchronize(st_));
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+            flexrt_status r = launch_step();
+            cudaError_t ee = cudaStreamEndCapture(st_, &g);
+            if (r != FLEXRT_OK) { if (g) cudaGraphDestroy(g); return r; }
+            if (ee != cudaSuccess) return cuda(ee, "graph capture");
+            ee = cudaGraphInstantiate(&graph_, g, 0);
+            cudaGraphDestroy(g);
+            if (ee != cudaSuccess) return cuda(ee, "graph instantiate");
+            graph_dirty_ = false;
+        }
+        CK(cudaGraphLaunch(graph_, st_));
+    } else {
+        flexrt_status r = launch_step();
+        if (r != FLEXRT_OK) return r;
+    }
+    CK(cudaMemcpyAsync(h_err_, (char *)ctl_ + offsetof(Ctl, err), sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    CK(cudaEventRecord(ev_err_, st_));
+    err_pending_ = true;
+    ++steps_taken_;
+    for (auto &sl : slots_)
+        if (sl.active) ++sl.h.step;
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::sync() {
+    CK(cudaStreamSynchronize(st_));
+    return poll(true);
+}
+
+flexrt_status Engine::retire(int s) {
+    if (s < 0 || s >= (int)slots_.size() || !slots_[s].active) return fail(FLEXRT_E_INVALID, "bad slot");
+    CK(cudaStreamSynchronize(st_));
+    Slot &sl = slots_[s];
+    sl.active = false;
+    sl.h.active = 0;
+    const int32_t zero = 0;
+    CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, active), &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    cell_alloc_.release(sl.cell0, sl.h.ncell);
+    sl.release_after = steps_taken_;   // its rays are dropped by the next step's march
+    return upload_lists();
+}
+
+flexrt_status Engine::reset_all() {
+    CK(cudaStreamSynchronize(st_));
+    latched_ = FLEXRT_OK;
+    err_pending_ = false;
+    CK(cudaMemset(ctl_, 0, offsetof(Ctl, emit_total)));   // counts, parity, error
+    for (int s = 0; s < (int)slots_.size(); ++s) {
+        Slot &sl = slots_[s];
+        if (!sl.active) continue;
+        sl.h.step = 0;
+        const int32_t zero = 0;
+        CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, step), &zero, sizeof(zero), cudaMemcpyHostToDevice));
+        // keep the monotonic marched-ray counter (last field) for profiling windows
+        CK(cudaMemset(acc_ + s, 0, offsetof(SimAcc, rays_in_total)));
+        CK(launch_init_cells(sims_, s, cells_, sl.h.ncell, st_));
+    }
+    CK(cudaStreamSynchronize(st_));
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::read_acc(int s, SimAcc &a) {
+    CK(cudaStreamSynchronize(st_));
+    CK(cudaMemcpy(&a, acc_ + s, sizeof(a), cudaMemcpyDeviceToHost));
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::fields(int s, flexrt_fields *f) {
+    const Slot *sl = slot(s);
+    if (!sl || !f) return fail(FLEXRT_E_INVALID, "bad slot or fields");
+    CK(cudaStreamSynchronize(st_));
+    poll(true);
+    const size_t n = (size_t)sl->h.ncell;
+    const long long c0 = sl->cell0;
+    std::vector<double> y;
+    std::vector<float> t;
+    if (f->T || f->gamma_HI || f->x_HII) t.resize(n);
+    if (f->n_HI) {
+        y.resize(n);
+        CK(cudaMemcpy(y.data(), cells_.y + c0, n * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(f->n_HI, cells_.nH + c0, n * sizeof(double), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) f->n_HI[i] *= y[i];
+    }
+    if (f->x_HII) {
+        CK(cudaMemcpy(t.data(), cells_.x + c0, n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) f->x_HII[i] = t[i];
+    }
+    if (f->T) {
+        CK(cudaMemcpy(t.data(), cells_.T + c0, n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) f->T[i] = t[i];
+    }
+    if (f->gamma_HI) {
+        CK(cudaMemcpy(t.data(), cells_.gamma + c0, n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) f->gamma_HI[i] = t[i];
+    }
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::budget(int s, double out[4]) {
+    const Slot *sl = slot(s);
+    if (!sl || !out) return fail(FLEXRT_E_INVALID, "bad slot");
+    SimAcc a;
+    flexrt_status r = read_acc(s, a);
+    if (r != FLEXRT_OK) return r;
+    const double k = sl->h.nref;
+    out[0] = a.emitted * k; out[1] = a.absorbed * k; out[2] = a.escaped * k; out[3] = a.in_flight * k;
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::counts(int s, int64_t out[6]) {
+    const Slot *sl = slot(s);
+    if (!sl || !out) return fail(FLEXRT_E_INVALID, "bad slot");
+    SimAcc a;
+    flexrt_status r = read_acc(s, a);
+    if (r != FLEXRT_OK) return r;
+    int32_t step = 0;
+    CK(cudaMemcpy(&step, (char *)(sims_ + s) + offsetof(SimDev, step), sizeof(step), cudaMemcpyDeviceToHost));
+    out[0] = (int64_t)a.rays_live; out[1] = (int64_t)a.seg_last; out[2] = (int64_t)a.seg_total;
+    out[3] = step; out[4] = cfg_.ray_capacity; out[5] = (int64_t)a.rays_in_last;
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::segment_counts(int s, int32_t *out) {
+    const Slot *sl = slot(s);
+    if (!sl || !out) return fail(FLEXRT_E_INVALID, "bad slot");
+    if (!cells_.segcnt) return fail(FLEXRT_E_STATE, "created without keep_diagnostics");
+    CK(cudaStreamSynchronize(st_));
+    CK(cudaMemcpy(out, cells_.segcnt + sl->cell0, (size_t)sl->h.ncell * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::rays(int s, int64_t cap, int32_t *level, int64_t *pixel, int32_t *emitter, int32_t *birth,
+                           int32_t *dir, double *photons, int64_t *n) {
+    const Slot *sl = slot(s);
+    if (!sl || !n || cap < 0) return fail(FLEXRT_E_INVALID, "bad arguments");
+    SimAcc a;
+    flexrt_status r = read_acc(s, a);
+    if (r != FLEXRT_OK) return r;
+    *n = (int64_t)a.rays_live;
+    Ctl hc;
+    CK(cudaMemcpy(&hc, ctl_, sizeof(hc), cudaMemcpyDeviceToHost));
+    const long long m = hc.cnt[hc.par];
+    if (m == 0 || cap == 0) return FLEXRT_OK;
+    const Queue &q = q_[hc.par];
+    std::vector<uint32_t> pl(m), em(m);
+    std::vector<int32_t> bi(m), d(3 * m);
+    CK(cudaMemcpy(pl.data(), q.pl, m * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(em.data(), q.em, m * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(bi.data(), q.bi, m * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(d.data(), q.dx, m * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(d.data() + m, q.dy, m * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(d.data() + 2 * m, q.dz, m * 4, cudaMemcpyDeviceToHost));
+    std::vector<std::vector<float>> ph(photons ? sl->h.nb : 0, std::vector<float>(m));
+    for (int b = 0; b < (int)ph.size(); ++b) CK(cudaMemcpy(ph[b].data(), q.ph[b], m * 4, cudaMemcpyDeviceToHost));
+    long long k = 0;  // this simulation's live rays; unused queue slots are skipped
+    for (long long i = 0; i < m && k < cap; ++i) {
+        if (pl[i] == DEAD_RAY) continue;
+        if ((long long)em[i] < sl->em0 || (long long)em[i] >= sl->em0 + sl->em_n) continue;
+        if (level) level[k] = (int32_t)(pl[i] >> LEVEL_SHIFT);
+        if (pixel) pixel[k] = (int64_t)(pl[i] & PIX_MASK);
+        if (emitter) emitter[k] = (int32_t)(em[i] - sl->em0);
+        if (birth) birth[k] = bi[i];
+        if (dir) { dir[3 * k] = d[i]; dir[3 * k + 1] = d[m + i]; dir[3 * k + 2] = d[2 * m + i]; }
+        for (int b = 0; b < (int)ph.size(); ++b) photons[(size_t)sl->h.nb * k + b] = (double)ph[b][i] * sl->h.nref;
+        ++k;
+    }
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::set_launch(int agg, int minb, int blocks_per_sm) {
+    if (!march_variant_exists(cfg_.nb, agg, minb) || blocks_per_sm < 0 || blocks_per_sm > 32)
+        return fail(FLEXRT_E_INVALID, "march kernel variant not built");
+    const int lim = march_max_blocks_per_sm(cfg_.nb, agg, minb, march_threads_, (int)slots_.size());
+    if (lim < 1) return fail(FLEXRT_E_INVALID, "variant cannot be resident");
+    const int bps = blocks_per_sm == 0 ? lim : std::min(blocks_per_sm, lim);
+    march_agg_ = agg;
+    march_minb_ = minb;
+    march_blocks_ = sm_count_ * bps;
+    graph_dirty_ = true;
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::profile(bool on) {
+    double ms[3];
+    int64_t l[3], r = 0;
+    flexrt_status s = kernel_times(ms, l, &r);
+    profiling_ = on;
+    return s;
+}
+
+flexrt_status Engine::kernel_times(double ms[3], int64_t launches[3], int64_t *rays) {
+    CK(cudaStreamSynchronize(st_));
+    for (int k = 0; k < 3; ++k) {
+        double t = 0.0;
+        for (auto &p : ev_k_[k]) {
+            float x = 0.f;
+            cudaEventElapsedTime(&x, p.first, p.second);
+            t += x;
+            ev_pool_.push_back(p.first);
+            ev_pool_.push_back(p.second);
+        }
+        ms[k] = t;
+        launches[k] = (int64_t)ev_k_[k].size();
+        ev_k_[k].clear();
+    }
+    std::vector<SimAcc> a(slots_.size());
+    CK(cudaMemcpy(a.data(), acc_, a.size() * sizeof(SimAcc), cudaMemcpyDeviceToHost));
+    double tot = 0.0;
+    for (auto &x : a) tot += x.rays_in_total;
+    if (rays) *rays = (int64_t)(tot - rays_at_profile_);
+    rays_at_profile_ = tot;
+    return FLEXRT_OK;
+}
+
+int Engine::active_count() const {
+    int n = 0;
+    for (auto &s : slots_) n += s.active ? 1 : 0;
+    return n;
+}
+
+}  // namespace frt

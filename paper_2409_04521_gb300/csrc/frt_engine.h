@@ -1,0 +1,140 @@
+// frt_engine.h -- host engine shared by the single-simulation context and
+// the batch: device arenas for cells, emitters and the ray queues, slots of
+// simulations, launch configuration, optional CUDA-graph replay of a step.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/flexrt.h"
+#include "frt_launch.h"
+
+namespace frt {
+
+// Process-wide fixed-point pixel-vector table of levels 0..level on `device`.
+cudaError_t get_pixtab(int device, int level, cudaStream_t st, const int4 **out);
+
+// First-fit allocator of [0, capacity) index ranges.
+class RangeAllocator {
+  public:
+    void reset(long long capacity);
+    long long alloc(long long n);          // -1 if no room
+    void release(long long start, long long n);
+    long long capacity() const { return cap_; }
+    long long used() const { return used_; }
+
+  private:
+    struct Free { long long start, n; };
+    std::vector<Free> free_;
+    long long cap_ = 0, used_ = 0;
+};
+
+struct Slot {
+    bool used = false;         // holds a simulation (active or retiring)
+    bool active = false;       // takes part in steps
+    SimDev h{};                // host copy of the constants
+    long long cell0 = 0;
+    std::vector<int4> ecell;   // per emitter of this simulation (x, y, z, slot)
+    std::vector<double> endot;
+    long long em0 = -1;        // first global emitter id of the slot's range
+    int em_n = 0;              // emitters in the range
+    bool nref_set = false;
+    int release_after = -1;    // engine step after which the emitter range is freed
+};
+
+struct EngineConfig {
+    int nb = 1;                // frequency bins of the queue layout
+    int max_sims = 1;
+    long long ray_capacity = 0;
+    long long cell_capacity = 0;
+    int emitter_capacity = 0;  // 0 = grow on demand (single simulation only)
+    int max_grid = 0;          // largest grid edge (rotation ring length)
+    int l_max = FLEXRT_MAX_LEVEL;
+    double n_ray_min = 3.0;
+    bool keep_diagnostics = false;
+    bool use_graph = false;
+    void *stream = nullptr;
+};
+
+class Engine {
+  public:
+    ~Engine();
+    flexrt_status init(const EngineConfig &cfg);
+    // Fill a simulation's constants from the public parameters (no device work).
+    static flexrt_status make_sim(const flexrt_grid *grid, const flexrt_box *box, const double *n_H,
+                                  const flexrt_mfp *mfp, const flexrt_spectrum *sp, const flexrt_options *opt,
+                                  SimDev &h, std::string &err);
+    flexrt_status add_sim(const SimDev &h, const double *n_H, int *slot);
+    flexrt_status add_sources(int slot, int32_t n, const int32_t *ijk, const double *ndot);
+    flexrt_status set_dt(int slot, double dt);
+    flexrt_status step();                     // one RT step of every active simulation
+    flexrt_status sync();
+    flexrt_status retire(int slot);
+    flexrt_status reset_all();                // single-simulation reset
+    flexrt_status fields(int slot, flexrt_fields *f);
+    flexrt_status budget(int slot, double out[4]);
+    flexrt_status counts(int slot, int64_t out[6]);
+    flexrt_status segment_counts(int slot, int32_t *out);
+    flexrt_status rays(int slot, int64_t cap, int32_t *level, int64_t *pixel, int32_t *emitter, int32_t *birth,
+                       int32_t *dir, double *photons, int64_t *n);
+    flexrt_status set_launch(int agg, int minb, int blocks_per_sm);
+    flexrt_status profile(bool on);
+    flexrt_status kernel_times(double ms[3], int64_t launches[3], int64_t *rays);
+    int active_count() const;
+    long long cells_free() const { return cell_alloc_.capacity() - cell_alloc_.used(); }
+    long long emitters_free() const { return em_alloc_.capacity() - em_alloc_.used(); }
+    const Slot *slot(int s) const { return (s >= 0 && s < (int)slots_.size() && slots_[s].used) ? &slots_[s] : nullptr; }
+    int nb() const { return cfg_.nb; }
+    long long ray_capacity() const { return cfg_.ray_capacity; }
+    const std::string &error() const { return err_; }
+    flexrt_status fail(flexrt_status s, const std::string &m) { err_ = m; return s; }
+    flexrt_status cuda(cudaError_t e, const char *what);
+
+  private:
+    flexrt_status grow_emitters(int need);
+    flexrt_status upload_lists();             // active emitters, cell ranges, counters
+    flexrt_status poll(bool wait);
+    flexrt_status launch_step();
+    flexrt_status read_acc(int slot, SimAcc &a);
+    void free_retired();
+
+    EngineConfig cfg_{};
+    int device_ = 0;
+    cudaStream_t st_ = nullptr;
+    bool own_stream_ = false;
+    std::string err_;
+    flexrt_status latched_ = FLEXRT_OK;
+
+    Ctl *ctl_ = nullptr;
+    SimDev *sims_ = nullptr;
+    SimAcc *acc_ = nullptr;
+    void *qmem_ = nullptr;
+    Queue q_[2]{};
+    Cells cells_{};
+    Emitters em_{};
+    Ranges rg_{};
+    const int4 *pixtab_ = nullptr;
+    int ltab_ = 0;
+    int em_cap_ = 0;
+    RangeAllocator cell_alloc_, em_alloc_;
+    std::vector<Slot> slots_;
+    long long steps_taken_ = 0;
+
+    int march_agg_ = 0, march_minb_ = 3, march_blocks_ = 1, march_threads_ = 256;
+    int chem_blocks_ = 1, emit_blocks_ = 1, sm_count_ = 1;
+
+    int32_t *h_err_ = nullptr;
+    double *h_stage_ = nullptr;
+    cudaEvent_t ev_err_ = nullptr, ev_stage_ = nullptr;
+    bool err_pending_ = false;
+
+    bool profiling_ = false;
+    std::vector<cudaEvent_t> ev_pool_;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_k_[3];
+    double rays_at_profile_ = 0.0;
+
+    cudaGraphExec_t graph_ = nullptr;
+    bool graph_dirty_ = true;
+};
+
+}  // namespace frt

@@ -55,6 +55,12 @@ class Options(C.Structure):
                 ("cuda_stream", C.c_void_p)]
 
 
+class BatchConfig(C.Structure):
+    _fields_ = [("max_sims", C.c_int32), ("max_grid", C.c_int32), ("nbins", C.c_int32), ("n_ray_min", C.c_double),
+                ("ray_capacity", C.c_int64), ("cell_capacity", C.c_int64), ("emitter_capacity", C.c_int32),
+                ("keep_diagnostics", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
 class Fields(C.Structure):
     _fields_ = [("gamma_HI", C.POINTER(C.c_double)), ("x_HII", C.POINTER(C.c_double)),
                 ("T", C.POINTER(C.c_double)), ("n_HI", C.POINTER(C.c_double))]
@@ -92,6 +98,24 @@ def lib():
             L.flexrt_last_error.restype = C.c_char_p
             L.flexrt_destroy.argtypes = [vp]
             L.flexrt_destroy.restype = None
+            L.flexrt_default_batch_config.argtypes = [P(BatchConfig)]
+            L.flexrt_batch_create.argtypes = [P(BatchConfig), P(vp)]
+            L.flexrt_batch_add.argtypes = [vp, P(Grid), P(Box), P(C.c_double), P(Mfp), P(Spectrum), P(Options),
+                                           C.c_int32, P(C.c_int32), P(C.c_double), C.c_double, P(C.c_int32)]
+            L.flexrt_batch_step.argtypes = [vp]
+            L.flexrt_batch_sync.argtypes = [vp]
+            L.flexrt_batch_retire.argtypes = [vp, C.c_int32]
+            L.flexrt_batch_get_fields.argtypes = [vp, C.c_int32, P(Fields)]
+            L.flexrt_batch_get_budget.argtypes = [vp, C.c_int32, P(C.c_double)]
+            L.flexrt_batch_get_counts.argtypes = [vp, C.c_int32, P(C.c_int64)]
+            L.flexrt_batch_get_rays.argtypes = [vp, C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32),
+                                                P(C.c_int32), P(C.c_int32), P(C.c_double), P(C.c_int64)]
+            L.flexrt_batch_info.argtypes = [vp, P(C.c_int64)]
+            L.flexrt_batch_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
+            L.flexrt_batch_last_error.argtypes = [vp]
+            L.flexrt_batch_last_error.restype = C.c_char_p
+            L.flexrt_batch_destroy.argtypes = [vp]
+            L.flexrt_batch_destroy.restype = None
             L.flexrt_probe_pixvec.argtypes = [C.c_int32, C.c_int64, C.c_int64, P(C.c_int32)]
             L.flexrt_probe_rotation.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int32, P(C.c_int32)]
             L.flexrt_probe_direction.argtypes = [C.c_int32, C.c_int64, C.c_int64, P(C.c_int32), P(C.c_int32)]
@@ -116,6 +140,133 @@ def default_options() -> Options:
     o = Options()
     lib().flexrt_default_options(C.byref(o))
     return o
+
+
+def _problem_structs(prob, keep):
+    """C structs (and the arrays they point to, kept alive in `keep`) of a
+    problem description."""
+    g = Grid(*[int(v) for v in prob.grid])
+    b = Box(float(prob.box_cm_comoving), float(prob.redshift))
+    sp = prob.spectrum
+    fr = np.ascontiguousarray(sp.frac, np.float64)
+    sg = np.ascontiguousarray(sp.sigma_cm2, np.float64)
+    eh = np.ascontiguousarray(sp.eheat_erg, np.float64)
+    keep += [fr, sg, eh]
+    s = Spectrum(int(sp.nbins), _p(fr, C.c_double), _p(sg, C.c_double), _p(eh, C.c_double))
+    m = prob.mfp
+    mf = Mfp(int(m.mode), m.lambda0_cm_comoving, m.delta_exp, m.gamma_ref, m.gamma_exp, m.gamma_floor,
+             m.xion_threshold, m.nH_mean)
+    o = default_options()
+    po = prob.options
+    o.l_src, o.l_max = po.l_src, po.l_max
+    o.n_ray_min, o.eps_term = po.n_ray_min, po.eps_term
+    o.seed = po.seed
+    o.rotate, o.isothermal, o.rates, o.chem_iters = int(po.rotate), int(po.isothermal), int(po.rates), po.chem_iters
+    o.alpha_B_const, o.x_init, o.T_init = po.alpha_B_const, po.x_init, po.T_init
+    return g, b, s, mf, o
+
+
+class Batch:
+    """Many simulations advanced together (flexrt_batch_*): members are added
+    and retired between steps; one step advances every active member."""
+
+    def __init__(self, max_sims=64, max_grid=160, nbins=3, ray_capacity=0, cell_capacity=None,
+                 emitter_capacity=65536, use_graph=True, keep_diagnostics=False, n_ray_min=3.0, stream=None):
+        L = lib()
+        c = BatchConfig()
+        L.flexrt_default_batch_config(C.byref(c))
+        c.max_sims, c.max_grid, c.nbins, c.n_ray_min = max_sims, max_grid, nbins, n_ray_min
+        c.ray_capacity = int(ray_capacity)
+        c.cell_capacity = int(cell_capacity if cell_capacity is not None else max_sims * max_grid ** 3)
+        c.emitter_capacity = int(emitter_capacity)
+        c.use_graph, c.keep_diagnostics = int(use_graph), int(keep_diagnostics)
+        c.cuda_stream = stream
+        h = C.c_void_p()
+        st = L.flexrt_batch_create(C.byref(c), C.byref(h))
+        if st != FLEXRT_OK:
+            m = L.flexrt_last_error(None)
+            raise FlexRTError(st, m.decode() if m else "")
+        self._h = h
+        self.members = {}
+
+    def _check(self, st):
+        if st != FLEXRT_OK:
+            m = lib().flexrt_batch_last_error(self._h)
+            raise FlexRTError(st, m.decode() if m else "")
+
+    def add(self, prob) -> int:
+        keep = []
+        g, b, s, mf, o = _problem_structs(prob, keep)
+        nH = np.ascontiguousarray(prob.nH, np.float64).reshape(-1)
+        cells = np.ascontiguousarray(np.asarray(prob.source_cells, np.int32).reshape(-1, 3))
+        nd = np.ascontiguousarray(np.asarray(prob.source_ndot, np.float64).reshape(-1))
+        slot = C.c_int32()
+        self._check(lib().flexrt_batch_add(self._h, C.byref(g), C.byref(b), _p(nH, C.c_double), C.byref(mf),
+                                           C.byref(s), C.byref(o), len(nd), _p(cells, C.c_int32),
+                                           _p(nd, C.c_double), float(prob.dt), C.byref(slot)))
+        self.members[slot.value] = (nH.size, int(prob.spectrum.nbins))
+        return slot.value
+
+    def step(self):
+        self._check(lib().flexrt_batch_step(self._h))
+
+    def sync(self):
+        self._check(lib().flexrt_batch_sync(self._h))
+
+    def retire(self, slot):
+        self._check(lib().flexrt_batch_retire(self._h, int(slot)))
+        self.members.pop(slot, None)
+
+    def fields(self, slot, which=("gamma_HI", "x_HII", "T", "n_HI")):
+        n = self.members[slot][0]
+        out = {k: np.zeros(n) for k in which}
+        f = Fields(*[(_p(out[k], C.c_double) if k in out else None) for k in ("gamma_HI", "x_HII", "T", "n_HI")])
+        self._check(lib().flexrt_batch_get_fields(self._h, int(slot), C.byref(f)))
+        return out
+
+    def budget(self, slot):
+        b = np.zeros(4)
+        self._check(lib().flexrt_batch_get_budget(self._h, int(slot), _p(b, C.c_double)))
+        return b
+
+    def counts(self, slot):
+        c = np.zeros(6, np.int64)
+        self._check(lib().flexrt_batch_get_counts(self._h, int(slot), _p(c, C.c_int64)))
+        return dict(rays=int(c[0]), segments_last=int(c[1]), segments_total=int(c[2]), step=int(c[3]),
+                    capacity=int(c[4]), rays_marched_last=int(c[5]))
+
+    def rays(self, slot):
+        nb = self.members[slot][1]
+        n = C.c_int64()
+        self._check(lib().flexrt_batch_get_rays(self._h, int(slot), 0, None, None, None, None, None, None,
+                                                C.byref(n)))
+        m = n.value
+        lv, pix = np.zeros(m, np.int32), np.zeros(m, np.int64)
+        em, bi = np.zeros(m, np.int32), np.zeros(m, np.int32)
+        d, N = np.zeros((m, 3), np.int32), np.zeros((m, nb))
+        self._check(lib().flexrt_batch_get_rays(self._h, int(slot), m, _p(lv, C.c_int32), _p(pix, C.c_int64),
+                                                _p(em, C.c_int32), _p(bi, C.c_int32), _p(d, C.c_int32),
+                                                _p(N, C.c_double), C.byref(n)))
+        return dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
+
+    def info(self):
+        o = np.zeros(4, np.int64)
+        self._check(lib().flexrt_batch_info(self._h, _p(o, C.c_int64)))
+        return dict(active=int(o[0]), cells_free=int(o[1]), emitters_free=int(o[2]), ray_capacity=int(o[3]))
+
+    def set_launch(self, agg, minb, blocks_per_sm=0):
+        self._check(lib().flexrt_batch_set_launch(self._h, int(agg), int(minb), int(blocks_per_sm)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().flexrt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Simulation:
