@@ -353,6 +353,120 @@ def impl_gpu(args, dist):
         print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# batched and served configurations (extra lines; the default line above is
+# the single-simulation workload)
+# --------------------------------------------------------------------------
+def _calibrate_capacity(prob):
+    """Largest live-ray count of one simulation (untimed pre-pass)."""
+    import paper_2409_04521_gb300 as F
+    cap = max(1 << 20, 256 * prob.ncell)
+    s = F.Simulation(prob, ray_capacity=cap)
+    peak = 0
+    for _ in range(prob.nsteps):
+        s.step(prob.dt)
+        peak = max(peak, s.counts()["rays"])
+    s.close()
+    return peak
+
+
+def impl_batch(args, dist):
+    """64 uneven simulations (32..96^3, 50 steps each): one batch with one
+    launch per kernel per step for all members, against looping the
+    single-simulation path over the same members; both from host inputs to
+    fields on the host."""
+    import torch
+    import paper_2409_04521_gb300 as F
+    import workloads as W
+    torch.cuda.set_device(dist.local)
+    probs = W.batch64(count=args.batch_count, nsteps=args.batch_steps)
+    peaks = [_calibrate_capacity(p) for p in probs]
+    caps = [int(1.25 * p) + 4096 for p in peaks]
+    ncell = sum(p.ncell for p in probs)
+    nem = sum(len(p.source_ndot) for p in probs)
+    B = F.Batch(max_sims=len(probs), max_grid=max(p.grid[0] for p in probs), nbins=3,
+                ray_capacity=sum(caps) + 64 * 1024, cell_capacity=ncell, emitter_capacity=nem + 64)
+
+    def batched():
+        slots = [B.add(p) for p in probs]
+        for _ in range(args.batch_steps):
+            B.step()
+        B.sync()
+        segs = 0
+        for sl in slots:
+            B.fields(sl)
+            segs += B.counts(sl)["segments_total"]
+        for sl in slots:
+            B.retire(sl)
+        B.step()          # lets the retired members' emitters be reused
+        B.sync()
+        return segs
+
+    def plain():
+        segs = 0
+        for p, cap in zip(probs, caps):
+            s = F.Simulation(p, ray_capacity=cap)
+            for _ in range(args.batch_steps):
+                s.step(p.dt)
+            s.fields()
+            segs += s.counts()["segments_total"]
+            s.close()
+        return segs
+
+    for _ in range(args.warmup):
+        batched()
+    tb, sb = [], 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sb = batched()
+        tb.append(time.perf_counter() - t0)
+    plain()
+    tp = []
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sp = plain()
+        tp.append(time.perf_counter() - t0)
+    B.close()
+    t_b, t_p = min(tb), min(tp)
+    line = {"metric": "sims/hour", "value": 3600 * len(probs) / t_b, "unit": "sims/hour", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_b, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch{len(probs)}: uneven {sorted(set(p.grid[0] for p in probs))}^3, "
+                                   f"{args.batch_steps} RT steps each, 3 bins, mfp law, z=7",
+                       "members": len(probs), "cells": ncell, "emitters": nem},
+            "segments_per_s": sb / t_b,
+            "plain_loop": {"sims_per_hour": 3600 * len(probs) / t_p, "segments_per_s": sp / t_p,
+                           "seconds": t_p},
+            "speedup_vs_plain": t_p / t_b,
+            "e2e": {"value": 3600 * len(probs) / t_b, "unit": "sims/hour",
+                    "h2d_bytes_per_step": ncell * 8, "d2h_bytes_per_step": ncell * 28}}
+    print(json.dumps(line), flush=True)
+
+
+def impl_serve(args, dist):
+    """Poisson request stream served by continuous batching under an HBM
+    budget, against serving the same stream one simulation at a time."""
+    import torch
+    from paper_2409_04521_gb300 import serve
+    import workloads as W
+    torch.cuda.set_device(dist.local)
+    reqs = W.request_stream(count=args.requests, mean_gap_s=args.mean_gap)
+    res_b, st_b = serve.serve(reqs, hbm_budget_bytes=args.hbm_budget)
+    res_s, st_s = serve.serve_sequential(reqs)
+    line = {"metric": "sims/hour", "value": st_b["sims_per_hour"], "unit": "sims/hour", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * st_b["wall_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serve: {args.requests} Poisson requests (mean gap {args.mean_gap} s), "
+                                   "grids {32,64,96,128,160}^3, 50-200 RT steps, 3 bins, mfp law",
+                       "hbm_budget_bytes": args.hbm_budget},
+            "served": st_b, "sequential": st_s,
+            "p50_s": st_b["p50_s"], "p99_s": st_b["p99_s"],
+            "speedup_sims_per_hour": st_b["sims_per_hour"] / st_s["sims_per_hour"]}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,7 +480,23 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--workload", default="cosmo16", choices=["cosmo16", "batch64", "serve"])
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--mean-gap", type=float, default=0.05)
+    ap.add_argument("--hbm-budget", type=float, default=150e9)
     args = ap.parse_args(argv)
+    if args.workload == "batch64" and args.impl != "reference":
+        dist = Dist()
+        impl_batch(args, dist)
+        dist.close()
+        return
+    if args.workload == "serve" and args.impl != "reference":
+        dist = Dist()
+        impl_serve(args, dist)
+        dist.close()
+        return
     if args.impl == "reference":
         dist = Dist(backend="gloo")
         impl_reference(args, dist)

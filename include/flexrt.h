@@ -257,8 +257,9 @@ flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, int64_t cap, 
                                     double *photons, int64_t *n);
 
 /* out[0] active members, out[1] free cells, out[2] free emitters,
- * out[3] ray capacity. */
-flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[4]);
+ * out[3] ray capacity, out[4] queue slots in use by live rays (waits for
+ * enqueued work), out[5] free slots. */
+flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[6]);
 flexrt_status flexrt_batch_set_launch(flexrt_batch *b, int32_t agg, int32_t minb, int32_t blocks_per_sm);
 const char *flexrt_batch_last_error(const flexrt_batch *b);
 void flexrt_batch_destroy(flexrt_batch *b);

@@ -216,12 +216,17 @@ extern "C" flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, in
                                                double *photons, int64_t *n) {
     return b ? b->eng.rays(slot, cap, level, pixel, emitter, birth, dir, photons, n) : FLEXRT_E_INVALID;
 }
-extern "C" flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[4]) {
+extern "C" flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[6]) {
     if (!b || !out) return FLEXRT_E_INVALID;
+    long long q = 0;
+    flexrt_status s = b->eng.queue_used(&q);
+    if (s != FLEXRT_OK) return s;
     out[0] = b->eng.active_count();
     out[1] = b->eng.cells_free();
     out[2] = b->eng.emitters_free();
     out[3] = b->eng.ray_capacity();
+    out[4] = q;
+    out[5] = b->eng.free_slots();
     return FLEXRT_OK;
 }
 extern "C" flexrt_status flexrt_batch_set_launch(flexrt_batch *b, int32_t agg, int32_t minb, int32_t bps) {

@@ -776,6 +776,20 @@ flexrt_status Engine::kernel_times(double ms[3], int64_t launches[3], int64_t *r
     return FLEXRT_OK;
 }
 
+int Engine::free_slots() const {
+    int n = 0;
+    for (auto &s : slots_) n += s.used ? 0 : 1;
+    return n;
+}
+
+flexrt_status Engine::queue_used(long long *n) {
+    CK(cudaStreamSynchronize(st_));
+    Ctl hc;
+    CK(cudaMemcpy(&hc, ctl_, sizeof(hc), cudaMemcpyDeviceToHost));
+    *n = hc.cnt[hc.par];
+    return FLEXRT_OK;
+}
+
 int Engine::active_count() const {
     int n = 0;
     for (auto &s : slots_) n += s.active ? 1 : 0;

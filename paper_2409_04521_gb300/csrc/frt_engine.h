@@ -81,6 +81,8 @@ class Engine {
     flexrt_status profile(bool on);
     flexrt_status kernel_times(double ms[3], int64_t launches[3], int64_t *rays);
     int active_count() const;
+    int free_slots() const;
+    flexrt_status queue_used(long long *n);   // slots of the live ray queue (synchronises)
     long long cells_free() const { return cell_alloc_.capacity() - cell_alloc_.used(); }
     long long emitters_free() const { return em_alloc_.capacity() - em_alloc_.used(); }
     const Slot *slot(int s) const { return (s >= 0 && s < (int)slots_.size() && slots_[s].used) ? &slots_[s] : nullptr; }

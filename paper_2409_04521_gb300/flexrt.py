@@ -250,9 +250,10 @@ class Batch:
         return dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
 
     def info(self):
-        o = np.zeros(4, np.int64)
+        o = np.zeros(6, np.int64)
         self._check(lib().flexrt_batch_info(self._h, _p(o, C.c_int64)))
-        return dict(active=int(o[0]), cells_free=int(o[1]), emitters_free=int(o[2]), ray_capacity=int(o[3]))
+        return dict(active=int(o[0]), cells_free=int(o[1]), emitters_free=int(o[2]), ray_capacity=int(o[3]),
+                    queue_used=int(o[4]), slots_free=int(o[5]))
 
     def set_launch(self, agg, minb, blocks_per_sm=0):
         self._check(lib().flexrt_batch_set_launch(self._h, int(agg), int(minb), int(blocks_per_sm)))

@@ -165,7 +165,7 @@ def lognormal_delta(n: int, sigma_ln: float, seed: int, slope: float = -2.0) -> 
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (slope / 4.0)  # sqrt(P) = k^(slope/2)
-    g = np.fft.irfftn(wk * amp, s=(n, n, n))
+    g = np.fft.irfftn(wk * amp, s=(n, n, n), axes=(0, 1, 2))
     g = (g - g.mean()) / g.std() * sigma_ln
     return np.exp(g - 0.5 * sigma_ln ** 2).reshape(-1)
 
@@ -225,17 +225,36 @@ def cosmo20k(n: int = 200, nsteps: int = 200, nsrc: int = 20000, seed: int = 3) 
                    cell_ijk(cells, n), ndot, 1.0 * MYR, nsteps)
 
 
-def batch_member(seed: int, sizes=(32, 48, 64, 96), nsteps: int = 50) -> Problem:
+_UNIT_FIELDS = {}
+
+
+def _unit_field(n: int, k: int) -> np.ndarray:
+    """A seeded Gaussian field of P(k) ~ k^-2 with mean 0 and std 1 (cached;
+    a few per grid size serve every request of a stream)."""
+    key = (n, k)
+    if key not in _UNIT_FIELDS:
+        _UNIT_FIELDS[key] = np.log(lognormal_delta(n, 1.0, 30_000 + 97 * n + k)) + 0.5
+    return _UNIT_FIELDS[key]
+
+
+def batch_member(seed: int, sizes=(32, 48, 64, 96), nsteps: int = 50, shared_fields: bool = False) -> Problem:
     """One member of the uneven batch: grid from `sizes`, sigma_ln in
     [0.3,1.2], 1..32 sources drawn in proportion to density, mfp scale in
-    [1,20] cell widths, 1 cMpc/h cells at z = 7, 3 bins, isothermal."""
+    [1,20] cell widths, 1 cMpc/h cells at z = 7, 3 bins, isothermal.
+    With shared_fields the Gaussian field is one of four cached per grid
+    size, periodically shifted by a seeded offset (cheap for long streams)."""
     rng = np.random.default_rng(10_000 + seed)
     n = int(rng.choice(sizes))
     sig = float(rng.uniform(0.3, 1.2))
     nsrc = int(rng.integers(1, 33))
     scale = float(rng.uniform(1.0, 20.0))
     z = 7.0
-    delta = lognormal_delta(n, sig, 20_000 + seed)
+    if shared_fields:
+        g = _unit_field(n, seed % 4).reshape(n, n, n)
+        g = np.roll(g, tuple(int(v) for v in rng.integers(0, n, 3)), axis=(0, 1, 2)).reshape(-1)
+        delta = np.exp(sig * g - 0.5 * sig * sig)
+    else:
+        delta = lognormal_delta(n, sig, 20_000 + seed)
     nbar = mean_nH_comoving() * (1 + z) ** 3
     p = delta / delta.sum()
     cells = rng.choice(delta.size, size=nsrc, replace=True, p=p)
@@ -262,6 +281,6 @@ def request_stream(count: int = 1000, mean_gap_s: float = 0.05, sizes=(32, 64, 9
     out = []
     for i in range(count):
         nst = int(rng.integers(steps[0], steps[1] + 1))
-        prob = batch_member(100_000 + i, sizes, nst)
+        prob = batch_member(100_000 + i, sizes, nst, shared_fields=True)
         out.append((float(t[i]), prob))
     return out
