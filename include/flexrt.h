@@ -101,7 +101,8 @@ typedef struct {
     int32_t chem_iters;     /* n_e re-evaluations of Eq. 7-10 per step          */
     double alpha_B_const;   /* cm^3/s, used when rates == 0                     */
     double x_init, T_init;  /* initial ionised fraction and temperature (K)     */
-    int64_t ray_capacity;   /* rays per queue; 0 = sized from free memory       */
+    int64_t ray_capacity;   /* live rays a queue holds (slots allocated: 1.25x
+                               plus 4096); 0 = sized from free memory         */
     int32_t keep_diagnostics; /* 1: keep per-cell segment counts of each step   */
     void *cuda_stream;      /* cudaStream_t, 0 = library-owned stream           */
 } flexrt_options;

@@ -154,6 +154,10 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     long long cap = cfg_.ray_capacity;
     if (cap <= 0) cap = (long long)(0.3 * (double)freeb / (2.0 * ray_bytes(cfg_.nb)));
     cfg_.ray_capacity = cap = std::max(cap, 1024LL);
+    // queue slots beyond the live-ray capacity for the unused tails of the
+    // march's warp-private output runs
+    cap += cap / 4 + 4096;
+    qcap_ = cap;
 
     // ray queues: one allocation, structure of arrays, two buffers
     {
@@ -328,6 +332,7 @@ flexrt_status Engine::make_sim(const flexrt_grid *grid, const flexrt_box *box, c
 }
 
 flexrt_status Engine::add_sim(const SimDev &proto, const double *n_H, int *slot_out) {
+    free_retired();
     const int ms = (int)slots_.size();
     int s = -1;
     for (int i = 0; i < ms; ++i)
@@ -520,8 +525,8 @@ static cudaEvent_t take_event(std::vector<cudaEvent_t> &pool) {
 
 flexrt_status Engine::launch_step() {
     const int ms = (int)slots_.size();
-    EmitArgs ea{ctl_, sims_, acc_, {q_[0], q_[1]}, cfg_.ray_capacity, em_, pixtab_, ltab_, cfg_.nb};
-    MarchArgs ma{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, cfg_.ray_capacity, em_, cells_, pixtab_, ltab_};
+    EmitArgs ea{ctl_, sims_, acc_, {q_[0], q_[1]}, qcap_, em_, pixtab_, ltab_, cfg_.nb};
+    MarchArgs ma{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, qcap_, em_, cells_, pixtab_, ltab_};
     ChemArgs ca{ctl_, sims_, acc_, ms, cells_, rg_};
     const bool prof = profiling_ && !cfg_.use_graph;
     cudaEvent_t e0 = nullptr;
@@ -583,6 +588,9 @@ flexrt_status Engine::step() {
     ++steps_taken_;
     for (auto &sl : slots_)
         if (sl.active) ++sl.h.step;
+    // the step just enqueued drops the rays of members retired before it;
+    // work enqueued later runs after it, so their emitters can be reused
+    free_retired();
     return FLEXRT_OK;
 }
 

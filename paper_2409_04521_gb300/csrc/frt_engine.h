@@ -118,6 +118,7 @@ class Engine {
     const int4 *pixtab_ = nullptr;
     int ltab_ = 0;
     int em_cap_ = 0;
+    long long qcap_ = 0;       // allocated queue slots (capacity plus run-tail margin)
     RangeAllocator cell_alloc_, em_alloc_;
     std::vector<Slot> slots_;
     long long steps_taken_ = 0;

@@ -180,9 +180,11 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         const long long n = C->cnt[par] + C->emit_total;
         const long long nr = (n + 31) & ~31LL;
         const long long stride = (long long)gridDim.x * blockDim.x;
-        // warp-private run of output slots [slab, slab + slab_left)
+        // warp-private run of output slots [slab, slab + slab_left), and this
+        // warp's outputs and iterations so far (its output rate)
         unsigned long long slab = 0;
         int slab_left = 0;
+        long long w_out = 0, w_it = 0;
         // the next ray's words are loaded one iteration ahead
         uint32_t npl = DEAD_RAY, ne_ = 0;
         int nbi = 0, ndx = 0, ndy = 0, ndz = 0;
@@ -350,14 +352,26 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     atomicAdd(dst + 5, (unsigned long long)__float2uint_rn(v[5]));
                 }
             }
-            // compacted output into the warp's slab
+            // compacted output into the warp's run of slots: the remainder of
+            // the current run first, then a new run reserved with one atomic
             const int incl = warp_incl_scan(nout);
             const int tot = __shfl_sync(FULL, incl, 31);
             if (tot > 0) {
+                const unsigned long long s0 = slab;
+                const int left = slab_left;
+                unsigned long long s1 = 0;
                 bool fits = true;
-                if (tot > slab_left) {
-                    for (int k = lane; k < slab_left; k += 32) qo.pl[slab + k] = DEAD_RAY;
-                    const int want = tot > OUT_SLAB ? tot : OUT_SLAB;
+                if (tot > left) {
+                    // reserve for this warp's next iterations at its own output
+                    // rate (at most 16 iterations ahead and OUT_SLAB slots), so the
+                    // unused tail stays small whatever the queue's dead fraction
+                    const int need = tot - left;
+                    const long long iters_left = (nr - i + stride - 1) / stride;
+                    const long long ahead = iters_left < 16 ? iters_left : 16;
+                    const long long rate = (w_out + tot + w_it) / (w_it + 1);
+                    long long guess = rate * ahead;
+                    if (guess > OUT_SLAB) guess = OUT_SLAB;
+                    const int want = need > guess ? need : (int)guess;
                     unsigned long long nbase = 0;
                     if (lane == 0) nbase = atomicAdd(out_cnt, (unsigned long long)want);
                     nbase = __shfl_sync(FULL, nbase, 0);
@@ -366,15 +380,22 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                         fits = false;
                         slab_left = 0;
                     } else {
-                        slab = nbase;
-                        slab_left = want;
+                        s1 = nbase;
+                        slab = nbase + need;
+                        slab_left = want - need;
                     }
+                } else {
+                    slab = s0 + tot;
+                    slab_left = left - tot;
                 }
-                const unsigned long long base = slab;
-                if (fits) { slab += tot; slab_left -= tot; }
+                w_out += tot;
                 if (fits && nout > 0) {
-                    const long long o = (long long)base + incl - nout;
+                    const int k0 = incl - nout;  // this lane's first output position
+                    auto slot_of = [&](int k) -> long long {
+                        return k < left ? (long long)(s0 + k) : (long long)(s1 + (k - left));
+                    };
                     if (nout == 1) {
+                        const long long o = slot_of(k0);
                         qo.pl[o] = pl; qo.em[o] = e; qo.bi[o] = bi;
                         qo.dx[o] = dx; qo.dy[o] = dy; qo.dz[o] = dz;
 #pragma unroll
@@ -393,7 +414,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                             const int4 vq = L <= A.ltab ? __ldg(&A.pixtab[level_offset(L) + pix]) : healpix_vq(L, pix);
                             int32_t cx, cy, cz;
                             rotate_dir(rows, vq, cx, cy, cz);
-                            const long long oc = o + c;
+                            const long long oc = slot_of(k0 + c);
                             qo.pl[oc] = ((uint32_t)L << LEVEL_SHIFT) | pix;
                             qo.em[oc] = e; qo.bi[oc] = bi;
                             qo.dx[oc] = cx; qo.dy[oc] = cy; qo.dz[oc] = cz;
@@ -403,6 +424,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     }
                 }
             }
+            ++w_it;
         }
         for (int k = lane; k < slab_left; k += 32) qo.pl[slab + k] = DEAD_RAY;
     }

@@ -119,3 +119,18 @@ def test_capacity_errors():
     with pytest.raises(F.FlexRTError):
         B.add(big)                     # larger than max_grid
     B.close()
+
+
+def test_served_results_equal_alone():
+    # a short Poisson stream served by continuous batching: every request's
+    # fields equal the same simulation run alone
+    from paper_2409_04521_gb300 import serve
+    reqs = W.request_stream(count=8, mean_gap_s=0.01, sizes=(16, 24, 32), steps=(3, 9), seed=11)
+    results, stats = serve.serve(reqs, hbm_budget_bytes=2e9, max_sims=4, max_grid=32, emitter_capacity=512,
+                                 keep_fields=True)
+    assert stats["requests"] == len(reqs)
+    for r in results:
+        _, prob = reqs[r.rid]
+        f, b, c = _alone(prob, prob.nsteps)
+        compare_fields(r.fields, f)
+        assert r.finished >= r.admitted >= r.arrival - 1e-9

@@ -122,12 +122,12 @@ def test_reset_reproduces_run():
 
 
 def test_capacity_overflow_keeps_last_good_step():
-    prob = W.stromgren(n=24, nsteps=12)
+    prob = W.stromgren(n=32, nsteps=30)
     ref = F.Simulation(prob, ray_capacity=1 << 20)
-    small = F.Simulation(prob, ray_capacity=3000)
+    small = F.Simulation(prob, ray_capacity=2000)
     good = None
     with pytest.raises(F.FlexRTError) as ei:
-        for s in range(12):
+        for s in range(30):
             small.step(prob.dt)
             small.sync()
             good = s + 1
