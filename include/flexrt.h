@@ -215,7 +215,7 @@ flexrt_status flexrt_probe_traverse(int64_t n, const int64_t *p0, const int32_t 
 /* be added and retired between steps (continuous batching).                */
 /* ----------------------------------------------------------------------- */
 typedef struct {
-    int32_t max_sims;        /* simulation slots                               */
+    int32_t max_sims;        /* simulation slots, 1..512                       */
     int32_t max_grid;        /* largest grid edge of any member                */
     int32_t nbins;           /* frequency bins of the ray layout (members may use fewer) */
     double n_ray_min;        /* N_min used to size the pixel table (members choose their own) */

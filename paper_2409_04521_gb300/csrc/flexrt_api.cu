@@ -147,7 +147,7 @@ extern "C" void flexrt_default_batch_config(flexrt_batch_config *b) {
 extern "C" flexrt_status flexrt_batch_create(const flexrt_batch_config *bc, flexrt_batch **out) {
     if (!out || !bc) return FLEXRT_E_INVALID;
     *out = nullptr;
-    if (bc->max_sims < 1 || bc->max_sims > 1024 || bc->max_grid < 1 || bc->max_grid > 1000 || bc->nbins < 1 ||
+    if (bc->max_sims < 1 || bc->max_sims > 512 || bc->max_grid < 1 || bc->max_grid > 1000 || bc->nbins < 1 ||
         bc->nbins > FLEXRT_MAX_BINS || bc->cell_capacity < 1 || bc->emitter_capacity < 1)
         return free_fail(FLEXRT_E_INVALID, "flexrt_batch_create: bad configuration");
     flexrt_batch *b = new (std::nothrow) flexrt_batch();

@@ -133,7 +133,7 @@ Engine::~Engine() {
 
 flexrt_status Engine::init(const EngineConfig &cfg) {
     cfg_ = cfg;
-    if (cfg_.nb < 1 || cfg_.nb > MAXB || cfg_.max_sims < 1 || cfg_.max_sims > 1024 || cfg_.cell_capacity < 1 ||
+    if (cfg_.nb < 1 || cfg_.nb > MAXB || cfg_.max_sims < 1 || cfg_.max_sims > 512 || cfg_.cell_capacity < 1 ||
         cfg_.max_grid < 1 || cfg_.max_grid > 1000)
         return fail(FLEXRT_E_INVALID, "bad engine configuration");
     CK(cudaGetDevice(&device_));
@@ -221,7 +221,9 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device_);
     sm_count_ = std::max(sms, 1);
     if (!march_variant_exists(cfg_.nb, march_agg_, march_minb_)) { march_agg_ = 0; march_minb_ = 2; }
+    CK(march_prepare(cfg_.nb, march_agg_, march_minb_, ms));
     const int per_sm = march_max_blocks_per_sm(cfg_.nb, march_agg_, march_minb_, march_threads_, ms);
+    if (per_sm < 1) return fail(FLEXRT_E_INVALID, "too many simulation slots for one march block");
     march_blocks_ = sm_count_ * std::max(per_sm, 1);
     chem_blocks_ = (int)std::max<long long>(1, std::min<long long>((nc + 255) / 256, (long long)sm_count_ * 8));
     CK(cudaStreamSynchronize(st_));
@@ -742,6 +744,7 @@ flexrt_status Engine::rays(int s, int64_t cap, int32_t *level, int64_t *pixel, i
 flexrt_status Engine::set_launch(int agg, int minb, int blocks_per_sm) {
     if (!march_variant_exists(cfg_.nb, agg, minb) || blocks_per_sm < 0 || blocks_per_sm > 32)
         return fail(FLEXRT_E_INVALID, "march kernel variant not built");
+    CK(march_prepare(cfg_.nb, agg, minb, (int)slots_.size()));
     const int lim = march_max_blocks_per_sm(cfg_.nb, agg, minb, march_threads_, (int)slots_.size());
     if (lim < 1) return fail(FLEXRT_E_INVALID, "variant cannot be resident");
     const int bps = blocks_per_sm == 0 ? lim : std::min(blocks_per_sm, lim);

@@ -675,6 +675,13 @@ static MarchFn march_fn(int nb, int agg, int minb) {
     }
 }
 bool march_variant_exists(int nb, int agg, int minb) { return march_fn(nb, agg, minb) != nullptr; }
+cudaError_t march_prepare(int nb, int agg, int minb, int nsims) {
+    MarchFn f = march_fn(nb, agg, minb);
+    if (!f) return cudaErrorInvalidValue;
+    const size_t sh = march_shared_bytes(nsims);
+    if (sh > 48 * 1024) return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    return cudaSuccess;
+}
 cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st) {
     MarchFn f = march_fn(nb, agg, minb);
     if (!f) return cudaErrorInvalidValue;

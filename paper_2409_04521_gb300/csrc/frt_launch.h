@@ -46,6 +46,8 @@ cudaError_t launch_pixtab(int4 *tab, int L, cudaStream_t st);
 cudaError_t launch_init_cells(const SimDev *sims, int sim, Cells c, long long ncell, cudaStream_t st);
 cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st);
 bool march_variant_exists(int nb, int agg, int minb);
+// opt the variant into the dynamic shared memory `nsims` slots need
+cudaError_t march_prepare(int nb, int agg, int minb, int nsims);
 cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st);
 int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims);
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st);
