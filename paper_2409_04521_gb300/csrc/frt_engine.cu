@@ -295,6 +295,7 @@ flexrt_status Engine::make_sim(const flexrt_grid *grid, const flexrt_box *box, c
     for (int b = 0; b < sp->nbins; ++b) {
         h.sig[b] = (float)(sp->sigma_cm2[b] / h.sigma_ref);
         h.sige[b] = (float)(sp->sigma_cm2[b] / h.sigma_ref * sp->eheat_erg[b] / EV_ERG);
+        h.eh[b] = (float)(sp->eheat_erg[b] / EV_ERG);
         h.frac[b] = (float)sp->frac[b];
     }
     h.dx_com = box->box_cm_comoving / grid->nx;

@@ -134,7 +134,40 @@ __global__ void k_emit(EmitArgs A) {
 // ---------------------------------------------------------------------------
 // march + deposit + terminate + split + compact
 // ---------------------------------------------------------------------------
-constexpr int NACC = 6;  // in, escaped, out, segments, rays in, rays out
+constexpr int NACC = 6;  // (unused), escaped, out, segments, rays in, rays out
+
+// Warp-wide flush of lane-private tallies (lane simulation `tsim`, -1 for
+// none) into the block's per-simulation fixed-point totals; clears them.
+__device__ __forceinline__ void flush_tallies(float &esc, float &out, unsigned &cnt, unsigned &rout, int &tsim,
+                                              unsigned long long *sh_acc) {
+    const int lane = lane_id();
+    const int kref = __reduce_max_sync(FULL, tsim);
+    if (kref < 0) return;                                   // warp-uniform
+    float v[NACC] = {0.0f, esc, out, (float)(cnt & 0xffffu), (float)(cnt >> 16), (float)rout};
+    bool lead;
+    int kk = tsim;
+    if (__all_sync(FULL, tsim < 0 || tsim == kref)) {
+        warp_sum<NACC>(v);                                  // empty lanes carry zeros
+        lead = lane == 0;
+        kk = kref;
+    } else {
+        const unsigned peers = __match_any_sync(FULL, tsim);
+        peer_sum<NACC>(peers, v);
+        lead = tsim >= 0 && (peers & ((1u << lane) - 1u)) == 0u;
+    }
+    if (lead) {
+        unsigned long long *dst = sh_acc + kk * NACC;
+        atomicAdd(dst + 0, fixed32(v[0]));
+        atomicAdd(dst + 1, fixed32(v[1]));
+        atomicAdd(dst + 2, fixed32(v[2]));
+        atomicAdd(dst + 3, (unsigned long long)__float2uint_rn(v[3]));
+        atomicAdd(dst + 4, (unsigned long long)__float2uint_rn(v[4]));
+        atomicAdd(dst + 5, (unsigned long long)__float2uint_rn(v[5]));
+    }
+    esc = out = 0.0f;
+    cnt = rout = 0u;
+    tsim = -1;
+}
 
 // The per-simulation constants the march needs, staged in shared memory.
 struct MarchSim {
@@ -142,7 +175,7 @@ struct MarchSim {
     long long coff;
     float eps;
     int K[MAXL];
-    float sig[MAXB], sige[MAXB];
+    float sig[MAXB], sige[MAXB], eh[MAXB];
 };
 
 __host__ __device__ constexpr size_t march_shared_bytes(int nsims) {
@@ -168,7 +201,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         m.nx = S.nx; m.ny = S.ny; m.nz = S.nz; m.step = S.step; m.l_src = S.l_src; m.l_max = S.l_max;
         m.active = S.active; m.pad = 0; m.coff = S.cell_off; m.eps = S.eps_term;
         for (int l = 0; l < MAXL; ++l) m.K[l] = S.K[l];
-        for (int b = 0; b < MAXB; ++b) { m.sig[b] = S.sig[b]; m.sige[b] = S.sige[b]; }
+        for (int b = 0; b < MAXB; ++b) { m.sig[b] = S.sig[b]; m.sige[b] = S.sige[b]; m.eh[b] = S.eh[b]; }
     }
     __syncthreads();
     Ctl *C = A.ctl;
@@ -184,19 +217,26 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         // warp's outputs and iterations so far (its output rate)
         unsigned long long slab = 0;
         int slab_left = 0;
-        long long w_out = 0, w_it = 0;
+        int w_out = 0, w_it = 0;
+        // lane-private tallies of one simulation, flushed by the warp:
+        // escaped and surviving photons, segments | rays in << 16, rays out
+        float t_esc = 0.0f, t_out = 0.0f;
+        unsigned t_cnt = 0u, t_rout = 0u;
+        int t_sim = -1, t_n = 0;
         // the next ray's words are loaded one iteration ahead
         uint32_t npl = DEAD_RAY, ne_ = 0;
         int nbi = 0, ndx = 0, ndy = 0, ndz = 0;
         float nph[NB];
         auto load_ray = [&](long long j) {
+            // the queue streams through once per step: evict-first loads keep
+            // the cells' opacities and deposit buffers resident in L2
             npl = DEAD_RAY;
-            if (j < n) npl = qi.pl[j];
+            if (j < n) npl = __ldcs(qi.pl + j);
             if (npl != DEAD_RAY) {
-                ne_ = qi.em[j]; nbi = qi.bi[j];
-                ndx = qi.dx[j]; ndy = qi.dy[j]; ndz = qi.dz[j];
+                ne_ = __ldcs(qi.em + j); nbi = __ldcs(qi.bi + j);
+                ndx = __ldcs(qi.dx + j); ndy = __ldcs(qi.dy + j); ndz = __ldcs(qi.dz + j);
 #pragma unroll
-                for (int b = 0; b < NB; ++b) nph[b] = qi.ph[b][j];
+                for (int b = 0; b < NB; ++b) nph[b] = __ldcs(qi.ph[b] + j);
             } else {
                 ne_ = 0; nbi = 0; ndx = ndy = ndz = 0;
 #pragma unroll
@@ -225,9 +265,6 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 atomicOr(&C->err, 2);
                 valid = false;
             }
-            float s_in = 0.0f;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) s_in += ph[b];
 
             // (1) integer walk of this step
             int key[4];
@@ -270,17 +307,35 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             for (int j = 0; j < 4; ++j) {
                 float v[4] = {0.f, 0.f, 0.f, 1.0f};
                 if (key[j] >= 0) {
+                    if (kc[j].y == 0.0f && kc[j].x > 0.0f) {
+                        // no sub-grid term: kappa_b = kappa_HI sigma_b for every bin,
+                        // so sigma_b a_b / kappa_b = a_b / kappa_HI (one reciprocal)
+                        float he = 0.0f;
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
-                        float tr, ab;
-                        absorb_transmit(kb * ds[j], ab, tr);
-                        const float a = ph[b] * ab;
-                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds[j];
-                        ph[b] *= tr;
-                        v[0] += a;
-                        v[1] = fmaf(S.sig[b], phin, v[1]);
-                        v[2] = fmaf(S.sige[b], phin, v[2]);
+                        for (int b = 0; b < NB; ++b) {
+                            float tr, ab;
+                            absorb_transmit(kc[j].x * S.sig[b] * ds[j], ab, tr);
+                            const float a = ph[b] * ab;
+                            ph[b] *= tr;
+                            v[0] += a;
+                            he = fmaf(S.eh[b], a, he);
+                        }
+                        const float r = __frcp_rn(kc[j].x);
+                        v[1] = v[0] * r;
+                        v[2] = he * r;
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) {
+                            const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
+                            float tr, ab;
+                            absorb_transmit(kb * ds[j], ab, tr);
+                            const float a = ph[b] * ab;
+                            const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds[j];
+                            ph[b] *= tr;
+                            v[0] += a;
+                            v[1] = fmaf(S.sig[b], phin, v[1]);
+                            v[2] = fmaf(S.sige[b], phin, v[2]);
+                        }
                     }
                     last = key[j];
                     lastk = kc[j];
@@ -325,32 +380,23 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     nout = 1 << (2 * m);
                 }
             }
-            // per-simulation tallies
+            // per-simulation tallies: each lane accumulates the rays of one
+            // simulation for up to four iterations, then the warp reduces them
+            // into the block's fixed-point totals
             {
-                float v[NACC] = {s_in, esc ? s_end : 0.0f, nout ? s_end : 0.0f, (float)nseg,
-                                 valid ? 1.0f : 0.0f, (float)nout};
-                const int key = valid ? sim : -1;
-                const int kref = __reduce_max_sync(FULL, key);
-                bool lead;
-                int kk = key;
-                if (__all_sync(FULL, key < 0 || key == kref)) {
-                    warp_sum<NACC>(v);               // invalid lanes carry zeros
-                    lead = lane == 0 && kref >= 0;
-                    kk = kref;
-                } else {
-                    const unsigned peers = __match_any_sync(FULL, key);
-                    peer_sum<NACC>(peers, v);
-                    lead = key >= 0 && (peers & ((1u << lane) - 1u)) == 0u;
+                const bool clash = valid && t_sim >= 0 && t_sim != sim;
+                if (__any_sync(FULL, clash) || t_n == 4) {
+                    flush_tallies(t_esc, t_out, t_cnt, t_rout, t_sim, sh_acc);
+                    t_n = 0;
                 }
-                if (lead) {
-                    unsigned long long *dst = sh_acc + kk * NACC;
-                    atomicAdd(dst + 0, fixed32(v[0]));
-                    atomicAdd(dst + 1, fixed32(v[1]));
-                    atomicAdd(dst + 2, fixed32(v[2]));
-                    atomicAdd(dst + 3, (unsigned long long)__float2uint_rn(v[3]));
-                    atomicAdd(dst + 4, (unsigned long long)__float2uint_rn(v[4]));
-                    atomicAdd(dst + 5, (unsigned long long)__float2uint_rn(v[5]));
+                if (valid) {
+                    if (esc) t_esc += s_end;
+                    if (nout) t_out += s_end;
+                    t_cnt += (unsigned)nseg + (1u << 16);
+                    t_rout += (unsigned)nout;
+                    t_sim = sim;
                 }
+                ++t_n;
             }
             // compacted output into the warp's run of slots: the remainder of
             // the current run first, then a new run reserved with one atomic
@@ -367,11 +413,10 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     // unused tail stays small whatever the queue's dead fraction
                     const int need = tot - left;
                     const long long iters_left = (nr - i + stride - 1) / stride;
-                    const long long ahead = iters_left < 16 ? iters_left : 16;
-                    const long long rate = (w_out + tot + w_it) / (w_it + 1);
-                    long long guess = rate * ahead;
-                    if (guess > OUT_SLAB) guess = OUT_SLAB;
-                    const int want = need > guess ? need : (int)guess;
+                    const int ahead = iters_left < 16 ? (int)iters_left : 16;
+                    const int rate = (w_out + tot + w_it) / (w_it + 1);
+                    const int guess = rate * ahead < OUT_SLAB ? rate * ahead : OUT_SLAB;
+                    const int want = need > guess ? need : guess;
                     unsigned long long nbase = 0;
                     if (lane == 0) nbase = atomicAdd(out_cnt, (unsigned long long)want);
                     nbase = __shfl_sync(FULL, nbase, 0);
@@ -396,10 +441,10 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     };
                     if (nout == 1) {
                         const long long o = slot_of(k0);
-                        qo.pl[o] = pl; qo.em[o] = e; qo.bi[o] = bi;
-                        qo.dx[o] = dx; qo.dy[o] = dy; qo.dz[o] = dz;
+                        __stcs(qo.pl + o, pl); __stcs(qo.em + o, e); __stcs(qo.bi + o, bi);
+                        __stcs(qo.dx + o, dx); __stcs(qo.dy + o, dy); __stcs(qo.dz + o, dz);
 #pragma unroll
-                        for (int b = 0; b < NB; ++b) qo.ph[b][o] = ph[b];
+                        for (int b = 0; b < NB; ++b) __stcs(qo.ph[b] + o, ph[b]);
                     } else {
                         const int L = lev + m;
                         const uint32_t pix0 = (pl & PIX_MASK) << (2 * m);
@@ -427,6 +472,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             ++w_it;
         }
         for (int k = lane; k < slab_left; k += 32) qo.pl[slab + k] = DEAD_RAY;
+        flush_tallies(t_esc, t_out, t_cnt, t_rout, t_sim, sh_acc);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) {

@@ -34,6 +34,7 @@ struct SimDev {
     float eps_term;
     float sig[MAXB];        // sigma_b / sigma_ref
     float sige[MAXB];       // sigma_b / sigma_ref * eheat_b / 1 eV
+    float eh[MAXB];         // eheat_b / 1 eV
     float frac[MAXB];       // photon fraction per bin
     double dt;              // s
     double gscale;          // Gamma per unit of the Gamma numerator: nref sigma_ref / (dx^2 dt)
