@@ -232,28 +232,22 @@ __device__ __forceinline__ bool walk_segment(Walk &w, float &ds) {
     const bool crx = w.sx != 0 && w.Dx < w.ax;
     const bool cry = w.sy != 0 && w.Dy < w.ay;
     const bool crz = w.sz != 0 && w.Dz < w.az;
-    // pairwise order of the crossing parameters t_a = D_a/|d_a| (exact)
-    const unsigned long long xy = wmul(w.Dx, w.ay), yx = wmul(w.Dy, w.ax);
-    const unsigned long long xz = wmul(w.Dx, w.az), zx = wmul(w.Dz, w.ax);
-    const unsigned long long yz = wmul(w.Dy, w.az), zy = wmul(w.Dz, w.ay);
-    // an axis is first if it crosses and no crossing axis comes strictly earlier
-    const bool fx = crx && (!cry || xy <= yx) && (!crz || xz <= zx);
-    const bool fy = cry && (!crx || yx <= xy) && (!crz || yz <= zy);
-    const bool fz = crz && (!crx || zx <= xz) && (!cry || zy <= yz);
-    const bool cross = fx || fy || fz;
     unsigned un = 1u, ud = 1u;
-    if (fz) { un = w.Dz; ud = w.az; }
-    if (fy) { un = w.Dy; ud = w.ay; }
-    if (fx) { un = w.Dx; ud = w.ax; }
+    bool cross = false;
+    if (crx) { un = w.Dx; ud = w.ax; cross = true; }
+    if (cry && (!cross || wmul(w.Dy, ud) < wmul(un, w.ay))) { un = w.Dy; ud = w.ay; cross = true; }
+    if (crz && (!cross || wmul(w.Dz, ud) < wmul(un, w.az))) { un = w.Dz; ud = w.az; cross = true; }
     // ds = un/ud - tn/td as one exact integer fraction
     const unsigned long long num = wmul(un, w.td) - wmul(w.tn, ud);
     const unsigned long long den = wmul(ud, w.td);
     ds = __fdividef(u64_to_float(num), u64_to_float(den));
-    // every first axis (ties included) steps to its next cell
-    if (fx) { w.cx += w.sx; w.Dx += (unsigned)ONE_CELL; }
-    if (fy) { w.cy += w.sy; w.Dy += (unsigned)ONE_CELL; }
-    if (fz) { w.cz += w.sz; w.Dz += (unsigned)ONE_CELL; }
-    if (cross) { w.tn = un; w.td = ud; }
+    if (cross) {
+        // every axis crossing at the same t steps together
+        if (crx && wmul(w.Dx, ud) == wmul(un, w.ax)) { w.cx += w.sx; w.Dx += (unsigned)ONE_CELL; }
+        if (cry && wmul(w.Dy, ud) == wmul(un, w.ay)) { w.cy += w.sy; w.Dy += (unsigned)ONE_CELL; }
+        if (crz && wmul(w.Dz, ud) == wmul(un, w.az)) { w.cz += w.sz; w.Dz += (unsigned)ONE_CELL; }
+        w.tn = un; w.td = ud;
+    }
     return cross;
 }
 

@@ -307,35 +307,17 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             for (int j = 0; j < 4; ++j) {
                 float v[4] = {0.f, 0.f, 0.f, 1.0f};
                 if (key[j] >= 0) {
-                    if (kc[j].y == 0.0f && kc[j].x > 0.0f) {
-                        // no sub-grid term: kappa_b = kappa_HI sigma_b for every bin,
-                        // so sigma_b a_b / kappa_b = a_b / kappa_HI (one reciprocal)
-                        float he = 0.0f;
 #pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            float tr, ab;
-                            absorb_transmit(kc[j].x * S.sig[b] * ds[j], ab, tr);
-                            const float a = ph[b] * ab;
-                            ph[b] *= tr;
-                            v[0] += a;
-                            he = fmaf(S.eh[b], a, he);
-                        }
-                        const float r = __frcp_rn(kc[j].x);
-                        v[1] = v[0] * r;
-                        v[2] = he * r;
-                    } else {
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
-                            float tr, ab;
-                            absorb_transmit(kb * ds[j], ab, tr);
-                            const float a = ph[b] * ab;
-                            const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds[j];
-                            ph[b] *= tr;
-                            v[0] += a;
-                            v[1] = fmaf(S.sig[b], phin, v[1]);
-                            v[2] = fmaf(S.sige[b], phin, v[2]);
-                        }
+                    for (int b = 0; b < NB; ++b) {
+                        const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
+                        float tr, ab;
+                        absorb_transmit(kb * ds[j], ab, tr);
+                        const float a = ph[b] * ab;
+                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds[j];
+                        ph[b] *= tr;
+                        v[0] += a;
+                        v[1] = fmaf(S.sig[b], phin, v[1]);
+                        v[2] = fmaf(S.sige[b], phin, v[2]);
                     }
                     last = key[j];
                     lastk = kc[j];
@@ -552,7 +534,8 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                     xb = xbn;
                     if (conv) break;
                 }
-                const float x1 = fmaf(x0f, ef, gf * idt);
+                // x1 + y1 = 1 holds to rounding: keep x1 in [0, 1]
+                const float x1 = fminf(fmaf(x0f, ef, gf * idt), 1.0f);
                 const double y1 = fma(y0, (double)ef, (double)(gf * bdt));   // neutral fraction kept in FP64
                 float T = T0;
                 if (!S.isothermal) {
