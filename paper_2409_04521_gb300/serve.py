@@ -52,12 +52,17 @@ def plan_capacity(hbm_budget_bytes: float, nbins: int, max_grid: int, queue_frac
 
 
 def serve(requests, hbm_budget_bytes=150e9, max_sims=256, max_grid=160, nbins=3, emitter_capacity=65536,
-          admit_queue_fraction=0.5, launch=None, clock=time.perf_counter, keep_fields=False, stream=None):
+          admit_queue_fraction=0.5, launch=None, clock=time.perf_counter, keep_fields=False, stream=None,
+          batch=None, sleep=time.sleep):
     """Run `requests` = [(arrival_seconds, problem), ...] (sorted by arrival)
-    through one continuously batched engine.  Returns (results, stats)."""
-    rays, cells = plan_capacity(hbm_budget_bytes, nbins, max_grid)
-    B = Batch(max_sims=max_sims, max_grid=max_grid, nbins=nbins, ray_capacity=rays, cell_capacity=cells,
-              emitter_capacity=emitter_capacity, use_graph=True, stream=stream)
+    through one continuously batched engine.  Returns (results, stats).
+    `batch` replaces the engine (an object with the Batch methods)."""
+    if batch is None:
+        rays, cells = plan_capacity(hbm_budget_bytes, nbins, max_grid)
+        B = Batch(max_sims=max_sims, max_grid=max_grid, nbins=nbins, ray_capacity=rays, cell_capacity=cells,
+                  emitter_capacity=emitter_capacity, use_graph=True, stream=stream)
+    else:
+        B = batch
     if launch:
         B.set_launch(*launch)
     pending = list(enumerate(requests))
@@ -86,7 +91,7 @@ def serve(requests, hbm_budget_bytes=150e9, max_sims=256, max_grid=160, nbins=3,
             # idle: wait for the next arrival
             wait = pending[0][1][0] - (clock() - t0)
             if wait > 0:
-                time.sleep(min(wait, 0.01))
+                sleep(min(wait, 0.01))
             continue
         peak_active = max(peak_active, len(active))
         B.step()
