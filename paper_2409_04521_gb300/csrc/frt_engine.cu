@@ -331,6 +331,17 @@ flexrt_status Engine::make_sim(const flexrt_grid *grid, const flexrt_box *box, c
     h.kap_sub0 = m.lambda0_cm_comoving > 0 ? (float)(h.dx_com / m.lambda0_cm_comoving) : 0.0f;
     h.x_init = opt.x_init; h.T_init = opt.T_init;
     h.nref = 1.0;
+    // an isothermal run evaluates its rate coefficients once (same fits as
+    // the per-cell device evaluation, in double precision)
+    {
+        const double T = opt.T_init, lam = 2.0 * 157807.0 / T;
+        const double aB = 2.753e-14 * std::pow(lam, 1.5) / std::pow(1.0 + std::pow(lam / 2.740, 0.407), 2.242);
+        const double ci = lam > 180.0 ? 0.0
+                                      : 21.11 * std::pow(T, -1.5) * std::exp(-0.5 * lam) * std::pow(lam, -1.089) /
+                                            std::pow(1.0 + std::pow(lam / 0.354, 0.874), 1.101);
+        h.alpha_iso = (float)(opt.rates ? aB : opt.alpha_B_const);
+        h.coll_iso = (float)(opt.rates ? ci : 0.0);
+    }
     return FLEXRT_OK;
 }
 

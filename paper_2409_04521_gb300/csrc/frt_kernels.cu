@@ -480,13 +480,19 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
 // chemistry
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
+    // per-simulation absorbed totals, then the active cell ranges
     extern __shared__ double sh_abs[];
-    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) sh_abs[i] = 0.0;
-    __syncthreads();
+    long long *s_pref = reinterpret_cast<long long *>(sh_abs + A.nsims);
+    long long *s_cell0 = s_pref + A.nsims + 1;
+    int *s_sim = reinterpret_cast<int *>(s_cell0 + A.nsims);
     const Ctl *C = A.ctl;
+    const int nrng = C->n_ranges;
+    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) sh_abs[i] = 0.0;
+    for (int i = threadIdx.x; i <= nrng; i += blockDim.x) s_pref[i] = A.rg.pref[i];
+    for (int i = threadIdx.x; i < nrng; i += blockDim.x) { s_cell0[i] = A.rg.cell0[i]; s_sim[i] = A.rg.sim[i]; }
+    __syncthreads();
     const bool err = C->err != 0;
     const long long n = C->ncell_active;
-    const int nrng = C->n_ranges;
     const long long nr = (n + 31) & ~31LL;
     const int lane = lane_id();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += (long long)gridDim.x * blockDim.x) {
@@ -496,10 +502,10 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
             int lo = 0, hi = nrng;  // largest r with pref[r] <= i
             while (hi - lo > 1) {
                 int mid = (lo + hi) >> 1;
-                if (A.rg.pref[mid] <= i) lo = mid; else hi = mid;
+                if (s_pref[mid] <= i) lo = mid; else hi = mid;
             }
-            sim = A.rg.sim[lo];
-            const long long g = A.rg.cell0[lo] + (i - A.rg.pref[lo]);
+            sim = s_sim[lo];
+            const long long g = s_cell0[lo] + (i - s_pref[lo]);
             const float4 d = A.cells.dep[g];
             A.cells.dep[g] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (A.cells.segcnt) A.cells.segcnt[g] = (int)d.w;
@@ -513,8 +519,9 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                 const float y0f = (float)y0, x0f = A.cells.x[g];
                 const float T0 = A.cells.T[g];
                 const float dtf = (float)S.dt;
-                const float alpha = S.rates ? alphaB_f(T0) : (float)S.alpha_const;
-                const float Cc = S.rates ? collion_f(T0) : 0.0f;
+                float alpha = S.alpha_iso, Cc = S.coll_iso;
+                if (!S.isothermal && S.rates) { alpha = alphaB_f(T0); Cc = collion_f(T0); }
+                else if (!S.isothermal) alpha = (float)S.alpha_const;
                 // Eq. 7-10 with n_e re-evaluated from <x>.  With i = Gamma + C n_e,
                 // b = alpha n_e, r = dt (i + b), e = e^-r, g = (1 - e)/r and
                 // h = (1 - g)/r, the solution x(t) = x_eq + (x0 - x_eq) e^{-t/t_i}
@@ -725,7 +732,9 @@ int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims) {
     return n;
 }
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st) {
-    k_chem<<<blocks, 256, (size_t)a.nsims * sizeof(double), st>>>(a);
+    const size_t sh = (size_t)a.nsims * sizeof(double) + (size_t)(2 * a.nsims + 1) * sizeof(long long) +
+                      (size_t)a.nsims * sizeof(int);
+    k_chem<<<blocks, 256, sh, st>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_t st) {

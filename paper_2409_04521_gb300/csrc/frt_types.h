@@ -42,6 +42,7 @@ struct SimDev {
     double ksc;             // sigma_ref * dx_phys: tau per cell per (n_HI in cm^-3)
     double inv_nH_mean, inv_gamma_ref, y_thr;  // 1/<n_H>, 1/Gamma_ref, 1 - x threshold
     float kap_sub0;         // dx_com / lambda0
+    float alpha_iso, coll_iso;  // rate coefficients at T_init (isothermal runs)
     float compton_c;        // Compton cooling coefficient at this redshift (erg s^-1 K^-1)
     float Tcmb;             // K
     double nref;            // photons per code photon
