@@ -67,6 +67,7 @@ class Config(C.Structure):
         ("seed", C.c_uint64),
         ("rotate", C.c_int32), ("isothermal", C.c_int32), ("rates", C.c_int32), ("chem_iters", C.c_int32),
         ("alpha_const", C.c_double), ("x_init", C.c_double), ("T_init", C.c_double),
+        ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double),
     ]
 
 
@@ -108,6 +109,16 @@ def lib():
             L.or_get_rays.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int64), P(C.c_int32), P(C.c_int32),
                                       P(C.c_int32), P(C.c_double), C.c_int64]
             L.or_get_rays.restype = C.c_int64
+            L.or_get_rays_aux.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_int64),
+                                          P(C.c_double), C.c_int64]
+            L.or_get_rays_aux.restype = C.c_int64
+            L.or_apply_merge.argtypes = [C.c_void_p, C.c_double]
+            L.or_merge_pixel.argtypes = [C.c_int, P(C.c_int32), P(C.c_int32)]
+            L.or_merge_pixel.restype = C.c_int64
+            L.or_vertex_child.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int64]
+            L.or_vertex_child.restype = C.c_int64
+            L.or_rank_content.argtypes = [P(C.c_double), C.c_int, C.c_int]
+            L.or_rank_content.restype = C.c_float
             L.or_num_emitters.argtypes = [C.c_void_p]
             L.or_num_emitters.restype = C.c_int32
             L.or_config_size.restype = C.c_int64
@@ -180,6 +191,27 @@ def traverse(p0, d, n):
     return cells[:k].copy(), ds[:k].copy(), bool(esc.value)
 
 
+def merge_pixel(level: int, Rq, d) -> int:
+    """Pixel at `level` of the fixed-point direction d on the merge sphere
+    rotated by Rq (Sec. 3.3), decided in single precision."""
+    Rq = np.ascontiguousarray(np.asarray(Rq, np.int32).reshape(9))
+    d = np.ascontiguousarray(np.asarray(d, np.int32).reshape(3))
+    return int(lib().or_merge_pixel(level, _p(Rq, C.c_int32), _p(d, C.c_int32)))
+
+
+def vertex_child(l_merge: int, pm: int, level: int, m: int, c: int) -> int:
+    """Pixel (level + m) of child c of a merged ray of `level` centred on
+    merge pixel pm of level l_merge."""
+    return int(lib().or_vertex_child(l_merge, pm, level, m, c))
+
+
+def rank_content(N, E: int = 0) -> float:
+    """A ray's photons as the merge ranks them: the single-precision sum of
+    its bins, in bin order, in units of 2^E photons."""
+    N = np.ascontiguousarray(np.asarray(N, np.float64).reshape(-1))
+    return float(lib().or_rank_content(_p(N, C.c_double), len(N), E))
+
+
 def alpha_B(T: float) -> float:
     return lib().or_alpha_B(T)
 
@@ -239,6 +271,9 @@ class OracleSim:
         c.seed = o.seed
         c.rotate, c.isothermal, c.rates, c.chem_iters = int(o.rotate), int(o.isothermal), int(o.rates), o.chem_iters
         c.alpha_const, c.x_init, c.T_init = o.alpha_B_const, o.x_init, o.T_init
+        c.merge = int(getattr(o, "merge", False))
+        c.l_merge = int(getattr(o, "l_merge", 0))
+        c.n_ex = float(getattr(o, "n_ex", 0.0))
         nH = np.ascontiguousarray(prob.nH, np.float64).reshape(-1)
         self.ncell = nH.size
         self.nb = sp.nbins
@@ -260,6 +295,11 @@ class OracleSim:
         r = lib().or_step(self._h, dt)
         if r != 0:
             raise RuntimeError(f"oracle step failed ({r})")
+
+    def apply_merge(self, dt: float):
+        """Test hook: merge the live rays as at the end of the last step."""
+        if lib().or_apply_merge(self._h, dt) != 0:
+            raise RuntimeError("oracle merge failed")
 
     def fields(self):
         out = {k: np.zeros(self.ncell) for k in ("gamma_HI", "x_HII", "T", "n_HI")}
@@ -298,7 +338,18 @@ class OracleSim:
         N = np.zeros((n, self.nb))
         lib().or_get_rays(self._h, _p(lv, C.c_int32), _p(pix, C.c_int64), _p(em, C.c_int32),
                           _p(bi, C.c_int32), _p(d, C.c_int32), _p(N, C.c_double), n)
-        return dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
+        kind = np.zeros(n, np.int32)
+        vflag = np.zeros(n, np.int32)
+        A = np.zeros(n, np.int32)
+        P = np.zeros((n, 3), np.int64)
+        thr = np.zeros(n)
+        lib().or_get_rays_aux(self._h, _p(kind, C.c_int32), _p(vflag, C.c_int32), _p(A, C.c_int32),
+                              _p(P, C.c_int64), _p(thr, C.c_double), n)
+        # emitter: the emitter of a cast ray; for a merged ray 2^31 + the
+        # local index of the cell it was merged in (its rotation key)
+        em64 = np.where(kind == 1, em.astype(np.int64) + (1 << 31), em.astype(np.int64))
+        return dict(level=lv, pixel=pix, emitter=em64, birth=bi, dir=d, N=N, merged=kind.astype(bool),
+                    vertex=vflag.astype(bool), A=A, P=P, thr=thr)
 
     def num_emitters(self):
         return lib().or_num_emitters(self._h)

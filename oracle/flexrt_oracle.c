@@ -16,6 +16,10 @@
  *                       absorbed in every cell it crosses;
  *   Sec. 3.2, Eq. 2-3 -- a level-l ray splits into (l+1, 4p+i), i=0..3, once
  *                       its distance from the source reaches r_split(l);
+ *   Sec. 3.3, Eq. 4  -- optional ray merging at the end of each step: the
+ *                       N_ex*N_RT brightest rays are exempt, the others merge
+ *                       per (cell, pixel of a randomly oriented level-l_merge
+ *                       sphere of that cell);
  *   Sec. 4.2, Eq. 13 and 17 -- tau = kappa*ds and the cell-averaged
  *                       photo-ionisation rate for a finite mean free path
  *                       (kappa = n_HI sigma + 1/lambda_mfp);
@@ -277,6 +281,119 @@ void or_split_table(double n_min, int32_t K[OR_MAXL])
 /* Returns the number of in-box segments; *escaped = 1 if the ray left the    */
 /* box [0,n)^3 (open boundaries).                                             */
 /* ------------------------------------------------------------------------- */
+/* Merge-sphere pixel of a direction (Sec. 3.3)                               */
+/* ------------------------------------------------------------------------- */
+/* Which rays merge is decided by the pixel each falls in on the randomly
+ * oriented level-l_merge sphere of its cell.  That is an integer decided by
+ * floating point, so it is evaluated in single precision as one fixed
+ * sequence of correctly rounded operations (the GPU evaluates the same
+ * sequence): v = Rq^T d with the quantised rotation (entries below 2^24 in
+ * magnitude, exact in float) and the fixed-point direction, then the NESTED
+ * ang2pix of Gorski et al. (2005), with the azimuth from an arctangent
+ * series instead of a library atan2. */
+
+static int64_t spread_bits(int64_t v) /* bit i of v to bit 2i */
+{
+    int64_t out = 0;
+    for (int i = 0; i < 31; ++i)
+        if (v & ((int64_t)1 << i)) out |= (int64_t)1 << (2 * i);
+    return out;
+}
+
+/* arctan(t) / (pi/2) for 0 <= t <= 1.  Above tan(pi/8), arctan t = pi/4 +
+ * arctan u with u = (t-1)/(t+1); then the Taylor series of arctan u to the
+ * u^19 term (|u| <= tan(pi/8): the next term is below 1e-9 relative). */
+static float f_atan_quarter(float t)
+{
+    static const float c[10] = {1.0f, -0.333333343f, 0.200000003f, -0.142857149f, 0.111111112f,
+                                -0.0909090936f, 0.0769230798f, -0.0666666701f, 0.0588235296f,
+                                -0.0526315793f};
+    float base = 0.0f, u = t;
+    if (t > 0.414213568f) {
+        u = (t - 1.0f) / (t + 1.0f);
+        base = 0.5f;
+    }
+    float s2 = u * u;
+    float p = c[9];
+    for (int k = 8; k >= 0; --k) p = p * s2 + c[k];
+    float a = u * p;
+    return base + a * 0.636619747f;
+}
+
+/* azimuth of (x, y) in quarter turns, in [0, 4) */
+static float f_phi_quarter(float x, float y)
+{
+    float ax = fabsf(x), ay = fabsf(y);
+    if (ax == 0.0f && ay == 0.0f) return 0.0f;
+    float a = ax >= ay ? f_atan_quarter(ay / ax) : 1.0f - f_atan_quarter(ax / ay);
+    float tt;
+    if (x >= 0.0f) tt = y >= 0.0f ? a : 4.0f - a;
+    else tt = y >= 0.0f ? 2.0f - a : 2.0f + a;
+    if (tt >= 4.0f) tt = tt - 4.0f;
+    return tt;
+}
+
+/* NESTED pixel at `level` of direction d (fixed point) on the sphere rotated
+ * by Rq (direction = Rq . pixel vector, so the pixel vector is Rq^T d). */
+int64_t or_merge_pixel(int level, const int32_t Rq[9], const int32_t d[3])
+{
+    const float df0 = (float)d[0], df1 = (float)d[1], df2 = (float)d[2];
+    float v[3];
+    for (int j = 0; j < 3; ++j) {
+        float a = (float)Rq[j] * df0;
+        float b = (float)Rq[3 + j] * df1;
+        float c = (float)Rq[6 + j] * df2;
+        v[j] = (a + b) + c;
+    }
+    const int64_t nside = (int64_t)1 << level;
+    const float ns = (float)nside;
+    float s2 = v[0] * v[0] + v[1] * v[1];
+    float r = sqrtf(s2 + v[2] * v[2]);
+    float z = v[2] / r;
+    float za = fabsf(z);
+    float tt = f_phi_quarter(v[0], v[1]);
+    int64_t face, ix, iy;
+    if (za <= 0.666666687f) {                       /* equatorial belt */
+        float t1 = ns * (0.5f + tt);
+        float t2 = ns * (z * 0.75f);
+        int64_t jp = (int64_t)(t1 - t2), jm = (int64_t)(t1 + t2);
+        int64_t ifp = jp >> level, ifm = jm >> level;
+        face = ifp == ifm ? (ifp | 4) : (ifp < ifm ? ifp : ifm + 8);
+        ix = jm & (nside - 1);
+        iy = nside - (jp & (nside - 1)) - 1;
+    } else {                                         /* polar caps */
+        int64_t ntt = (int64_t)tt;
+        if (ntt > 3) ntt = 3;
+        float tp = tt - (float)ntt;
+        float omz = s2 / (r * (r + fabsf(v[2])));    /* 1 - |z| without cancellation */
+        float tmp = ns * sqrtf(3.0f * omz);
+        int64_t jp = (int64_t)(tp * tmp), jm = (int64_t)((1.0f - tp) * tmp);
+        if (jp > nside - 1) jp = nside - 1;
+        if (jm > nside - 1) jm = nside - 1;
+        if (z >= 0.0f) { face = ntt; ix = nside - jm - 1; iy = nside - jp - 1; }
+        else { face = ntt + 8; ix = jp; iy = jm; }
+    }
+    return face * nside * nside + spread_bits(ix) + 2 * spread_bits(iy);
+}
+
+/* Children of a merged "vertex" ray (reading of Sec. 3.2-3.3).  A merged ray
+ * points along the centre of merge pixel pm (level lm) and carries level
+ * l >= lm.  In the NESTED scheme the centre of a pixel is the corner shared
+ * by its four children, and at every deeper level by exactly four pixels:
+ * descend into child i, then always into the sub-pixel 3-i that touches that
+ * corner.  These four level-(l+1) pixels tile the solid angle of one level-l
+ * pixel around the merged direction and are its split children; child
+ * c = i*4^(m-1) + j of an m-level split is their descendant j. */
+int64_t or_vertex_child(int lm, int64_t pm, int l, int m, int64_t c)
+{
+    const int depth = l + 1 - lm;                   /* >= 1 */
+    const int64_t i = c >> (2 * (m - 1)), j = c & (((int64_t)1 << (2 * (m - 1))) - 1);
+    int64_t q = pm * 4 + i;
+    for (int k = 1; k < depth; ++k) q = q * 4 + (3 - i);
+    return (q << (2 * (m - 1))) + j;
+}
+
+/* ------------------------------------------------------------------------- */
 int or_traverse(const int64_t p0[3], const int32_t d[3], const int32_t n[3],
                 int32_t cells[4][3], double ds[4], int *escaped)
 {
@@ -421,10 +538,18 @@ double or_temperature(double T, double nH, double x0, double x1, double xbar,
 typedef struct {
     int32_t l;       /* HEALPix level                */
     int64_t p;       /* NESTED pixel                 */
-    int32_t e;       /* emitter (source cell)        */
-    int32_t b;       /* birth step                   */
+    int32_t e;       /* emitter (source cell); merged rays: local cell of the merge */
+    int32_t b;       /* birth step; merged rays: step of the merge  */
     int32_t d[3];    /* fixed-point direction        */
     double N[OR_MAXB]; /* photons per bin            */
+    /* merged rays (Sec. 3.3) and their split children only */
+    int32_t kind;    /* 0 cast by an emitter, 1 made by a merge           */
+    int32_t vflag;   /* 1: unsplit merged ray of level l > l_merge, centred
+                        on the vertex shared by its four level-(l+1) children
+                        (p is then the level-l_merge merge pixel)         */
+    int32_t A;       /* distance travelled at the merge, in cells         */
+    int64_t P[3];    /* position at the merge (fixed point)               */
+    double thr;      /* termination threshold, photons                    */
 } or_ray;
 
 typedef struct {
@@ -440,6 +565,8 @@ typedef struct {
     uint64_t seed;
     int32_t rotate, isothermal, rates, chem_iters;
     double alpha_const, x_init, T_init;
+    int32_t merge, l_merge;   /* ray merging on/off, level of the merge sphere */
+    double n_ex;              /* rays exempt from merging per RT cell          */
 } or_config;
 
 typedef struct {
@@ -577,6 +704,162 @@ static void deposit_all(or_sim *S, int64_t cell, const double *N, const double *
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Ray merging at the end of a step (Sec. 3.3, Eq. 4)                         */
+/* ------------------------------------------------------------------------- */
+/* Readings where the section is silent:
+ *  - rank: a ray's photon content is the sum over bins in single precision
+ *    (an integer decision taken in the precision of the GPU path); with
+ *    K = floor(N_ex * N_RT), every ray whose content is at least the K-th
+ *    largest is exempt (ties at the K-th value are all exempt);
+ *  - cell: the cell holding the ray's end point (floor per axis); a ray whose
+ *    end point is on the far face of the box is not merged;
+ *  - sphere: one random rotation per (cell, step), drawn like an emitter's
+ *    with the key 2^31 + local cell index;
+ *  - merged ray: photons summed per bin; position, distance travelled and
+ *    level are photon-weighted means of the constituents' (rounded to the
+ *    fixed-point grid, whole cells and whole levels; the level at least
+ *    l_merge); direction the centre of the merge pixel; termination threshold
+ *    the sum of the constituents'.  A group of one ray keeps the ray. */
+#define OR_MERGE_KEY ((int64_t)1 << 31)
+
+typedef struct { int64_t key, idx; } or_mkey;
+
+static int cmp_mkey(const void *a, const void *b)
+{
+    const or_mkey *x = (const or_mkey *)a, *y = (const or_mkey *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static int cmp_float_desc(const void *a, const void *b)
+{
+    float x = *(const float *)a, y = *(const float *)b;
+    return x > y ? -1 : (x < y);
+}
+
+/* Photons of a ray as the merge ranks them: the single-precision sum, in bin
+ * order, of its bins in units of 2^E photons.  Rounding commutes with a
+ * power-of-two unit, so the order (and its ties) is the same for any unit
+ * that keeps the values in the normal single-precision range. */
+float or_rank_content(const double *N, int nb, int E)
+{
+    float t = (float)ldexp(N[0], -E);
+    for (int b = 1; b < nb; ++b) t = t + (float)ldexp(N[b], -E);
+    return t;
+}
+
+static int or_merge(or_sim *S, double dt, int64_t s)
+{
+    const or_config *c = &S->c;
+    const int64_t n = S->nray;
+    const double Kd = floor(c->n_ex * (double)S->ncell);
+    if (Kd >= (double)n) return 0;
+    const int64_t K = (int64_t)Kd;
+    const int64_t ncast = 12LL << (2 * c->l_src);
+    const int64_t ndir = 12LL << (2 * c->l_merge);
+    float *T = malloc((size_t)n * sizeof(float)), *Ts = malloc((size_t)n * sizeof(float));
+    or_mkey *mk = malloc((size_t)n * sizeof(or_mkey));
+    int64_t (*p1) = malloc((size_t)n * 3 * sizeof(int64_t));
+    char *dead = calloc((size_t)n, 1);
+    if (!T || !Ts || !mk || !p1 || !dead) return -1;
+    double nmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int b = 0; b < c->nb; ++b) t += S->rays[i].N[b];
+        if (t > nmax) nmax = t;
+    }
+    int E = 0;
+    frexp(nmax, &E);                                   /* unit: the largest content is below 1 */
+    for (int64_t i = 0; i < n; ++i) Ts[i] = T[i] = or_rank_content(S->rays[i].N, c->nb, E);
+    float Tstar = INFINITY;
+    if (K > 0) {
+        qsort(Ts, (size_t)n, sizeof(float), cmp_float_desc);
+        Tstar = Ts[K - 1];
+    }
+    int64_t nm = 0;
+    const int64_t nn[3] = {c->nx, c->ny, c->nz};
+    for (int64_t i = 0; i < n; ++i) {
+        const or_ray *r = &S->rays[i];
+        if (T[i] >= Tstar) continue;                        /* exempt */
+        int64_t *q = p1 + 3 * i, cell[3];
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (r->kind == 0) q[a] = (2 * (int64_t)S->ecell[3 * r->e + a] + 1) * (OR_S / 2) + (s - r->b + 1) * (int64_t)r->d[a];
+            else q[a] = r->P[a] + (s - r->b) * (int64_t)r->d[a];
+            cell[a] = floordiv64(q[a], OR_S);
+            if (cell[a] < 0 || cell[a] >= nn[a]) inside = 0;
+        }
+        if (!inside) continue;
+        int64_t local = (cell[2] * c->ny + cell[1]) * c->nx + cell[0];
+        double R[9];
+        int32_t Rq[9];
+        or_rotation(c->seed, OR_MERGE_KEY + local, s, c->rotate, R, Rq);
+        mk[nm].key = local * ndir + or_merge_pixel(c->l_merge, Rq, r->d);
+        mk[nm].idx = i;
+        nm++;
+    }
+    qsort(mk, (size_t)nm, sizeof(or_mkey), cmp_mkey);
+    or_ray *merged = NULL;
+    int64_t nmerged = 0, mcap = 0;
+    for (int64_t g0 = 0; g0 < nm;) {
+        int64_t g1 = g0 + 1;
+        while (g1 < nm && mk[g1].key == mk[g0].key) g1++;
+        if (g1 - g0 >= 2) {
+            or_ray m;
+            memset(&m, 0, sizeof(m));
+            double W = 0.0, wp[3] = {0, 0, 0}, wa = 0.0, wl = 0.0, thr = 0.0;
+            for (int64_t k = g0; k < g1; ++k) {
+                const int64_t i = mk[k].idx;
+                const or_ray *r = &S->rays[i];
+                double w = 0.0;
+                for (int b = 0; b < c->nb; ++b) { w += r->N[b]; m.N[b] += r->N[b]; }
+                for (int a = 0; a < 3; ++a) wp[a] += w * (double)p1[3 * i + a];
+                double dist = r->kind == 0 ? (double)(s - r->b + 1) : (double)(r->A + (s - r->b));
+                wa += w * dist;
+                wl += w * (double)r->l;
+                thr += r->kind == 0 ? c->eps_term * S->endot[r->e] * dt / (double)ncast * ldexp(1.0, -2 * (r->l - c->l_src))
+                                    : r->thr;
+                W += w;
+                dead[i] = 1;
+            }
+            const int64_t local = mk[g0].key / ndir, pm = mk[g0].key % ndir;
+            const int64_t cell[3] = {local % c->nx, (local / c->nx) % c->ny, local / ((int64_t)c->nx * c->ny)};
+            for (int a = 0; a < 3; ++a) {
+                int64_t v = (int64_t)rint(wp[a] / W), lo = cell[a] * OR_S;
+                m.P[a] = v < lo ? lo : (v > lo + OR_S - 1 ? lo + OR_S - 1 : v);
+            }
+            int64_t A = (int64_t)rint(wa / W);
+            m.A = (int32_t)(A < 0 ? 0 : (A > 65535 ? 65535 : A));
+            int64_t L = (int64_t)rint(wl / W);
+            if (L < c->l_merge) L = c->l_merge;
+            if (L > c->l_max) L = c->l_max;
+            m.l = (int32_t)L;
+            m.p = pm;
+            m.kind = 1;
+            m.vflag = L > c->l_merge;
+            m.e = (int32_t)local;
+            m.b = (int32_t)s;
+            m.thr = thr;
+            double R[9];
+            int32_t Rq[9];
+            or_rotation(c->seed, OR_MERGE_KEY + local, s, c->rotate, R, Rq);
+            or_direction(c->l_merge, pm, Rq, m.d);
+            if (grow_rays(&merged, &mcap, nmerged + 1)) return -1;
+            merged[nmerged++] = m;
+        }
+        g0 = g1;
+    }
+    int64_t w = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (!dead[i]) S->rays[w++] = S->rays[i];
+    if (grow_rays(&S->rays, &S->rcap, w + nmerged)) return -1;
+    for (int64_t k = 0; k < nmerged; ++k) S->rays[w++] = merged[k];
+    S->nray = w;
+    free(T); free(Ts); free(mk); free(p1); free(dead); free(merged);
+    return 0;
+}
+
 int or_step(or_sim *S, double dt)
 {
     const or_config *c = &S->c;
@@ -594,6 +877,7 @@ int or_step(or_sim *S, double dt)
         double N0 = S->endot[e] * dt / (double)ncast;
         for (int64_t p = 0; p < ncast; ++p) {
             or_ray *r = &S->rays[S->nray++];
+            memset(r, 0, sizeof(*r));
             r->l = c->l_src; r->p = p; r->e = e; r->b = (int32_t)s;
             or_direction(c->l_src, p, Rq, r->d);
             for (int b = 0; b < c->nb; ++b) {
@@ -611,10 +895,19 @@ int or_step(or_sim *S, double dt)
     int64_t segs = 0;
     for (int64_t ir = 0; ir < S->nray; ++ir) {
         or_ray r = S->rays[ir];
-        int64_t age = s - r.b;
-        int64_t p0[3];
-        const int32_t *ec = S->ecell + 3 * r.e;
-        for (int a = 0; a < 3; ++a) p0[a] = (2 * (int64_t)ec[a] + 1) * (OR_S / 2) + age * (int64_t)r.d[a];
+        /* age: distance travelled before this step, in cells.  A ray cast by
+         * an emitter starts at the emitter's cell centre; a merged ray at its
+         * merge position, with the distance its constituents had travelled */
+        int64_t age, p0[3];
+        if (r.kind == 0) {
+            age = s - r.b;
+            const int32_t *ec = S->ecell + 3 * r.e;
+            for (int a = 0; a < 3; ++a) p0[a] = (2 * (int64_t)ec[a] + 1) * (OR_S / 2) + age * (int64_t)r.d[a];
+        } else {
+            int64_t since = s - r.b - 1;
+            age = r.A + since;
+            for (int a = 0; a < 3; ++a) p0[a] = r.P[a] + since * (int64_t)r.d[a];
+        }
         int32_t cells[4][3];
         double ds[4];
         int esc;
@@ -649,8 +942,8 @@ int or_step(or_sim *S, double dt)
         /* termination: below eps of the ray's unattenuated content */
         double tot = 0.0;
         for (int b = 0; b < c->nb; ++b) tot += r.N[b];
-        double N0 = S->endot[r.e] * dt / (double)ncast;
-        double thr = c->eps_term * N0 * ldexp(1.0, -2 * (r.l - c->l_src));
+        double thr = r.kind == 0 ? c->eps_term * S->endot[r.e] * dt / (double)ncast * ldexp(1.0, -2 * (r.l - c->l_src))
+                                 : r.thr;
         if (fabs(tot - thr) <= 1e-4 * thr) S->near_threshold++;
         if (tot < thr) {
             deposit_all(S, last, r.N, kap);
@@ -662,13 +955,17 @@ int or_step(or_sim *S, double dt)
         int64_t nchild = (int64_t)1 << (2 * m);
         if (grow_rays(&out, &ocap, nout + nchild)) return -2;
         if (m == 0) { out[nout++] = r; continue; }
+        /* children keep the rotation of their parent's sphere (Sec. 3.2):
+         * the emitter's at the birth step, or the merge cell's at the merge */
         double R[9];
         int32_t Rq[9];
-        or_rotation(c->seed, r.e, r.b, c->rotate, R, Rq);
+        or_rotation(c->seed, r.kind == 0 ? (int64_t)r.e : OR_MERGE_KEY + r.e, r.b, c->rotate, R, Rq);
         for (int64_t j = 0; j < nchild; ++j) {
             or_ray ch = r;
             ch.l = r.l + m;
-            ch.p = r.p * nchild + j;
+            ch.p = r.vflag ? or_vertex_child(c->l_merge, r.p, r.l, m, j) : r.p * nchild + j;
+            ch.vflag = 0;
+            ch.thr = r.thr / (double)nchild;
             or_direction(ch.l, ch.p, Rq, ch.d);
             for (int b = 0; b < c->nb; ++b) ch.N[b] = r.N[b] / (double)nchild;
             out[nout++] = ch;
@@ -676,6 +973,7 @@ int or_step(or_sim *S, double dt)
     }
     free(S->rays);
     S->rays = out; S->nray = nout; S->rcap = ocap;
+    if (c->merge && or_merge(S, dt, s)) return -2;
     S->segments_last = segs;
     S->segments_total += segs;
     S->in_flight = 0.0;
@@ -747,3 +1045,28 @@ int64_t or_get_rays(const or_sim *S, int32_t *lv, int64_t *pix, int32_t *em, int
 }
 int32_t or_num_emitters(const or_sim *S) { return S->ne; }
 int64_t or_config_size(void) { return (int64_t)sizeof(or_config); }
+
+/* Test hook: merge the live rays as at the end of the last step taken
+ * (whether or not merging is switched on), with that step's dt. */
+int or_apply_merge(or_sim *S, double dt)
+{
+    if (S->step < 1) return -1;
+    if (or_merge(S, dt, S->step - 1)) return -2;
+    S->in_flight = 0.0;
+    for (int64_t i = 0; i < S->nray; ++i)
+        for (int b = 0; b < S->c.nb; ++b) S->in_flight += S->rays[i].N[b];
+    return 0;
+}
+
+/* merged-ray fields of the live rays, same order as or_get_rays */
+int64_t or_get_rays_aux(const or_sim *S, int32_t *kind, int32_t *vflag, int32_t *A, int64_t *P, double *thr,
+                        int64_t cap)
+{
+    int64_t n = S->nray < cap ? S->nray : cap;
+    for (int64_t i = 0; i < n; ++i) {
+        const or_ray *r = &S->rays[i];
+        kind[i] = r->kind; vflag[i] = r->vflag; A[i] = r->A; thr[i] = r->thr;
+        for (int a = 0; a < 3; ++a) P[3 * i + a] = r->P[a];
+    }
+    return S->nray;
+}

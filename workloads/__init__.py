@@ -82,6 +82,9 @@ class Options:
     alpha_B_const: float = 2.59e-13
     x_init: float = 1.2e-3
     T_init: float = 1.0e4
+    merge: bool = False                 # ray merging at the end of each step
+    l_merge: int = 0                    # HEALPix level of the merge sphere
+    n_ex: float = 16.0                  # rays exempt from merging per RT cell
 
 
 @dc.dataclass
