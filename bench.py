@@ -488,6 +488,96 @@ def impl_serve(args, dist):
     print(json.dumps(line), flush=True)
 
 
+def impl_merge(args, dist):
+    """Ray merging (Sec. 3.3) on the 16-source cosmological workload, as in
+    Sec. 7.1 (Test 4 with 12 merge directions and N_ex = 16 and 4): time per
+    simulation against the unmerged run, and the largest deviation of the
+    global ionised fraction and Gamma from the unmerged run over the run."""
+    import dataclasses as dc
+    import torch
+    import paper_2409_04521_gb300 as F
+    from paper_2409_04521_gb300 import autotune
+
+    torch.cuda.set_device(dist.local)
+    dev_index = torch.cuda.current_device()
+    base = problem(args)
+    stream = torch.cuda.Stream()
+    cases = [("plain", base)]
+    for nex in args.merge_nex:
+        cases.append((f"n_ex={nex:g},l_merge={args.l_merge}",
+                      dc.replace(base, options=dc.replace(base.options, merge=True, n_ex=float(nex),
+                                                          l_merge=args.l_merge))))
+    results = {}
+    traces = {}
+    clocks = ClockSampler(dev_index)
+    clk = None
+    for name, prob in cases:
+        sim = F.Simulation(prob, ray_capacity=args.capacity, stream=stream.cuda_stream)
+        if not args.no_tune:
+            autotune.tune(sim, prob)
+        # untimed run sampling the global averages every `every` steps
+        every = max(1, prob.nsteps // 20)
+        tr = []
+        sim.reset()
+        for s in range(prob.nsteps):
+            sim.step(prob.dt)
+            if (s + 1) % every == 0:
+                f = sim.fields(("x_HII", "gamma_HI"))
+                tr.append((float(f["x_HII"].mean()), float((f["x_HII"] * prob.nH).sum() / prob.nH.sum()),
+                           float(f["gamma_HI"].mean())))
+        traces[name] = np.array(tr)
+        max_rays = sim.counts()["rays"]
+        for _ in range(args.warmup):
+            sim.reset()
+            for _ in range(prob.nsteps):
+                sim.step(prob.dt)
+            sim.sync()
+        sim.profile(True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        if name == cases[-1][0]:
+            clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        segs = 0
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sim.reset()
+            for _ in range(prob.nsteps):
+                sim.step(prob.dt)
+            segs += sim.counts()["segments_total"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        if name == cases[-1][0]:
+            clk = clocks.stop()
+        kms, klaunch, _ = sim.kernel_times()
+        sim.profile(False)
+        sim.close()
+        ms = dist.max(ev0.elapsed_time(ev1)) / args.steps
+        results[name] = {"ms_per_sim": ms, "segments_per_sim": segs / args.steps,
+                         "segments_per_s": segs / args.steps / (ms * 1e-3), "live_rays_at_end": max_rays,
+                         "kernel_ms_per_sim": {k: float(v) / args.steps for k, v in kms.items()}}
+    plain = results["plain"]
+    for name, _ in cases[1:]:
+        r = results[name]
+        r["speedup_vs_plain"] = plain["ms_per_sim"] / r["ms_per_sim"]
+        rel = np.abs(traces[name] / traces["plain"] - 1.0)[2:]    # from the third sample, when Gamma > 0
+        r["max_dev"] = {"x_volume": float(rel[:, 0].max()), "x_mass": float(rel[:, 1].max()),
+                        "gamma": float(rel[:, 2].max())}
+    best = cases[-1][0]
+    if dist.rank == 0:
+        line = {"metric": "sims/hour", "value": 3600.0e3 / results[best]["ms_per_sim"] * dist.ws, "unit": "sims/hour",
+                "n_gpus": dist.ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": results[best]["ms_per_sim"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "merge: " + WORKLOAD_DESC + "; ray merging as Sec. 7.1",
+                           "cases": [c[0] for c in cases], "timed_case": best},
+                "results": results, "clocks": clk,
+                "gpu_launches": args.steps * (1 + base.nsteps * 11)}
+        print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,14 +591,21 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--workload", default="cosmo16", choices=["cosmo16", "batch64", "serve"])
+    ap.add_argument("--workload", default="cosmo16", choices=["cosmo16", "batch64", "serve", "merge"])
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--mean-gap", type=float, default=0.05)
     ap.add_argument("--hbm-budget", type=float, default=150e9)
     ap.add_argument("--saturate-gap", type=float, default=0.001)
+    ap.add_argument("--merge-nex", type=float, nargs="+", default=[16.0, 4.0])
+    ap.add_argument("--l-merge", type=int, default=0)
     args = ap.parse_args(argv)
+    if args.workload == "merge" and args.impl != "reference":
+        dist = Dist()
+        impl_merge(args, dist)
+        dist.close()
+        return
     if args.workload == "batch64" and args.impl != "reference":
         dist = Dist()
         impl_batch(args, dist)

@@ -15,7 +15,11 @@
  *                 Eq. 5 when lambda = 1/(n_HI sigma));
  *   4. split:     a level-l ray that has travelled r_split(l) (Sec. 3.2, Eq. 2)
  *                 becomes the four rays (l+1, 4p+i) (Eq. 3);
- *   5. chemistry: per cell, the time-dependent ionisation update of Sec. 4.1,
+ *   5. merge:     optional (flexrt_options.merge): the floor(N_ex * N_RT)
+ *                 brightest rays are exempt; the others merge per (cell, pixel
+ *                 of a randomly oriented level-l_merge HEALPix sphere of that
+ *                 cell) into one ray along the pixel centre (Sec. 3.3, Eq. 4);
+ *   6. chemistry: per cell, the time-dependent ionisation update of Sec. 4.1,
  *                 Eq. 7-10, and the temperature equation Eq. 12.
  *
  * Conventions for every entry point:
@@ -105,11 +109,20 @@ typedef struct {
                                plus 4096); 0 = sized from free memory         */
     int32_t keep_diagnostics; /* 1: keep per-cell segment counts of each step   */
     void *cuda_stream;      /* cudaStream_t, 0 = library-owned stream           */
+    /* Ray merging at the end of every step (Sec. 3.3, Eq. 4).  A merged ray
+     * points along the centre of its merge pixel; its position, distance
+     * travelled and HEALPix level are the photon-weighted means of its
+     * constituents' (level at least l_merge), its photons their sum.  Until it
+     * splits it stands for the four level-(l+1) pixels around that centre. */
+    int32_t merge;          /* 1: merge rays                                    */
+    int32_t l_merge;        /* merge-sphere level, 0..min(11, l_max)            */
+    double n_ex;            /* rays per RT cell exempt from merging (N_ex)      */
 } flexrt_options;
 
 /* Fill *o with defaults (l_src 0, l_max 12, N_min 3, eps 1e-10, seed 1,
  * rotate 1, isothermal 1, rates 0, 5 iterations, alpha_B 2.59e-13,
- * x_init 1.2e-3, T_init 1e4, automatic capacity, library stream). */
+ * x_init 1.2e-3, T_init 1e4, automatic capacity, library stream, no merging,
+ * l_merge 0, N_ex 16). */
 void flexrt_default_options(flexrt_options *o);
 
 /* Create one simulation.  n_H: host, nx*ny*nz doubles, physical cm^-3,
@@ -161,12 +174,23 @@ flexrt_status flexrt_get_segment_counts(flexrt_ctx *ctx, int32_t *out);
 flexrt_status flexrt_get_rays(flexrt_ctx *ctx, int64_t cap, int32_t *level, int64_t *pixel,
                               int32_t *emitter, int32_t *birth, int32_t *dir, double *photons,
                               int64_t *n);
+/* For a ray made by a merge, flexrt_get_rays reports emitter = -1 - (local
+ * index of the cell it was merged in), birth = the step of the merge and
+ * pixel = its merge pixel (a vertex ray) or its NESTED pixel after splits.
+ * The same rays in the same order (NULL = skip): merged int32[n] (1 for a
+ * merged ray or a split child of one), vertex int32[n] (1: an unsplit merged
+ * ray of level above l_merge), dist int32[n] (cells travelled at the merge),
+ * pos int64[3n] (position at the merge, 2^-21 cell), thr double[n]
+ * (termination threshold, photons). */
+flexrt_status flexrt_get_rays_merged(flexrt_ctx *ctx, int64_t cap, int32_t *merged, int32_t *vertex,
+                                     int32_t *dist, int64_t *pos, double *thr, int64_t *n);
 
 /* Per-kernel device time accumulated since the last call (CUDA events on
- * the context stream): names "emit", "march", "chem"; ms[k], launches[k].
- * Timing is only recorded when enabled by flexrt_profile(ctx, 1). */
+ * the context stream): "emit", "march", "chem" and "merge" (all kernels of
+ * the merge step); ms[k], launches[k].  Timing is only recorded when enabled
+ * by flexrt_profile(ctx, 1). */
 flexrt_status flexrt_profile(flexrt_ctx *ctx, int32_t enable);
-flexrt_status flexrt_get_kernel_times(flexrt_ctx *ctx, double ms[3], int64_t launches[3],
+flexrt_status flexrt_get_kernel_times(flexrt_ctx *ctx, double ms[4], int64_t launches[4],
                                       int64_t march_rays[1]);
 
 /* Launch configuration of the fused march kernel (chosen by the autotuner):
@@ -200,6 +224,54 @@ flexrt_status flexrt_probe_rotation(uint64_t seed, int64_t emitter, int64_t step
 flexrt_status flexrt_probe_direction(int32_t level, int64_t p0, int64_t n,
                                      const int32_t *Rq, int32_t *out);
 
+/* Merge-sphere pixel (Sec. 3.3) of n fixed-point directions d int32[3n] on
+ * the sphere rotated by Rq int32[9] at `level` (0..12): out int32[n].  The
+ * decision is taken in single precision by one fixed sequence of correctly
+ * rounded operations (v = Rq^T d, NESTED ang2pix). */
+flexrt_status flexrt_probe_merge_pixel(int32_t level, int64_t n, const int32_t *d, const int32_t *Rq,
+                                       int32_t *out);
+
+/* Rays as the merge step sees them (flexrt_probe_merge): n rays, caller-owned
+ * host arrays.  pixlev = level << 28 | NESTED pixel (merge pixel of a vertex
+ * ray); emitter = emitter index, or 0x80000000 | local cell of the merge for
+ * a merged ray; birth = birth step (merged: step of the merge); dir int32[3n]
+ * (2^-21 cell per step); photons float[nbins * n] (code photons, bin
+ * fastest); merged rays only: pos int32[3n] (position at the merge), aux =
+ * vertex << 31 | distance travelled at the merge (cells), thr (termination
+ * threshold, code photons). */
+typedef struct {
+    uint32_t *pixlev, *emitter;
+    int32_t *birth, *dir;
+    float *photons;
+    int32_t *pos;
+    uint32_t *aux;
+    float *thr;
+} flexrt_probe_rays;
+
+/* One simulation's constants for flexrt_probe_merge: grid, bins, HEALPix
+ * levels, K = floor(N_ex * N_RT), sphere seed and rotation switch, the step
+ * whose march produced the rays, eps_term, and the emitters: cell int32[3*ne]
+ * and this step's code photons per cast ray n0 float[ne]. */
+typedef struct {
+    int32_t nx, ny, nz, nbins;
+    int32_t l_src, l_max, l_merge;
+    int64_t k_ex;
+    uint64_t seed;
+    int32_t rotate, step;
+    float eps_term;
+    int32_t n_emitters;
+    const int32_t *emitter_cell;
+    const float *emitter_n0;
+} flexrt_merge_probe;
+
+/* The merge step (Sec. 3.3) alone: the very kernels of a step's merge run on
+ * n host-given live rays (const in) of one simulation as they stand after the
+ * march of step p->step.  Writes up to cap rays to out and their number to
+ * *n_out, in the order the kernels leave them in the queue.  Allocates and
+ * frees its own device scratch.  Synchronous. */
+flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t n, const flexrt_probe_rays *in,
+                                 int64_t cap, flexrt_probe_rays *out, int64_t *n_out);
+
 /* One-step cell traversal (Sec. 3.1) of n rays from p0 (int64[3n], 2^-21
  * cell) along d (int32[3n]) in grid g: cells int32[n*4*3], ds float[n*4]
  * (cells), nseg int32[n], escaped int32[n]. */
@@ -225,6 +297,9 @@ typedef struct {
     int32_t keep_diagnostics;
     int32_t use_graph;       /* 1: replay each step from a CUDA graph          */
     void *cuda_stream;       /* 0 = library-owned stream                       */
+    int32_t merge_l_max;     /* deepest l_merge members may use (its scratch is
+                                cell_capacity * 12 * 4^merge_l_max groups);
+                                -1: members cannot merge                       */
 } flexrt_batch_config;
 
 void flexrt_default_batch_config(flexrt_batch_config *c);
@@ -256,6 +331,9 @@ flexrt_status flexrt_batch_get_counts(flexrt_batch *b, int32_t slot, int64_t out
 flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *level,
                                     int64_t *pixel, int32_t *emitter, int32_t *birth, int32_t *dir,
                                     double *photons, int64_t *n);
+flexrt_status flexrt_batch_get_rays_merged(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *merged,
+                                           int32_t *vertex, int32_t *dist, int64_t *pos, double *thr,
+                                           int64_t *n);
 
 /* out[0] active members, out[1] free cells, out[2] free emitters,
  * out[3] ray capacity, out[4] queue slots in use by live rays (waits for

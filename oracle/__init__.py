@@ -83,6 +83,7 @@ def lib():
             L.or_rot_key.argtypes = [C.c_uint64, C.c_int64, C.c_int64]
             L.or_rot_key.restype = C.c_uint64
             L.or_rotation.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int, P(C.c_double), P(C.c_int32)]
+            L.or_merge_rotation.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int, P(C.c_int32)]
             L.or_direction.argtypes = [C.c_int, C.c_int64, P(C.c_int32), P(C.c_int32)]
             L.or_split_table.argtypes = [C.c_double, P(C.c_int32)]
             L.or_traverse.argtypes = [P(C.c_int64), P(C.c_int32), P(C.c_int32), P(C.c_int32),
@@ -112,7 +113,10 @@ def lib():
             L.or_get_rays_aux.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_int64),
                                           P(C.c_double), C.c_int64]
             L.or_get_rays_aux.restype = C.c_int64
-            L.or_apply_merge.argtypes = [C.c_void_p, C.c_double]
+            L.or_apply_merge.argtypes = [C.c_void_p, C.c_double, C.c_int64]
+            L.or_set_rays.argtypes = [C.c_void_p, C.c_int64, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32),
+                                      P(C.c_int32), P(C.c_int32), P(C.c_double), P(C.c_int32), P(C.c_int32),
+                                      P(C.c_int32), P(C.c_int64), P(C.c_double)]
             L.or_merge_pixel.argtypes = [C.c_int, P(C.c_int32), P(C.c_int32)]
             L.or_merge_pixel.restype = C.c_int64
             L.or_vertex_child.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int64]
@@ -157,6 +161,14 @@ def rotation(seed: int, emitter: int, step: int, rotate: bool = True):
     Rq = np.zeros(9, np.int32)
     lib().or_rotation(seed, emitter, step, int(rotate), _p(R, C.c_double), _p(Rq, C.c_int32))
     return R.reshape(3, 3), Rq.reshape(3, 3)
+
+
+def merge_rotation(seed: int, cell: int, step: int, rotate: bool = True) -> np.ndarray:
+    """Rotation of a cell's merge sphere (Sec. 3.3), single precision:
+    Rq int32[3,3] = round(R * 2^24)."""
+    Rq = np.zeros(9, np.int32)
+    lib().or_merge_rotation(seed, cell, step, int(rotate), _p(Rq, C.c_int32))
+    return Rq.reshape(3, 3)
 
 
 def direction(level: int, p: int, Rq) -> np.ndarray:
@@ -296,10 +308,28 @@ class OracleSim:
         if r != 0:
             raise RuntimeError(f"oracle step failed ({r})")
 
-    def apply_merge(self, dt: float):
-        """Test hook: merge the live rays as at the end of the last step."""
-        if lib().or_apply_merge(self._h, dt) != 0:
+    def apply_merge(self, dt: float, K: int = -1):
+        """Test hook: merge the live rays as at the end of the last step (K < 0:
+        floor(N_ex * N_RT) rays exempt)."""
+        if lib().or_apply_merge(self._h, dt, int(K)) != 0:
             raise RuntimeError("oracle merge failed")
+
+    def set_rays(self, step: int, r):
+        """Test hook: replace the live rays by `r` (a dict as rays() returns)
+        as they stand after the march of `step`."""
+        n = len(r["level"])
+        def a(k, t, shape=None):
+            return np.ascontiguousarray(np.asarray(r[k]).astype(t).reshape(shape if shape else (n,)))
+        em = np.asarray(r["emitter"]).astype(np.int64)
+        merged = np.asarray(r.get("merged", np.zeros(n, bool))).astype(bool)
+        em32 = np.ascontiguousarray(np.where(merged, em - (1 << 31), em).astype(np.int32))
+        arrs = [a("level", np.int32), a("pixel", np.int64), em32, a("birth", np.int32), a("dir", np.int32, (n, 3)),
+                a("N", np.float64, (n, self.nb)), np.ascontiguousarray(merged.astype(np.int32)),
+                a("vertex", np.int32), a("A", np.int32), a("P", np.int64, (n, 3)), a("thr", np.float64)]
+        cts = [C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_int32,
+               C.c_int64, C.c_double]
+        if lib().or_set_rays(self._h, int(step), n, *[_p(x, t) for x, t in zip(arrs, cts)]) != 0:
+            raise MemoryError("oracle set_rays failed")
 
     def fields(self):
         out = {k: np.zeros(self.ncell) for k in ("gamma_HI", "x_HII", "T", "n_HI")}

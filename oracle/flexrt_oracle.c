@@ -240,6 +240,51 @@ void or_rotation(uint64_t seed, int64_t e, int64_t s, int rotate, double R[9], i
 
 /* Fixed-point direction of pixel (l,p) under rotation Rq:
  * vq = round(v * 2^24), d = round(Rq . vq / 2^27), |d| <= 2^21 per axis. */
+/* Random rotation of a cell's merge sphere (Sec. 3.3: one randomly oriented
+ * HEALPix sphere per cell and merge).  The same counter-based stream and
+ * Marsaglia quaternion as the emitters' rotations, evaluated in single
+ * precision (24-bit uniforms, correctly rounded float operations in a fixed
+ * order): these spheres are drawn for every cell at every merge, and the
+ * result only has to be one identical random rotation on both sides.
+ * Rq = round(R * 2^24). */
+void or_merge_rotation(uint64_t seed, int64_t cell, int64_t s, int rotate, int32_t Rq[9])
+{
+    float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
+    if (rotate) {
+        const uint64_t key = rot_key(seed, ((int64_t)1 << 31) + cell, s);
+        int draw = 0;
+        float a = 0.0f, b = 0.0f, s1 = 2.0f, c = 0.0f, d = 0.0f, s2 = 2.0f;
+        int ok1 = 0, ok2 = 0;
+        for (int t = 0; t < 64 && !ok1; ++t) {
+            a = 2.0f * ((float)(or_sm_draw(key, draw++) >> 40) * 0x1p-24f) - 1.0f;
+            b = 2.0f * ((float)(or_sm_draw(key, draw++) >> 40) * 0x1p-24f) - 1.0f;
+            s1 = a * a + b * b;
+            ok1 = s1 < 1.0f;
+        }
+        for (int t = 0; t < 64 && ok1 && !ok2; ++t) {
+            c = 2.0f * ((float)(or_sm_draw(key, draw++) >> 40) * 0x1p-24f) - 1.0f;
+            d = 2.0f * ((float)(or_sm_draw(key, draw++) >> 40) * 0x1p-24f) - 1.0f;
+            s2 = c * c + d * d;
+            ok2 = s2 < 1.0f && s2 > 0.0f;
+        }
+        if (ok1 && ok2) {
+            float f = sqrtf((1.0f - s1) / s2);
+            w = a; x = b; y = c * f; z = d * f;
+        }
+    }
+    float R[9];
+    R[0] = 1.0f - 2.0f * (y * y + z * z);
+    R[1] = 2.0f * (x * y - w * z);
+    R[2] = 2.0f * (x * z + w * y);
+    R[3] = 2.0f * (x * y + w * z);
+    R[4] = 1.0f - 2.0f * (x * x + z * z);
+    R[5] = 2.0f * (y * z - w * x);
+    R[6] = 2.0f * (x * z - w * y);
+    R[7] = 2.0f * (y * z + w * x);
+    R[8] = 1.0f - 2.0f * (x * x + y * y);
+    for (int k = 0; k < 9; ++k) Rq[k] = (int32_t)rintf(R[k] * 16777216.0f);
+}
+
 int or_direction(int level, int64_t p, const int32_t Rq[9], int32_t d[3])
 {
     double v[3];
@@ -711,19 +756,35 @@ static void deposit_all(or_sim *S, int64_t cell, const double *N, const double *
  *  - rank: a ray's photon content is the sum over bins in single precision
  *    (an integer decision taken in the precision of the GPU path); with
  *    K = floor(N_ex * N_RT), every ray whose content is at least the K-th
- *    largest is exempt (ties at the K-th value are all exempt);
+ *    largest, T_ref, is exempt (ties at the K-th value are all exempt; with
+ *    K = 0 nothing is exempt and T_ref is the largest content);
  *  - cell: the cell holding the ray's end point (floor per axis); a ray whose
  *    end point is on the far face of the box is not merged;
  *  - sphere: one random rotation per (cell, step), drawn like an emitter's
- *    with the key 2^31 + local cell index;
+ *    with the key 2^31 + local cell index, in single precision
+ *    (or_merge_rotation);
  *  - merged ray: photons summed per bin; position, distance travelled and
- *    level are photon-weighted means of the constituents' (rounded to the
- *    fixed-point grid, whole cells and whole levels; the level at least
- *    l_merge); direction the centre of the merge pixel; termination threshold
- *    the sum of the constituents'.  A group of one ray keeps the ray. */
+ *    level are photon-weighted means of the constituents' (rounded half to
+ *    even to the fixed-point grid, whole cells and whole levels; the level
+ *    at least l_merge); direction the centre of the merge pixel; termination
+ *    threshold the sum of the constituents'.  A group of one ray keeps the
+ *    ray.  The means are exact integer quotients: a ray's weight is its
+ *    content on a grid of 2^-26 of the power of two above T_ref (truncated,
+ *    at least 1), so the position is an integer decided identically in any
+ *    summation order. */
 #define OR_MERGE_KEY ((int64_t)1 << 31)
 
+#define OR_WBITS 26                          /* merge weights below 2^26 */
+
 typedef struct { int64_t key, idx; } or_mkey;
+
+/* num / den rounded to nearest, ties to even */
+static uint64_t div_rne(uint64_t num, uint64_t den)
+{
+    uint64_t q = num / den, r = num - q * den;
+    if (2 * r > den || (2 * r == den && (q & 1))) q++;
+    return q;
+}
 
 static int cmp_mkey(const void *a, const void *b)
 {
@@ -749,11 +810,11 @@ float or_rank_content(const double *N, int nb, int E)
     return t;
 }
 
-static int or_merge(or_sim *S, double dt, int64_t s)
+static int or_merge(or_sim *S, double dt, int64_t s, int64_t Kin)
 {
     const or_config *c = &S->c;
     const int64_t n = S->nray;
-    const double Kd = floor(c->n_ex * (double)S->ncell);
+    const double Kd = Kin >= 0 ? (double)Kin : floor(c->n_ex * (double)S->ncell);
     if (Kd >= (double)n) return 0;
     const int64_t K = (int64_t)Kd;
     const int64_t ncast = 12LL << (2 * c->l_src);
@@ -772,11 +833,12 @@ static int or_merge(or_sim *S, double dt, int64_t s)
     int E = 0;
     frexp(nmax, &E);                                   /* unit: the largest content is below 1 */
     for (int64_t i = 0; i < n; ++i) Ts[i] = T[i] = or_rank_content(S->rays[i].N, c->nb, E);
-    float Tstar = INFINITY;
-    if (K > 0) {
-        qsort(Ts, (size_t)n, sizeof(float), cmp_float_desc);
-        Tstar = Ts[K - 1];
-    }
+    qsort(Ts, (size_t)n, sizeof(float), cmp_float_desc);
+    const float Tref = Ts[(K > 0 ? K : 1) - 1];
+    const float Tstar = K > 0 ? Tref : INFINITY;
+    int eref = 0;
+    frexpf(Tref, &eref);                               /* Tref < 2^eref */
+    const float wscale = ldexpf(1.0f, OR_WBITS - eref);
     int64_t nm = 0;
     const int64_t nn[3] = {c->nx, c->ny, c->nz};
     for (int64_t i = 0; i < n; ++i) {
@@ -792,9 +854,8 @@ static int or_merge(or_sim *S, double dt, int64_t s)
         }
         if (!inside) continue;
         int64_t local = (cell[2] * c->ny + cell[1]) * c->nx + cell[0];
-        double R[9];
         int32_t Rq[9];
-        or_rotation(c->seed, OR_MERGE_KEY + local, s, c->rotate, R, Rq);
+        or_merge_rotation(c->seed, local, s, c->rotate, Rq);
         mk[nm].key = local * ndir + or_merge_pixel(c->l_merge, Rq, r->d);
         mk[nm].idx = i;
         nm++;
@@ -808,30 +869,30 @@ static int or_merge(or_sim *S, double dt, int64_t s)
         if (g1 - g0 >= 2) {
             or_ray m;
             memset(&m, 0, sizeof(m));
-            double W = 0.0, wp[3] = {0, 0, 0}, wa = 0.0, wl = 0.0, thr = 0.0;
+            const int64_t local = mk[g0].key / ndir, pm = mk[g0].key % ndir;
+            const int64_t cell[3] = {local % c->nx, (local / c->nx) % c->ny, local / ((int64_t)c->nx * c->ny)};
+            uint64_t W = 0, wp[3] = {0, 0, 0}, wa = 0, wl = 0;
+            double thr = 0.0;
             for (int64_t k = g0; k < g1; ++k) {
                 const int64_t i = mk[k].idx;
                 const or_ray *r = &S->rays[i];
-                double w = 0.0;
-                for (int b = 0; b < c->nb; ++b) { w += r->N[b]; m.N[b] += r->N[b]; }
-                for (int a = 0; a < 3; ++a) wp[a] += w * (double)p1[3 * i + a];
-                double dist = r->kind == 0 ? (double)(s - r->b + 1) : (double)(r->A + (s - r->b));
-                wa += w * dist;
-                wl += w * (double)r->l;
+                for (int b = 0; b < c->nb; ++b) m.N[b] += r->N[b];
+                float qf = T[i] * wscale;                      /* exact unless below 2^-126 */
+                uint64_t q = (uint64_t)qf;
+                if (q < 1) q = 1;
+                for (int a = 0; a < 3; ++a) wp[a] += q * (uint64_t)(p1[3 * i + a] - cell[a] * OR_S);
+                int64_t dist = r->kind == 0 ? s - r->b + 1 : r->A + (s - r->b);
+                wa += q * (uint64_t)dist;
+                wl += q * (uint64_t)r->l;
                 thr += r->kind == 0 ? c->eps_term * S->endot[r->e] * dt / (double)ncast * ldexp(1.0, -2 * (r->l - c->l_src))
                                     : r->thr;
-                W += w;
+                W += q;
                 dead[i] = 1;
             }
-            const int64_t local = mk[g0].key / ndir, pm = mk[g0].key % ndir;
-            const int64_t cell[3] = {local % c->nx, (local / c->nx) % c->ny, local / ((int64_t)c->nx * c->ny)};
-            for (int a = 0; a < 3; ++a) {
-                int64_t v = (int64_t)rint(wp[a] / W), lo = cell[a] * OR_S;
-                m.P[a] = v < lo ? lo : (v > lo + OR_S - 1 ? lo + OR_S - 1 : v);
-            }
-            int64_t A = (int64_t)rint(wa / W);
-            m.A = (int32_t)(A < 0 ? 0 : (A > 65535 ? 65535 : A));
-            int64_t L = (int64_t)rint(wl / W);
+            for (int a = 0; a < 3; ++a) m.P[a] = cell[a] * OR_S + (int64_t)div_rne(wp[a], W);
+            uint64_t A = div_rne(wa, W);
+            m.A = (int32_t)(A > 65535 ? 65535 : A);
+            int64_t L = (int64_t)div_rne(wl, W);
             if (L < c->l_merge) L = c->l_merge;
             if (L > c->l_max) L = c->l_max;
             m.l = (int32_t)L;
@@ -841,9 +902,8 @@ static int or_merge(or_sim *S, double dt, int64_t s)
             m.e = (int32_t)local;
             m.b = (int32_t)s;
             m.thr = thr;
-            double R[9];
             int32_t Rq[9];
-            or_rotation(c->seed, OR_MERGE_KEY + local, s, c->rotate, R, Rq);
+            or_merge_rotation(c->seed, local, s, c->rotate, Rq);
             or_direction(c->l_merge, pm, Rq, m.d);
             if (grow_rays(&merged, &mcap, nmerged + 1)) return -1;
             merged[nmerged++] = m;
@@ -959,7 +1019,8 @@ int or_step(or_sim *S, double dt)
          * the emitter's at the birth step, or the merge cell's at the merge */
         double R[9];
         int32_t Rq[9];
-        or_rotation(c->seed, r.kind == 0 ? (int64_t)r.e : OR_MERGE_KEY + r.e, r.b, c->rotate, R, Rq);
+        if (r.kind == 0) or_rotation(c->seed, r.e, r.b, c->rotate, R, Rq);
+        else or_merge_rotation(c->seed, r.e, r.b, c->rotate, Rq);
         for (int64_t j = 0; j < nchild; ++j) {
             or_ray ch = r;
             ch.l = r.l + m;
@@ -973,7 +1034,7 @@ int or_step(or_sim *S, double dt)
     }
     free(S->rays);
     S->rays = out; S->nray = nout; S->rcap = ocap;
-    if (c->merge && or_merge(S, dt, s)) return -2;
+    if (c->merge && or_merge(S, dt, s, -1)) return -2;
     S->segments_last = segs;
     S->segments_total += segs;
     S->in_flight = 0.0;
@@ -1047,11 +1108,12 @@ int32_t or_num_emitters(const or_sim *S) { return S->ne; }
 int64_t or_config_size(void) { return (int64_t)sizeof(or_config); }
 
 /* Test hook: merge the live rays as at the end of the last step taken
- * (whether or not merging is switched on), with that step's dt. */
-int or_apply_merge(or_sim *S, double dt)
+ * (whether or not merging is switched on), with that step's dt; K < 0 takes
+ * floor(N_ex * N_RT) from the configuration. */
+int or_apply_merge(or_sim *S, double dt, int64_t K)
 {
     if (S->step < 1) return -1;
-    if (or_merge(S, dt, S->step - 1)) return -2;
+    if (or_merge(S, dt, S->step - 1, K)) return -2;
     S->in_flight = 0.0;
     for (int64_t i = 0; i < S->nray; ++i)
         for (int b = 0; b < S->c.nb; ++b) S->in_flight += S->rays[i].N[b];
@@ -1069,4 +1131,25 @@ int64_t or_get_rays_aux(const or_sim *S, int32_t *kind, int32_t *vflag, int32_t 
         for (int a = 0; a < 3; ++a) P[3 * i + a] = r->P[a];
     }
     return S->nray;
+}
+
+/* Test hook: replace the live rays (as they stand after the march of step
+ * `step`; the next step taken is step + 1).  Arrays as or_get_rays and
+ * or_get_rays_aux return them. */
+int or_set_rays(or_sim *S, int64_t step, int64_t n, const int32_t *lv, const int64_t *pix, const int32_t *em,
+                const int32_t *birth, const int32_t *dir, const double *N, const int32_t *kind, const int32_t *vflag,
+                const int32_t *A, const int64_t *P, const double *thr)
+{
+    if (grow_rays(&S->rays, &S->rcap, n)) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        or_ray *r = &S->rays[i];
+        memset(r, 0, sizeof(*r));
+        r->l = lv[i]; r->p = pix[i]; r->e = em[i]; r->b = birth[i];
+        for (int a = 0; a < 3; ++a) { r->d[a] = dir[3 * i + a]; r->P[a] = P[3 * i + a]; }
+        for (int b = 0; b < S->c.nb; ++b) r->N[b] = N[(int64_t)S->c.nb * i + b];
+        r->kind = kind[i]; r->vflag = vflag[i]; r->A = A[i]; r->thr = thr[i];
+    }
+    S->nray = n;
+    S->step = step + 1;
+    return 0;
 }

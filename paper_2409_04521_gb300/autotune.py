@@ -26,8 +26,10 @@ CANDIDATES = [(a, m, 0) for a in (0, 1, 2) for m in (2, 3, 4)] + [(1, 3, 2), (2,
 
 def signature(prob, nsteps: int) -> str:
     h = hashlib.sha1()
+    o = prob.options
+    merge = (bool(getattr(o, "merge", False)), getattr(o, "l_merge", 0), getattr(o, "n_ex", 0.0))
     h.update(repr((tuple(prob.grid), prob.spectrum.nbins, len(prob.source_ndot), nsteps,
-                   prob.options.l_src, prob.options.n_ray_min, prob.mfp.mode)).encode())
+                   o.l_src, o.n_ray_min, prob.mfp.mode) + (merge if merge[0] else ())).encode())
     return h.hexdigest()[:16]
 
 

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libflexrt.so")
-SOURCES = ["flexrt_api.cu", "frt_engine.cu", "frt_kernels.cu", "frt_static.cu"]
+SOURCES = ["flexrt_api.cu", "frt_engine.cu", "frt_kernels.cu", "frt_merge.cu", "frt_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

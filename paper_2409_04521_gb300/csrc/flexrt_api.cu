@@ -42,6 +42,9 @@ extern "C" void flexrt_default_options(flexrt_options *o) {
     o->alpha_B_const = 2.59e-13;
     o->x_init = 1.2e-3;
     o->T_init = 1e4;
+    o->merge = 0;
+    o->l_merge = 0;
+    o->n_ex = 16.0;
 }
 
 static flexrt_status free_fail(flexrt_status s, const std::string &m) {
@@ -74,6 +77,7 @@ extern "C" flexrt_status flexrt_create(const flexrt_grid *grid, const flexrt_box
     cfg.keep_diagnostics = opt.keep_diagnostics != 0;
     cfg.use_graph = false;
     cfg.stream = opt.cuda_stream;
+    cfg.merge_l_max = opt.merge ? opt.l_merge : -1;
     s = c->eng.init(cfg);
     if (s == FLEXRT_OK) s = c->eng.add_sim(h, n_H, &c->slot);
     if (s != FLEXRT_OK) {
@@ -116,10 +120,14 @@ extern "C" flexrt_status flexrt_get_rays(flexrt_ctx *c, int64_t cap, int32_t *le
                                          int64_t *n) {
     return c ? c->eng.rays(c->slot, cap, level, pixel, emitter, birth, dir, photons, n) : FLEXRT_E_INVALID;
 }
+extern "C" flexrt_status flexrt_get_rays_merged(flexrt_ctx *c, int64_t cap, int32_t *merged, int32_t *vertex,
+                                                int32_t *dist, int64_t *pos, double *thr, int64_t *n) {
+    return c ? c->eng.rays_merged(c->slot, cap, merged, vertex, dist, pos, thr, n) : FLEXRT_E_INVALID;
+}
 extern "C" flexrt_status flexrt_profile(flexrt_ctx *c, int32_t enable) {
     return c ? c->eng.profile(enable != 0) : FLEXRT_E_INVALID;
 }
-extern "C" flexrt_status flexrt_get_kernel_times(flexrt_ctx *c, double ms[3], int64_t launches[3],
+extern "C" flexrt_status flexrt_get_kernel_times(flexrt_ctx *c, double ms[4], int64_t launches[4],
                                                  int64_t march_rays[1]) {
     if (!c || !ms || !launches) return FLEXRT_E_INVALID;
     return c->eng.kernel_times(ms, launches, march_rays);
@@ -142,6 +150,7 @@ extern "C" void flexrt_default_batch_config(flexrt_batch_config *b) {
     b->nbins = 3;
     b->n_ray_min = 3.0;
     b->use_graph = 1;
+    b->merge_l_max = -1;
 }
 
 extern "C" flexrt_status flexrt_batch_create(const flexrt_batch_config *bc, flexrt_batch **out) {
@@ -164,6 +173,7 @@ extern "C" flexrt_status flexrt_batch_create(const flexrt_batch_config *bc, flex
     cfg.keep_diagnostics = bc->keep_diagnostics != 0;
     cfg.use_graph = bc->use_graph != 0;
     cfg.stream = bc->cuda_stream;
+    cfg.merge_l_max = bc->merge_l_max;
     flexrt_status s = b->eng.init(cfg);
     if (s != FLEXRT_OK) {
         free_fail(s, "flexrt_batch_create: " + b->eng.error());
@@ -215,6 +225,11 @@ extern "C" flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, in
                                                int64_t *pixel, int32_t *emitter, int32_t *birth, int32_t *dir,
                                                double *photons, int64_t *n) {
     return b ? b->eng.rays(slot, cap, level, pixel, emitter, birth, dir, photons, n) : FLEXRT_E_INVALID;
+}
+extern "C" flexrt_status flexrt_batch_get_rays_merged(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *merged,
+                                                      int32_t *vertex, int32_t *dist, int64_t *pos, double *thr,
+                                                      int64_t *n) {
+    return b ? b->eng.rays_merged(slot, cap, merged, vertex, dist, pos, thr, n) : FLEXRT_E_INVALID;
 }
 extern "C" flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[6]) {
     if (!b || !out) return FLEXRT_E_INVALID;
@@ -283,6 +298,173 @@ extern "C" flexrt_status flexrt_probe_direction(int32_t level, int64_t p0, int64
     if (cudaMemcpy(dr.p, Rq, 9 * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) return FLEXRT_E_CUDA;
     if (launch_probe_direction(level, p0, n, dr.p, tab, lt, d.p, 0) != cudaSuccess) return FLEXRT_E_CUDA;
     if (cudaMemcpy(out, d.p, 3 * n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return FLEXRT_E_CUDA;
+    return FLEXRT_OK;
+}
+
+extern "C" flexrt_status flexrt_probe_merge_pixel(int32_t level, int64_t n, const int32_t *d, const int32_t *Rq,
+                                                  int32_t *out) {
+    if (level < 0 || level > FLEXRT_MAX_LEVEL || n < 0 || !Rq || (n && (!d || !out))) return FLEXRT_E_INVALID;
+    for (int64_t i = 0; i < 3 * n; ++i)
+        if (d[i] > (1 << 21) || d[i] < -(1 << 21)) return FLEXRT_E_INVALID;
+    for (int k = 0; k < 9; ++k)
+        if (Rq[k] > (1 << 24) || Rq[k] < -(1 << 24)) return FLEXRT_E_INVALID;
+    DevBuf<int32_t> dd, dr;
+    DevBuf<uint32_t> dout;
+    if (dd.alloc(3 * n) != cudaSuccess || dr.alloc(9) != cudaSuccess || dout.alloc(n) != cudaSuccess)
+        return FLEXRT_E_OOM;
+    if (cudaMemcpy(dd.p, d, 3 * n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dr.p, Rq, 9 * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FLEXRT_E_CUDA;
+    if (launch_probe_merge_pixel(level, n, dd.p, dr.p, dout.p, 0) != cudaSuccess) return FLEXRT_E_CUDA;
+    if (cudaMemcpy(out, dout.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return FLEXRT_E_CUDA;
+    return FLEXRT_OK;
+}
+
+extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t n, const flexrt_probe_rays *in,
+                                           int64_t cap, flexrt_probe_rays *out, int64_t *n_out) {
+    if (!p || !in || !out || !n_out || n < 0 || cap < 0) return free_fail(FLEXRT_E_INVALID, "probe_merge: null");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nx > 1000 || p->ny > 1000 || p->nz > 1000 || p->nbins < 1 ||
+        p->nbins > FLEXRT_MAX_BINS || p->l_merge < 0 || p->l_merge > 11 || p->l_src < 0 || p->l_max > 12 ||
+        p->l_max < p->l_src || p->k_ex < 0 || p->n_emitters < 0 || (p->n_emitters && (!p->emitter_cell || !p->emitter_n0)))
+        return free_fail(FLEXRT_E_INVALID, "probe_merge: bad constants");
+    if (n && (!in->pixlev || !in->emitter || !in->birth || !in->dir || !in->photons || !in->pos || !in->aux || !in->thr))
+        return free_fail(FLEXRT_E_INVALID, "probe_merge: null ray array");
+    if (cap && (!out->pixlev || !out->emitter || !out->birth || !out->dir || !out->photons || !out->pos || !out->aux ||
+                !out->thr))
+        return free_fail(FLEXRT_E_INVALID, "probe_merge: null output array");
+    const long long ncell = (long long)p->nx * p->ny * p->nz;
+    const int nb = p->nbins, ndir = 12 << (2 * p->l_merge);
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t e = in->emitter[i];
+        const bool mg = (e & 0x80000000u) != 0;
+        if (mg ? (long long)(e & 0x7fffffffu) >= ncell : (int32_t)e >= p->n_emitters)
+            return free_fail(FLEXRT_E_INVALID, "probe_merge: emitter out of range");
+        if ((in->pixlev[i] >> 28) > (uint32_t)p->l_max || (mg && (in->aux[i] & 0x7fff0000u)))
+            return free_fail(FLEXRT_E_INVALID, "probe_merge: bad level or aux word");
+        for (int a = 0; a < 3; ++a)
+            if (in->dir[3 * i + a] > (1 << 21) || in->dir[3 * i + a] < -(1 << 21))
+                return free_fail(FLEXRT_E_INVALID, "probe_merge: direction out of range");
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int4 *tab = nullptr;
+    const int lt = p->l_merge;
+    if (get_pixtab(dev, lt, 0, &tab) != cudaSuccess) return free_fail(FLEXRT_E_CUDA, "probe_merge: pixel table");
+    // one simulation (slot 0) whose march left the n rays in queue 1
+    SimDev h;
+    std::memset(&h, 0, sizeof(h));
+    h.nx = p->nx; h.ny = p->ny; h.nz = p->nz; h.nb = nb;
+    h.ncell = ncell;
+    h.l_src = p->l_src; h.l_max = p->l_max;
+    h.active = 1; h.step = p->step; h.rotate = p->rotate; h.seed = p->seed; h.eps_term = p->eps_term;
+    h.merge = 1; h.l_merge = p->l_merge; h.ndir = ndir; h.k_ex = p->k_ex;
+    SimAcc acc;
+    std::memset(&acc, 0, sizeof(acc));
+    acc.p_rays_out = (double)n;
+    Ctl ctl;
+    std::memset(&ctl, 0, sizeof(ctl));
+    ctl.par = 0; ctl.cnt[1] = n; ctl.n_ranges = 1; ctl.ncell_active = ncell;
+    const long long m = std::max<long long>(n, 1);
+    const int gw = 12 + 4 * ((nb + 4) / 4);
+    DevBuf<Ctl> dctl;
+    DevBuf<SimDev> dsim;
+    DevBuf<SimAcc> dacc;
+    DevBuf<uint32_t> qpl[2], qem[2], qma[2], hist, sel, tkey, gid, gcnt;
+    DevBuf<int32_t> qbi[2], qd[2], qm[2], tsim, rsim;
+    DevBuf<float> qph[2], qthr[2], grp, n0;
+    DevBuf<int4> ecell, rot;
+    DevBuf<long long> pref, cell0, boff;
+    DevBuf<uint32_t> bcount;
+    bool ok = dctl.alloc(1) == cudaSuccess && dsim.alloc(1) == cudaSuccess && dacc.alloc(1) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k)
+        ok = qpl[k].alloc(m) == cudaSuccess && qem[k].alloc(m) == cudaSuccess && qma[k].alloc(m) == cudaSuccess &&
+             qbi[k].alloc(m) == cudaSuccess && qd[k].alloc(3 * m) == cudaSuccess && qm[k].alloc(3 * m) == cudaSuccess &&
+             qph[k].alloc(nb * m) == cudaSuccess && qthr[k].alloc(m) == cudaSuccess;
+    ok = ok && hist.alloc(HIST_BINS) == cudaSuccess && sel.alloc(8) == cudaSuccess && tkey.alloc(m) == cudaSuccess &&
+         tsim.alloc(m) == cudaSuccess && gid.alloc(m) == cudaSuccess && gcnt.alloc(ncell * ndir) == cudaSuccess &&
+         grp.alloc(ncell * ndir * gw) == cudaSuccess && rot.alloc(3 * ncell) == cudaSuccess &&
+         ecell.alloc(std::max(p->n_emitters, 1)) == cudaSuccess && n0.alloc(std::max(p->n_emitters, 1)) == cudaSuccess &&
+         pref.alloc(2) == cudaSuccess && cell0.alloc(1) == cudaSuccess && rsim.alloc(1) == cudaSuccess &&
+         bcount.alloc(MERGE_MAX_BLOCKS * 8) == cudaSuccess && boff.alloc(MERGE_MAX_BLOCKS * 8) == cudaSuccess;
+    if (!ok) return free_fail(FLEXRT_E_OOM, "probe_merge: device allocation failed");
+    // queue layout: structure of arrays, photons bin-major
+    auto queue = [&](int k) {
+        Queue q{};
+        q.pl = qpl[k].p; q.em = qem[k].p; q.bi = qbi[k].p;
+        q.dx = qd[k].p; q.dy = qd[k].p + m; q.dz = qd[k].p + 2 * m;
+        for (int b = 0; b < nb; ++b) q.ph[b] = qph[k].p + b * m;
+        q.mx = qm[k].p; q.my = qm[k].p + m; q.mz = qm[k].p + 2 * m;
+        q.ma = qma[k].p; q.mthr = qthr[k].p;
+        return q;
+    };
+    const Queue q0 = queue(0), q1 = queue(1);
+    std::vector<int32_t> d3(3 * m), m3(3 * m);
+    std::vector<float> ph(nb * m);
+    std::vector<uint32_t> ma(m);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) { d3[a * m + i] = in->dir[3 * i + a]; m3[a * m + i] = in->pos[3 * i + a]; }
+        for (int b = 0; b < nb; ++b) ph[b * m + i] = in->photons[(size_t)nb * i + b];
+        ma[i] = in->aux[i] & 0x8000ffffu;              // simulation 0
+    }
+    std::vector<int4> ec(std::max(p->n_emitters, 1));
+    for (int k = 0; k < p->n_emitters; ++k)
+        ec[k] = make_int4(p->emitter_cell[3 * k], p->emitter_cell[3 * k + 1], p->emitter_cell[3 * k + 2], 0);
+    const long long pr[2] = {0, ncell}, c0 = 0;
+    const int32_t s0 = 0;
+    auto up = [](void *dst, const void *src, size_t bytes) {
+        return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    ok = up(dctl.p, &ctl, sizeof(ctl)) && up(dsim.p, &h, sizeof(h)) && up(dacc.p, &acc, sizeof(acc)) &&
+         up(q1.pl, in->pixlev, n * 4) && up(q1.em, in->emitter, n * 4) && up(q1.bi, in->birth, n * 4) &&
+         up(qd[1].p, d3.data(), 3 * m * 4) && up(qm[1].p, m3.data(), 3 * m * 4) && up(qph[1].p, ph.data(), nb * m * 4) &&
+         up(q1.ma, ma.data(), m * 4) && up(q1.mthr, in->thr, n * 4) && up(ecell.p, ec.data(), ec.size() * sizeof(int4)) &&
+         up(n0.p, p->emitter_n0, p->n_emitters * sizeof(float)) && up(pref.p, pr, sizeof(pr)) &&
+         up(cell0.p, &c0, sizeof(c0)) && up(rsim.p, &s0, sizeof(s0));
+    ok = ok && cudaMemset(hist.p, 0, HIST_BINS * 4) == cudaSuccess && cudaMemset(sel.p, 0, 32) == cudaSuccess &&
+         cudaMemset(gcnt.p, 0, ncell * ndir * 4) == cudaSuccess &&
+         cudaMemset(grp.p, 0, (size_t)ncell * ndir * gw * 4) == cudaSuccess;
+    if (!ok) return free_fail(FLEXRT_E_CUDA, "probe_merge: upload failed");
+    Emitters em{};
+    em.cell = ecell.p; em.n0 = n0.p;
+    Ranges rg{pref.p, cell0.p, rsim.p};
+    MergeWork w{};
+    w.hist = hist.p; w.sel = sel.p; w.tkey = tkey.p; w.tsim = tsim.p; w.gid = gid.p;
+    w.grp = grp.p; w.gcnt = gcnt.p; w.rot = rot.p; w.ndir = ndir; w.grp_w = gw;
+    w.bcount = bcount.p; w.boff = boff.p; w.hrep = 1;
+    MergeArgs a{dctl.p, dsim.p, dacc.p, 1, {q0, q1}, em, rg, tab, lt, w, nb};
+    if (launch_merge(a, sms, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return free_fail(FLEXRT_E_CUDA, "probe_merge: kernels failed");
+    Ctl hc;
+    if (cudaMemcpy(&hc, dctl.p, sizeof(hc), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return free_fail(FLEXRT_E_CUDA, "probe_merge: read-back failed");
+    // merged: the kernels wrote the rays back to queue 0; otherwise unchanged
+    const int k = hc.merged ? 0 : 1;
+    const long long cnt = hc.cnt[k];
+    *n_out = cnt;
+    const long long c = std::min<long long>(cnt, cap);
+    std::vector<int32_t> od(3 * m), om(3 * m);
+    std::vector<float> oph(nb * m);
+    std::vector<uint32_t> oma(m);
+    auto down = [](void *dst, const void *src, size_t bytes) {
+        return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+    };
+    const Queue qq = k ? q1 : q0;
+    ok = down(out->pixlev, qq.pl, c * 4) && down(out->emitter, qq.em, c * 4) && down(out->birth, qq.bi, c * 4) &&
+         down(od.data(), qd[k].p, 3 * m * 4) && down(om.data(), qm[k].p, 3 * m * 4) &&
+         down(oph.data(), qph[k].p, nb * m * 4) && down(oma.data(), qq.ma, m * 4) && down(out->thr, qq.mthr, c * 4);
+    if (!ok) return free_fail(FLEXRT_E_CUDA, "probe_merge: read-back failed");
+    for (long long i = 0; i < c; ++i) {
+        const bool mg = (out->emitter[i] & 0x80000000u) != 0;
+        for (int a2 = 0; a2 < 3; ++a2) {
+            out->dir[3 * i + a2] = od[a2 * m + i];
+            out->pos[3 * i + a2] = mg ? om[a2 * m + i] : 0;
+        }
+        for (int b = 0; b < nb; ++b) out->photons[(size_t)nb * i + b] = oph[b * m + i];
+        out->aux[i] = mg ? (oma[i] & 0x8000ffffu) : 0u;
+        if (!mg) out->thr[i] = 0.0f;
+    }
     return FLEXRT_OK;
 }
 

@@ -169,6 +169,57 @@ __device__ inline void rotation_rows(uint64_t seed, long long e, long long s, in
                             __double2int_rn(__dmul_rn(R[3 * r + 2], Q)), 0);
 }
 
+// Rotation of a cell's merge sphere (Sec. 3.3) for (seed, local cell, step):
+// the same counter-based stream (key 2^31 + cell) and Marsaglia quaternion,
+// in single precision -- 24-bit uniforms and correctly rounded float
+// operations in a fixed order (explicit _rn intrinsics).  Rows round(R * 2^24).
+__device__ inline void merge_rotation_rows(uint64_t seed, long long cell, long long s, int rotate, int4 rows[3]) {
+    float w = 1.0f, x = 0.0f, y = 0.0f, zz = 0.0f;
+    if (rotate) {
+        uint64_t h = sm64(seed + GOLD);
+        h = sm64(h + GOLD * (uint64_t)((1LL << 31) + cell + 1));
+        h = sm64(h + GOLD * (uint64_t)(s + 1));
+        int draw = 0;
+        auto uni = [&](void) -> float {
+            const uint64_t u = sm64(h + GOLD * (uint64_t)(draw + 1));
+            ++draw;
+            return __fmul_rn((float)(uint32_t)(u >> 40), 5.9604644775390625e-08f);   // 2^-24
+        };
+        float a = 0, b = 0, s1 = 0, c = 0, d = 0, s2 = 0;
+        bool ok1 = false, ok2 = false;
+        for (int t = 0; t < 64 && !ok1; ++t) {
+            a = __fadd_rn(__fmul_rn(2.0f, uni()), -1.0f);
+            b = __fadd_rn(__fmul_rn(2.0f, uni()), -1.0f);
+            s1 = __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b));
+            ok1 = s1 < 1.0f;
+        }
+        for (int t = 0; t < 64 && ok1 && !ok2; ++t) {
+            c = __fadd_rn(__fmul_rn(2.0f, uni()), -1.0f);
+            d = __fadd_rn(__fmul_rn(2.0f, uni()), -1.0f);
+            s2 = __fadd_rn(__fmul_rn(c, c), __fmul_rn(d, d));
+            ok2 = (s2 < 1.0f) && (s2 > 0.0f);
+        }
+        if (ok1 && ok2) {
+            const float f = __fsqrt_rn(__fdiv_rn(__fadd_rn(1.0f, -s1), s2));
+            w = a; x = b; y = __fmul_rn(c, f); zz = __fmul_rn(d, f);
+        }
+    }
+    float R[9];
+    R[0] = __fadd_rn(1.0f, -__fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, y), __fmul_rn(zz, zz))));
+    R[1] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, y), -__fmul_rn(w, zz)));
+    R[2] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, zz), __fmul_rn(w, y)));
+    R[3] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, y), __fmul_rn(w, zz)));
+    R[4] = __fadd_rn(1.0f, -__fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(zz, zz))));
+    R[5] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, zz), -__fmul_rn(w, x)));
+    R[6] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, zz), -__fmul_rn(w, y)));
+    R[7] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, zz), __fmul_rn(w, x)));
+    R[8] = __fadd_rn(1.0f, -__fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y))));
+    for (int r = 0; r < 3; ++r)
+        rows[r] = make_int4(__float2int_rn(__fmul_rn(R[3 * r], 16777216.0f)),
+                            __float2int_rn(__fmul_rn(R[3 * r + 1], 16777216.0f)),
+                            __float2int_rn(__fmul_rn(R[3 * r + 2], 16777216.0f)), 0);
+}
+
 // round(X / 2^27), ties to even (X = Rq . vq, 2^48 scale -> 2^21 scale)
 __device__ __forceinline__ int32_t rne_shift27(long long X) {
     long long q = X >> 27;                 // arithmetic shift = floor
@@ -181,6 +232,98 @@ __device__ __forceinline__ void rotate_dir(const int4 rows[3], int4 v, int32_t &
     dx = rne_shift27((long long)rows[0].x * v.x + (long long)rows[0].y * v.y + (long long)rows[0].z * v.z);
     dy = rne_shift27((long long)rows[1].x * v.x + (long long)rows[1].y * v.y + (long long)rows[1].z * v.z);
     dz = rne_shift27((long long)rows[2].x * v.x + (long long)rows[2].y * v.y + (long long)rows[2].z * v.z);
+}
+
+// ---------------------------------------------------------------------------
+// Merge-sphere pixel (Sec. 3.3).  The pixel decides which rays merge, so it
+// is computed in single precision as one fixed sequence of correctly rounded
+// operations (explicit _rn intrinsics: nothing is contracted into an FMA):
+// v = Rq^T d, then the NESTED HEALPix ang2pix (Gorski et al. 2005) with the
+// azimuth from an arctangent series.  The quantised rotation entries
+// (|Rq| <= 2^24) and the fixed-point direction (|d| <= 2^21) are exact floats.
+// ---------------------------------------------------------------------------
+// arctan(t) / (pi/2), 0 <= t <= 1: t > tan(pi/8) uses arctan t = pi/4 +
+// arctan((t-1)/(t+1)); then Taylor terms u^(2k+1)/(2k+1), k = 0..9.
+__device__ __forceinline__ float atan_quarter(float t) {
+    const float c[10] = {1.0f, -0.333333343f, 0.200000003f, -0.142857149f, 0.111111112f,
+                         -0.0909090936f, 0.0769230798f, -0.0666666701f, 0.0588235296f, -0.0526315793f};
+    float base = 0.0f, u = t;
+    if (t > 0.414213568f) {
+        u = __fdiv_rn(__fadd_rn(t, -1.0f), __fadd_rn(t, 1.0f));
+        base = 0.5f;
+    }
+    const float u2 = __fmul_rn(u, u);
+    float p = c[9];
+#pragma unroll
+    for (int k = 8; k >= 0; --k) p = __fadd_rn(__fmul_rn(p, u2), c[k]);
+    return __fadd_rn(base, __fmul_rn(__fmul_rn(u, p), 0.636619747f));
+}
+// azimuth of (x, y) in quarter turns, [0, 4)
+__device__ __forceinline__ float azimuth_quarter(float x, float y) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    if (ax == 0.0f && ay == 0.0f) return 0.0f;
+    const float a = ax >= ay ? atan_quarter(__fdiv_rn(ay, ax)) : __fadd_rn(1.0f, -atan_quarter(__fdiv_rn(ax, ay)));
+    float tt;
+    if (x >= 0.0f) tt = y >= 0.0f ? a : __fadd_rn(4.0f, -a);
+    else tt = y >= 0.0f ? __fadd_rn(2.0f, -a) : __fadd_rn(2.0f, a);
+    if (tt >= 4.0f) tt = __fadd_rn(tt, -4.0f);
+    return tt;
+}
+__device__ __forceinline__ uint32_t interleave_bits(uint32_t ix, uint32_t iy) {
+    uint32_t out = 0;
+    for (int i = 0; i < 13; ++i) out |= (((ix >> i) & 1u) << (2 * i)) | (((iy >> i) & 1u) << (2 * i + 1));
+    return out;
+}
+// NESTED pixel at `level` (<= 12) of fixed-point direction d on the sphere
+// whose pixel vectors are rotated by `rows` (d = Rq . v, so v = Rq^T d)
+__device__ __forceinline__ uint32_t merge_pixel(int level, const int4 rows[3], int32_t dx, int32_t dy, int32_t dz) {
+    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+    const float v0 = __fadd_rn(__fadd_rn(__fmul_rn((float)rows[0].x, fx), __fmul_rn((float)rows[1].x, fy)),
+                               __fmul_rn((float)rows[2].x, fz));
+    const float v1 = __fadd_rn(__fadd_rn(__fmul_rn((float)rows[0].y, fx), __fmul_rn((float)rows[1].y, fy)),
+                               __fmul_rn((float)rows[2].y, fz));
+    const float v2 = __fadd_rn(__fadd_rn(__fmul_rn((float)rows[0].z, fx), __fmul_rn((float)rows[1].z, fy)),
+                               __fmul_rn((float)rows[2].z, fz));
+    const int nside = 1 << level;
+    const float ns = (float)nside;
+    const float s2 = __fadd_rn(__fmul_rn(v0, v0), __fmul_rn(v1, v1));
+    const float r = __fsqrt_rn(__fadd_rn(s2, __fmul_rn(v2, v2)));
+    const float z = __fdiv_rn(v2, r);
+    const float tt = azimuth_quarter(v0, v1);
+    int face, ix, iy;
+    if (fabsf(z) <= 0.666666687f) {                  // equatorial belt
+        const float t1 = __fmul_rn(ns, __fadd_rn(0.5f, tt));
+        const float t2 = __fmul_rn(ns, __fmul_rn(z, 0.75f));
+        const int jp = (int)__fadd_rn(t1, -t2), jm = (int)__fadd_rn(t1, t2);
+        const int ifp = jp >> level, ifm = jm >> level;
+        face = ifp == ifm ? (ifp | 4) : (ifp < ifm ? ifp : ifm + 8);
+        ix = jm & (nside - 1);
+        iy = nside - (jp & (nside - 1)) - 1;
+    } else {                                         // polar caps
+        int ntt = (int)tt;
+        if (ntt > 3) ntt = 3;
+        const float tp = __fadd_rn(tt, -(float)ntt);
+        const float omz = __fdiv_rn(s2, __fmul_rn(r, __fadd_rn(r, fabsf(v2))));   // 1 - |z|
+        const float tmp = __fmul_rn(ns, __fsqrt_rn(__fmul_rn(3.0f, omz)));
+        int jp = (int)__fmul_rn(tp, tmp), jm = (int)__fmul_rn(__fadd_rn(1.0f, -tp), tmp);
+        jp = min(jp, nside - 1);
+        jm = min(jm, nside - 1);
+        if (z >= 0.0f) { face = ntt; ix = nside - jm - 1; iy = nside - jp - 1; }
+        else { face = ntt + 8; ix = jp; iy = jm; }
+    }
+    return (uint32_t)face * (uint32_t)(nside * nside) + interleave_bits((uint32_t)ix, (uint32_t)iy);
+}
+
+// Split children of a merged ray of level l centred on merge pixel pm (level
+// lm <= l).  A NESTED pixel's centre is the corner its four children share,
+// and at each deeper level the corner of exactly four pixels: child i, then
+// always sub-pixel 3-i.  Child c of an m-level split is descendant
+// c mod 4^(m-1) of the (c >> 2(m-1))-th of these level-(l+1) pixels.
+__device__ __forceinline__ uint32_t vertex_child(int lm, uint32_t pm, int l, int m, uint32_t c) {
+    const uint32_t i = c >> (2 * (m - 1)), j = c & ((1u << (2 * (m - 1))) - 1u);
+    uint32_t q = pm * 4u + i;
+    for (int k = l - lm; k > 0; --k) q = q * 4u + (3u - i);
+    return (q << (2 * (m - 1))) + j;
 }
 
 // ---------------------------------------------------------------------------
@@ -259,8 +402,8 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 // Sum NV values over the lanes of each peer group (lanes with the same key);
 // the lowest lane of each group ends with the group sum.  Pairwise tree over
 // the ranks within each group: log2(group size) rounds.
-template <int NV>
-__device__ __forceinline__ void peer_sum(unsigned peers, float (&v)[NV]) {
+template <int NV, typename T = float>
+__device__ __forceinline__ void peer_sum(unsigned peers, T (&v)[NV]) {
     const int lane = lane_id();
     const unsigned below = (1u << lane) - 1u;
     unsigned above = lane == 31 ? 0u : (peers & (0xffffffffu << (lane + 1)));
@@ -270,7 +413,7 @@ __device__ __forceinline__ void peer_sum(unsigned peers, float (&v)[NV]) {
         int src = above ? (__ffs(above) - 1) : lane;
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            float t = __shfl_sync(FULL, v[k], src);
+            T t = __shfl_sync(FULL, v[k], src);
             if (alive && !(rank & 1) && above) v[k] += t;
         }
         unsigned odd = __ballot_sync(FULL, alive && (rank & 1));

@@ -37,7 +37,8 @@ void split_table(double nmin, int32_t *K) {
 
 int ring_length(int n) { return (int)std::ceil(std::sqrt(3.0) * n) + 4; }
 
-size_t ray_bytes(int nb) { return 6 * sizeof(int32_t) + (size_t)nb * sizeof(float); }
+// queue bytes per ray slot; merged rays add position, distance word and threshold
+size_t ray_bytes(int nb, bool merge) { return 6 * sizeof(int32_t) + (size_t)nb * sizeof(float) + (merge ? 20 : 0); }
 
 }  // namespace
 
@@ -121,6 +122,7 @@ Engine::~Engine() {
     cudaFree(em_.cell); cudaFree(em_.local); cudaFree(em_.ndot); cudaFree(em_.n0);
     cudaFree(em_.ring); cudaFree(em_.act); cudaFree(em_.act_off);
     cudaFree(rg_.pref); cudaFree(rg_.cell0); cudaFree(rg_.sim);
+    cudaFree(mwmem_);
     if (h_err_) cudaFreeHost(h_err_);
     if (h_stage_) cudaFreeHost(h_stage_);
     if (ev_err_) cudaEventDestroy(ev_err_);
@@ -151,8 +153,10 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
 
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
+    const bool mrg = cfg_.merge_l_max >= 0;
+    if (cfg_.merge_l_max > 11) return fail(FLEXRT_E_INVALID, "merge level above 11");
     long long cap = cfg_.ray_capacity;
-    if (cap <= 0) cap = (long long)(0.3 * (double)freeb / (2.0 * ray_bytes(cfg_.nb)));
+    if (cap <= 0) cap = (long long)(0.3 * (double)freeb / (2.0 * ray_bytes(cfg_.nb, mrg)));
     cfg_.ray_capacity = cap = std::max(cap, 1024LL);
     // queue slots beyond the live-ray capacity for the unused tails of the
     // march's warp-private output runs
@@ -161,7 +165,7 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
 
     // ray queues: one allocation, structure of arrays, two buffers
     {
-        const size_t a = (size_t)cap * 4, per = ray_bytes(cfg_.nb) * (size_t)cap;
+        const size_t a = (size_t)cap * 4, per = ray_bytes(cfg_.nb, mrg) * (size_t)cap;
         char *base = nullptr;
         if (cudaMalloc(&base, 2 * per + 256) != cudaSuccess) return fail(FLEXRT_E_OOM, "ray queue allocation failed");
         qmem_ = base;
@@ -176,6 +180,13 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
             for (int b = 0; b < MAXB; ++b) {
                 q_[k].ph[b] = b < cfg_.nb ? (float *)p : nullptr;
                 if (b < cfg_.nb) p += a;
+            }
+            if (mrg) {
+                q_[k].mx = (int32_t *)p; p += a;
+                q_[k].my = (int32_t *)p; p += a;
+                q_[k].mz = (int32_t *)p; p += a;
+                q_[k].ma = (uint32_t *)p; p += a;
+                q_[k].mthr = (float *)p; p += a;
             }
         }
     }
@@ -199,6 +210,28 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     ALLOC(rg_.cell0, ms);
     ALLOC(rg_.sim, ms);
 #undef ALLOC
+    if (mrg) {
+        // merge scratch (Sec. 3.3): histograms and selections per slot, rank
+        // content / simulation / group per queue slot, group sums and sizes
+        // per (cell, merge pixel), rotation rows per cell
+        mw_.ndir = 12 << (2 * cfg_.merge_l_max);
+        mw_.grp_w = 12 + 4 * ((cfg_.nb + 4) / 4);   // 6 integer sums, photons and threshold
+        const long long ngrp = nc * (long long)mw_.ndir;
+        if (ngrp >= (1LL << 31)) return fail(FLEXRT_E_INVALID, "cells x merge directions must stay below 2^31");
+        mw_.hrep = std::max(1, std::min(32, 64 / ms));
+        const size_t sz[] = {(size_t)ms * mw_.hrep * HIST_BINS * 4, (size_t)ms * 32, (size_t)cap * 4,
+                             (size_t)cap * 4, (size_t)cap * 4, (size_t)ngrp * mw_.grp_w * 4, (size_t)ngrp * 4,
+                             (size_t)nc * 48, (size_t)MERGE_MAX_BLOCKS * 8 * 4, (size_t)MERGE_MAX_BLOCKS * 8 * 8};
+        size_t tot = 0;
+        for (size_t v : sz) tot += (v + 255) & ~(size_t)255;
+        if (cudaMalloc(&mwmem_, tot) != cudaSuccess) return fail(FLEXRT_E_OOM, "merge scratch allocation failed");
+        char *p = (char *)mwmem_;
+        void **dst[] = {(void **)&mw_.hist, (void **)&mw_.sel, (void **)&mw_.tkey, (void **)&mw_.tsim,
+                        (void **)&mw_.gid, (void **)&mw_.grp, (void **)&mw_.gcnt, (void **)&mw_.rot,
+                        (void **)&mw_.bcount, (void **)&mw_.boff};
+        for (int k = 0; k < 10; ++k) { *dst[k] = p; p += (sz[k] + 255) & ~(size_t)255; }
+        CK(cudaMemsetAsync(mwmem_, 0, tot, st_));
+    }
     if (cudaMallocHost(&h_err_, 64) != cudaSuccess) return fail(FLEXRT_E_OOM, "pinned allocation failed");
     if (cudaMallocHost(&h_stage_, (size_t)(ms + 1) * 4 * sizeof(double)) != cudaSuccess)
         return fail(FLEXRT_E_OOM, "pinned allocation failed");
@@ -220,9 +253,9 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device_);
     sm_count_ = std::max(sms, 1);
-    if (!march_variant_exists(cfg_.nb, march_agg_, march_minb_)) { march_agg_ = 0; march_minb_ = 2; }
-    CK(march_prepare(cfg_.nb, march_agg_, march_minb_, ms));
-    const int per_sm = march_max_blocks_per_sm(cfg_.nb, march_agg_, march_minb_, march_threads_, ms);
+    if (!march_variant_exists(cfg_.nb, march_agg_, march_minb_, mrg)) { march_agg_ = 0; march_minb_ = 2; }
+    CK(march_prepare(cfg_.nb, march_agg_, march_minb_, ms, mrg));
+    const int per_sm = march_max_blocks_per_sm(cfg_.nb, march_agg_, march_minb_, march_threads_, ms, mrg);
     if (per_sm < 1) return fail(FLEXRT_E_INVALID, "too many simulation slots for one march block");
     march_blocks_ = sm_count_ * std::max(per_sm, 1);
     chem_blocks_ = (int)std::max<long long>(1, std::min<long long>((nc + 255) / 256, (long long)sm_count_ * 8));
@@ -331,6 +364,16 @@ flexrt_status Engine::make_sim(const flexrt_grid *grid, const flexrt_box *box, c
     h.kap_sub0 = m.lambda0_cm_comoving > 0 ? (float)(h.dx_com / m.lambda0_cm_comoving) : 0.0f;
     h.x_init = opt.x_init; h.T_init = opt.T_init;
     h.nref = 1.0;
+    if (opt.merge) {
+        if (opt.l_merge < 0 || opt.l_merge > 11 || opt.l_merge > opt.l_max || !(opt.n_ex >= 0.0)) {
+            err = "bad merge options (0 <= l_merge <= min(11, l_max), n_ex >= 0)"; return FLEXRT_E_INVALID;
+        }
+        h.merge = 1;
+        h.l_merge = opt.l_merge;
+        h.ndir = 12 << (2 * opt.l_merge);
+        const double k = std::floor(opt.n_ex * (double)h.ncell);
+        h.k_ex = k > 4e18 ? (long long)4e18 : (long long)k;
+    }
     // an isothermal run evaluates its rate coefficients once (same fits as
     // the per-cell device evaluation, in double precision)
     {
@@ -355,6 +398,8 @@ flexrt_status Engine::add_sim(const SimDev &proto, const double *n_H, int *slot_
     const int edge = std::max(proto.nx, std::max(proto.ny, proto.nz));
     if (edge > cfg_.max_grid) return fail(FLEXRT_E_INVALID, "grid larger than the engine's max_grid");
     if (proto.nb > cfg_.nb) return fail(FLEXRT_E_INVALID, "more frequency bins than the engine's layout");
+    if (proto.merge && proto.l_merge > cfg_.merge_l_max)
+        return fail(FLEXRT_E_INVALID, "merge level deeper than the engine's merge scratch allows");
     const long long c0 = cell_alloc_.alloc(proto.ncell);
     if (c0 < 0) return fail(FLEXRT_E_CAPACITY, "cell arena full");
     CK(cudaStreamSynchronize(st_));
@@ -554,8 +599,14 @@ flexrt_status Engine::launch_step() {
     CK(launch_emit(ea, emit_blocks_, st_));
     toc(0);
     tic();
-    CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_));
+    CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, merge_built()));
     toc(1);
+    if (merge_built()) {
+        MergeArgs ga{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, em_, rg_, pixtab_, ltab_, mw_, cfg_.nb};
+        tic();
+        CK(launch_merge(ga, sm_count_, st_));
+        toc(3);
+    }
     tic();
     CK(launch_chem(ca, chem_blocks_, st_));
     toc(2);
@@ -715,6 +766,22 @@ flexrt_status Engine::segment_counts(int s, int32_t *out) {
     return FLEXRT_OK;
 }
 
+// the live rays of simulation s in queue order: indices into the queue copy
+static std::vector<long long> member_rays(const std::vector<uint32_t> &pl, const std::vector<uint32_t> &em,
+                                          const std::vector<uint32_t> &ma, int s, long long em0, int em_n) {
+    std::vector<long long> idx;
+    for (long long i = 0; i < (long long)pl.size(); ++i) {
+        if (pl[i] == DEAD_RAY) continue;
+        if (em[i] & MERGED_BIT) {
+            if (ma.empty() || (int)((ma[i] >> 16) & 0x7fffu) != s) continue;
+        } else if ((long long)em[i] < em0 || (long long)em[i] >= em0 + em_n) {
+            continue;
+        }
+        idx.push_back(i);
+    }
+    return idx;
+}
+
 flexrt_status Engine::rays(int s, int64_t cap, int32_t *level, int64_t *pixel, int32_t *emitter, int32_t *birth,
                            int32_t *dir, double *photons, int64_t *n) {
     const Slot *sl = slot(s);
@@ -728,36 +795,75 @@ flexrt_status Engine::rays(int s, int64_t cap, int32_t *level, int64_t *pixel, i
     const long long m = hc.cnt[hc.par];
     if (m == 0 || cap == 0) return FLEXRT_OK;
     const Queue &q = q_[hc.par];
-    std::vector<uint32_t> pl(m), em(m);
+    std::vector<uint32_t> pl(m), em(m), ma(merge_built() ? m : 0);
     std::vector<int32_t> bi(m), d(3 * m);
     CK(cudaMemcpy(pl.data(), q.pl, m * 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(em.data(), q.em, m * 4, cudaMemcpyDeviceToHost));
+    if (!ma.empty()) CK(cudaMemcpy(ma.data(), q.ma, m * 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(bi.data(), q.bi, m * 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(d.data(), q.dx, m * 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(d.data() + m, q.dy, m * 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(d.data() + 2 * m, q.dz, m * 4, cudaMemcpyDeviceToHost));
     std::vector<std::vector<float>> ph(photons ? sl->h.nb : 0, std::vector<float>(m));
     for (int b = 0; b < (int)ph.size(); ++b) CK(cudaMemcpy(ph[b].data(), q.ph[b], m * 4, cudaMemcpyDeviceToHost));
-    long long k = 0;  // this simulation's live rays; unused queue slots are skipped
-    for (long long i = 0; i < m && k < cap; ++i) {
-        if (pl[i] == DEAD_RAY) continue;
-        if ((long long)em[i] < sl->em0 || (long long)em[i] >= sl->em0 + sl->em_n) continue;
+    const std::vector<long long> idx = member_rays(pl, em, ma, s, sl->em0, sl->em_n);
+    for (long long k = 0; k < (long long)idx.size() && k < cap; ++k) {
+        const long long i = idx[k];
         if (level) level[k] = (int32_t)(pl[i] >> LEVEL_SHIFT);
         if (pixel) pixel[k] = (int64_t)(pl[i] & PIX_MASK);
-        if (emitter) emitter[k] = (int32_t)(em[i] - sl->em0);
+        if (emitter)
+            emitter[k] = (em[i] & MERGED_BIT) ? -1 - (int32_t)(em[i] & ~MERGED_BIT) : (int32_t)(em[i] - sl->em0);
         if (birth) birth[k] = bi[i];
         if (dir) { dir[3 * k] = d[i]; dir[3 * k + 1] = d[m + i]; dir[3 * k + 2] = d[2 * m + i]; }
         for (int b = 0; b < (int)ph.size(); ++b) photons[(size_t)sl->h.nb * k + b] = (double)ph[b][i] * sl->h.nref;
-        ++k;
+    }
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::rays_merged(int s, int64_t cap, int32_t *merged, int32_t *vertex, int32_t *dist, int64_t *pos,
+                                  double *thr, int64_t *n) {
+    const Slot *sl = slot(s);
+    if (!sl || !n || cap < 0) return fail(FLEXRT_E_INVALID, "bad arguments");
+    CK(cudaStreamSynchronize(st_));
+    Ctl hc;
+    CK(cudaMemcpy(&hc, ctl_, sizeof(hc), cudaMemcpyDeviceToHost));
+    const long long m = hc.cnt[hc.par];
+    const Queue &q = q_[hc.par];
+    std::vector<uint32_t> pl(m), em(m), ma(merge_built() ? m : 0);
+    std::vector<int32_t> mx(ma.size()), my(ma.size()), mz(ma.size());
+    std::vector<float> mt(ma.size());
+    if (m > 0) {
+        CK(cudaMemcpy(pl.data(), q.pl, m * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(em.data(), q.em, m * 4, cudaMemcpyDeviceToHost));
+    }
+    if (!ma.empty()) {
+        CK(cudaMemcpy(ma.data(), q.ma, m * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(mx.data(), q.mx, m * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(my.data(), q.my, m * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(mz.data(), q.mz, m * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(mt.data(), q.mthr, m * 4, cudaMemcpyDeviceToHost));
+    }
+    const std::vector<long long> idx = member_rays(pl, em, ma, s, sl->em0, sl->em_n);
+    *n = (int64_t)idx.size();
+    for (long long k = 0; k < (long long)idx.size() && k < cap; ++k) {
+        const long long i = idx[k];
+        const bool mg = (em[i] & MERGED_BIT) != 0;
+        if (merged) merged[k] = mg ? 1 : 0;
+        if (vertex) vertex[k] = mg && (ma[i] >> 31) ? 1 : 0;
+        if (dist) dist[k] = mg ? (int32_t)(ma[i] & 0xffffu) : 0;
+        if (pos) {
+            pos[3 * k] = mg ? mx[i] : 0; pos[3 * k + 1] = mg ? my[i] : 0; pos[3 * k + 2] = mg ? mz[i] : 0;
+        }
+        if (thr) thr[k] = mg ? (double)mt[i] * sl->h.nref : 0.0;
     }
     return FLEXRT_OK;
 }
 
 flexrt_status Engine::set_launch(int agg, int minb, int blocks_per_sm) {
-    if (!march_variant_exists(cfg_.nb, agg, minb) || blocks_per_sm < 0 || blocks_per_sm > 32)
+    if (!march_variant_exists(cfg_.nb, agg, minb, merge_built()) || blocks_per_sm < 0 || blocks_per_sm > 32)
         return fail(FLEXRT_E_INVALID, "march kernel variant not built");
-    CK(march_prepare(cfg_.nb, agg, minb, (int)slots_.size()));
-    const int lim = march_max_blocks_per_sm(cfg_.nb, agg, minb, march_threads_, (int)slots_.size());
+    CK(march_prepare(cfg_.nb, agg, minb, (int)slots_.size(), merge_built()));
+    const int lim = march_max_blocks_per_sm(cfg_.nb, agg, minb, march_threads_, (int)slots_.size(), merge_built());
     if (lim < 1) return fail(FLEXRT_E_INVALID, "variant cannot be resident");
     const int bps = blocks_per_sm == 0 ? lim : std::min(blocks_per_sm, lim);
     march_agg_ = agg;
@@ -768,16 +874,16 @@ flexrt_status Engine::set_launch(int agg, int minb, int blocks_per_sm) {
 }
 
 flexrt_status Engine::profile(bool on) {
-    double ms[3];
-    int64_t l[3], r = 0;
+    double ms[4];
+    int64_t l[4], r = 0;
     flexrt_status s = kernel_times(ms, l, &r);
     profiling_ = on;
     return s;
 }
 
-flexrt_status Engine::kernel_times(double ms[3], int64_t launches[3], int64_t *rays) {
+flexrt_status Engine::kernel_times(double ms[4], int64_t launches[4], int64_t *rays) {
     CK(cudaStreamSynchronize(st_));
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         double t = 0.0;
         for (auto &p : ev_k_[k]) {
             float x = 0.f;

@@ -54,6 +54,7 @@ struct EngineConfig {
     bool keep_diagnostics = false;
     bool use_graph = false;
     void *stream = nullptr;
+    int merge_l_max = -1;      // deepest merge-sphere level members may use; -1: no merging
 };
 
 class Engine {
@@ -77,9 +78,12 @@ class Engine {
     flexrt_status segment_counts(int slot, int32_t *out);
     flexrt_status rays(int slot, int64_t cap, int32_t *level, int64_t *pixel, int32_t *emitter, int32_t *birth,
                        int32_t *dir, double *photons, int64_t *n);
+    flexrt_status rays_merged(int slot, int64_t cap, int32_t *merged, int32_t *vertex, int32_t *dist, int64_t *pos,
+                              double *thr, int64_t *n);
+    bool merge_built() const { return cfg_.merge_l_max >= 0; }
     flexrt_status set_launch(int agg, int minb, int blocks_per_sm);
     flexrt_status profile(bool on);
-    flexrt_status kernel_times(double ms[3], int64_t launches[3], int64_t *rays);
+    flexrt_status kernel_times(double ms[4], int64_t launches[4], int64_t *rays);
     int active_count() const;
     int free_slots() const;
     flexrt_status queue_used(long long *n);   // slots of the live ray queue (synchronises)
@@ -115,6 +119,8 @@ class Engine {
     Cells cells_{};
     Emitters em_{};
     Ranges rg_{};
+    MergeWork mw_{};
+    void *mwmem_ = nullptr;
     const int4 *pixtab_ = nullptr;
     int ltab_ = 0;
     int em_cap_ = 0;
@@ -133,7 +139,7 @@ class Engine {
 
     bool profiling_ = false;
     std::vector<cudaEvent_t> ev_pool_;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_k_[3];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_k_[4];
     double rays_at_profile_ = 0.0;
 
     cudaGraphExec_t graph_ = nullptr;

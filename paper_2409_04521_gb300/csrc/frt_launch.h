@@ -30,6 +30,20 @@ struct MarchArgs {
     int ltab;
 };
 
+struct MergeArgs {
+    Ctl *ctl;
+    const SimDev *sims;
+    SimAcc *acc;
+    int nsims;
+    Queue q[2];
+    Emitters em;
+    Ranges rg;
+    const int4 *pixtab;
+    int ltab;
+    MergeWork w;
+    int nbq;                 // photon bins of the queue layout
+};
+
 struct ChemArgs {
     const Ctl *ctl;
     const SimDev *sims;
@@ -45,13 +59,21 @@ void set_free_error(const std::string &msg);
 cudaError_t launch_pixtab(int4 *tab, int L, cudaStream_t st);
 cudaError_t launch_init_cells(const SimDev *sims, int sim, Cells c, long long ncell, cudaStream_t st);
 cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st);
-bool march_variant_exists(int nb, int agg, int minb);
+using MarchFn = void (*)(MarchArgs);
+// the march variant with merged rays (nullptr if not built)
+MarchFn march_fn_merge(int nb, int agg, int minb);
+bool march_variant_exists(int nb, int agg, int minb, bool merge);
 // opt the variant into the dynamic shared memory `nsims` slots need
-cudaError_t march_prepare(int nb, int agg, int minb, int nsims);
-cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st);
-int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims);
+cudaError_t march_prepare(int nb, int agg, int minb, int nsims, bool merge);
+cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st,
+                         bool merge);
+int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims, bool merge);
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st);
 cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_t st);
+// the merge step (Sec. 3.3) between the march and the chemistry
+cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st);
+cudaError_t launch_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, uint32_t *out,
+                                     cudaStream_t st);
 cudaError_t launch_probe_pixvec(int level, long long p0, long long n, int32_t *out, cudaStream_t st);
 cudaError_t launch_probe_rotation(uint64_t seed, long long e, long long s, int rotate, int32_t *out, cudaStream_t st);
 cudaError_t launch_probe_direction(int level, long long p0, long long n, const int32_t *Rq, const int4 *tab, int ltab,

@@ -1,0 +1,403 @@
+// frt_march.cuh -- the fused per-ray kernel of one RT step, shared by the
+// translation unit that builds the plain variants and the one that builds
+// the variants carrying merged rays.
+//
+//   k_march : per ray, the one-cell march with exp(-tau) attenuation
+//             (Sec. 3.1; Sec. 4.2, Eq. 13), the Eq. 17 deposit (warp-aggregated
+//             vector reductions into the per-cell buffers), escape,
+//             termination, the Eq. 2-3 split and the compacted write of
+//             survivors and children.
+#pragma once
+#include "frt_device.cuh"
+#include "frt_launch.h"
+
+namespace frt {
+
+constexpr int NACC = 6;  // (unused), escaped, out, segments, rays in, rays out
+
+// Warp-wide flush of lane-private tallies (lane simulation `tsim`, -1 for
+// none) into the block's per-simulation fixed-point totals; clears them.
+__device__ __forceinline__ void flush_tallies(float &esc, float &out, unsigned &cnt, unsigned &rout, int &tsim,
+                                              unsigned long long *sh_acc) {
+    const int lane = lane_id();
+    const int kref = __reduce_max_sync(FULL, tsim);
+    if (kref < 0) return;                                   // warp-uniform
+    float v[NACC] = {0.0f, esc, out, (float)(cnt & 0xffffu), (float)(cnt >> 16), (float)rout};
+    bool lead;
+    int kk = tsim;
+    if (__all_sync(FULL, tsim < 0 || tsim == kref)) {
+        warp_sum<NACC>(v);                                  // empty lanes carry zeros
+        lead = lane == 0;
+        kk = kref;
+    } else {
+        const unsigned peers = __match_any_sync(FULL, tsim);
+        peer_sum<NACC>(peers, v);
+        lead = tsim >= 0 && (peers & ((1u << lane) - 1u)) == 0u;
+    }
+    if (lead) {
+        unsigned long long *dst = sh_acc + kk * NACC;
+        atomicAdd(dst + 0, fixed32(v[0]));
+        atomicAdd(dst + 1, fixed32(v[1]));
+        atomicAdd(dst + 2, fixed32(v[2]));
+        atomicAdd(dst + 3, (unsigned long long)__float2uint_rn(v[3]));
+        atomicAdd(dst + 4, (unsigned long long)__float2uint_rn(v[4]));
+        atomicAdd(dst + 5, (unsigned long long)__float2uint_rn(v[5]));
+    }
+    esc = out = 0.0f;
+    cnt = rout = 0u;
+    tsim = -1;
+}
+
+// The per-simulation constants the march needs, staged in shared memory.
+struct MarchSim {
+    int nx, ny, nz, step, l_src, l_max, active, l_merge;
+    long long coff;
+    float eps;
+    int K[MAXL];
+    float sig[MAXB], sige[MAXB], eh[MAXB];
+};
+
+__host__ __device__ constexpr size_t march_shared_bytes(int nsims) {
+    return (size_t)nsims * (NACC * sizeof(unsigned long long) + sizeof(MarchSim));
+}
+
+// Phases per ray: (1) the integer walk of the whole step, (2) the opacity
+// loads of every crossed cell at once, (3) attenuation and deposits.
+// AGG selects how the lanes of a warp combine deposits into the same cell
+// before the vector reduction: 0 none, 1 peer groups of equal keys
+// (match_any + pairwise tree), 2 runs of equal consecutive keys.
+// MINB is the resident-block target per SM (register budget).  MERGE adds
+// the rays made by the merge step (Sec. 3.3): they start from their merge
+// position and carry their own distance and termination threshold.
+template <int NB, int AGG, int MINB, int MERGE>
+__global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
+    // per-simulation tallies of this block (photons in 2^-32 fixed point,
+    // counts as integers), then the staged constants
+    extern __shared__ unsigned long long sh_acc[];
+    MarchSim *msim = reinterpret_cast<MarchSim *>(sh_acc + A.nsims * NACC);
+    for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) sh_acc[i] = 0ull;
+    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) {
+        const SimDev &S = A.sims[i];
+        MarchSim &m = msim[i];
+        m.nx = S.nx; m.ny = S.ny; m.nz = S.nz; m.step = S.step; m.l_src = S.l_src; m.l_max = S.l_max;
+        m.active = S.active; m.l_merge = S.l_merge; m.coff = S.cell_off; m.eps = S.eps_term;
+        for (int l = 0; l < MAXL; ++l) m.K[l] = S.K[l];
+        for (int b = 0; b < MAXB; ++b) { m.sig[b] = S.sig[b]; m.sige[b] = S.sige[b]; m.eh[b] = S.eh[b]; }
+    }
+    __syncthreads();
+    Ctl *C = A.ctl;
+    const int lane = lane_id();
+    if (C->err == 0) {
+        const int par = C->par;
+        const Queue qi = A.q[par], qo = A.q[par ^ 1];
+        unsigned long long *out_cnt = (unsigned long long *)&C->cnt[par ^ 1];
+        const long long n = C->cnt[par] + C->emit_total;
+        const long long nr = (n + 31) & ~31LL;
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        // warp-private run of output slots [slab, slab + slab_left), and this
+        // warp's outputs and iterations so far (its output rate)
+        unsigned long long slab = 0;
+        int slab_left = 0;
+        int w_out = 0, w_it = 0;
+        // lane-private tallies of one simulation, flushed by the warp:
+        // escaped and surviving photons, segments | rays in << 16, rays out
+        float t_esc = 0.0f, t_out = 0.0f;
+        unsigned t_cnt = 0u, t_rout = 0u;
+        int t_sim = -1, t_n = 0;
+        // the next ray's words are loaded one iteration ahead
+        uint32_t npl = DEAD_RAY, ne_ = 0;
+        int nbi = 0, ndx = 0, ndy = 0, ndz = 0;
+        float nph[NB];
+        int nmx = 0, nmy = 0, nmz = 0;
+        uint32_t nma = 0;
+        float nmthr = 0.0f;
+        auto load_ray = [&](long long j) {
+            // the queue streams through once per step: evict-first loads keep
+            // the cells' opacities and deposit buffers resident in L2
+            npl = DEAD_RAY;
+            if (j < n) npl = __ldcs(qi.pl + j);
+            if (npl != DEAD_RAY) {
+                ne_ = __ldcs(qi.em + j); nbi = __ldcs(qi.bi + j);
+                ndx = __ldcs(qi.dx + j); ndy = __ldcs(qi.dy + j); ndz = __ldcs(qi.dz + j);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) nph[b] = __ldcs(qi.ph[b] + j);
+                if (MERGE && (ne_ & MERGED_BIT)) {
+                    nmx = __ldcs(qi.mx + j); nmy = __ldcs(qi.my + j); nmz = __ldcs(qi.mz + j);
+                    nma = __ldcs(qi.ma + j); nmthr = __ldcs(qi.mthr + j);
+                }
+            } else {
+                ne_ = 0; nbi = 0; ndx = ndy = ndz = 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) nph[b] = 0.0f;
+            }
+        };
+        load_ray(blockIdx.x * (long long)blockDim.x + threadIdx.x);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += stride) {
+            const uint32_t pl = npl, e = ne_;
+            const int bi = nbi, dx = ndx, dy = ndy, dz = ndz;
+            const int mx = nmx, my = nmy, mz = nmz;
+            const uint32_t ma = nma;
+            const float mthr = nmthr;
+            float ph[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) ph[b] = nph[b];
+            load_ray(i + stride);
+            bool valid = pl != DEAD_RAY;
+            const bool mrg = MERGE && valid && (e & MERGED_BIT);
+            int sim = 0;
+            int4 ec = make_int4(0, 0, 0, 0);
+            if (mrg) {
+                sim = (int)((ma >> 16) & 0x7fffu);
+            } else if (valid) {
+                ec = __ldg(&A.em.cell[e]);
+                sim = ec.w;
+            }
+            const MarchSim &S = msim[sim];
+            if (!S.active) valid = false;
+            // age: cells travelled before this step.  A merged ray has moved
+            // `since` steps from its merge position and had travelled its
+            // constituents' mean distance when it was made.
+            const int since = S.step - bi - 1;
+            const int age = mrg ? (int)(ma & 0xffffu) + since : S.step - bi;
+            if (valid && (mrg ? since < 0 : (age < 0 || age >= A.em.ring_w))) {
+                atomicOr(&C->err, 2);
+                valid = false;
+            }
+
+            // (1) integer walk of this step
+            int key[4];
+            float ds[4];
+            bool esc = false;
+            int nseg = 0;
+            {
+                Walk w;
+                long long px, py, pz;
+                if (mrg) {
+                    px = (long long)mx + (long long)since * dx;
+                    py = (long long)my + (long long)since * dy;
+                    pz = (long long)mz + (long long)since * dz;
+                } else {
+                    px = ((2LL * ec.x + 1) << (FRAC_BITS - 1)) + (long long)age * dx;
+                    py = ((2LL * ec.y + 1) << (FRAC_BITS - 1)) + (long long)age * dy;
+                    pz = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + (long long)age * dz;
+                }
+                walk_init(w, px, py, pz, dx, dy, dz);
+                bool live = valid;
+                if (live && walk_outside(w, S.nx, S.ny, S.nz)) { esc = true; live = false; }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    key[j] = -1;
+                    ds[j] = 0.0f;
+                    if (live) {
+                        key[j] = (int)(S.coff + ((long long)w.cz * S.ny + w.cy) * S.nx + w.cx);
+                        const bool more = walk_segment(w, ds[j]);
+                        ++nseg;
+                        if (!more) live = false;
+                        else if (walk_outside(w, S.nx, S.ny, S.nz)) { esc = true; live = false; }
+                    }
+                }
+                if (live) {  // more than four segments: impossible for |d| <= 2^21
+                    atomicOr(&C->err, 4);
+                    valid = false;
+                }
+            }
+            // (2) opacities of the crossed cells
+            float2 kc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) kc[j] = key[j] >= 0 ? __ldg(&A.cells.kap[key[j]]) : make_float2(0.f, 0.f);
+            // (3) attenuation and deposits (Eq. 13, Eq. 17)
+            int last = -1;
+            float2 lastk = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float v[4] = {0.f, 0.f, 0.f, 1.0f};
+                if (key[j] >= 0) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
+                        float tr, ab;
+                        absorb_transmit(kb * ds[j], ab, tr);
+                        const float a = ph[b] * ab;
+                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds[j];
+                        ph[b] *= tr;
+                        v[0] += a;
+                        v[1] = fmaf(S.sig[b], phin, v[1]);
+                        v[2] = fmaf(S.sige[b], phin, v[2]);
+                    }
+                    last = key[j];
+                    lastk = kc[j];
+                }
+                if (AGG == 0) {
+                    if (key[j] >= 0) red_add_v4(A.cells.dep + key[j], v[0], v[1], v[2], v[3]);
+                } else {
+                    if (__ballot_sync(FULL, key[j] >= 0) == 0u) break;
+                    if (AGG == 1) {
+                        const unsigned peers = __match_any_sync(FULL, key[j]);
+                        if (__any_sync(FULL, key[j] >= 0 && __popc(peers) > 1)) peer_sum<4>(peers, v);
+                        if (key[j] >= 0 && (peers & ((1u << lane) - 1u)) == 0u)
+                            red_add_v4(A.cells.dep + key[j], v[0], v[1], v[2], v[3]);
+                    } else {
+                        const bool head = run_sum<4>(key[j], v);
+                        if (key[j] >= 0 && head) red_add_v4(A.cells.dep + key[j], v[0], v[1], v[2], v[3]);
+                    }
+                }
+            }
+            float s_end = 0.0f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) s_end += ph[b];
+            int nout = 0, m = 0;
+            const int lev = (int)(pl >> LEVEL_SHIFT);
+            if (valid && !esc) {
+                const float thr = mrg ? mthr : S.eps * __ldg(&A.em.n0[e]) * pow2_neg(2 * (lev - S.l_src));
+                if (s_end < thr) {
+                    // termination: the ray's last photons stay in its last cell
+                    float g = 0.f, h = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const float kb = fmaf(lastk.x, S.sig[b], lastk.y);
+                        if (kb > 0.0f) {
+                            const float q = __fdividef(ph[b], kb);
+                            g = fmaf(S.sig[b], q, g);
+                            h = fmaf(S.sige[b], q, h);
+                        }
+                    }
+                    red_add_v4(A.cells.dep + last, s_end, g, h, 0.0f);
+                } else {
+                    while (lev + m < S.l_max && age + 1 >= S.K[lev + m]) ++m;
+                    nout = 1 << (2 * m);
+                }
+            }
+            // per-simulation tallies: each lane accumulates the rays of one
+            // simulation for up to four iterations, then the warp reduces them
+            // into the block's fixed-point totals
+            {
+                const bool clash = valid && t_sim >= 0 && t_sim != sim;
+                if (__any_sync(FULL, clash) || t_n == 4) {
+                    flush_tallies(t_esc, t_out, t_cnt, t_rout, t_sim, sh_acc);
+                    t_n = 0;
+                }
+                if (valid) {
+                    if (esc) t_esc += s_end;
+                    if (nout) t_out += s_end;
+                    t_cnt += (unsigned)nseg + (1u << 16);
+                    t_rout += (unsigned)nout;
+                    t_sim = sim;
+                }
+                ++t_n;
+            }
+            // compacted output into the warp's run of slots: the remainder of
+            // the current run first, then a new run reserved with one atomic
+            const int incl = warp_incl_scan(nout);
+            const int tot = __shfl_sync(FULL, incl, 31);
+            if (tot > 0) {
+                const unsigned long long s0 = slab;
+                const int left = slab_left;
+                unsigned long long s1 = 0;
+                bool fits = true;
+                if (tot > left) {
+                    // reserve for this warp's next iterations at its own output
+                    // rate (at most 16 iterations ahead and OUT_SLAB slots), so the
+                    // unused tail stays small whatever the queue's dead fraction
+                    const int need = tot - left;
+                    const long long iters_left = (nr - i + stride - 1) / stride;
+                    const int ahead = iters_left < 16 ? (int)iters_left : 16;
+                    const int rate = (w_out + tot + w_it) / (w_it + 1);
+                    const int guess = rate * ahead < OUT_SLAB ? rate * ahead : OUT_SLAB;
+                    const int want = need > guess ? need : guess;
+                    unsigned long long nbase = 0;
+                    if (lane == 0) nbase = atomicAdd(out_cnt, (unsigned long long)want);
+                    nbase = __shfl_sync(FULL, nbase, 0);
+                    if ((long long)(nbase + want) > A.cap) {
+                        if (lane == 0) atomicOr(&C->err, 1);
+                        fits = false;
+                        slab_left = 0;
+                    } else {
+                        s1 = nbase;
+                        slab = nbase + need;
+                        slab_left = want - need;
+                    }
+                } else {
+                    slab = s0 + tot;
+                    slab_left = left - tot;
+                }
+                w_out += tot;
+                if (fits && nout > 0) {
+                    const int k0 = incl - nout;  // this lane's first output position
+                    auto slot_of = [&](int k) -> long long {
+                        return k < left ? (long long)(s0 + k) : (long long)(s1 + (k - left));
+                    };
+                    if (nout == 1) {
+                        const long long o = slot_of(k0);
+                        __stcs(qo.pl + o, pl); __stcs(qo.em + o, e); __stcs(qo.bi + o, bi);
+                        __stcs(qo.dx + o, dx); __stcs(qo.dy + o, dy); __stcs(qo.dz + o, dz);
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) __stcs(qo.ph[b] + o, ph[b]);
+                        if (mrg) {
+                            __stcs(qo.mx + o, mx); __stcs(qo.my + o, my); __stcs(qo.mz + o, mz);
+                            __stcs(qo.ma + o, ma); __stcs(qo.mthr + o, mthr);
+                        }
+                    } else {
+                        const int L = lev + m;
+                        const uint32_t pix0 = (pl & PIX_MASK) << (2 * m);
+                        // children keep their parent's sphere (Sec. 3.2): the
+                        // emitter's of the birth step, or the merge cell's
+                        int4 rows[3];
+                        if (mrg) {
+                            const SimDev &SD = A.sims[sim];
+                            merge_rotation_rows(SD.seed, (long long)(e & ~MERGED_BIT), bi, SD.rotate, rows);
+                        } else {
+                            const int4 *rg = A.em.ring + ((long long)e * A.em.ring_w + (bi % A.em.ring_w)) * 3;
+                            rows[0] = rg[0]; rows[1] = rg[1]; rows[2] = rg[2];
+                        }
+                        const bool vert = mrg && (ma >> 31);
+                        const float scale = pow2_neg(2 * m);
+                        float cph[NB];
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) cph[b] = ph[b] * scale;
+                        for (int c = 0; c < nout; ++c) {
+                            const uint32_t pix = vert ? vertex_child(S.l_merge, pl & PIX_MASK, lev, m, (uint32_t)c)
+                                                      : pix0 + (uint32_t)c;
+                            const int4 vq = L <= A.ltab ? __ldg(&A.pixtab[level_offset(L) + pix]) : healpix_vq(L, pix);
+                            int32_t cx, cy, cz;
+                            rotate_dir(rows, vq, cx, cy, cz);
+                            const long long oc = slot_of(k0 + c);
+                            qo.pl[oc] = ((uint32_t)L << LEVEL_SHIFT) | pix;
+                            qo.em[oc] = e; qo.bi[oc] = bi;
+                            qo.dx[oc] = cx; qo.dy[oc] = cy; qo.dz[oc] = cz;
+#pragma unroll
+                            for (int b = 0; b < NB; ++b) qo.ph[b][oc] = cph[b];
+                            if (mrg) {
+                                qo.mx[oc] = mx; qo.my[oc] = my; qo.mz[oc] = mz;
+                                qo.ma[oc] = ma & 0x7fffffffu;
+                                qo.mthr[oc] = mthr * scale;
+                            }
+                        }
+                    }
+                }
+            }
+            ++w_it;
+        }
+        for (int k = lane; k < slab_left; k += 32) qo.pl[slab + k] = DEAD_RAY;
+        flush_tallies(t_esc, t_out, t_cnt, t_rout, t_sim, sh_acc);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.nsims * NACC; i += blockDim.x) {
+        const unsigned long long u = sh_acc[i];
+        const double v = (i % NACC) < 3 ? (double)u * 0x1p-32 : (double)u;
+        if (u != 0ull) {
+            SimAcc &a = A.acc[i / NACC];
+            double *dst = nullptr;
+            switch (i % NACC) {
+                case 0: dst = &a.p_in; break;
+                case 1: dst = &a.p_esc; break;
+                case 2: dst = &a.p_out; break;
+                case 3: dst = &a.p_seg; break;
+                case 4: dst = &a.p_rays_in; break;
+                default: dst = &a.p_rays_out; break;
+            }
+            atomicAdd(dst, v);
+        }
+    }
+}
+
+}  // namespace frt

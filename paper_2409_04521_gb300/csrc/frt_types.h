@@ -19,6 +19,11 @@ constexpr int LEVEL_SHIFT = 28;                     // pixlev = level<<28 | pixe
 constexpr uint32_t PIX_MASK = (1u << LEVEL_SHIFT) - 1u;
 constexpr uint32_t DEAD_RAY = 0xffffffffu;         // unused queue slot (level 15 never occurs)
 constexpr int OUT_SLAB = 512;                       // queue slots a warp reserves at once
+constexpr uint32_t MERGED_BIT = 0x80000000u;        // emitter word of a merged ray: bit | local cell
+constexpr uint32_t MERGE_KEEP = 0xffffffffu;        // merge group word: ray not merged
+constexpr uint32_t MERGE_FOLLOWER = 0x80000000u;    // merge group word: not the group's leader
+constexpr int HIST_BINS = 65536;                    // radix-select bins per pass (16 bits)
+constexpr int MERGE_MAX_BLOCKS = 4096;              // blocks of the merge's per-ray passes (8 warps each)
 
 // Per-simulation constants and step state.
 struct SimDev {
@@ -55,6 +60,10 @@ struct SimDev {
     int32_t rates, isothermal, chem_iters, mfp_mode;
     double lambda0_c, delta_exp, gamma_ref, gamma_exp, gamma_floor, xion_thr, nH_mean;
     double x_init, T_init;
+    // ray merging (Sec. 3.3): on/off, merge-sphere level, directions, and the
+    // number of rays exempt from merging, floor(N_ex * N_RT)
+    int32_t merge, l_merge, ndir, pad_m;
+    long long k_ex;
 };
 
 // Per-simulation accumulators, code photons (double) and counters.
@@ -74,6 +83,8 @@ struct Ctl {
     int32_t n_act_emit;      // active emitters
     int32_t n_ranges;        // active cell ranges
     long long ncell_active;  // cells in active simulations
+    int32_t merged;          // this step merged rays into the other queue
+    int32_t pad;
 };
 
 // Structure-of-arrays ray queue.
@@ -83,6 +94,10 @@ struct Queue {
     int32_t *bi;             // birth step
     int32_t *dx, *dy, *dz;   // direction, 2^-21 cell per step
     float *ph[MAXB];         // code photons per bin
+    // merged rays only (Sec. 3.3); null when merging is not built in
+    int32_t *mx, *my, *mz;   // position at the merge, 2^-21 cell
+    uint32_t *ma;            // vertex << 31 | simulation << 16 | distance travelled at the merge
+    float *mthr;             // termination threshold, code photons
 };
 
 struct Cells {
@@ -105,6 +120,24 @@ struct Emitters {
     int32_t ring_w;          // slots per emitter (same for all)
     int32_t *act;            // active emitter ids
     long long *act_off;      // first emitted ray of each active emitter
+};
+
+// Scratch of the merge step (Sec. 3.3).
+struct MergeWork {
+    uint32_t *hist;          // [slot][hrep][HIST_BINS] radix-select counts
+    uint32_t *sel;           // [slot][8]: selection state, upper bits, rays above, T_ref bits, any exempt
+    uint32_t *tkey;          // per queue slot: rank content (float bits)
+    int32_t *tsim;           // per queue slot: simulation taking part, -1 none
+    uint32_t *gid;           // per queue slot: merge group, MERGE_FOLLOWER flag, or MERGE_KEEP
+    float *grp;              // [cell * ndir + pixel][grp_w]: 6 uint64 weighted sums, photons, threshold
+    uint32_t *gcnt;          // [cell * ndir + pixel] group sizes
+    int4 *rot;               // [cell][3] merge-sphere rotation rows of this step
+    uint32_t *bcount;        // per warp of the group pass: rays it sends to the merged queue
+    long long *boff;         // their exclusive prefix: where each warp writes
+    int32_t ndir;            // group slots per cell (12 * 4^l_merge of the deepest allowed level)
+    int32_t grp_w;           // floats per group
+    int32_t hrep;            // copies of each simulation's histogram (spreads hot bins)
+    int32_t pad;
 };
 
 struct Ranges {              // active cell ranges for the chemistry kernel

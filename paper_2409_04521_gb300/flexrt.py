@@ -52,13 +52,28 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("rotate", C.c_int32), ("isothermal", C.c_int32), ("rates", C.c_int32),
                 ("chem_iters", C.c_int32), ("alpha_B_const", C.c_double), ("x_init", C.c_double),
                 ("T_init", C.c_double), ("ray_capacity", C.c_int64), ("keep_diagnostics", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double)]
 
 
 class BatchConfig(C.Structure):
     _fields_ = [("max_sims", C.c_int32), ("max_grid", C.c_int32), ("nbins", C.c_int32), ("n_ray_min", C.c_double),
                 ("ray_capacity", C.c_int64), ("cell_capacity", C.c_int64), ("emitter_capacity", C.c_int32),
-                ("keep_diagnostics", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("keep_diagnostics", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("merge_l_max", C.c_int32)]
+
+
+class ProbeRays(C.Structure):
+    _fields_ = [("pixlev", C.POINTER(C.c_uint32)), ("emitter", C.POINTER(C.c_uint32)),
+                ("birth", C.POINTER(C.c_int32)), ("dir", C.POINTER(C.c_int32)), ("photons", C.POINTER(C.c_float)),
+                ("pos", C.POINTER(C.c_int32)), ("aux", C.POINTER(C.c_uint32)), ("thr", C.POINTER(C.c_float))]
+
+
+class MergeProbe(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nbins", C.c_int32),
+                ("l_src", C.c_int32), ("l_max", C.c_int32), ("l_merge", C.c_int32), ("k_ex", C.c_int64),
+                ("seed", C.c_uint64), ("rotate", C.c_int32), ("step", C.c_int32), ("eps_term", C.c_float),
+                ("n_emitters", C.c_int32), ("emitter_cell", C.POINTER(C.c_int32)),
+                ("emitter_n0", C.POINTER(C.c_float))]
 
 
 class Fields(C.Structure):
@@ -91,6 +106,8 @@ def lib():
             L.flexrt_get_segment_counts.argtypes = [vp, P(C.c_int32)]
             L.flexrt_get_rays.argtypes = [vp, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32), P(C.c_int32),
                                           P(C.c_int32), P(C.c_double), P(C.c_int64)]
+            L.flexrt_get_rays_merged.argtypes = [vp, C.c_int64, P(C.c_int32), P(C.c_int32), P(C.c_int32),
+                                                 P(C.c_int64), P(C.c_double), P(C.c_int64)]
             L.flexrt_profile.argtypes = [vp, C.c_int32]
             L.flexrt_get_kernel_times.argtypes = [vp, P(C.c_double), P(C.c_int64), P(C.c_int64)]
             L.flexrt_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
@@ -110,6 +127,8 @@ def lib():
             L.flexrt_batch_get_counts.argtypes = [vp, C.c_int32, P(C.c_int64)]
             L.flexrt_batch_get_rays.argtypes = [vp, C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32),
                                                 P(C.c_int32), P(C.c_int32), P(C.c_double), P(C.c_int64)]
+            L.flexrt_batch_get_rays_merged.argtypes = [vp, C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int32),
+                                                       P(C.c_int32), P(C.c_int64), P(C.c_double), P(C.c_int64)]
             L.flexrt_batch_info.argtypes = [vp, P(C.c_int64)]
             L.flexrt_batch_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
             L.flexrt_batch_last_error.argtypes = [vp]
@@ -122,6 +141,9 @@ def lib():
             L.flexrt_probe_traverse.argtypes = [C.c_int64, P(C.c_int64), P(C.c_int32), P(Grid), P(C.c_int32),
                                                 P(C.c_float), P(C.c_int32), P(C.c_int32)]
             L.flexrt_probe_traverse_static.argtypes = L.flexrt_probe_traverse.argtypes
+            L.flexrt_probe_merge.argtypes = [P(MergeProbe), C.c_int64, P(ProbeRays), C.c_int64, P(ProbeRays),
+                                             P(C.c_int64)]
+            L.flexrt_probe_merge_pixel.argtypes = [C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
             _lib = L
     return _lib
 
@@ -140,6 +162,26 @@ def default_options() -> Options:
     o = Options()
     lib().flexrt_default_options(C.byref(o))
     return o
+
+
+def _merge_options(o, po):
+    o.merge = int(getattr(po, "merge", False))
+    o.l_merge = int(getattr(po, "l_merge", 0))
+    o.n_ex = float(getattr(po, "n_ex", 16.0))
+
+
+def _merged_fields(getter, out, m):
+    """Add the merged-ray fields to a ray dictionary; emitter of a merged ray
+    becomes 2^31 + the local index of its merge cell (its rotation key)."""
+    n = C.c_int64()
+    mg, vx, ds = np.zeros(m, np.int32), np.zeros(m, np.int32), np.zeros(m, np.int32)
+    P, thr = np.zeros((m, 3), np.int64), np.zeros(m)
+    getter(m, _p(mg, C.c_int32), _p(vx, C.c_int32), _p(ds, C.c_int32), _p(P, C.c_int64), _p(thr, C.c_double),
+           C.byref(n))
+    em = out["emitter"].astype(np.int64)
+    out["emitter"] = np.where(mg == 1, (1 << 31) - 1 - em, em)
+    out.update(merged=mg.astype(bool), vertex=vx.astype(bool), A=ds, P=P, thr=thr)
+    return out
 
 
 def _problem_structs(prob, keep):
@@ -163,6 +205,7 @@ def _problem_structs(prob, keep):
     o.seed = po.seed
     o.rotate, o.isothermal, o.rates, o.chem_iters = int(po.rotate), int(po.isothermal), int(po.rates), po.chem_iters
     o.alpha_B_const, o.x_init, o.T_init = po.alpha_B_const, po.x_init, po.T_init
+    _merge_options(o, po)
     return g, b, s, mf, o
 
 
@@ -171,10 +214,12 @@ class Batch:
     and retired between steps; one step advances every active member."""
 
     def __init__(self, max_sims=64, max_grid=160, nbins=3, ray_capacity=0, cell_capacity=None,
-                 emitter_capacity=65536, use_graph=True, keep_diagnostics=False, n_ray_min=3.0, stream=None):
+                 emitter_capacity=65536, use_graph=True, keep_diagnostics=False, n_ray_min=3.0, stream=None,
+                 merge_l_max=-1):
         L = lib()
         c = BatchConfig()
         L.flexrt_default_batch_config(C.byref(c))
+        c.merge_l_max = int(merge_l_max)
         c.max_sims, c.max_grid, c.nbins, c.n_ray_min = max_sims, max_grid, nbins, n_ray_min
         c.ray_capacity = int(ray_capacity)
         c.cell_capacity = int(cell_capacity if cell_capacity is not None else max_sims * max_grid ** 3)
@@ -247,7 +292,9 @@ class Batch:
         self._check(lib().flexrt_batch_get_rays(self._h, int(slot), m, _p(lv, C.c_int32), _p(pix, C.c_int64),
                                                 _p(em, C.c_int32), _p(bi, C.c_int32), _p(d, C.c_int32),
                                                 _p(N, C.c_double), C.byref(n)))
-        return dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
+        out = dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
+        return _merged_fields(lambda *a: self._check(lib().flexrt_batch_get_rays_merged(self._h, int(slot), *a)),
+                              out, m)
 
     def info(self):
         o = np.zeros(6, np.int64)
@@ -294,6 +341,7 @@ class Simulation:
         o.seed = po.seed
         o.rotate, o.isothermal, o.rates, o.chem_iters = int(po.rotate), int(po.isothermal), int(po.rates), po.chem_iters
         o.alpha_B_const, o.x_init, o.T_init = po.alpha_B_const, po.x_init, po.T_init
+        _merge_options(o, po)
         o.ray_capacity = int(ray_capacity)
         o.keep_diagnostics = int(keep_diagnostics)
         o.cuda_stream = stream
@@ -357,18 +405,20 @@ class Simulation:
         N = np.zeros((m, self.nb))
         _check(lib().flexrt_get_rays(self._h, m, _p(lv, C.c_int32), _p(pix, C.c_int64), _p(em, C.c_int32),
                                      _p(bi, C.c_int32), _p(d, C.c_int32), _p(N, C.c_double), C.byref(n)), self._h)
-        return dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
+        out = dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
+        return _merged_fields(lambda *a: _check(lib().flexrt_get_rays_merged(self._h, *a), self._h), out, m)
 
     def profile(self, enable=True):
         _check(lib().flexrt_profile(self._h, int(enable)), self._h)
 
     def kernel_times(self):
-        ms = np.zeros(3)
-        ln = np.zeros(3, np.int64)
+        ms = np.zeros(4)
+        ln = np.zeros(4, np.int64)
         rays = np.zeros(1, np.int64)
         _check(lib().flexrt_get_kernel_times(self._h, _p(ms, C.c_double), _p(ln, C.c_int64), _p(rays, C.c_int64)),
                self._h)
-        return dict(zip(("emit", "march", "chem"), ms)), dict(zip(("emit", "march", "chem"), ln)), int(rays[0])
+        names = ("emit", "march", "chem", "merge")
+        return dict(zip(names, ms)), dict(zip(names, ln)), int(rays[0])
 
     def set_launch(self, agg: int, minb: int, blocks_per_sm: int = 0):
         _check(lib().flexrt_set_launch(self._h, int(agg), int(minb), int(blocks_per_sm)), self._h)
@@ -408,6 +458,66 @@ def probe_direction(level: int, p0: int, n: int, Rq) -> np.ndarray:
 
 
 STATIC_MAX_RAYS = 32768
+
+
+def probe_merge_pixel(level: int, d, Rq) -> np.ndarray:
+    """Merge-sphere pixels (Sec. 3.3) of fixed-point directions d [n,3] on the
+    sphere rotated by Rq (3x3 int32), decided on the GPU."""
+    d = np.ascontiguousarray(np.asarray(d, np.int32).reshape(-1, 3))
+    Rq = np.ascontiguousarray(np.asarray(Rq, np.int32).reshape(9))
+    out = np.zeros(len(d), np.int32)
+    _check(lib().flexrt_probe_merge_pixel(int(level), len(d), _p(d, C.c_int32), _p(Rq, C.c_int32),
+                                          _p(out, C.c_int32)))
+    return out
+
+
+def probe_merge(grid, nbins, l_src, l_max, l_merge, k_ex, seed, rotate, step, eps_term, emitter_cells,
+                emitter_n0, rays):
+    """Run the merge step's kernels (Sec. 3.3) on the rays `rays` of one
+    simulation as they stand after the march of `step`.  `rays`: level,
+    pixel, emitter (2^31 + local cell for a merged ray), birth, dir [n,3],
+    N [n,nbins] (code photons, float32), and for merged rays merged, vertex,
+    A, P [n,3], thr (code photons).  Returns the rays after the merge in the
+    same form."""
+    n = len(rays["level"])
+    merged = np.asarray(rays.get("merged", np.zeros(n, bool)), bool)
+    u32 = lambda x: np.ascontiguousarray(np.asarray(x).astype(np.int64).astype(np.uint32))
+    i32 = lambda x: np.ascontiguousarray(np.asarray(x).astype(np.int32))
+    pl = u32((np.asarray(rays["level"], np.int64) << 28) | np.asarray(rays["pixel"], np.int64))
+    em64 = np.asarray(rays["emitter"]).astype(np.int64)
+    em = u32(np.where(merged, (1 << 31) | (em64 - (1 << 31)), em64))
+    bi = i32(rays["birth"])
+    d = i32(np.asarray(rays["dir"]).reshape(n, 3))
+    ph = np.ascontiguousarray(np.asarray(rays["N"], np.float32).reshape(n, nbins))
+    pos = i32(np.where(merged[:, None], np.asarray(rays.get("P", np.zeros((n, 3)))), 0).reshape(n, 3))
+    aux = u32(np.where(merged, (np.asarray(rays.get("vertex", np.zeros(n)), np.int64) << 31)
+                       | np.asarray(rays.get("A", np.zeros(n)), np.int64), 0))
+    thr = np.ascontiguousarray(np.where(merged, np.asarray(rays.get("thr", np.zeros(n))), 0).astype(np.float32))
+    keep = [pl, em, bi, d, ph, pos, aux, thr]
+    rin = ProbeRays(*[_p(x, t) for x, t in zip(keep, (C.c_uint32, C.c_uint32, C.c_int32, C.c_int32, C.c_float,
+                                                      C.c_int32, C.c_uint32, C.c_float))])
+    cap = max(n, 1)
+    o = dict(pixlev=np.zeros(cap, np.uint32), emitter=np.zeros(cap, np.uint32), birth=np.zeros(cap, np.int32),
+             dir=np.zeros((cap, 3), np.int32), N=np.zeros((cap, nbins), np.float32), P=np.zeros((cap, 3), np.int32),
+             aux=np.zeros(cap, np.uint32), thr=np.zeros(cap, np.float32))
+    rout = ProbeRays(*[_p(o[k], t) for k, t in zip(("pixlev", "emitter", "birth", "dir", "N", "P", "aux", "thr"),
+                                                    (C.c_uint32, C.c_uint32, C.c_int32, C.c_int32, C.c_float,
+                                                     C.c_int32, C.c_uint32, C.c_float))])
+    ec = np.ascontiguousarray(np.asarray(emitter_cells, np.int32).reshape(-1, 3))
+    n0 = np.ascontiguousarray(np.asarray(emitter_n0, np.float32).reshape(-1))
+    mp = MergeProbe(int(grid[0]), int(grid[1]), int(grid[2]), int(nbins), int(l_src), int(l_max), int(l_merge),
+                    int(k_ex), int(seed), int(rotate), int(step), float(eps_term), len(n0), _p(ec, C.c_int32),
+                    _p(n0, C.c_float))
+    nout = C.c_int64()
+    _check(lib().flexrt_probe_merge(C.byref(mp), n, C.byref(rin), cap, C.byref(rout), C.byref(nout)))
+    m = nout.value
+    em_o = o["emitter"][:m].astype(np.int64)
+    mg = (em_o & (1 << 31)) != 0
+    return dict(level=(o["pixlev"][:m] >> 28).astype(np.int32), pixel=(o["pixlev"][:m] & 0x0FFFFFFF).astype(np.int64),
+                emitter=em_o, birth=o["birth"][:m], dir=o["dir"][:m], N=o["N"][:m].astype(np.float64),
+                merged=mg, vertex=mg & ((o["aux"][:m] >> 31) == 1), A=np.where(mg, o["aux"][:m] & 0xffff, 0),
+                P=np.where(mg[:, None], o["P"][:m].astype(np.int64), 0),
+                thr=np.where(mg, o["thr"][:m].astype(np.float64), 0.0))
 
 
 def probe_traverse_static(p0, d, grid):

@@ -1,0 +1,236 @@
+"""Ray merging (Sec. 3.3, Eq. 4) on the GPU against the oracle on identical
+seeded inputs: the merge-pixel decision bit for bit; the merge step on the
+same rays bit for bit (exempt set, groups, merged ids, directions,
+positions, distances, levels; photons to single-precision summation); whole
+runs element by element up to the first merge and on global averages after
+it; the ray-count ceiling of Eq. 4; batch members equal to the same
+simulation alone."""
+import dataclasses as dc
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2409_04521_gb300 as F
+import workloads as W
+from parity_util import BUDGET_RTOL, BUDGET_XTOL, RAY_RTOL, compare_fields
+
+pytestmark = pytest.mark.gpu
+S = 2 ** 21
+
+
+def test_merge_pixel_probe_bit_exact():
+    rng = np.random.default_rng(11)
+    for level in range(6):
+        for key in ((1 << 31) + 3, (1 << 31) + 70000, 5):
+            Rq = oracle.rotation(17, key, level + 3)[1]
+            v = rng.normal(size=(4000, 3))
+            v /= np.linalg.norm(v, axis=1)[:, None]
+            d = np.rint(v * (S - 1)).astype(np.int32)
+            if level <= 3:      # and every rotated pixel centre
+                d = np.vstack([d, [oracle.direction(level, p, Rq) for p in range(12 * 4 ** level)]])
+            got = F.probe_merge_pixel(level, d, Rq)
+            ref = np.array([oracle.merge_pixel(level, Rq, x) for x in d])
+            assert np.array_equal(got, ref)
+
+
+def _emitters(prob):
+    cells, first = [], {}
+    for ijk in map(tuple, prob.source_cells):
+        if ijk not in first:
+            first[ijk] = len(cells)
+            cells.append(ijk)
+    ndot = np.zeros(len(cells))
+    for ijk, nd in zip(map(tuple, prob.source_cells), prob.source_ndot):
+        ndot[first[ijk]] += nd
+    return np.array(cells, np.int32), ndot
+
+
+@pytest.mark.parametrize("n_ex,l_merge,with_merged", [(1.0, 0, False), (2.0, 1, True), (0.0, 0, True),
+                                                      (0.5, 2, True)])
+def test_merge_step_bit_exact_on_identical_rays(n_ex, l_merge, with_merged):
+    # the same live rays (photons exact in single precision) merged by the GPU
+    # kernels and by the oracle: identical exempt sets and groups, identical
+    # merged ids, directions, positions, distances and levels; photons and
+    # thresholds to single-precision summation
+    prob = _prob(n_ex, l_merge, n=16, nsteps=8)
+    plain = dc.replace(prob, options=dc.replace(prob.options, merge=False))
+    dt, k = prob.dt, 6
+    B = oracle.OracleSim(plain)
+    if with_merged:                # a state that already holds merged rays and their children
+        A = oracle.OracleSim(prob)
+        for _ in range(k - 1):
+            A.step(dt)
+        B.set_rays(k - 2, A.rays())
+        B.step(dt)
+    else:
+        for _ in range(k):
+            B.step(dt)
+    step = k - 1
+    pre = B.rays()
+    nref = 2.0 ** round(np.log2(pre["N"].max()))
+    N32 = (pre["N"] / nref).astype(np.float32)
+    thr32 = (pre["thr"] / nref).astype(np.float32)
+    pre["N"], pre["thr"] = N32.astype(np.float64) * nref, thr32.astype(np.float64) * nref
+    B.set_rays(step, pre)
+    K = int(np.floor(n_ex * prob.ncell))
+    cells, ndot = _emitters(prob)
+    o = prob.options
+    n0 = (ndot * dt / (12 * 4 ** o.l_src) / nref).astype(np.float32)
+    gin = dict(pre, N=N32, thr=thr32)
+    got = F.probe_merge(prob.grid, prob.spectrum.nbins, o.l_src, o.l_max, l_merge, K, o.seed, int(o.rotate), step,
+                        o.eps_term, cells, n0, gin)
+    B.apply_merge(dt, K)
+    ref = B.rays()
+    assert len(got["level"]) == len(ref["level"]) < len(pre["level"])
+    gk, g = _table(got)
+    rk, r = _table(ref)
+    assert np.array_equal(gk, rk)
+    assert np.array_equal(g["dir"], r["dir"])
+    assert np.array_equal(g["merged"], r["merged"])
+    m = r["merged"]
+    assert np.array_equal(g["P"][m], r["P"][m]) and np.array_equal(g["A"][m], r["A"][m])
+    assert np.allclose(g["N"] * nref, r["N"], rtol=2e-6, atol=0)
+    assert np.allclose(g["thr"][m] * nref, r["thr"][m], rtol=2e-6)
+    assert (r["birth"][m] == step).sum() > 0
+
+
+def _prob(n_ex, l_merge, n=16, nsteps=10, nsrc=8, seed=2):
+    p = W.cosmo16(n=n, nsteps=nsteps, nsrc=nsrc, seed=seed)
+    return dc.replace(p, options=dc.replace(p.options, merge=True, n_ex=n_ex, l_merge=l_merge))
+
+
+def _table(r):
+    key = np.stack([r["emitter"].astype(np.int64), r["birth"].astype(np.int64), r["level"].astype(np.int64),
+                    r["pixel"].astype(np.int64), r["vertex"].astype(np.int64)], axis=1)
+    order = np.lexsort(key.T[::-1])
+    return key[order], {k: np.asarray(v)[order] for k, v in r.items()}
+
+
+def compare_merged_rays(gr, orr, n0_max, allow=0):
+    """Same ray ids; bit-exact directions; photons within FP32 accuracy;
+    merged rays' merge position within rounding, distance and level exact.
+    Returns the number of ray ids present on one side only (<= allow)."""
+    gk, g = _table(gr)
+    ok, o = _table(orr)
+    gi = {tuple(k): i for i, k in enumerate(gk)}
+    oi = {tuple(k): i for i, k in enumerate(ok)}
+    only = set(gi) ^ set(oi)
+    assert len(only) <= allow, len(only)
+    common = sorted(set(gi) & set(oi))
+    a = np.array([gi[k] for k in common], np.int64)
+    b = np.array([oi[k] for k in common], np.int64)
+    assert np.array_equal(g["dir"][a], o["dir"][b])
+    assert np.array_equal(g["merged"][a], o["merged"][b])
+    big = o["N"][b] > 1e-9 * n0_max
+    assert np.all(np.abs(g["N"][a] - o["N"][b])[big] <= RAY_RTOL * o["N"][b][big])
+    m = o["merged"][b]
+    if m.any():
+        assert np.all(np.abs(g["P"][a][m] - o["P"][b][m]) <= 2)
+        assert np.array_equal(g["A"][a][m], o["A"][b][m])
+        assert np.allclose(g["thr"][a][m], o["thr"][b][m], rtol=1e-5)
+    return len(only), int(m.sum())
+
+
+@pytest.mark.parametrize("n_ex,l_merge,seed", [(1.0, 0, 2), (2.0, 1, 4), (0.0, 0, 6)])
+def test_merge_run_matches_oracle(n_ex, l_merge, seed):
+    # Up to and including the first step that merges, the two runs hold the
+    # same rays element by element.  After it, merged positions are means
+    # weighted by photon contents that differ at single-precision rounding
+    # (the GPU marches in FP32), which moves them by a few 2^-21 cell; merging
+    # amplifies such differences into different groupings later on (the shot
+    # noise of Sec. 7.1).  Later steps are compared on the quantities Sec. 7.1
+    # uses to validate merging: global ionised fraction and Gamma, and on the
+    # ray count and the photon budget.
+    prob = _prob(n_ex, l_merge, seed=seed)
+    g = F.Simulation(prob, ray_capacity=1 << 22)
+    o = oracle.OracleSim(prob)
+    n0_max = float(np.max(prob.source_ndot)) * prob.dt / 12
+    first = None
+    for s in range(prob.nsteps):
+        g.step(prob.dt)
+        o.step(prob.dt)
+        gb, ob = g.budget(), o.budget()
+        for b in (gb, ob):
+            assert abs(b[0] - b[1] - b[2] - b[3]) <= BUDGET_RTOL * b[0]
+        assert abs(gb[0] - ob[0]) <= 1e-6 * ob[0]
+        oc, gc = o.counts(), g.counts()
+        gf, of = g.fields(), o.fields()
+        orr = o.rays()
+        if first is None:
+            compare_merged_rays(g.rays(), orr, n0_max, allow=64 * oc["near_threshold"])
+            compare_fields(gf, of)
+            if oc["near_threshold"] == 0:
+                assert gc["rays"] == oc["rays"]
+                assert gc["segments_total"] == oc["segments_total"]
+            if orr["merged"].any():
+                first = s
+        else:
+            assert abs(gc["rays"] - oc["rays"]) <= 0.02 * oc["rays"] + 16
+            assert abs(gf["x_HII"].mean() - of["x_HII"].mean()) <= 0.01 * of["x_HII"].mean()
+            assert abs(gf["gamma_HI"].mean() - of["gamma_HI"].mean()) <= 0.02 * of["gamma_HI"].mean()
+            assert np.all(np.abs(gb - ob) <= 0.01 * ob[0])
+    assert first is not None and first < prob.nsteps - 1
+    g.close()
+    o.close()
+
+
+def test_merge_with_everything_exempt_equals_plain_run():
+    p = _prob(1e9, 1)
+    plain = dc.replace(p, options=dc.replace(p.options, merge=False))
+    a = F.Simulation(p, ray_capacity=1 << 22)
+    b = F.Simulation(plain, ray_capacity=1 << 22)
+    for _ in range(p.nsteps):
+        a.step(p.dt)
+        b.step(p.dt)
+    assert a.counts()["rays"] == b.counts()["rays"]
+    assert a.counts()["segments_total"] == b.counts()["segments_total"]
+    compare_fields(a.fields(), b.fields(), x_atol=1e-6, g_rtol=1e-5)
+    assert not a.rays()["merged"].any()
+
+
+def test_merge_ceiling_and_merged_geometry():
+    # Eq. 4 after every merge: live rays <= floor(N_ex N_RT) (+ ties) + N_dir
+    # per occupied cell; merged rays point along their merge pixel's centre
+    prob = _prob(1.0, 1, n=24, nsteps=14, nsrc=16)
+    g = F.Simulation(prob, ray_capacity=1 << 23)
+    K = int(np.floor(prob.options.n_ex * prob.ncell))
+    for s in range(prob.nsteps):
+        g.step(prob.dt)
+        c = g.counts()
+        assert c["rays"] <= K + 48 * prob.ncell + 1024
+    r = g.rays()
+    m = np.nonzero(r["merged"] & (r["birth"] == prob.nsteps - 1) & ~r["vertex"] | (r["vertex"]))[0]
+    assert len(m) > 0
+    for i in m[:500]:
+        if r["level"][i] != prob.options.l_merge and not r["vertex"][i]:
+            continue
+        local = int(r["emitter"][i]) - (1 << 31)
+        Rq = oracle.merge_rotation(prob.options.seed, local, int(r["birth"][i]))
+        assert np.array_equal(r["dir"][i], oracle.direction(prob.options.l_merge, int(r["pixel"][i]), Rq))
+        cell = np.array([local % 24, (local // 24) % 24, local // 576])
+        assert np.all(r["P"][i] // S == cell)
+    b = g.budget()
+    assert abs(b[0] - b[1] - b[2] - b[3]) <= BUDGET_RTOL * b[0]
+    g.close()
+
+
+def test_batch_members_with_merging_equal_alone():
+    steps = 8
+    probs = [_prob(1.0, l, n=n, nsteps=steps, nsrc=6, seed=20 + i)
+             for i, (l, n) in enumerate([(0, 16), (1, 24), (0, 24)])]
+    probs.append(dc.replace(probs[0], options=dc.replace(probs[0].options, merge=False)))
+    B = F.Batch(max_sims=4, max_grid=24, nbins=4, ray_capacity=1 << 22, emitter_capacity=256, merge_l_max=1)
+    slots = [B.add(p) for p in probs]
+    for _ in range(steps):
+        B.step()
+    B.sync()
+    for s, p in zip(slots, probs):
+        a = F.Simulation(p, ray_capacity=1 << 22)
+        for _ in range(steps):
+            a.step(p.dt)
+        compare_fields(B.fields(s), a.fields(), x_atol=1e-5, g_rtol=1e-4)
+        assert B.counts(s)["rays"] == a.counts()["rays"]
+        assert np.allclose(B.budget(s), a.budget(), rtol=1e-5)
+        a.close()
+    B.close()

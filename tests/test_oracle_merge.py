@@ -25,6 +25,22 @@ def _rot(seed, key, step):
     return oracle.rotation(seed, key, step)[1]
 
 
+def test_merge_rotation_is_a_uniform_random_rotation():
+    # single-precision quaternion rotations: orthonormal to float rounding,
+    # proper, and uniform on SO(3) (E[R] = 0, E[R_ij^2] = 1/3)
+    Rs = np.array([oracle.merge_rotation(9, c, s) for c in range(2000) for s in (0, 7)], np.float64) / 2 ** 24
+    for R in Rs[:200]:
+        assert np.abs(R @ R.T - np.eye(3)).max() < 2e-6      # a few float ulps
+        assert abs(np.linalg.det(R) - 1.0) < 3e-6
+    n = len(Rs)
+    assert np.all(np.abs(Rs.mean(0)) < 4.0 * np.sqrt(1.0 / 3.0 / n))
+    assert np.all(np.abs((Rs ** 2).mean(0) - 1.0 / 3.0) < 4.0 * np.sqrt(4.0 / 45.0 / n))
+    assert np.array_equal(oracle.merge_rotation(9, 5, 3, rotate=False), np.eye(3, dtype=np.int32) * 2 ** 24)
+    # distinct cells and steps draw distinct spheres
+    assert not np.array_equal(oracle.merge_rotation(9, 5, 3), oracle.merge_rotation(9, 6, 3))
+    assert not np.array_equal(oracle.merge_rotation(9, 5, 3), oracle.merge_rotation(9, 5, 4))
+
+
 @pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
 def test_merge_pixel_of_pixel_centres(level):
     # a rotated pixel centre falls in its own pixel on the same rotated sphere
@@ -104,6 +120,11 @@ def _end_points(prob, r, step):
     return out
 
 
+def _div_rne(num, den):
+    q, r = divmod(num, den)
+    return q + (1 if 2 * r > den or (2 * r == den and q % 2) else 0)
+
+
 def _key(r, i):
     return (int(r["emitter"][i]), int(r["birth"][i]), int(r["level"][i]), int(r["pixel"][i]), bool(r["vertex"][i]))
 
@@ -132,6 +153,9 @@ def test_merge_step_invariants(n_ex, l_merge):
     T = np.array([oracle.rank_content(x, E) for x in pre["N"]], np.float32)
     Tstar = np.sort(T)[::-1][K - 1]
     exempt = T >= Tstar
+    # merge weights: contents on a 2^-26 grid of the power of two above T_ref
+    wscale = np.float32(2.0 ** (26 - np.frexp(Tstar)[1]))
+    q = np.maximum(1, np.trunc(T * wscale)).astype(np.int64)
     assert exempt.sum() >= K
     post_keys = {_key(post, i): i for i in range(len(post["level"]))}
     for i in np.nonzero(exempt)[0]:
@@ -148,7 +172,7 @@ def test_merge_step_invariants(n_ex, l_merge):
             kept += 1
             continue
         local = int((c[2] * grid[1] + c[1]) * grid[0] + c[0])
-        Rq = _rot(prob.options.seed, (1 << 31) + local, step)
+        Rq = oracle.merge_rotation(prob.options.seed, local, step)
         groups.setdefault((local, oracle.merge_pixel(l_merge, Rq, pre["dir"][i])), []).append(i)
     singles = sum(1 for g in groups.values() if len(g) == 1)
     multi = {k: g for k, g in groups.items() if len(g) > 1}
@@ -162,17 +186,22 @@ def test_merge_step_invariants(n_ex, l_merge):
         local = int(post["emitter"][j]) - (1 << 31)
         pm = int(post["pixel"][j])
         g = multi[(local, pm)]
-        Rq = _rot(prob.options.seed, (1 << 31) + local, step)
+        Rq = oracle.merge_rotation(prob.options.seed, local, step)
         assert np.array_equal(post["dir"][j], oracle.direction(l_merge, pm, Rq))
         assert np.allclose(post["N"][j], pre["N"][g].sum(0), rtol=1e-13)
-        w = pre["N"][g].sum(1)
+        w = [int(x) for x in q[g]]
+        W = sum(w)
         cell = np.array([local % grid[0], (local // grid[0]) % grid[1], local // (grid[0] * grid[1])])
-        P = np.clip(np.rint((w[:, None] * ends[g]).sum(0) / w.sum()), cell * S, cell * S + S - 1)
-        assert np.array_equal(post["P"][j], P)
+        off = ends[g] - cell * S
+        P = [int(cell[a]) * S + _div_rne(sum(wi * int(o) for wi, o in zip(w, off[:, a])), W) for a in range(3)]
+        assert list(post["P"][j]) == P
         assert np.all(post["P"][j] // S == cell)
+        # the photon-weighted mean it stands for, to the weights' resolution
+        wt = pre["N"][g].sum(1)
+        assert np.all(np.abs(post["P"][j] - (wt[:, None] * ends[g]).sum(0) / wt.sum()) <= 1.0 + 1e-6 * S)
         dist = np.where(pre["merged"][g], pre["A"][g] + step - pre["birth"][g], step - pre["birth"][g] + 1)
-        assert post["A"][j] == int(np.rint((w * dist).sum() / w.sum()))
-        L = max(l_merge, int(np.rint((w * pre["level"][g]).sum() / w.sum())))
+        assert post["A"][j] == _div_rne(sum(wi * int(d) for wi, d in zip(w, dist)), W)
+        L = max(l_merge, _div_rne(sum(wi * int(x) for wi, x in zip(w, pre["level"][g])), W))
         assert post["level"][j] == L and post["vertex"][j] == (L > l_merge)
     # every non-exempt ray alone in its group is kept unchanged
     for g in groups.values():
