@@ -376,7 +376,7 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     DevBuf<float> qph[2], qthr[2], grp, n0;
     DevBuf<int4> ecell, rot;
     DevBuf<long long> pref, cell0, boff;
-    DevBuf<uint32_t> bcount;
+    DevBuf<uint32_t> bcount, hole, mover;
     bool ok = dctl.alloc(1) == cudaSuccess && dsim.alloc(1) == cudaSuccess && dacc.alloc(1) == cudaSuccess;
     for (int k = 0; k < 2 && ok; ++k)
         ok = qpl[k].alloc(m) == cudaSuccess && qem[k].alloc(m) == cudaSuccess && qma[k].alloc(m) == cudaSuccess &&
@@ -387,7 +387,8 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
          grp.alloc(ncell * ndir * gw) == cudaSuccess && rot.alloc(3 * ncell) == cudaSuccess &&
          ecell.alloc(std::max(p->n_emitters, 1)) == cudaSuccess && n0.alloc(std::max(p->n_emitters, 1)) == cudaSuccess &&
          pref.alloc(2) == cudaSuccess && cell0.alloc(1) == cudaSuccess && rsim.alloc(1) == cudaSuccess &&
-         bcount.alloc(MERGE_MAX_BLOCKS * 8) == cudaSuccess && boff.alloc(MERGE_MAX_BLOCKS * 8) == cudaSuccess;
+         bcount.alloc(MERGE_MAX_BLOCKS * 8) == cudaSuccess && boff.alloc(MERGE_MAX_BLOCKS * 8) == cudaSuccess &&
+         hole.alloc(m) == cudaSuccess && mover.alloc(m) == cudaSuccess;
     if (!ok) return free_fail(FLEXRT_E_OOM, "probe_merge: device allocation failed");
     // queue layout: structure of arrays, photons bin-major
     auto queue = [&](int k) {
@@ -432,16 +433,16 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     MergeWork w{};
     w.hist = hist.p; w.sel = sel.p; w.tkey = tkey.p; w.tsim = tsim.p; w.gid = gid.p;
     w.grp = grp.p; w.gcnt = gcnt.p; w.rot = rot.p; w.ndir = ndir; w.grp_w = gw;
-    w.bcount = bcount.p; w.boff = boff.p; w.hrep = 1;
+    w.bcount = bcount.p; w.boff = boff.p; w.hrep = 1; w.hole = hole.p; w.mover = mover.p;
     MergeArgs a{dctl.p, dsim.p, dacc.p, 1, {q0, q1}, em, rg, tab, lt, w, nb};
     if (launch_merge(a, sms, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
         return free_fail(FLEXRT_E_CUDA, "probe_merge: kernels failed");
     Ctl hc;
     if (cudaMemcpy(&hc, dctl.p, sizeof(hc), cudaMemcpyDeviceToHost) != cudaSuccess)
         return free_fail(FLEXRT_E_CUDA, "probe_merge: read-back failed");
-    // merged: the kernels wrote the rays back to queue 0; otherwise unchanged
-    const int k = hc.merged ? 0 : 1;
-    const long long cnt = hc.cnt[k];
+    // the rays stay in queue 1, compacted to mlive slots when merged
+    const int k = 1;
+    const long long cnt = hc.merged ? hc.mlive : hc.cnt[1];
     *n_out = cnt;
     const long long c = std::min<long long>(cnt, cap);
     std::vector<int32_t> od(3 * m), om(3 * m);

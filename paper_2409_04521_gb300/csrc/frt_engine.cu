@@ -221,15 +221,17 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
         mw_.hrep = std::max(1, std::min(32, 64 / ms));
         const size_t sz[] = {(size_t)ms * mw_.hrep * HIST_BINS * 4, (size_t)ms * 32, (size_t)cap * 4,
                              (size_t)cap * 4, (size_t)cap * 4, (size_t)ngrp * mw_.grp_w * 4, (size_t)ngrp * 4,
-                             (size_t)nc * 48, (size_t)MERGE_MAX_BLOCKS * 8 * 4, (size_t)MERGE_MAX_BLOCKS * 8 * 8};
+                             (size_t)nc * 48, (size_t)MERGE_MAX_BLOCKS * 8 * 4, (size_t)MERGE_MAX_BLOCKS * 8 * 8,
+                             (size_t)cap * 4, (size_t)cap * 4};
         size_t tot = 0;
         for (size_t v : sz) tot += (v + 255) & ~(size_t)255;
         if (cudaMalloc(&mwmem_, tot) != cudaSuccess) return fail(FLEXRT_E_OOM, "merge scratch allocation failed");
         char *p = (char *)mwmem_;
         void **dst[] = {(void **)&mw_.hist, (void **)&mw_.sel, (void **)&mw_.tkey, (void **)&mw_.tsim,
                         (void **)&mw_.gid, (void **)&mw_.grp, (void **)&mw_.gcnt, (void **)&mw_.rot,
-                        (void **)&mw_.bcount, (void **)&mw_.boff};
-        for (int k = 0; k < 10; ++k) { *dst[k] = p; p += (sz[k] + 255) & ~(size_t)255; }
+                        (void **)&mw_.bcount, (void **)&mw_.boff, (void **)&mw_.hole, (void **)&mw_.mover};
+        for (int k = 0; k < 12; ++k) { *dst[k] = p; p += (sz[k] + 255) & ~(size_t)255; }
+        if (cap >= (1LL << 32)) return fail(FLEXRT_E_INVALID, "merging needs fewer than 2^32 queue slots");
         CK(cudaMemsetAsync(mwmem_, 0, tot, st_));
     }
     if (cudaMallocHost(&h_err_, 64) != cudaSuccess) return fail(FLEXRT_E_OOM, "pinned allocation failed");

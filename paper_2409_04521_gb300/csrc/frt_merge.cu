@@ -18,9 +18,12 @@
 //              leads the group).  The weight is the content on a grid of
 //              2^-26 of the power of two above T_ref (at least 1), so the
 //              means are exact quotients, independent of summation order;
-//   k_memit  : per ray, the compacted copy back into the march's input queue:
-//              exempt and lone rays unchanged, one merged ray per group of two
-//              or more, written by its leader, which also clears the slot.
+//   k_mscan  : the new queue length L (rays left: exempt, lone, one per group)
+//              and the number H of holes below it;
+//   k_memit  : in place: each group's leader overwrites its own slot with the
+//              merged ray and clears the group; holes below L and live rays
+//              at or above L are listed;
+//   k_mmove  : the H live rays at or above L move down into the H holes.
 // Contents are non-negative floats, so their bit patterns order as unsigned
 // integers and the select works on the bits.
 #include "frt_march.cuh"
@@ -89,6 +92,24 @@ __device__ __forceinline__ void hist_add(uint32_t *hist, long long bin) {
 // the simulation a queued ray belongs to
 __device__ __forceinline__ int ray_sim(const Queue &q, const Emitters &em, long long i, uint32_t e) {
     return (e & MERGED_BIT) ? (int)((q.ma[i] >> 16) & 0x7fffu) : __ldg(&em.cell[e]).w;
+}
+
+// The contiguous queue slots [c0, c1) a warp owns in the group and emit
+// passes (the same for both, so per-warp prefix counts follow slot order).
+__device__ __forceinline__ long long warp_chunk_len(long long n, long long nwarps) {
+    return ((n + 31) / 32 + nwarps - 1) / nwarps * 32;
+}
+__device__ __forceinline__ void warp_chunk(long long n, long long &c0, long long &c1) {
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long per = warp_chunk_len(n, nw);
+    c0 = min(w * per, n);
+    c1 = min(c0 + per, n);
+}
+
+// a ray that stays live after the merge: exempt, alone in its group, or a leader
+__device__ __forceinline__ bool stays(uint32_t pl, uint32_t gid) {
+    return pl != DEAD_RAY && (gid == MERGE_KEEP || !(gid & MERGE_FOLLOWER));
 }
 
 // inclusive scan of one value per thread over a block of 1024 threads
@@ -250,7 +271,6 @@ __global__ void __launch_bounds__(1024) k_mfind(MergeArgs A, int pass) {
     uint32_t *hist = A.w.hist + (long long)s * A.w.hrep * HIST_BINS;
     const SimDev &S = A.sims[s];
     if (pass == 1) {
-        if (s == 0 && threadIdx.x == 0) C->cnt[C->par] = 0;   // the merge writes the live rays back here
         if (!merges(S, A.acc[s])) {
             if (threadIdx.x == 0) sel[SEL_STATE] = SEL_OFF;
             return;
@@ -317,11 +337,12 @@ __global__ void __launch_bounds__(256) k_mgroup(MergeArgs A) {
         const int par = C->par;
         const Queue q = A.q[par ^ 1];
         const long long n = C->cnt[par ^ 1];
-        const long long nr = (n + 31) & ~31LL;
         const int ndir = A.w.ndir, gw = A.w.grp_w;
         const int lane = lane_id();
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr;
-             i += (long long)gridDim.x * blockDim.x) {
+        long long c0, c1;
+        warp_chunk(n, c0, c1);
+        for (long long base = c0; base < c1; base += 32) {
+            const long long i = base + lane;
             uint32_t gid = MERGE_KEEP;
             long long slot = -1;
             unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
@@ -330,7 +351,7 @@ __global__ void __launch_bounds__(256) k_mgroup(MergeArgs A) {
             for (int k = 0; k < MAXB + 4; ++k) f[k] = 0.0f;
             int nbf = 0;
             bool live = false;
-            if (i < n) {
+            if (i < c1) {
                 live = q.pl[i] != DEAD_RAY;
                 const int sim = A.w.tsim[i];
                 if (sim >= 0) {
@@ -415,7 +436,7 @@ __global__ void __launch_bounds__(256) k_mgroup(MergeArgs A) {
                 const uint32_t rank = base + (uint32_t)__popc(below);
                 gid = (uint32_t)slot | (rank ? MERGE_FOLLOWER : 0u);
             }
-            if (i < n) {
+            if (i < c1) {
                 A.w.gid[i] = gid;
                 outs += live && (gid == MERGE_KEEP || !(gid & MERGE_FOLLOWER)) ? 1u : 0u;
             }
@@ -428,27 +449,49 @@ __global__ void __launch_bounds__(256) k_mgroup(MergeArgs A) {
     if (lane_id() == 0) A.w.bcount[blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)] = t;
 }
 
-// exclusive prefix of the per-warp output counts; the merged queue's size
-__global__ void __launch_bounds__(1024) k_mscan(MergeArgs A, int nblocks) {
+// exclusive prefix of the per-warp counts of rays that stay; the new queue
+// length L and the number H of holes below it
+__global__ void __launch_bounds__(1024) k_mscan(MergeArgs A, int nwarps) {
     __shared__ unsigned long long sh[32];
     Ctl *C = A.ctl;
     if (C->err || !C->merged) return;
     unsigned long long run = 0;
-    for (int b0 = 0; b0 < nblocks; b0 += blockDim.x) {
+    for (int b0 = 0; b0 < nwarps; b0 += blockDim.x) {
         const int b = b0 + threadIdx.x;
-        const unsigned long long v = b < nblocks ? A.w.bcount[b] : 0ull;
+        const unsigned long long v = b < nwarps ? A.w.bcount[b] : 0ull;
         const unsigned long long incl = block_incl_scan(v, sh);
-        if (b < nblocks) A.w.boff[b] = (long long)(run + incl - v);
+        if (b < nwarps) A.w.boff[b] = (long long)(run + incl - v);
         if (threadIdx.x == blockDim.x - 1) sh[0] = incl;     // block_incl_scan's last barrier has passed
         __syncthreads();
         run += sh[0];
         __syncthreads();
     }
-    if (threadIdx.x == 0) C->cnt[C->par] = (long long)run;
+    // rays that stay below L: the prefix of L's warp plus its own below L
+    const int par = C->par;
+    const long long n = C->cnt[par ^ 1];
+    const long long L = (long long)run;
+    const long long per = warp_chunk_len(n, nwarps);
+    unsigned long long below = 0;
+    if (L < n) {
+        const long long w = L / per;
+        const Queue q = A.q[par ^ 1];
+        unsigned long long c = 0;
+        for (long long i = w * per + threadIdx.x; i < L; i += blockDim.x) c += stays(q.pl[i], A.w.gid[i]) ? 1ull : 0ull;
+        const unsigned long long tot = block_incl_scan(c, sh);
+        if (threadIdx.x == blockDim.x - 1) sh[0] = tot;
+        __syncthreads();
+        below = (unsigned long long)A.w.boff[w] + sh[0];
+    } else {
+        below = run;
+    }
+    if (threadIdx.x == 0) {
+        C->mlive = L;
+        C->mmoves = L - (long long)below;
+    }
 }
 
 // ---------------------------------------------------------------------------
-// compacted copy back: exempt and lone rays unchanged, merged rays by leaders
+// in place: merged rays into their leaders' slots; holes and movers listed
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
     extern __shared__ int sh_drop[];              // per simulation: rays removed by merging
@@ -457,44 +500,35 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
     Ctl *C = A.ctl;
     if (!C->err && C->merged) {
         const int par = C->par;
-        const Queue qs = A.q[par ^ 1], qd = A.q[par];
+        const Queue q = A.q[par ^ 1];
         const long long n = C->cnt[par ^ 1];
-        const long long nr = (n + 31) & ~31LL;
-        const long long stride = (long long)gridDim.x * blockDim.x;
+        const long long L = C->mlive;
         const int ndir = A.w.ndir, gw = A.w.grp_w, nbq = A.nbq;
         const int lane = lane_id();
-        long long out = A.w.boff[blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)];
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += stride) {
-            // 0 nothing, 1 copy, 2 merged ray of group `slot`
-            int what = 0;
-            bool leader = false;
+        long long c0, c1;
+        warp_chunk(n, c0, c1);
+        long long rank0 = A.w.boff[blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)];
+        for (long long base = c0; base < c1; base += 32) {
+            const long long i = base + lane;
+            bool stay = false, leader = false;
             uint32_t slot = 0, gsize = 0;
-            if (i < n && qs.pl[i] != DEAD_RAY) {
-                const uint32_t gid = A.w.gid[i];
-                if (gid == MERGE_KEEP) what = 1;
-                else if (!(gid & MERGE_FOLLOWER)) {
+            if (i < c1) {
+                const uint32_t pl = q.pl[i], gid = A.w.gid[i];
+                stay = stays(pl, gid);
+                if (stay && gid != MERGE_KEEP) {
                     leader = true;
                     slot = gid;
                     gsize = A.w.gcnt[slot];
-                    what = gsize > 1 ? 2 : 1;
                 }
             }
-            // this warp's next slots in the merged queue
-            const unsigned has = __ballot_sync(FULL, what != 0);
-            const long long o = out + __popc(has & ((1u << lane) - 1u));
-            out += __popc(has);
-            if (what == 1) {
-                const uint32_t e = qs.em[i];
-                qd.pl[o] = qs.pl[i]; qd.em[o] = e; qd.bi[o] = qs.bi[i];
-                qd.dx[o] = qs.dx[i]; qd.dy[o] = qs.dy[i]; qd.dz[o] = qs.dz[i];
-#pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < nbq) qd.ph[b][o] = qs.ph[b][i];
-                if (e & MERGED_BIT) {
-                    qd.mx[o] = qs.mx[i]; qd.my[o] = qs.my[i]; qd.mz[o] = qs.mz[i];
-                    qd.ma[o] = qs.ma[i]; qd.mthr[o] = qs.mthr[i];
-                }
-            } else if (what == 2) {
+            const unsigned has = __ballot_sync(FULL, stay);
+            const long long rank = rank0 + __popc(has & ((1u << lane) - 1u));   // live rays before slot i
+            rank0 += __popc(has);
+            if (i < c1) {
+                if (!stay && i < L) A.w.hole[i - rank] = (uint32_t)i;
+                if (stay && i >= L) A.w.mover[L - 1 - rank] = (uint32_t)i;
+            }
+            if (leader && gsize > 1) {
                 const int sim = A.w.tsim[i];
                 const SimDev &S = A.sims[sim];
                 const float *gp = A.w.grp + (long long)slot * gw;
@@ -508,7 +542,7 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) P[k] = (int)(cell[k] << FRAC_BITS) + (int)div_rne(gs[1 + k], W);
                 const int Adist = (int)min(div_rne(gs[4], W), 65535ull);
-                const int L = min(max((int)div_rne(gs[5], W), S.l_merge), S.l_max);
+                const int L2 = min(max((int)div_rne(gs[5], W), S.l_merge), S.l_max);
                 const float *gph = gp + 2 * GSUMS;
                 const int4 *rp = A.w.rot + 3 * g;
                 const int4 rows[3] = {rp[0], rp[1], rp[2]};
@@ -516,16 +550,16 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
                                                     : healpix_vq(S.l_merge, pm);
                 int32_t dx, dy, dz;
                 rotate_dir(rows, vq, dx, dy, dz);
-                qd.pl[o] = ((uint32_t)L << LEVEL_SHIFT) | pm;
-                qd.em[o] = MERGED_BIT | (uint32_t)local;
-                qd.bi[o] = S.step;
-                qd.dx[o] = dx; qd.dy[o] = dy; qd.dz[o] = dz;
+                q.pl[i] = ((uint32_t)L2 << LEVEL_SHIFT) | pm;
+                q.em[i] = MERGED_BIT | (uint32_t)local;
+                q.bi[i] = S.step;
+                q.dx[i] = dx; q.dy[i] = dy; q.dz[i] = dz;
 #pragma unroll
                 for (int k = 0; k < MAXB; ++k)
-                    if (k < nbq) qd.ph[k][o] = k < S.nb ? gph[k] : 0.0f;
-                qd.mx[o] = P[0]; qd.my[o] = P[1]; qd.mz[o] = P[2];
-                qd.ma[o] = (L > S.l_merge ? 0x80000000u : 0u) | ((uint32_t)sim << 16) | (uint32_t)Adist;
-                qd.mthr[o] = gph[S.nb];
+                    if (k < nbq) q.ph[k][i] = k < S.nb ? gph[k] : 0.0f;
+                q.mx[i] = P[0]; q.my[i] = P[1]; q.mz[i] = P[2];
+                q.ma[i] = (L2 > S.l_merge ? 0x80000000u : 0u) | ((uint32_t)sim << 16) | (uint32_t)Adist;
+                q.mthr[i] = gph[S.nb];
                 atomicAdd(&sh_drop[sim], (int)gsize - 1);
             }
             if (leader) {
@@ -539,6 +573,28 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
     __syncthreads();
     for (int k = threadIdx.x; k < A.nsims; k += blockDim.x)
         if (sh_drop[k]) atomicAdd(&A.acc[k].p_rays_out, -(double)sh_drop[k]);
+}
+
+// the live rays at or above L move into the holes below it
+__global__ void __launch_bounds__(256) k_mmove(MergeArgs A) {
+    const Ctl *C = A.ctl;
+    if (C->err || !C->merged) return;
+    const Queue q = A.q[C->par ^ 1];
+    const long long H = C->mmoves;
+    const int nbq = A.nbq;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < H; k += (long long)gridDim.x * blockDim.x) {
+        const long long i = A.w.mover[k], o = A.w.hole[k];
+        const uint32_t e = q.em[i];
+        q.pl[o] = q.pl[i]; q.em[o] = e; q.bi[o] = q.bi[i];
+        q.dx[o] = q.dx[i]; q.dy[o] = q.dy[i]; q.dz[o] = q.dz[i];
+#pragma unroll
+        for (int b = 0; b < MAXB; ++b)
+            if (b < nbq) q.ph[b][o] = q.ph[b][i];
+        if (e & MERGED_BIT) {
+            q.mx[o] = q.mx[i]; q.my[o] = q.my[i]; q.mz[o] = q.mz[i];
+            q.ma[o] = q.ma[i]; q.mthr[o] = q.mthr[i];
+        }
+    }
 }
 
 __global__ void k_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, uint32_t *out) {
@@ -561,6 +617,7 @@ cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st) {
     k_mgroup<<<rblocks, 256, 0, st>>>(a);
     k_mscan<<<1, 1024, 0, st>>>(a, rblocks * 8);
     k_memit<<<rblocks, 256, (size_t)a.nsims * sizeof(int), st>>>(a);
+    k_mmove<<<rblocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -83,8 +83,10 @@ struct Ctl {
     int32_t n_act_emit;      // active emitters
     int32_t n_ranges;        // active cell ranges
     long long ncell_active;  // cells in active simulations
-    int32_t merged;          // this step merged rays into the other queue
+    int32_t merged;          // a simulation merged rays this step
     int32_t pad;
+    long long mlive;         // rays left by the merge (the queue's new length)
+    long long mmoves;        // live rays moved down into holes by the merge
 };
 
 // Structure-of-arrays ray queue.
@@ -132,8 +134,10 @@ struct MergeWork {
     float *grp;              // [cell * ndir + pixel][grp_w]: 6 uint64 weighted sums, photons, threshold
     uint32_t *gcnt;          // [cell * ndir + pixel] group sizes
     int4 *rot;               // [cell][3] merge-sphere rotation rows of this step
-    uint32_t *bcount;        // per warp of the group pass: rays it sends to the merged queue
-    long long *boff;         // their exclusive prefix: where each warp writes
+    uint32_t *bcount;        // per warp of the group pass: rays that stay live after the merge
+    long long *boff;         // their exclusive prefix (warps own contiguous chunks of the queue)
+    uint32_t *hole;          // k-th hole below the new length
+    uint32_t *mover;         // k-th live ray at or above the new length, from the top
     int32_t ndir;            // group slots per cell (12 * 4^l_merge of the deepest allowed level)
     int32_t grp_w;           // floats per group
     int32_t hrep;            // copies of each simulation's histogram (spreads hot bins)
