@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) k_mhist2(MergeArgs A) {
 // leaders go to the merged queue, followers do not -- so the pass also
 // counts each warp's outputs for the exact compaction of k_memit (both
 // kernels give a warp the same queue slots).
-__global__ void __launch_bounds__(256) k_mgroup(MergeArgs A) {
+__global__ void __launch_bounds__(256, 5) k_mgroup(MergeArgs A) {
     const Ctl *C = A.ctl;
     const bool on = !C->err && C->merged;
     uint32_t outs = 0;
@@ -495,7 +495,9 @@ __global__ void __launch_bounds__(1024) k_mscan(MergeArgs A, int nwarps) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
     extern __shared__ int sh_drop[];              // per simulation: rays removed by merging
+    __shared__ int s_done;                        // warps of this block that have finished
     for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) sh_drop[k] = 0;
+    if (threadIdx.x == 0) s_done = 0;
     __syncthreads();
     Ctl *C = A.ctl;
     if (!C->err && C->merged) {
@@ -570,9 +572,19 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
             }
         }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < A.nsims; k += blockDim.x)
-        if (sh_drop[k]) atomicAdd(&A.acc[k].p_rays_out, -(double)sh_drop[k]);
+    // the block's last warp to finish adds the block's counts (no barrier:
+    // warps of unequal work do not wait for each other)
+    __threadfence_block();
+    int last = 0;
+    if (lane_id() == 0) last = atomicAdd(&s_done, 1) == (int)(blockDim.x >> 5) - 1;
+    last = __shfl_sync(FULL, last, 0);
+    if (last) {
+        __threadfence_block();
+        for (int k = lane_id(); k < A.nsims; k += 32) {
+            const int d = atomicAdd(&sh_drop[k], 0);
+            if (d) atomicAdd(&A.acc[k].p_rays_out, -(double)d);
+        }
+    }
 }
 
 // the live rays at or above L move into the holes below it
