@@ -101,7 +101,7 @@ def measured_peak():
 def kernel_sources_sha1():
     import hashlib
     h = hashlib.sha1()
-    for f in ("frt_kernels.cu", "frt_device.cuh", "frt_types.h"):
+    for f in ("frt_march.cuh", "frt_kernels.cu", "frt_device.cuh", "frt_types.h"):
         with open(os.path.join(ROOT, "paper_2409_04521_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
