@@ -176,8 +176,12 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------
 def problem(args):
+    import dataclasses as dc
     import workloads as W
-    return W.cosmo16(n=args.grid, nsteps=args.rt_steps)
+    p = W.cosmo16(n=args.grid, nsteps=args.rt_steps)
+    if getattr(args, "gamma_iters", 1) > 1:
+        p = dc.replace(p, options=dc.replace(p.options, gamma_iters=args.gamma_iters))
+    return p
 
 
 def run_oracle_sample(prob, budget_s):
@@ -334,13 +338,14 @@ def impl_gpu(args, dist):
                "sample": f"first {k} of {prob.nsteps} RT steps of the same workload, single-thread FP64 C "
                          f"({t:.1f} s)"}
 
-    launches_per_sim = 1 + prob.nsteps * (3 + (1 if len(prob.source_ndot) else 0))
+    launches_per_sim = 1 + prob.nsteps * (3 + (1 if len(prob.source_ndot) else 0) + 3 * (args.gamma_iters - 1))
     if dist.rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD_DESC, "grid": args.grid, "rt_steps": prob.nsteps,
+                           "gamma_iters": args.gamma_iters,
                            "ray_capacity": args.capacity, "max_live_rays": max_rays,
                            "parallelism": f"replicas x{dist.ws}",
                            "l2": "working set larger than L2 (ray queues of several GB)",
@@ -600,6 +605,8 @@ def main(argv=None):
     ap.add_argument("--saturate-gap", type=float, default=0.001)
     ap.add_argument("--merge-nex", type=float, nargs="+", default=[16.0, 4.0])
     ap.add_argument("--l-merge", type=int, default=0)
+    ap.add_argument("--gamma-iters", type=int, default=1,
+                    help="passes of the Gamma - <n_HI> iteration per RT step (1 = the plain step)")
     args = ap.parse_args(argv)
     if args.workload == "merge" and args.impl != "reference":
         dist = Dist()

@@ -117,12 +117,19 @@ typedef struct {
     int32_t merge;          /* 1: merge rays                                    */
     int32_t l_merge;        /* merge-sphere level, 0..min(11, l_max)            */
     double n_ex;            /* rays per RT cell exempt from merging (N_ex)      */
+    /* Passes of the Gamma - <n_HI> iteration (Sec. 4.1, Eq. 7-11; with the
+     * sub-grid law also lambda - Gamma, Sec. 4.2): each pass re-marches the
+     * step from the same start with the opacity of the previous pass's
+     * time-averaged neutral fraction (and its Gamma in lambda); the last pass
+     * is committed.  1 = one pass with the start-of-step opacity.  Members of
+     * a batch must all use the same value. */
+    int32_t gamma_iters;
 } flexrt_options;
 
 /* Fill *o with defaults (l_src 0, l_max 12, N_min 3, eps 1e-10, seed 1,
  * rotate 1, isothermal 1, rates 0, 5 iterations, alpha_B 2.59e-13,
  * x_init 1.2e-3, T_init 1e4, automatic capacity, library stream, no merging,
- * l_merge 0, N_ex 16). */
+ * l_merge 0, N_ex 16, one pass per step). */
 void flexrt_default_options(flexrt_options *o);
 
 /* Create one simulation.  n_H: host, nx*ny*nz doubles, physical cm^-3,

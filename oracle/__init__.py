@@ -68,6 +68,7 @@ class Config(C.Structure):
         ("rotate", C.c_int32), ("isothermal", C.c_int32), ("rates", C.c_int32), ("chem_iters", C.c_int32),
         ("alpha_const", C.c_double), ("x_init", C.c_double), ("T_init", C.c_double),
         ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double),
+        ("gamma_iters", C.c_int32), ("pad", C.c_int32),
     ]
 
 
@@ -286,6 +287,7 @@ class OracleSim:
         c.merge = int(getattr(o, "merge", False))
         c.l_merge = int(getattr(o, "l_merge", 0))
         c.n_ex = float(getattr(o, "n_ex", 0.0))
+        c.gamma_iters = int(getattr(o, "gamma_iters", 1))
         nH = np.ascontiguousarray(prob.nH, np.float64).reshape(-1)
         self.ncell = nH.size
         self.nb = sp.nbins

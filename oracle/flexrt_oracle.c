@@ -23,7 +23,9 @@
  *   Sec. 4.2, Eq. 13 and 17 -- tau = kappa*ds and the cell-averaged
  *                       photo-ionisation rate for a finite mean free path
  *                       (kappa = n_HI sigma + 1/lambda_mfp);
- *   Sec. 4.1, Eq. 6-10 -- C2-Ray style time-dependent ionisation update;
+ *   Sec. 4.1, Eq. 6-11 -- C2-Ray style time-dependent ionisation update,
+ *                       optionally iterated with the march (Gamma from the
+ *                       time-averaged n_HI, Eq. 11);
  *   Sec. 4.1, Eq. 12 -- temperature equation (static density, fixed z).
  * Where the paper is silent the reading taken is stated at the spot
  * (fixed-point geometry, termination, rotation sampler, rate fits ...).
@@ -612,6 +614,8 @@ typedef struct {
     double alpha_const, x_init, T_init;
     int32_t merge, l_merge;   /* ray merging on/off, level of the merge sphere */
     double n_ex;              /* rays exempt from merging per RT cell          */
+    int32_t gamma_iters;      /* passes of the Gamma - <n_HI> iteration (>= 1)  */
+    int32_t pad;
 } or_config;
 
 typedef struct {
@@ -619,6 +623,7 @@ typedef struct {
     int64_t ncell;
     double *nH, *y, *T, *gamma, *kap_sub;  /* per cell state; kap_sub in cm^-1 */
     double *ion, *heat, *absd;            /* per step accumulators           */
+    double *y_est, *k_est;                /* iteration: <y> and sub-grid opacity */
     int32_t *segcnt;                      /* segments per cell, last step    */
     int32_t K[OR_MAXL];
     /* emitters */
@@ -645,21 +650,28 @@ static int grow_rays(or_ray **buf, int64_t *cap, int64_t need)
     return 0;
 }
 
-static void update_kappa_sub(or_sim *S, int64_t i)
+/* Sub-grid opacity (cm^-1) of cell i for neutral fraction y and photo-
+ * ionisation rate G (Sec. 4.2, the lambda law of the configuration) */
+static double kappa_sub_of(const or_sim *S, int64_t i, double y, double G)
 {
     const or_config *c = &S->c;
     double k = 0.0;
     if (c->mfp_mode == 1) {
         k = (1.0 + c->z) / c->lambda0_c;
     } else if (c->mfp_mode == 2) {
-        if (1.0 - S->y[i] >= c->xion_thr) {
+        if (1.0 - y >= c->xion_thr) {
             double delta = S->nH[i] / c->nH_mean;
-            double g = S->gamma[i] > c->gamma_floor ? S->gamma[i] : c->gamma_floor;
+            double g = G > c->gamma_floor ? G : c->gamma_floor;
             double lam_c = c->lambda0_c * pow(delta, -c->delta_exp) * pow(g / c->gamma_ref, c->gamma_exp);
             k = (1.0 + c->z) / lam_c;
         }
     }
-    S->kap_sub[i] = k;
+    return k;
+}
+
+static void update_kappa_sub(or_sim *S, int64_t i)
+{
+    S->kap_sub[i] = kappa_sub_of(S, i, S->y[i], S->gamma[i]);
 }
 
 or_sim *or_create(const or_config *cfg, const double *nH)
@@ -678,7 +690,10 @@ or_sim *or_create(const or_config *cfg, const double *nH)
     S->heat = calloc(n, sizeof(double));
     S->absd = calloc(n, sizeof(double));
     S->segcnt = calloc(n, sizeof(int32_t));
-    if (!S->nH || !S->y || !S->T || !S->gamma || !S->kap_sub || !S->ion || !S->heat || !S->absd || !S->segcnt)
+    S->y_est = calloc(n, sizeof(double));
+    S->k_est = calloc(n, sizeof(double));
+    if (!S->nH || !S->y || !S->T || !S->gamma || !S->kap_sub || !S->ion || !S->heat || !S->absd || !S->segcnt ||
+        !S->y_est || !S->k_est)
         return NULL;
     if (S->c.nH_mean <= 0.0) {
         double s = 0.0;
@@ -699,7 +714,7 @@ void or_destroy(or_sim *S)
 {
     if (!S) return;
     free(S->nH); free(S->y); free(S->T); free(S->gamma); free(S->kap_sub);
-    free(S->ion); free(S->heat); free(S->absd); free(S->segcnt);
+    free(S->ion); free(S->heat); free(S->absd); free(S->segcnt); free(S->y_est); free(S->k_est);
     free(S->ecell); free(S->endot); free(S->rays);
     free(S);
 }
@@ -736,12 +751,12 @@ int or_add_sources(or_sim *S, int32_t n, const int32_t *ijk, const double *ndot)
 /* Deposit the photons a ray still carries into `cell` as if the ray stayed
  * there for ever (termination; reading of Sec. 2.1's "rays disappear when
  * tau >> 1": the leftover is absorbed where the ray stops). */
-static void deposit_all(or_sim *S, int64_t cell, const double *N, const double *kap)
+static void deposit_all(or_sim *S, int64_t cell, const double *N, const double *kap, double *absorbed)
 {
     const or_config *c = &S->c;
     for (int b = 0; b < c->nb; ++b) {
         S->absd[cell] += N[b];
-        S->absorbed += N[b];
+        *absorbed += N[b];
         if (kap[b] > 0.0) {
             S->ion[cell] += c->sigma[b] * N[b] / kap[b];
             S->heat[cell] += c->eheat[b] * c->sigma[b] * N[b] / kap[b];
@@ -920,39 +935,24 @@ static int or_merge(or_sim *S, double dt, int64_t s, int64_t Kin)
     return 0;
 }
 
-int or_step(or_sim *S, double dt)
+/* One march of every live ray by one cell width (Sec. 3.1) with absorption
+ * (Eq. 13, 17), escape, termination and splits, through the opacities of
+ * neutral fraction yk and sub-grid opacity ksub (cm^-1) per cell.  Fills the
+ * per-cell deposits and returns the surviving rays and children in *out; the
+ * photon tallies go to *t.  The live rays themselves are not changed. */
+typedef struct { double absorbed, escaped; int64_t segs, near; } or_tally;
+
+static int or_march(or_sim *S, double dt, const double *yk, const double *ksub, or_ray **out_p, int64_t *nout_p,
+                    int64_t *ocap_p, or_tally *t)
 {
     const or_config *c = &S->c;
     const int32_t n3[3] = {c->nx, c->ny, c->nz};
     const int64_t ncast = 12LL << (2 * c->l_src);
-    const double V = c->dx * c->dx * c->dx;
     const int64_t s = S->step;
-
-    /* 1. emission (Sec. 3.1, Eq. 1): new rays march in this same step */
-    if (grow_rays(&S->rays, &S->rcap, S->nray + (int64_t)S->ne * ncast)) return -2;
-    for (int32_t e = 0; e < S->ne; ++e) {
-        double R[9];
-        int32_t Rq[9];
-        or_rotation(c->seed, e, s, c->rotate, R, Rq);
-        double N0 = S->endot[e] * dt / (double)ncast;
-        for (int64_t p = 0; p < ncast; ++p) {
-            or_ray *r = &S->rays[S->nray++];
-            memset(r, 0, sizeof(*r));
-            r->l = c->l_src; r->p = p; r->e = e; r->b = (int32_t)s;
-            or_direction(c->l_src, p, Rq, r->d);
-            for (int b = 0; b < c->nb; ++b) {
-                r->N[b] = c->frac[b] * N0;
-                S->emitted += r->N[b];
-            }
-        }
-    }
-
+    memset(t, 0, sizeof(*t));
     for (int64_t i = 0; i < S->ncell; ++i) { S->ion[i] = 0.0; S->heat[i] = 0.0; S->absd[i] = 0.0; S->segcnt[i] = 0; }
-
-    /* 2. march every ray one cell width (Sec. 3.1) with absorption (Eq. 13, 17) */
     or_ray *out = NULL;
     int64_t nout = 0, ocap = 0;
-    int64_t segs = 0;
     for (int64_t ir = 0; ir < S->nray; ++ir) {
         or_ray r = S->rays[ir];
         /* age: distance travelled before this step, in cells.  A ray cast by
@@ -977,10 +977,10 @@ int or_step(or_sim *S, double dt)
         double kap[OR_MAXB];
         for (int k = 0; k < ns; ++k) {
             int64_t ci = ((int64_t)cells[k][2] * c->ny + cells[k][1]) * c->nx + cells[k][0];
-            double nHI = S->nH[ci] * S->y[ci];
+            double nHI = S->nH[ci] * yk[ci];
             double dsp = ds[k] * c->dx; /* path length, cm */
             for (int b = 0; b < c->nb; ++b) {
-                kap[b] = nHI * c->sigma[b] + S->kap_sub[ci];
+                kap[b] = nHI * c->sigma[b] + ksub[ci];
                 double tau = kap[b] * dsp;
                 double absb = -r.N[b] * expm1(-tau); /* N (1 - e^-tau) */
                 /* Eq. 17: N (1 - e^{-ds/lambda}) sigma lambda, lambda = 1/kappa */
@@ -988,15 +988,15 @@ int or_step(or_sim *S, double dt)
                 S->ion[ci] += ion;
                 S->heat[ci] += c->eheat[b] * ion;
                 S->absd[ci] += absb;
-                S->absorbed += absb;
+                t->absorbed += absb;
                 r.N[b] = r.N[b] * exp(-tau);
             }
             S->segcnt[ci] += 1;
             last = ci;
         }
-        segs += ns;
+        t->segs += ns;
         if (esc) {
-            for (int b = 0; b < c->nb; ++b) S->escaped += r.N[b];
+            for (int b = 0; b < c->nb; ++b) t->escaped += r.N[b];
             continue;
         }
         /* termination: below eps of the ray's unattenuated content */
@@ -1004,9 +1004,9 @@ int or_step(or_sim *S, double dt)
         for (int b = 0; b < c->nb; ++b) tot += r.N[b];
         double thr = r.kind == 0 ? c->eps_term * S->endot[r.e] * dt / (double)ncast * ldexp(1.0, -2 * (r.l - c->l_src))
                                  : r.thr;
-        if (fabs(tot - thr) <= 1e-4 * thr) S->near_threshold++;
+        if (fabs(tot - thr) <= 1e-4 * thr) t->near++;
         if (tot < thr) {
-            deposit_all(S, last, r.N, kap);
+            deposit_all(S, last, r.N, kap, &t->absorbed);
             continue;
         }
         /* splitting (Sec. 3.2, Eq. 2-3): the ray has travelled age+1 cells */
@@ -1032,16 +1032,20 @@ int or_step(or_sim *S, double dt)
             out[nout++] = ch;
         }
     }
-    free(S->rays);
-    S->rays = out; S->nray = nout; S->rcap = ocap;
-    if (c->merge && or_merge(S, dt, s, -1)) return -2;
-    S->segments_last = segs;
-    S->segments_total += segs;
-    S->in_flight = 0.0;
-    for (int64_t i = 0; i < S->nray; ++i)
-        for (int b = 0; b < c->nb; ++b) S->in_flight += S->rays[i].N[b];
+    *out_p = out; *nout_p = nout; *ocap_p = ocap;
+    return 0;
+}
 
-    /* 3. chemistry and temperature per cell (Sec. 4.1) */
+/* Chemistry and temperature per cell (Sec. 4.1) from this step's deposits.
+ * final = 0: one pass of the Gamma - <n_HI> iteration (Eq. 7-11; with the
+ * sub-grid law also the lambda - Gamma iteration of Sec. 4.2): the state is
+ * left unchanged, and y_est / ksub_est receive the time-averaged neutral
+ * fraction and the sub-grid opacity the next march uses.  final = 1: the
+ * step's update is committed. */
+static void or_chem(or_sim *S, double dt, int final, double *y_est, double *ksub_est)
+{
+    const or_config *c = &S->c;
+    const double V = c->dx * c->dx * c->dx;
     for (int64_t i = 0; i < S->ncell; ++i) {
         double G = S->ion[i] / (V * dt);     /* Eq. 17 */
         double Hn = S->heat[i] / (V * dt);   /* sum_nu E_nu Gamma_nu */
@@ -1050,6 +1054,11 @@ int or_step(or_sim *S, double dt)
         double C = c->rates ? or_coll_ion(T0) : 0.0;
         double y0 = S->y[i], y1, ybar;
         or_chem_cell(S->nH[i], G, alpha, C, dt, c->chem_iters, y0, &y1, &ybar);
+        if (!final) {
+            y_est[i] = ybar;
+            ksub_est[i] = kappa_sub_of(S, i, ybar, G);
+            continue;
+        }
         if (!c->isothermal) {
             double heat = S->nH[i] * ybar * Hn;
             S->T[i] = or_temperature(T0, S->nH[i], 1.0 - y0, 1.0 - y1, 1.0 - ybar, heat, c->z, dt);
@@ -1057,6 +1066,64 @@ int or_step(or_sim *S, double dt)
         S->y[i] = y1;
         S->gamma[i] = G;
         update_kappa_sub(S, i);
+    }
+}
+
+int or_step(or_sim *S, double dt)
+{
+    const or_config *c = &S->c;
+    const int64_t ncast = 12LL << (2 * c->l_src);
+    const int64_t s = S->step;
+
+    /* 1. emission (Sec. 3.1, Eq. 1): new rays march in this same step */
+    if (grow_rays(&S->rays, &S->rcap, S->nray + (int64_t)S->ne * ncast)) return -2;
+    for (int32_t e = 0; e < S->ne; ++e) {
+        double R[9];
+        int32_t Rq[9];
+        or_rotation(c->seed, e, s, c->rotate, R, Rq);
+        double N0 = S->endot[e] * dt / (double)ncast;
+        for (int64_t p = 0; p < ncast; ++p) {
+            or_ray *r = &S->rays[S->nray++];
+            memset(r, 0, sizeof(*r));
+            r->l = c->l_src; r->p = p; r->e = e; r->b = (int32_t)s;
+            or_direction(c->l_src, p, Rq, r->d);
+            for (int b = 0; b < c->nb; ++b) {
+                r->N[b] = c->frac[b] * N0;
+                S->emitted += r->N[b];
+            }
+        }
+    }
+
+    /* 2-3. march (Sec. 3.1, Eq. 13, 17) and chemistry (Sec. 4.1).  With
+     * gamma_iters > 1 the step is repeated from the same start state with the
+     * opacity of the time-averaged neutral fraction (and sub-grid opacity) of
+     * the previous pass, until the last pass, which is committed. */
+    const int iters = c->gamma_iters > 1 ? c->gamma_iters : 1;
+    double *yk = S->y, *kk = S->kap_sub;
+    for (int it = 0; it < iters; ++it) {
+        or_ray *out = NULL;
+        int64_t nout = 0, ocap = 0;
+        or_tally t;
+        if (or_march(S, dt, yk, kk, &out, &nout, &ocap, &t)) return -2;
+        if (it + 1 < iters) {
+            free(out);
+            or_chem(S, dt, 0, S->y_est, S->k_est);
+            yk = S->y_est;
+            kk = S->k_est;
+            continue;
+        }
+        free(S->rays);
+        S->rays = out; S->nray = nout; S->rcap = ocap;
+        S->absorbed += t.absorbed;
+        S->escaped += t.escaped;
+        S->near_threshold += t.near;
+        if (c->merge && or_merge(S, dt, s, -1)) return -2;
+        S->segments_last = t.segs;
+        S->segments_total += t.segs;
+        S->in_flight = 0.0;
+        for (int64_t i = 0; i < S->nray; ++i)
+            for (int b = 0; b < c->nb; ++b) S->in_flight += S->rays[i].N[b];
+        or_chem(S, dt, 1, NULL, NULL);
     }
     S->step++;
     return 0;

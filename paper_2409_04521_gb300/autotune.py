@@ -28,8 +28,10 @@ def signature(prob, nsteps: int) -> str:
     h = hashlib.sha1()
     o = prob.options
     merge = (bool(getattr(o, "merge", False)), getattr(o, "l_merge", 0), getattr(o, "n_ex", 0.0))
+    iters = int(getattr(o, "gamma_iters", 1))
     h.update(repr((tuple(prob.grid), prob.spectrum.nbins, len(prob.source_ndot), nsteps,
-                   o.l_src, o.n_ray_min, prob.mfp.mode) + (merge if merge[0] else ())).encode())
+                   o.l_src, o.n_ray_min, prob.mfp.mode) + (merge if merge[0] else ())
+                  + ((iters,) if iters > 1 else ())).encode())
     return h.hexdigest()[:16]
 
 

@@ -45,6 +45,7 @@ extern "C" void flexrt_default_options(flexrt_options *o) {
     o->merge = 0;
     o->l_merge = 0;
     o->n_ex = 16.0;
+    o->gamma_iters = 1;
 }
 
 static flexrt_status free_fail(flexrt_status s, const std::string &m) {

@@ -366,6 +366,8 @@ flexrt_status Engine::make_sim(const flexrt_grid *grid, const flexrt_box *box, c
     h.kap_sub0 = m.lambda0_cm_comoving > 0 ? (float)(h.dx_com / m.lambda0_cm_comoving) : 0.0f;
     h.x_init = opt.x_init; h.T_init = opt.T_init;
     h.nref = 1.0;
+    if (opt.gamma_iters < 1 || opt.gamma_iters > 64) { err = "gamma_iters must be 1..64"; return FLEXRT_E_INVALID; }
+    h.gamma_iters = opt.gamma_iters;
     if (opt.merge) {
         if (opt.l_merge < 0 || opt.l_merge > 11 || opt.l_merge > opt.l_max || !(opt.n_ex >= 0.0)) {
             err = "bad merge options (0 <= l_merge <= min(11, l_max), n_ex >= 0)"; return FLEXRT_E_INVALID;
@@ -402,6 +404,9 @@ flexrt_status Engine::add_sim(const SimDev &proto, const double *n_H, int *slot_
     if (proto.nb > cfg_.nb) return fail(FLEXRT_E_INVALID, "more frequency bins than the engine's layout");
     if (proto.merge && proto.l_merge > cfg_.merge_l_max)
         return fail(FLEXRT_E_INVALID, "merge level deeper than the engine's merge scratch allows");
+    for (const Slot &o : slots_)
+        if (o.used && o.h.gamma_iters != proto.gamma_iters)
+            return fail(FLEXRT_E_INVALID, "members of one engine must use the same gamma_iters");
     const long long c0 = cell_alloc_.alloc(proto.ncell);
     if (c0 < 0) return fail(FLEXRT_E_CAPACITY, "cell arena full");
     CK(cudaStreamSynchronize(st_));
@@ -588,7 +593,7 @@ flexrt_status Engine::launch_step() {
     const int ms = (int)slots_.size();
     EmitArgs ea{ctl_, sims_, acc_, {q_[0], q_[1]}, qcap_, em_, pixtab_, ltab_, cfg_.nb};
     MarchArgs ma{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, qcap_, em_, cells_, pixtab_, ltab_};
-    ChemArgs ca{ctl_, sims_, acc_, ms, cells_, rg_};
+    ChemArgs ca{ctl_, sims_, acc_, ms, cells_, rg_, 1};
     const bool prof = profiling_ && !cfg_.use_graph;
     cudaEvent_t e0 = nullptr;
     auto tic = [&]() {
@@ -600,6 +605,23 @@ flexrt_status Engine::launch_step() {
     tic();
     CK(launch_emit(ea, emit_blocks_, st_));
     toc(0);
+    // passes of the Gamma - <n_HI> iteration before the committed one: march,
+    // trial chemistry (opacity of the time-averaged state), reset of the
+    // step's march output and tallies
+    int iters = 1;
+    for (const Slot &sl : slots_)
+        if (sl.used) iters = std::max(iters, (int)sl.h.gamma_iters);
+    for (int it = 0; it + 1 < iters; ++it) {
+        tic();
+        CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, merge_built()));
+        toc(1);
+        ChemArgs ct = ca;
+        ct.final_pass = 0;
+        tic();
+        CK(launch_chem(ct, chem_blocks_, st_));
+        toc(2);
+        CK(launch_iter_reset(ctl_, acc_, ms, st_));
+    }
     tic();
     CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, merge_built()));
     toc(1);

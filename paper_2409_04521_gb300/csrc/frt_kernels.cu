@@ -197,6 +197,12 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                     xb = xbn;
                     if (conv) break;
                 }
+                if (!A.final_pass) {
+                    // a trial pass of the Gamma - <n_HI> iteration (Eq. 11; with
+                    // the sub-grid law lambda - Gamma): the next march sees the
+                    // opacity of the time-averaged state; the state is kept
+                    A.cells.kap[g] = cell_kappa(S, nH, (double)yb, Gf);
+                } else {
                 // x1 + y1 = 1 holds to rounding: keep x1 in [0, 1]
                 const float x1 = fminf(fmaf(x0f, ef, gf * idt), 1.0f);
                 const double y1 = fma(y0, (double)ef, (double)(gf * bdt));   // neutral fraction kept in FP64
@@ -223,6 +229,7 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                 A.cells.T[g] = T;
                 A.cells.gamma[g] = Gf;
                 A.cells.kap[g] = cell_kappa(S, nH, y1, Gf);
+                }
             }
         }
         const unsigned peers = __match_any_sync(FULL, sim);
@@ -270,6 +277,20 @@ __global__ void k_end(Ctl *C, SimDev *sims, SimAcc *acc, int nsims) {
         }
         C->merged = 0;
     }
+}
+
+// between passes of the Gamma - <n_HI> iteration: the next pass marches the
+// same rays again, so the march's output and the step's tallies are dropped
+// (emission happens once per step; the marched-ray counter keeps every pass)
+__global__ void k_iter_reset(Ctl *C, SimAcc *acc, int nsims) {
+    if (C->err) return;
+    for (int j = threadIdx.x; j < nsims; j += blockDim.x) {
+        SimAcc &a = acc[j];
+        a.rays_in_total += a.p_rays_in;
+        a.p_abs = a.p_esc = a.p_out = a.p_in = 0.0;
+        a.p_seg = a.p_rays_in = a.p_rays_out = 0.0;
+    }
+    if (threadIdx.x == 0) C->cnt[C->par ^ 1] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -402,6 +423,10 @@ cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st) {
     const size_t sh = (size_t)a.nsims * sizeof(double) + (size_t)(2 * a.nsims + 1) * sizeof(long long) +
                       (size_t)a.nsims * sizeof(int);
     k_chem<<<blocks, 256, sh, st>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_iter_reset(Ctl *c, SimAcc *acc, int nsims, cudaStream_t st) {
+    k_iter_reset<<<1, 256, 0, st>>>(c, acc, nsims);
     return cudaGetLastError();
 }
 cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_t st) {

@@ -51,6 +51,7 @@ struct ChemArgs {
     int nsims;
     Cells cells;
     Ranges rg;
+    int final_pass;          // 0: a trial pass of the Gamma - <n_HI> iteration (state unchanged)
 };
 
 // message of the last failed call that has no context (this host thread)
@@ -70,6 +71,8 @@ cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int bloc
 int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims, bool merge);
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st);
 cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_t st);
+// between passes of the iteration: drop the march's output and the step's tallies (not emission)
+cudaError_t launch_iter_reset(Ctl *c, SimAcc *acc, int nsims, cudaStream_t st);
 // the merge step (Sec. 3.3) between the march and the chemistry
 cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st);
 cudaError_t launch_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, uint32_t *out,

@@ -64,6 +64,8 @@ struct SimDev {
     // number of rays exempt from merging, floor(N_ex * N_RT)
     int32_t merge, l_merge, ndir, pad_m;
     long long k_ex;
+    int32_t gamma_iters;    // passes of the Gamma - <n_HI> iteration per step (Sec. 4.1, Eq. 11)
+    int32_t pad_g;
 };
 
 // Per-simulation accumulators, code photons (double) and counters.

@@ -52,7 +52,8 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("rotate", C.c_int32), ("isothermal", C.c_int32), ("rates", C.c_int32),
                 ("chem_iters", C.c_int32), ("alpha_B_const", C.c_double), ("x_init", C.c_double),
                 ("T_init", C.c_double), ("ray_capacity", C.c_int64), ("keep_diagnostics", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double)]
+                ("cuda_stream", C.c_void_p), ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double),
+                ("gamma_iters", C.c_int32)]
 
 
 class BatchConfig(C.Structure):
@@ -168,6 +169,7 @@ def _merge_options(o, po):
     o.merge = int(getattr(po, "merge", False))
     o.l_merge = int(getattr(po, "l_merge", 0))
     o.n_ex = float(getattr(po, "n_ex", 16.0))
+    o.gamma_iters = int(getattr(po, "gamma_iters", 1))
 
 
 def _merged_fields(getter, out, m):

@@ -85,6 +85,7 @@ class Options:
     merge: bool = False                 # ray merging at the end of each step
     l_merge: int = 0                    # HEALPix level of the merge sphere
     n_ex: float = 16.0                  # rays exempt from merging per RT cell
+    gamma_iters: int = 1                # passes of the Gamma - <n_HI> (and lambda - Gamma) iteration
 
 
 @dc.dataclass
