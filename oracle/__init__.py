@@ -68,7 +68,7 @@ class Config(C.Structure):
         ("rotate", C.c_int32), ("isothermal", C.c_int32), ("rates", C.c_int32), ("chem_iters", C.c_int32),
         ("alpha_const", C.c_double), ("x_init", C.c_double), ("T_init", C.c_double),
         ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double),
-        ("gamma_iters", C.c_int32), ("pad", C.c_int32),
+        ("gamma_iters", C.c_int32), ("gen_mode", C.c_int32), ("chi", C.c_double),
     ]
 
 
@@ -114,6 +114,7 @@ def lib():
             L.or_get_rays_aux.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_int64),
                                           P(C.c_double), C.c_int64]
             L.or_get_rays_aux.restype = C.c_int64
+            L.or_get_gen.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
             L.or_apply_merge.argtypes = [C.c_void_p, C.c_double, C.c_int64]
             L.or_set_rays.argtypes = [C.c_void_p, C.c_int64, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32),
                                       P(C.c_int32), P(C.c_int32), P(C.c_double), P(C.c_int32), P(C.c_int32),
@@ -288,6 +289,8 @@ class OracleSim:
         c.l_merge = int(getattr(o, "l_merge", 0))
         c.n_ex = float(getattr(o, "n_ex", 0.0))
         c.gamma_iters = int(getattr(o, "gamma_iters", 1))
+        c.gen_mode = int(getattr(o, "gen_mode", False))
+        c.chi = float(getattr(o, "chi", 0.0))
         nH = np.ascontiguousarray(prob.nH, np.float64).reshape(-1)
         self.ncell = nH.size
         self.nb = sp.nbins
@@ -337,6 +340,13 @@ class OracleSim:
         out = {k: np.zeros(self.ncell) for k in ("gamma_HI", "x_HII", "T", "n_HI")}
         lib().or_get_fields(self._h, *[_p(out[k], C.c_double) for k in ("gamma_HI", "x_HII", "T", "n_HI")])
         return out
+
+    def gen_state(self):
+        """Generalized mode: (ionised volume fraction, neutral fraction inside it) per cell."""
+        x = np.zeros(self.ncell)
+        y = np.zeros(self.ncell)
+        lib().or_get_gen(self._h, _p(x, C.c_double), _p(y, C.c_double))
+        return x, y
 
     def budget(self):
         b = np.zeros(4)

@@ -26,7 +26,11 @@
  *   Sec. 4.1, Eq. 6-11 -- C2-Ray style time-dependent ionisation update,
  *                       optionally iterated with the march (Gamma from the
  *                       time-averaged n_HI, Eq. 11);
- *   Sec. 4.1, Eq. 12 -- temperature equation (static density, fixed z).
+ *   Sec. 4.1, Eq. 12 -- temperature equation (static density, fixed z);
+ *   Sec. 4.2, Eq. 14-19 -- optional Generalized Opacity mode: a cell is a
+ *                       highly ionised fraction x_ion with the sub-grid
+ *                       opacity and a neutral rest behind an infinitely thin
+ *                       moving screen that the photons reaching it advance.
  * Where the paper is silent the reading taken is stated at the spot
  * (fixed-point geometry, termination, rotation sampler, rate fits ...).
  *
@@ -615,7 +619,8 @@ typedef struct {
     int32_t merge, l_merge;   /* ray merging on/off, level of the merge sphere */
     double n_ex;              /* rays exempt from merging per RT cell          */
     int32_t gamma_iters;      /* passes of the Gamma - <n_HI> iteration (>= 1)  */
-    int32_t pad;
+    int32_t gen_mode;         /* 1: Generalized Opacity mode (Sec. 4.2)        */
+    double chi;               /* He/H number ratio of Eq. 18 (singly ionised He) */
 } or_config;
 
 typedef struct {
@@ -624,6 +629,10 @@ typedef struct {
     double *nH, *y, *T, *gamma, *kap_sub;  /* per cell state; kap_sub in cm^-1 */
     double *ion, *heat, *absd;            /* per step accumulators           */
     double *y_est, *k_est;                /* iteration: <y> and sub-grid opacity */
+    double *xion, *yion, *front, *fall, *rho;   /* Generalized mode: ionised volume fraction,
+                                             neutral fraction inside it, photons the screen
+                                             absorbed / that reached it this pass, and the
+                                             fraction of arriving photons it absorbs */
     int32_t *segcnt;                      /* segments per cell, last step    */
     int32_t K[OR_MAXL];
     /* emitters */
@@ -658,6 +667,14 @@ static double kappa_sub_of(const or_sim *S, int64_t i, double y, double G)
     double k = 0.0;
     if (c->mfp_mode == 1) {
         k = (1.0 + c->z) / c->lambda0_c;
+    } else if (c->mfp_mode == 2 && c->gen_mode) {
+        /* the ionised component; a cell never lit yet is optically thin
+         * (the Eq. 14 guess) */
+        if (G > 0.0) {
+            double delta = S->nH[i] / c->nH_mean;
+            double g = G > c->gamma_floor ? G : c->gamma_floor;
+            k = (1.0 + c->z) / (c->lambda0_c * pow(delta, -c->delta_exp) * pow(g / c->gamma_ref, c->gamma_exp));
+        }
     } else if (c->mfp_mode == 2) {
         if (1.0 - y >= c->xion_thr) {
             double delta = S->nH[i] / c->nH_mean;
@@ -667,6 +684,21 @@ static double kappa_sub_of(const or_sim *S, int64_t i, double y, double G)
         }
     }
     return k;
+}
+
+/* Generalized mode, neutral fraction of the highly ionised component: with
+ * the equilibrium model (mfp mode 3, Eq. 20-22) n_HI = alpha n_e n_HII /
+ * Gamma = alpha (1 + chi) n_H^2 / Gamma; a cell never lit yet (Gamma = 0) is
+ * optically thin (the Eq. 14 guess); other laws carry their opacity in
+ * kappa_sub. */
+static double gen_y_ion(const or_sim *S, int64_t i, double G)
+{
+    const or_config *c = &S->c;
+    if (c->mfp_mode != 3 || !(G > 0.0)) return 0.0;
+    double alpha = c->rates ? or_alpha_B(S->T[i]) : c->alpha_const;
+    double g = G > c->gamma_floor ? G : c->gamma_floor;
+    double y = alpha * (1.0 + c->chi) * S->nH[i] / g;
+    return y < 1.0 ? y : 1.0;
 }
 
 static void update_kappa_sub(or_sim *S, int64_t i)
@@ -692,8 +724,13 @@ or_sim *or_create(const or_config *cfg, const double *nH)
     S->segcnt = calloc(n, sizeof(int32_t));
     S->y_est = calloc(n, sizeof(double));
     S->k_est = calloc(n, sizeof(double));
+    S->xion = calloc(n, sizeof(double));
+    S->yion = calloc(n, sizeof(double));
+    S->front = calloc(n, sizeof(double));
+    S->fall = calloc(n, sizeof(double));
+    S->rho = malloc(n * sizeof(double));
     if (!S->nH || !S->y || !S->T || !S->gamma || !S->kap_sub || !S->ion || !S->heat || !S->absd || !S->segcnt ||
-        !S->y_est || !S->k_est)
+        !S->y_est || !S->k_est || !S->xion || !S->yion || !S->front || !S->fall || !S->rho)
         return NULL;
     if (S->c.nH_mean <= 0.0) {
         double s = 0.0;
@@ -702,7 +739,8 @@ or_sim *or_create(const or_config *cfg, const double *nH)
     }
     for (int64_t i = 0; i < n; ++i) {
         S->nH[i] = nH[i];
-        S->y[i] = 1.0 - cfg->x_init;
+        S->y[i] = cfg->gen_mode ? 1.0 : 1.0 - cfg->x_init;   /* Generalized mode: no ionised fraction yet */
+        S->rho[i] = 1.0;
         S->T[i] = cfg->T_init;
         update_kappa_sub(S, i);
     }
@@ -715,6 +753,7 @@ void or_destroy(or_sim *S)
     if (!S) return;
     free(S->nH); free(S->y); free(S->T); free(S->gamma); free(S->kap_sub);
     free(S->ion); free(S->heat); free(S->absd); free(S->segcnt); free(S->y_est); free(S->k_est);
+    free(S->xion); free(S->yion); free(S->front); free(S->fall); free(S->rho);
     free(S->ecell); free(S->endot); free(S->rays);
     free(S);
 }
@@ -950,7 +989,9 @@ static int or_march(or_sim *S, double dt, const double *yk, const double *ksub, 
     const int64_t ncast = 12LL << (2 * c->l_src);
     const int64_t s = S->step;
     memset(t, 0, sizeof(*t));
-    for (int64_t i = 0; i < S->ncell; ++i) { S->ion[i] = 0.0; S->heat[i] = 0.0; S->absd[i] = 0.0; S->segcnt[i] = 0; }
+    for (int64_t i = 0; i < S->ncell; ++i) {
+        S->ion[i] = 0.0; S->heat[i] = 0.0; S->absd[i] = 0.0; S->segcnt[i] = 0; S->front[i] = 0.0; S->fall[i] = 0.0;
+    }
     or_ray *out = NULL;
     int64_t nout = 0, ocap = 0;
     for (int64_t ir = 0; ir < S->nray; ++ir) {
@@ -975,10 +1016,16 @@ static int or_march(or_sim *S, double dt, const double *yk, const double *ksub, 
         if (ns < 0) return -3;
         int64_t last = -1;
         double kap[OR_MAXB];
-        for (int k = 0; k < ns; ++k) {
+        int screened = 0;
+        for (int k = 0; k < ns && !screened; ++k) {
             int64_t ci = ((int64_t)cells[k][2] * c->ny + cells[k][1]) * c->nx + cells[k][0];
             double nHI = S->nH[ci] * yk[ci];
             double dsp = ds[k] * c->dx; /* path length, cm */
+            /* Generalized mode (Sec. 4.2, Eq. 19): the ray crosses the ionised
+             * fraction x_ion of its path with the sub-grid opacity; what then
+             * reaches the neutral rest stops at the screen (Eq. 18) */
+            const double xg = c->gen_mode ? S->xion[ci] : 1.0;
+            if (c->gen_mode) dsp *= xg;
             for (int b = 0; b < c->nb; ++b) {
                 kap[b] = nHI * c->sigma[b] + ksub[ci];
                 double tau = kap[b] * dsp;
@@ -993,7 +1040,26 @@ static int or_march(or_sim *S, double dt, const double *yk, const double *ksub, 
             }
             S->segcnt[ci] += 1;
             last = ci;
+            if (xg < 1.0) {
+                /* the screen absorbs the fraction rho of what reaches it (all of
+                 * it while the cell has atoms to spare); the rest crosses the
+                 * gas the front ionises during the step and goes on */
+                const double rh = S->rho[ci];
+                double nf = 0.0;
+                for (int b = 0; b < c->nb; ++b) {
+                    nf += r.N[b];
+                    r.N[b] = rh >= 1.0 ? 0.0 : r.N[b] * (1.0 - rh);
+                }
+                S->fall[ci] += nf;
+                S->front[ci] += rh * nf;
+                t->absorbed += rh * nf;
+                if (rh >= 1.0) {
+                    t->segs += k + 1;
+                    screened = 1;
+                }
+            }
         }
+        if (screened) continue;
         t->segs += ns;
         if (esc) {
             for (int b = 0; b < c->nb; ++b) t->escaped += r.N[b];
@@ -1046,6 +1112,41 @@ static void or_chem(or_sim *S, double dt, int final, double *y_est, double *ksub
 {
     const or_config *c = &S->c;
     const double V = c->dx * c->dx * c->dx;
+    if (c->gen_mode) {
+        /* Generalized mode: Gamma of the ionised component (Eq. 17 with
+         * ds -> x_ion ds and V -> x_ion V); the screen advances by the photons
+         * it absorbed over the atoms it ionises (Eq. 18), the ionised part
+         * loses what recombines beyond its absorptions; isothermal.  The
+         * screen's share of arriving photons for the next pass (or step) is
+         * the atoms it has left over the photons that reached it */
+        for (int64_t i = 0; i < S->ncell; ++i) {
+            const double x = S->xion[i];
+            const double G = x > 0.0 ? S->ion[i] / (x * V * dt) : 0.0;
+            const double A = (1.0 + c->chi) * S->nH[i] * V;      /* atoms of a whole cell */
+            if (!final) {
+                y_est[i] = gen_y_ion(S, i, G);
+                ksub_est[i] = kappa_sub_of(S, i, 0.0, G);
+                S->rho[i] = S->fall[i] > (1.0 - x) * A ? (1.0 - x) * A / S->fall[i] : 1.0;
+                continue;
+            }
+            /* net atom balance of the cell: photons absorbed at the screen and
+             * in the ionised part, minus recombinations in the ionised part
+             * (alpha (1 + chi) n_H^2 x V dt, the approximation of Eq. 22); in
+             * photo-ionisation equilibrium the last two cancel and this is Eq. 18 */
+            const double alpha = c->rates ? or_alpha_B(S->T[i]) : c->alpha_const;
+            const double rec = alpha * (1.0 + c->chi) * S->nH[i] * S->nH[i] * x * V * dt;
+            double x1 = x + (S->front[i] + S->absd[i] - rec) / A;
+            if (x1 > 1.0) x1 = 1.0;
+            if (x1 < 0.0) x1 = 0.0;
+            S->rho[i] = S->fall[i] > (1.0 - x1) * A ? (1.0 - x1) * A / S->fall[i] : 1.0;
+            S->xion[i] = x1;
+            S->gamma[i] = G;
+            S->yion[i] = gen_y_ion(S, i, G);
+            S->kap_sub[i] = kappa_sub_of(S, i, 0.0, G);
+            S->y[i] = (1.0 - x1) + x1 * S->yion[i];
+        }
+        return;
+    }
     for (int64_t i = 0; i < S->ncell; ++i) {
         double G = S->ion[i] / (V * dt);     /* Eq. 17 */
         double Hn = S->heat[i] / (V * dt);   /* sum_nu E_nu Gamma_nu */
@@ -1099,7 +1200,7 @@ int or_step(or_sim *S, double dt)
      * opacity of the time-averaged neutral fraction (and sub-grid opacity) of
      * the previous pass, until the last pass, which is committed. */
     const int iters = c->gamma_iters > 1 ? c->gamma_iters : 1;
-    double *yk = S->y, *kk = S->kap_sub;
+    double *yk = c->gen_mode ? S->yion : S->y, *kk = S->kap_sub;
     for (int it = 0; it < iters; ++it) {
         or_ray *out = NULL;
         int64_t nout = 0, ocap = 0;
@@ -1219,4 +1320,13 @@ int or_set_rays(or_sim *S, int64_t step, int64_t n, const int32_t *lv, const int
     S->nray = n;
     S->step = step + 1;
     return 0;
+}
+
+/* Generalized mode: ionised volume fraction and neutral fraction inside it */
+void or_get_gen(const or_sim *S, double *xion, double *yion)
+{
+    for (int64_t i = 0; i < S->ncell; ++i) {
+        if (xion) xion[i] = S->xion[i];
+        if (yion) yion[i] = S->yion[i];
+    }
 }

@@ -1,0 +1,69 @@
+"""Pins of the oracle's Generalized Opacity mode (Sec. 4.2, Eq. 14-22;
+Sec. 5.1): a cell is a highly ionised fraction x_ion whose opacity comes
+from a sub-grid law and a neutral rest behind an infinitely thin moving
+screen; with the photo-ionisation-equilibrium law (Eq. 20-22) the ionised
+volume of an isothermal Stromgren sphere follows the analytic I-front law
+(Eq. 21) to better than 1 % after two recombination times, as Sec. 5.1
+reports, and photons are conserved."""
+import dataclasses as dc
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+def _gen_stromgren(nsteps, iters=3, n=32):
+    p = W.stromgren(n=n, nsteps=nsteps)
+    return dc.replace(p, mfp=dc.replace(p.mfp, mode=3),
+                      options=dc.replace(p.options, gen_mode=True, gamma_iters=iters))
+
+
+def test_stromgren_law_after_two_recombination_times():
+    p = _gen_stromgren(380)
+    o = oracle.OracleSim(p)
+    nH, a, ndot = p.nH[0], p.options.alpha_B_const, p.source_ndot.sum()
+    rS = (3 * ndot / (4 * math.pi * a * nH * nH)) ** (1 / 3) / p.dx_phys_cm
+    trec = 1 / (a * nH)
+    for s in range(p.nsteps):
+        o.step(p.dt)
+        t = (s + 1) * p.dt
+        if t >= 2 * trec and (s + 1) % 20 == 0:
+            x, _ = o.gen_state()
+            R = (3 * x.sum() / (4 * math.pi)) ** (1 / 3)
+            assert abs(R / (rS * (1 - math.exp(-t / trec)) ** (1 / 3)) - 1) < 0.01
+        b = o.budget()
+        assert abs(b[0] - b[1] - b[2] - b[3]) <= 1e-11 * b[0]
+
+
+def test_screen_and_ionised_part():
+    p = _gen_stromgren(40)
+    o = oracle.OracleSim(p)
+    for _ in range(p.nsteps):
+        o.step(p.dt)
+    x, y = o.gen_state()
+    f = o.fields()
+    assert np.all((x >= 0) & (x <= 1)) and np.all((y >= 0) & (y <= 1))
+    # the ionised fraction reported is the ionised volume less its residual HI
+    assert np.allclose(f["x_HII"], x * (1 - y), atol=1e-12)
+    # the ionised part is in photo-ionisation equilibrium: y = alpha n_H / Gamma (Eq. 22)
+    lit = (x > 0.5) & (f["gamma_HI"] > 0) & (y < 1)
+    assert lit.sum() > 100
+    assert np.allclose(y[lit], np.minimum(1.0, p.options.alpha_B_const * p.nH[lit] / f["gamma_HI"][lit]), rtol=1e-12)
+    # the neutral rest is sharp: beyond the front cells nothing is ionised
+    assert (x == 0).sum() > 0.5 * x.size and ((x > 0) & (x < 1)).sum() < (x >= 1).sum() + 2000
+
+
+def test_helium_ratio_slows_the_screen():
+    # Eq. 18: the screen ionises (1 + chi) n_H atoms per unit volume
+    res = []
+    for chi in (0.0, 0.08):
+        p = _gen_stromgren(30)
+        p = dc.replace(p, options=dc.replace(p.options, chi=chi))
+        o = oracle.OracleSim(p)
+        for _ in range(p.nsteps):
+            o.step(p.dt)
+        res.append(o.gen_state()[0].sum())
+    assert res[1] < res[0] * 0.97

@@ -58,7 +58,8 @@ class Spectrum:
 
 @dc.dataclass
 class Mfp:
-    mode: int = 0                       # 0 none, 1 constant lambda, 2 power law in ionised cells
+    mode: int = 0                       # 0 none, 1 constant lambda, 2 power law in ionised cells,
+                                        # 3 photo-ionisation equilibrium (Generalized mode only)
     lambda0_cm_comoving: float = 0.0
     delta_exp: float = 1.0
     gamma_ref: float = 1e-12
@@ -86,6 +87,8 @@ class Options:
     l_merge: int = 0                    # HEALPix level of the merge sphere
     n_ex: float = 16.0                  # rays exempt from merging per RT cell
     gamma_iters: int = 1                # passes of the Gamma - <n_HI> (and lambda - Gamma) iteration
+    gen_mode: bool = False              # Generalized Opacity mode (moving-screen I-fronts)
+    chi: float = 0.0                    # He/H number ratio (singly ionised helium, Eq. 18)
 
 
 @dc.dataclass
