@@ -85,7 +85,12 @@ typedef struct {
  * mode 2: in cells with x_HII >= xion_threshold,
  *   lambda = lambda0 * Delta^-delta_exp * (max(Gamma, gamma_floor)/gamma_ref)^gamma_exp
  *   with Delta = n_H / nH_mean (nH_mean = 0: mean of the grid) and Gamma the
- *   previous step's rate. */
+ *   previous step's rate (in Generalized mode: the ionised part of every
+ *   lit cell);
+ * mode 3 (Generalized mode only): photo-ionisation equilibrium in the
+ *   ionised part, n_HI = alpha_B (1 + chi) n_H^2 / max(Gamma, gamma_floor),
+ *   kappa_nu = sigma_nu n_HI (Sec. 5.1, Eq. 20-22).  A part not lit yet is
+ *   optically thin (Eq. 14). */
 typedef struct {
     int32_t mode;
     double lambda0_cm_comoving, delta_exp, gamma_ref, gamma_exp, gamma_floor,
@@ -124,12 +129,21 @@ typedef struct {
      * is committed.  1 = one pass with the start-of-step opacity.  Members of
      * a batch must all use the same value. */
     int32_t gamma_iters;
+    /* Generalized Opacity mode (Sec. 4.2, Eq. 14-22): a cell is a highly
+     * ionised fraction x_ion, crossed with the sub-grid opacity of its mfp
+     * law, and a neutral rest behind an infinitely thin screen that absorbs
+     * what reaches it and advances (Eq. 18-19); chemistry is the cell's atom
+     * balance instead of Eq. 7-10.  Needs isothermal = 1 and gamma_iters >= 2
+     * (lambda and Gamma are iterated to self-consistency).  chi: He/H number
+     * ratio, singly ionised helium in Eq. 18. */
+    int32_t gen_mode;
+    double chi;
 } flexrt_options;
 
 /* Fill *o with defaults (l_src 0, l_max 12, N_min 3, eps 1e-10, seed 1,
  * rotate 1, isothermal 1, rates 0, 5 iterations, alpha_B 2.59e-13,
  * x_init 1.2e-3, T_init 1e4, automatic capacity, library stream, no merging,
- * l_merge 0, N_ex 16, one pass per step). */
+ * l_merge 0, N_ex 16, one pass per step, Standard mode, chi 0). */
 void flexrt_default_options(flexrt_options *o);
 
 /* Create one simulation.  n_H: host, nx*ny*nz doubles, physical cm^-3,
@@ -181,6 +195,10 @@ flexrt_status flexrt_get_segment_counts(flexrt_ctx *ctx, int32_t *out);
 flexrt_status flexrt_get_rays(flexrt_ctx *ctx, int64_t cap, int32_t *level, int64_t *pixel,
                               int32_t *emitter, int32_t *birth, int32_t *dir, double *photons,
                               int64_t *n);
+/* Generalized mode: the highly ionised volume fraction x_ion per cell, host
+ * doubles[ncell] (0 for a Standard-mode simulation).  Synchronises. */
+flexrt_status flexrt_get_ionized_volume(flexrt_ctx *ctx, double *x_ion);
+
 /* For a ray made by a merge, flexrt_get_rays reports emitter = -1 - (local
  * index of the cell it was merged in), birth = the step of the merge and
  * pixel = its merge pixel (a vertex ray) or its NESTED pixel after splits.
@@ -307,6 +325,7 @@ typedef struct {
     int32_t merge_l_max;     /* deepest l_merge members may use (its scratch is
                                 cell_capacity * 12 * 4^merge_l_max groups);
                                 -1: members cannot merge                       */
+    int32_t gen_capable;     /* 1: members may run Generalized mode            */
 } flexrt_batch_config;
 
 void flexrt_default_batch_config(flexrt_batch_config *c);
@@ -338,6 +357,7 @@ flexrt_status flexrt_batch_get_counts(flexrt_batch *b, int32_t slot, int64_t out
 flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *level,
                                     int64_t *pixel, int32_t *emitter, int32_t *birth, int32_t *dir,
                                     double *photons, int64_t *n);
+flexrt_status flexrt_batch_get_ionized_volume(flexrt_batch *b, int32_t slot, double *x_ion);
 flexrt_status flexrt_batch_get_rays_merged(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *merged,
                                            int32_t *vertex, int32_t *dist, int64_t *pos, double *thr,
                                            int64_t *n);

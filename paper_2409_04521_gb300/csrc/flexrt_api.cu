@@ -46,6 +46,8 @@ extern "C" void flexrt_default_options(flexrt_options *o) {
     o->l_merge = 0;
     o->n_ex = 16.0;
     o->gamma_iters = 1;
+    o->gen_mode = 0;
+    o->chi = 0.0;
 }
 
 static flexrt_status free_fail(flexrt_status s, const std::string &m) {
@@ -79,6 +81,7 @@ extern "C" flexrt_status flexrt_create(const flexrt_grid *grid, const flexrt_box
     cfg.use_graph = false;
     cfg.stream = opt.cuda_stream;
     cfg.merge_l_max = opt.merge ? opt.l_merge : -1;
+    cfg.gen_capable = opt.gen_mode != 0;
     s = c->eng.init(cfg);
     if (s == FLEXRT_OK) s = c->eng.add_sim(h, n_H, &c->slot);
     if (s != FLEXRT_OK) {
@@ -120,6 +123,9 @@ extern "C" flexrt_status flexrt_get_rays(flexrt_ctx *c, int64_t cap, int32_t *le
                                          int32_t *emitter, int32_t *birth, int32_t *dir, double *photons,
                                          int64_t *n) {
     return c ? c->eng.rays(c->slot, cap, level, pixel, emitter, birth, dir, photons, n) : FLEXRT_E_INVALID;
+}
+extern "C" flexrt_status flexrt_get_ionized_volume(flexrt_ctx *c, double *x_ion) {
+    return c ? c->eng.ionized_volume(c->slot, x_ion) : FLEXRT_E_INVALID;
 }
 extern "C" flexrt_status flexrt_get_rays_merged(flexrt_ctx *c, int64_t cap, int32_t *merged, int32_t *vertex,
                                                 int32_t *dist, int64_t *pos, double *thr, int64_t *n) {
@@ -175,6 +181,7 @@ extern "C" flexrt_status flexrt_batch_create(const flexrt_batch_config *bc, flex
     cfg.use_graph = bc->use_graph != 0;
     cfg.stream = bc->cuda_stream;
     cfg.merge_l_max = bc->merge_l_max;
+    cfg.gen_capable = bc->gen_capable != 0;
     flexrt_status s = b->eng.init(cfg);
     if (s != FLEXRT_OK) {
         free_fail(s, "flexrt_batch_create: " + b->eng.error());
@@ -226,6 +233,9 @@ extern "C" flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, in
                                                int64_t *pixel, int32_t *emitter, int32_t *birth, int32_t *dir,
                                                double *photons, int64_t *n) {
     return b ? b->eng.rays(slot, cap, level, pixel, emitter, birth, dir, photons, n) : FLEXRT_E_INVALID;
+}
+extern "C" flexrt_status flexrt_batch_get_ionized_volume(flexrt_batch *b, int32_t slot, double *x_ion) {
+    return b ? b->eng.ionized_volume(slot, x_ion) : FLEXRT_E_INVALID;
 }
 extern "C" flexrt_status flexrt_batch_get_rays_merged(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *merged,
                                                       int32_t *vertex, int32_t *dist, int64_t *pos, double *thr,

@@ -505,6 +505,9 @@ __device__ __forceinline__ unsigned long long fixed32(float v) {
     return (m + (1ull << (r - 1))) >> r;
 }
 
+__device__ __forceinline__ void red_add_v2(float2 *addr, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
 __device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                  : "memory");

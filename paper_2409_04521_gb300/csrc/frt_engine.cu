@@ -119,6 +119,7 @@ Engine::~Engine() {
     cudaFree(ctl_); cudaFree(sims_); cudaFree(acc_); cudaFree(qmem_);
     cudaFree(cells_.nH); cudaFree(cells_.y); cudaFree(cells_.x); cudaFree(cells_.T); cudaFree(cells_.gamma);
     cudaFree(cells_.kap); cudaFree(cells_.dep); cudaFree(cells_.segcnt);
+    cudaFree(cells_.xion); cudaFree(cells_.rho); cudaFree(cells_.fscr);
     cudaFree(em_.cell); cudaFree(em_.local); cudaFree(em_.ndot); cudaFree(em_.n0);
     cudaFree(em_.ring); cudaFree(em_.act); cudaFree(em_.act_off);
     cudaFree(rg_.pref); cudaFree(rg_.cell0); cudaFree(rg_.sim);
@@ -206,6 +207,9 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     ALLOC(cells_.kap, nc);
     ALLOC(cells_.dep, nc);
     if (cfg_.keep_diagnostics) ALLOC(cells_.segcnt, nc);
+    ALLOC(cells_.xion, nc);
+    ALLOC(cells_.rho, nc);
+    ALLOC(cells_.fscr, nc);
     ALLOC(rg_.pref, ms + 1);
     ALLOC(rg_.cell0, ms);
     ALLOC(rg_.sim, ms);
@@ -255,9 +259,10 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device_);
     sm_count_ = std::max(sms, 1);
-    if (!march_variant_exists(cfg_.nb, march_agg_, march_minb_, mrg)) { march_agg_ = 0; march_minb_ = 2; }
-    CK(march_prepare(cfg_.nb, march_agg_, march_minb_, ms, mrg));
-    const int per_sm = march_max_blocks_per_sm(cfg_.nb, march_agg_, march_minb_, march_threads_, ms, mrg);
+    const bool ext = ext_variants();
+    if (!march_variant_exists(cfg_.nb, march_agg_, march_minb_, ext)) { march_agg_ = 0; march_minb_ = 2; }
+    CK(march_prepare(cfg_.nb, march_agg_, march_minb_, ms, ext));
+    const int per_sm = march_max_blocks_per_sm(cfg_.nb, march_agg_, march_minb_, march_threads_, ms, ext);
     if (per_sm < 1) return fail(FLEXRT_E_INVALID, "too many simulation slots for one march block");
     march_blocks_ = sm_count_ * std::max(per_sm, 1);
     chem_blocks_ = (int)std::max<long long>(1, std::min<long long>((nc + 255) / 256, (long long)sm_count_ * 8));
@@ -368,6 +373,16 @@ flexrt_status Engine::make_sim(const flexrt_grid *grid, const flexrt_box *box, c
     h.nref = 1.0;
     if (opt.gamma_iters < 1 || opt.gamma_iters > 64) { err = "gamma_iters must be 1..64"; return FLEXRT_E_INVALID; }
     h.gamma_iters = opt.gamma_iters;
+    if (opt.gen_mode) {
+        // Generalized Opacity mode (Sec. 4.2): isothermal here (its T_reion
+        // model is not part of this step), and lambda and Gamma are iterated
+        if (!opt.isothermal || opt.gamma_iters < 2 || !(opt.chi >= 0.0)) {
+            err = "Generalized mode needs isothermal = 1, gamma_iters >= 2 and chi >= 0"; return FLEXRT_E_INVALID;
+        }
+        h.gen_mode = 1;
+        h.chi = opt.chi;
+    }
+    if (m.mode == 3 && !opt.gen_mode) { err = "mfp mode 3 is for Generalized mode"; return FLEXRT_E_INVALID; }
     if (opt.merge) {
         if (opt.l_merge < 0 || opt.l_merge > 11 || opt.l_merge > opt.l_max || !(opt.n_ex >= 0.0)) {
             err = "bad merge options (0 <= l_merge <= min(11, l_max), n_ex >= 0)"; return FLEXRT_E_INVALID;
@@ -402,6 +417,8 @@ flexrt_status Engine::add_sim(const SimDev &proto, const double *n_H, int *slot_
     const int edge = std::max(proto.nx, std::max(proto.ny, proto.nz));
     if (edge > cfg_.max_grid) return fail(FLEXRT_E_INVALID, "grid larger than the engine's max_grid");
     if (proto.nb > cfg_.nb) return fail(FLEXRT_E_INVALID, "more frequency bins than the engine's layout");
+    if (proto.gen_mode && !cfg_.gen_capable)
+        return fail(FLEXRT_E_INVALID, "engine not built for Generalized mode members");
     if (proto.merge && proto.l_merge > cfg_.merge_l_max)
         return fail(FLEXRT_E_INVALID, "merge level deeper than the engine's merge scratch allows");
     for (const Slot &o : slots_)
@@ -613,7 +630,7 @@ flexrt_status Engine::launch_step() {
         if (sl.used) iters = std::max(iters, (int)sl.h.gamma_iters);
     for (int it = 0; it + 1 < iters; ++it) {
         tic();
-        CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, merge_built()));
+        CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, ext_variants()));
         toc(1);
         ChemArgs ct = ca;
         ct.final_pass = 0;
@@ -623,7 +640,7 @@ flexrt_status Engine::launch_step() {
         CK(launch_iter_reset(ctl_, acc_, ms, st_));
     }
     tic();
-    CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, merge_built()));
+    CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, ext_variants()));
     toc(1);
     if (merge_built()) {
         MergeArgs ga{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, em_, rg_, pixtab_, ltab_, mw_, cfg_.nb};
@@ -883,11 +900,22 @@ flexrt_status Engine::rays_merged(int s, int64_t cap, int32_t *merged, int32_t *
     return FLEXRT_OK;
 }
 
+flexrt_status Engine::ionized_volume(int s, double *x_ion) {
+    const Slot *sl = slot(s);
+    if (!sl || !x_ion) return fail(FLEXRT_E_INVALID, "bad slot or buffer");
+    CK(cudaStreamSynchronize(st_));
+    poll(true);
+    std::vector<double> v((size_t)sl->h.ncell);
+    CK(cudaMemcpy(v.data(), cells_.xion + sl->cell0, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < v.size(); ++i) x_ion[i] = sl->h.gen_mode ? (double)v[i] : 0.0;
+    return FLEXRT_OK;
+}
+
 flexrt_status Engine::set_launch(int agg, int minb, int blocks_per_sm) {
-    if (!march_variant_exists(cfg_.nb, agg, minb, merge_built()) || blocks_per_sm < 0 || blocks_per_sm > 32)
+    if (!march_variant_exists(cfg_.nb, agg, minb, ext_variants()) || blocks_per_sm < 0 || blocks_per_sm > 32)
         return fail(FLEXRT_E_INVALID, "march kernel variant not built");
-    CK(march_prepare(cfg_.nb, agg, minb, (int)slots_.size(), merge_built()));
-    const int lim = march_max_blocks_per_sm(cfg_.nb, agg, minb, march_threads_, (int)slots_.size(), merge_built());
+    CK(march_prepare(cfg_.nb, agg, minb, (int)slots_.size(), ext_variants()));
+    const int lim = march_max_blocks_per_sm(cfg_.nb, agg, minb, march_threads_, (int)slots_.size(), ext_variants());
     if (lim < 1) return fail(FLEXRT_E_INVALID, "variant cannot be resident");
     const int bps = blocks_per_sm == 0 ? lim : std::min(blocks_per_sm, lim);
     march_agg_ = agg;

@@ -55,6 +55,7 @@ struct EngineConfig {
     bool use_graph = false;
     void *stream = nullptr;
     int merge_l_max = -1;      // deepest merge-sphere level members may use; -1: no merging
+    bool gen_capable = false;  // members may run Generalized Opacity mode
 };
 
 class Engine {
@@ -81,6 +82,9 @@ class Engine {
     flexrt_status rays_merged(int slot, int64_t cap, int32_t *merged, int32_t *vertex, int32_t *dist, int64_t *pos,
                               double *thr, int64_t *n);
     bool merge_built() const { return cfg_.merge_l_max >= 0; }
+    // the march variants that carry merged rays and the moving screen
+    bool ext_variants() const { return merge_built() || cfg_.gen_capable; }
+    flexrt_status ionized_volume(int slot, double *x_ion);
     flexrt_status set_launch(int agg, int minb, int blocks_per_sm);
     flexrt_status profile(bool on);
     flexrt_status kernel_times(double ms[4], int64_t launches[4], int64_t *rays);

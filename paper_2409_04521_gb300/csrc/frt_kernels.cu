@@ -46,6 +46,30 @@ __device__ __forceinline__ float2 cell_kappa(const SimDev &S, double nH, double 
     return make_float2(kx, ks);
 }
 
+// Generalized mode (Sec. 4.2): neutral fraction of the highly ionised part
+// -- with the photo-ionisation-equilibrium law (mfp mode 3, Eq. 20-22)
+// alpha (1 + chi) n_H / Gamma, else 0 -- and its opacity: n_HI sigma from
+// that fraction plus the sub-grid law's 1/lambda.  A part never lit yet
+// (Gamma = 0) is optically thin (the Eq. 14 guess).
+__device__ __forceinline__ float gen_y_ion(const SimDev &S, double nH, float G) {
+    if (S.mfp_mode != 3 || !(G > 0.0f)) return 0.0f;
+    const float g = fmaxf(G, (float)S.gamma_floor);
+    return fminf(1.0f, S.alpha_iso * (float)(1.0 + S.chi) * (float)nH / g);
+}
+__device__ __forceinline__ float2 gen_kappa(const SimDev &S, double nH, float yion, float G) {
+    const float kx = (float)nH * yion * (float)S.ksc;
+    float ks = 0.0f;
+    if (S.mfp_mode == 1) {
+        ks = S.kap_sub0;
+    } else if (S.mfp_mode == 2 && G > 0.0f) {
+        const float g = fmaxf(G, (float)S.gamma_floor);
+        const float f = powf((float)nH * (float)S.inv_nH_mean, (float)(-S.delta_exp)) *
+                        powf(g * (float)S.inv_gamma_ref, (float)S.gamma_exp);
+        ks = __fdividef(S.kap_sub0, f);
+    }
+    return make_float2(kx, ks);
+}
+
 // e = e^-r, g = (1 - e^-r)/r and h = (1 - g)/r for r >= 0 in single
 // precision: Taylor series below r = 1/2, closed forms above.
 __device__ __forceinline__ void relax_factors(float r, float &e, float &g, float &h) {
@@ -67,14 +91,18 @@ __global__ void k_init_cells(const SimDev *sims, int sim, Cells c) {
     const SimDev &S = sims[sim];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.ncell; i += (long long)gridDim.x * blockDim.x) {
         long long g = S.cell_off + i;
-        double y = 1.0 - S.x_init;
+        // Generalized mode starts with no ionised fraction
+        double y = S.gen_mode ? 1.0 : 1.0 - S.x_init;
         c.y[g] = y;
-        c.x[g] = (float)S.x_init;
+        c.x[g] = S.gen_mode ? 0.0f : (float)S.x_init;
         c.T[g] = (float)S.T_init;
         c.gamma[g] = 0.0f;
         c.dep[g] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (c.segcnt) c.segcnt[g] = 0;
-        c.kap[g] = cell_kappa(S, c.nH[g], y, 0.0f);
+        c.xion[g] = 0.0;
+        c.rho[g] = 1.0f;
+        c.fscr[g] = make_float2(0.f, 0.f);
+        c.kap[g] = S.gen_mode ? gen_kappa(S, c.nH[g], 0.0f, 0.0f) : cell_kappa(S, c.nH[g], y, 0.0f);
     }
 }
 
@@ -165,7 +193,41 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
             const float4 d = A.cells.dep[g];
             A.cells.dep[g] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (A.cells.segcnt) A.cells.segcnt[g] = (int)d.w;
-            if (!err) {
+            const SimDev &SG = A.sims[sim];
+            if (SG.gen_mode) {
+                // Generalized mode (Sec. 4.2): Gamma of the ionised part (Eq. 17
+                // with ds -> x ds, V -> x V); the cell's atom balance -- photons
+                // absorbed at the screen and in the ionised part less the
+                // recombinations there, alpha (1 + chi) n_H^2 x V dt (Eq. 22's
+                // approximation) -- moves x (Eq. 18 when the last two cancel);
+                // the screen's share rho for the next pass or step
+                const float2 fs = A.cells.fscr[g];
+                A.cells.fscr[g] = make_float2(0.f, 0.f);
+                if (!err) {
+                    a_abs = d.x + fs.x;
+                    const double nH = A.cells.nH[g];
+                    const double x = A.cells.xion[g];
+                    const double V = SG.dx_phys * SG.dx_phys * SG.dx_phys;
+                    const double Acell = (1.0 + SG.chi) * nH * V;                // atoms of a whole cell
+                    const float Gf = x > 0.0 ? (float)((double)d.y * SG.gscale / x) : 0.0f;
+                    const double fall = (double)fs.y * SG.nref;
+                    if (!A.final_pass) {
+                        A.cells.rho[g] = fall > (1.0 - x) * Acell ? (float)((1.0 - x) * Acell / fall) : 1.0f;
+                        A.cells.kap[g] = gen_kappa(SG, nH, gen_y_ion(SG, nH, Gf), Gf);
+                    } else {
+                        const double rec = (double)SG.alpha_iso * (1.0 + SG.chi) * nH * nH * x * V * SG.dt;
+                        double x1 = x + ((double)fs.x * SG.nref + (double)d.x * SG.nref - rec) / Acell;
+                        x1 = fmin(fmax(x1, 0.0), 1.0);
+                        A.cells.rho[g] = fall > (1.0 - x1) * Acell ? (float)((1.0 - x1) * Acell / fall) : 1.0f;
+                        const float yi = gen_y_ion(SG, nH, Gf);
+                        A.cells.xion[g] = x1;
+                        A.cells.y[g] = (1.0 - x1) + x1 * (double)yi;
+                        A.cells.x[g] = (float)(x1 * (1.0 - (double)yi));
+                        A.cells.gamma[g] = Gf;
+                        A.cells.kap[g] = gen_kappa(SG, nH, yi, Gf);
+                    }
+                }
+            } else if (!err) {
                 a_abs = d.x;
                 const SimDev &S = A.sims[sim];
                 const float Gf = d.y * (float)S.gscale;               // Eq. 17, 1/s

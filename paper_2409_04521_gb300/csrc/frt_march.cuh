@@ -50,7 +50,7 @@ __device__ __forceinline__ void flush_tallies(float &esc, float &out, unsigned &
 
 // The per-simulation constants the march needs, staged in shared memory.
 struct MarchSim {
-    int nx, ny, nz, step, l_src, l_max, active, l_merge;
+    int nx, ny, nz, step, l_src, l_max, active, l_merge, gen, pad0, pad1, pad2;
     long long coff;
     float eps;
     int K[MAXL];
@@ -66,10 +66,13 @@ __host__ __device__ constexpr size_t march_shared_bytes(int nsims) {
 // AGG selects how the lanes of a warp combine deposits into the same cell
 // before the vector reduction: 0 none, 1 peer groups of equal keys
 // (match_any + pairwise tree), 2 runs of equal consecutive keys.
-// MINB is the resident-block target per SM (register budget).  MERGE adds
-// the rays made by the merge step (Sec. 3.3): they start from their merge
-// position and carry their own distance and termination threshold.
-template <int NB, int AGG, int MINB, int MERGE>
+// MINB is the resident-block target per SM (register budget).  EXT adds
+// the rays made by the merge step (Sec. 3.3), which start from their merge
+// position and carry their own distance and termination threshold, and
+// Generalized Opacity mode (Sec. 4.2): a ray crosses the ionised fraction
+// x_ion of each cell's path with the sub-grid opacity, then meets the moving
+// screen, which absorbs the share rho of what reaches it (Eq. 18-19).
+template <int NB, int AGG, int MINB, int EXT>
 __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
     // per-simulation tallies of this block (photons in 2^-32 fixed point,
     // counts as integers), then the staged constants
@@ -81,6 +84,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         MarchSim &m = msim[i];
         m.nx = S.nx; m.ny = S.ny; m.nz = S.nz; m.step = S.step; m.l_src = S.l_src; m.l_max = S.l_max;
         m.active = S.active; m.l_merge = S.l_merge; m.coff = S.cell_off; m.eps = S.eps_term;
+        m.gen = S.gen_mode; m.pad0 = m.pad1 = m.pad2 = 0;
         for (int l = 0; l < MAXL; ++l) m.K[l] = S.K[l];
         for (int b = 0; b < MAXB; ++b) { m.sig[b] = S.sig[b]; m.sige[b] = S.sige[b]; m.eh[b] = S.eh[b]; }
     }
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 ndx = __ldcs(qi.dx + j); ndy = __ldcs(qi.dy + j); ndz = __ldcs(qi.dz + j);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) nph[b] = __ldcs(qi.ph[b] + j);
-                if (MERGE && (ne_ & MERGED_BIT)) {
+                if (EXT && (ne_ & MERGED_BIT)) {
                     nmx = __ldcs(qi.mx + j); nmy = __ldcs(qi.my + j); nmz = __ldcs(qi.mz + j);
                     nma = __ldcs(qi.ma + j); nmthr = __ldcs(qi.mthr + j);
                 }
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             for (int b = 0; b < NB; ++b) ph[b] = nph[b];
             load_ray(i + stride);
             bool valid = pl != DEAD_RAY;
-            const bool mrg = MERGE && valid && (e & MERGED_BIT);
+            const bool mrg = EXT && valid && (e & MERGED_BIT);
             int sim = 0;
             int4 ec = make_int4(0, 0, 0, 0);
             if (mrg) {
@@ -201,24 +205,36 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     valid = false;
                 }
             }
-            // (2) opacities of the crossed cells
+            // (2) opacities of the crossed cells (Generalized mode: also the
+            // ionised fraction and the screen's share)
             float2 kc[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) kc[j] = key[j] >= 0 ? __ldg(&A.cells.kap[key[j]]) : make_float2(0.f, 0.f);
+            const bool gen = EXT && valid && S.gen;
+            float xg[4], rg[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                xg[j] = 1.0f;
+                rg[j] = 1.0f;
+                if (EXT && gen && key[j] >= 0) { xg[j] = (float)__ldg(&A.cells.xion[key[j]]); rg[j] = __ldg(&A.cells.rho[key[j]]); }
+            }
+            bool screened = false;
             // (3) attenuation and deposits (Eq. 13, Eq. 17)
             int last = -1;
             float2 lastk = make_float2(0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float v[4] = {0.f, 0.f, 0.f, 1.0f};
+                if (EXT && screened) key[j] = -1;
                 if (key[j] >= 0) {
+                    const float dse = EXT ? xg[j] * ds[j] : ds[j];
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
                         float tr, ab;
-                        absorb_transmit(kb * ds[j], ab, tr);
+                        absorb_transmit(kb * dse, ab, tr);
                         const float a = ph[b] * ab;
-                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * ds[j];
+                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * dse;
                         ph[b] *= tr;
                         v[0] += a;
                         v[1] = fmaf(S.sig[b], phin, v[1]);
@@ -226,6 +242,20 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     }
                     last = key[j];
                     lastk = kc[j];
+                    if (EXT && xg[j] < 1.0f) {
+                        // the screen: it absorbs the share rho of what reaches it
+                        float nf = 0.0f;
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) nf += ph[b];
+                        red_add_v2(A.cells.fscr + key[j], rg[j] * nf, nf);
+                        const float keep = rg[j] >= 1.0f ? 0.0f : 1.0f - rg[j];
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) ph[b] *= keep;
+                        if (rg[j] >= 1.0f) {
+                            screened = true;
+                            nseg = j + 1;
+                        }
+                    }
                 }
                 if (AGG == 0) {
                     if (key[j] >= 0) red_add_v4(A.cells.dep + key[j], v[0], v[1], v[2], v[3]);
@@ -247,7 +277,8 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             for (int b = 0; b < NB; ++b) s_end += ph[b];
             int nout = 0, m = 0;
             const int lev = (int)(pl >> LEVEL_SHIFT);
-            if (valid && !esc) {
+            if (EXT && screened) esc = false;
+            if (valid && !esc && !(EXT && screened)) {
                 const float thr = mrg ? mthr : S.eps * __ldg(&A.em.n0[e]) * pow2_neg(2 * (lev - S.l_src));
                 if (s_end < thr) {
                     // termination: the ray's last photons stay in its last cell

@@ -65,7 +65,8 @@ struct SimDev {
     int32_t merge, l_merge, ndir, pad_m;
     long long k_ex;
     int32_t gamma_iters;    // passes of the Gamma - <n_HI> iteration per step (Sec. 4.1, Eq. 11)
-    int32_t pad_g;
+    int32_t gen_mode;       // Generalized Opacity mode (Sec. 4.2): ionised fraction + moving screen
+    double chi;             // He/H number ratio (Eq. 18)
 };
 
 // Per-simulation accumulators, code photons (double) and counters.
@@ -113,6 +114,11 @@ struct Cells {
     float2 *kap;             // (tau per cell at sigma_ref from HI, sub-grid tau per cell)
     float4 *dep;             // (absorbed, Gamma numerator, heating numerator, segments)
     int32_t *segcnt;         // segments of the last step (diagnostics) or null
+    // Generalized Opacity mode (Sec. 4.2)
+    double *xion;            // highly ionised volume fraction (double: it takes per-step
+                             // residuals far below float resolution near 1)
+    float *rho;              // share of the photons reaching the screen that it absorbs
+    float2 *fscr;            // this pass: photons the screen absorbed, photons that reached it
 };
 
 struct Emitters {

@@ -53,14 +53,14 @@ class Options(C.Structure):
                 ("chem_iters", C.c_int32), ("alpha_B_const", C.c_double), ("x_init", C.c_double),
                 ("T_init", C.c_double), ("ray_capacity", C.c_int64), ("keep_diagnostics", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double),
-                ("gamma_iters", C.c_int32)]
+                ("gamma_iters", C.c_int32), ("gen_mode", C.c_int32), ("chi", C.c_double)]
 
 
 class BatchConfig(C.Structure):
     _fields_ = [("max_sims", C.c_int32), ("max_grid", C.c_int32), ("nbins", C.c_int32), ("n_ray_min", C.c_double),
                 ("ray_capacity", C.c_int64), ("cell_capacity", C.c_int64), ("emitter_capacity", C.c_int32),
                 ("keep_diagnostics", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("merge_l_max", C.c_int32)]
+                ("merge_l_max", C.c_int32), ("gen_capable", C.c_int32)]
 
 
 class ProbeRays(C.Structure):
@@ -107,6 +107,8 @@ def lib():
             L.flexrt_get_segment_counts.argtypes = [vp, P(C.c_int32)]
             L.flexrt_get_rays.argtypes = [vp, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32), P(C.c_int32),
                                           P(C.c_int32), P(C.c_double), P(C.c_int64)]
+            L.flexrt_get_ionized_volume.argtypes = [vp, P(C.c_double)]
+            L.flexrt_batch_get_ionized_volume.argtypes = [vp, C.c_int32, P(C.c_double)]
             L.flexrt_get_rays_merged.argtypes = [vp, C.c_int64, P(C.c_int32), P(C.c_int32), P(C.c_int32),
                                                  P(C.c_int64), P(C.c_double), P(C.c_int64)]
             L.flexrt_profile.argtypes = [vp, C.c_int32]
@@ -170,6 +172,8 @@ def _merge_options(o, po):
     o.l_merge = int(getattr(po, "l_merge", 0))
     o.n_ex = float(getattr(po, "n_ex", 16.0))
     o.gamma_iters = int(getattr(po, "gamma_iters", 1))
+    o.gen_mode = int(getattr(po, "gen_mode", False))
+    o.chi = float(getattr(po, "chi", 0.0))
 
 
 def _merged_fields(getter, out, m):
@@ -217,11 +221,12 @@ class Batch:
 
     def __init__(self, max_sims=64, max_grid=160, nbins=3, ray_capacity=0, cell_capacity=None,
                  emitter_capacity=65536, use_graph=True, keep_diagnostics=False, n_ray_min=3.0, stream=None,
-                 merge_l_max=-1):
+                 merge_l_max=-1, gen_capable=False):
         L = lib()
         c = BatchConfig()
         L.flexrt_default_batch_config(C.byref(c))
         c.merge_l_max = int(merge_l_max)
+        c.gen_capable = int(gen_capable)
         c.max_sims, c.max_grid, c.nbins, c.n_ray_min = max_sims, max_grid, nbins, n_ray_min
         c.ray_capacity = int(ray_capacity)
         c.cell_capacity = int(cell_capacity if cell_capacity is not None else max_sims * max_grid ** 3)
@@ -297,6 +302,11 @@ class Batch:
         out = dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
         return _merged_fields(lambda *a: self._check(lib().flexrt_batch_get_rays_merged(self._h, int(slot), *a)),
                               out, m)
+
+    def ionized_volume(self, slot):
+        x = np.zeros(self.members[slot][0])
+        self._check(lib().flexrt_batch_get_ionized_volume(self._h, int(slot), _p(x, C.c_double)))
+        return x
 
     def info(self):
         o = np.zeros(6, np.int64)
@@ -409,6 +419,12 @@ class Simulation:
                                      _p(bi, C.c_int32), _p(d, C.c_int32), _p(N, C.c_double), C.byref(n)), self._h)
         out = dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
         return _merged_fields(lambda *a: _check(lib().flexrt_get_rays_merged(self._h, *a), self._h), out, m)
+
+    def ionized_volume(self):
+        """Generalized mode: the highly ionised volume fraction per cell."""
+        x = np.zeros(self.ncell)
+        _check(lib().flexrt_get_ionized_volume(self._h, _p(x, C.c_double)), self._h)
+        return x
 
     def profile(self, enable=True):
         _check(lib().flexrt_profile(self._h, int(enable)), self._h)
