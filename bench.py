@@ -178,10 +178,26 @@ class ClockSampler:
 def problem(args):
     import dataclasses as dc
     import workloads as W
-    p = W.cosmo16(n=args.grid, nsteps=args.rt_steps)
+    if getattr(args, "problem", "cosmo16") == "cosmo20k":
+        p = W.cosmo20k()
+    else:
+        p = W.cosmo16(n=args.grid, nsteps=args.rt_steps)
     if getattr(args, "gamma_iters", 1) > 1:
         p = dc.replace(p, options=dc.replace(p.options, gamma_iters=args.gamma_iters))
+    if getattr(args, "gen_mode", False):
+        p = dc.replace(p, options=dc.replace(p.options, gen_mode=True, gamma_iters=max(args.gamma_iters, 2)))
     return p
+
+
+def workload_desc(args):
+    if getattr(args, "problem", "cosmo16") == "cosmo20k":
+        d = ("cosmo20k: 200^3 lognormal (sigma_ln=0.6) 200 Mpc/h z=7, 2e4 sources drawn by density, "
+             "3 bins, sub-grid mfp law, isothermal, 200 RT steps x 1 Myr (one simulation per step)")
+    else:
+        d = WORKLOAD_DESC
+    if getattr(args, "gen_mode", False):
+        d += "; Generalized Opacity mode"
+    return d
 
 
 def run_oracle_sample(prob, budget_s):
@@ -338,14 +354,15 @@ def impl_gpu(args, dist):
                "sample": f"first {k} of {prob.nsteps} RT steps of the same workload, single-thread FP64 C "
                          f"({t:.1f} s)"}
 
-    launches_per_sim = 1 + prob.nsteps * (3 + (1 if len(prob.source_ndot) else 0) + 3 * (args.gamma_iters - 1))
+    launches_per_sim = 1 + prob.nsteps * (3 + (1 if len(prob.source_ndot) else 0)
+                                          + 3 * (prob.options.gamma_iters - 1))
     if dist.rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD_DESC, "grid": args.grid, "rt_steps": prob.nsteps,
-                           "gamma_iters": args.gamma_iters,
+                "config": {"workload": workload_desc(args), "grid": prob.grid[0], "rt_steps": prob.nsteps,
+                           "gamma_iters": prob.options.gamma_iters,
                            "ray_capacity": args.capacity, "max_live_rays": max_rays,
                            "parallelism": f"replicas x{dist.ws}",
                            "l2": "working set larger than L2 (ray queues of several GB)",
@@ -607,6 +624,9 @@ def main(argv=None):
     ap.add_argument("--l-merge", type=int, default=0)
     ap.add_argument("--gamma-iters", type=int, default=1,
                     help="passes of the Gamma - <n_HI> iteration per RT step (1 = the plain step)")
+    ap.add_argument("--problem", default="cosmo16", choices=["cosmo16", "cosmo20k"],
+                    help="single-simulation workload of the default line")
+    ap.add_argument("--gen-mode", action="store_true", help="Generalized Opacity mode (at least 2 passes)")
     args = ap.parse_args(argv)
     if args.workload == "merge" and args.impl != "reference":
         dist = Dist()
