@@ -69,6 +69,7 @@ class Config(C.Structure):
         ("alpha_const", C.c_double), ("x_init", C.c_double), ("T_init", C.c_double),
         ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double),
         ("gamma_iters", C.c_int32), ("gen_mode", C.c_int32), ("chi", C.c_double),
+        ("t_reion", C.c_double), ("alpha_pl", C.c_double),
     ]
 
 
@@ -91,6 +92,12 @@ def lib():
                                       P(C.c_double), P(C.c_int)]
             L.or_alpha_B.argtypes = [C.c_double]
             L.or_alpha_B.restype = C.c_double
+            L.or_alpha_A.argtypes = [C.c_double]
+            L.or_alpha_A.restype = C.c_double
+            L.or_pl_heat_per_ion.argtypes = [C.c_double]
+            L.or_pl_heat_per_ion.restype = C.c_double
+            L.or_gen_temperature.argtypes = [C.c_double] * 10
+            L.or_gen_temperature.restype = C.c_double
             L.or_coll_ion.argtypes = [C.c_double]
             L.or_coll_ion.restype = C.c_double
             L.or_cooling.argtypes = [C.c_double] * 5
@@ -230,6 +237,22 @@ def alpha_B(T: float) -> float:
     return lib().or_alpha_B(T)
 
 
+def alpha_A(T: float) -> float:
+    """Case-A recombination coefficient (Hui & Gnedin 1997), cm^3/s."""
+    return lib().or_alpha_A(T)
+
+
+def pl_heat_per_ion(alpha_pl: float) -> float:
+    """Mean excess energy per HI photo-ionisation of a power-law spectrum
+    (index alpha_pl, cut at 4 Ryd, sigma ~ nu^-2.75), the bracket of Eq. 22, erg."""
+    return lib().or_pl_heat_per_ion(alpha_pl)
+
+
+def gen_temperature(T, x0, x1, yion, nH, chi, t_reion, alpha_pl, z, dt) -> float:
+    """Generalized-mode temperature of a cell's ionised part after dt."""
+    return lib().or_gen_temperature(T, x0, x1, yion, nH, chi, t_reion, alpha_pl, z, dt)
+
+
 def coll_ion(T: float) -> float:
     return lib().or_coll_ion(T)
 
@@ -291,6 +314,8 @@ class OracleSim:
         c.gamma_iters = int(getattr(o, "gamma_iters", 1))
         c.gen_mode = int(getattr(o, "gen_mode", False))
         c.chi = float(getattr(o, "chi", 0.0))
+        c.t_reion = float(getattr(o, "t_reion", 2.0e4))
+        c.alpha_pl = float(getattr(o, "alpha_pl", 1.5))
         nH = np.ascontiguousarray(prob.nH, np.float64).reshape(-1)
         self.ncell = nH.size
         self.nb = sp.nbins

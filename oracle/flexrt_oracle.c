@@ -513,6 +513,22 @@ double or_alpha_B(double T)
     double lam = 2.0 * T_HI / T;
     return 2.753e-14 * pow(lam, 1.5) / pow(1.0 + pow(lam / 2.740, 0.407), 2.242);
 }
+/* case-A recombination coefficient (Hui & Gnedin 1997), cm^3/s */
+double or_alpha_A(double T)
+{
+    double lam = 2.0 * T_HI / T;
+    return 1.269e-13 * pow(lam, 1.503) / pow(1.0 + pow(lam / 0.522, 0.470), 1.923);
+}
+
+/* Mean energy given to the gas per HI photo-ionisation for a power-law
+ * spectrum J ~ nu^-alpha cut off at 4 Ryd with sigma ~ nu^-beta, beta = 2.75
+ * (the bracket of Sec. 4.2, Eq. 22), erg */
+double or_pl_heat_per_ion(double alpha_pl)
+{
+    const double a = alpha_pl + 2.75;
+    return 13.6 * EV * (a / (a - 1.0) * (1.0 - pow(4.0, 1.0 - a)) / (1.0 - pow(4.0, -a)) - 1.0);
+}
+
 double or_coll_ion(double T)
 {
     double lam = 2.0 * T_HI / T;
@@ -621,6 +637,8 @@ typedef struct {
     int32_t gamma_iters;      /* passes of the Gamma - <n_HI> iteration (>= 1)  */
     int32_t gen_mode;         /* 1: Generalized Opacity mode (Sec. 4.2)        */
     double chi;               /* He/H number ratio of Eq. 18 (singly ionised He) */
+    double t_reion;           /* Generalized mode: temperature of newly ionised gas (K) */
+    double alpha_pl;          /* Generalized mode: spectral index of Eq. 22's heating   */
 } or_config;
 
 typedef struct {
@@ -699,6 +717,60 @@ static double gen_y_ion(const or_sim *S, int64_t i, double G)
     double g = G > c->gamma_floor ? G : c->gamma_floor;
     double y = alpha * (1.0 + c->chi) * S->nH[i] / g;
     return y < 1.0 ? y : 1.0;
+}
+
+/* Generalized mode, temperature of the ionised gas (Sec. 4.2): newly
+ * ionised gas enters at T_reion and mixes by mass with the gas already
+ * ionised; then Eq. 12 (static density) with the photo-heating of Eq. 22 --
+ * photo-ionisation equilibrium, so each recombination (case A) is one
+ * ionisation bringing the power-law mean excess energy -- against the
+ * cooling rates, with n_HI from the ionised part's neutral fraction and
+ * n_e = n_HII + chi n_H (singly ionised helium).
+ * Sub-steps are the two-stage Rosenbrock scheme ROS2 (Verwer, Spee, Blom
+ * & Hundsdorfer 1999; gamma = 1 + 1/sqrt 2), second order whatever the
+ * Jacobian used: here f' from a one-sided difference over 10^-3 T, taken
+ * as 0 where it is positive.  Each sub-step is at most the one that would
+ * change T by 5% explicitly (at most 1000 sub-steps, the last takes what is
+ * left); the scheme is L-stable, so a step far longer than the time the gas
+ * takes to reach its equilibrium temperature ends at that temperature. */
+static double gen_dTdt(double T, double nHI, double nHII, double ne, double ntot, double epl, double z)
+{
+    const double heat = epl * or_alpha_A(T) * ne * nHII;
+    return 2.0 / (3.0 * KB * ntot) * (heat - or_cooling(T, ne, nHI, nHII, z));
+}
+
+double or_gen_temperature(double T, double x0, double x1, double yion, double nH, double chi, double t_reion,
+                          double alpha_pl, double z, double dt)
+{
+    if (x1 > x0) T = (x0 * T + (x1 - x0) * t_reion) / x1;
+    const double nHII = nH * (1.0 - yion), nHI = nH * yion, ne = nHII + chi * nH;
+    const double ntot = nH * (1.0 + chi) + ne;
+    const double epl = or_pl_heat_per_ion(alpha_pl);
+    double left = dt;
+    const double g = 1.0 + 1.0 / sqrt(2.0);
+    for (int k = 0; k < 1000 && left > 0.0; ++k) {
+        const double f = gen_dTdt(T, nHI, nHII, ne, ntot, epl, z);
+        if (f == 0.0) break;
+        double J = (gen_dTdt(T * 1.001, nHI, nHII, ne, ntot, epl, z) - f) / (0.001 * T);
+        if (J > 0.0) J = 0.0;
+        double h = left;
+        if (k < 999) {
+            double lim = 0.05 * T / fabs(f);
+            if (lim < h) h = lim;
+        }
+        const double w = 1.0 / (1.0 - g * h * J);
+        const double k1 = w * f;
+        const double k2 = w * (gen_dTdt(T + h * k1, nHI, nHII, ne, ntot, epl, z) - 2.0 * k1);
+        T += h * (1.5 * k1 + 0.5 * k2);
+        left -= h;
+    }
+    return T;
+}
+
+static double gen_temperature(const or_sim *S, int64_t i, double x0, double x1, double yion, double dt)
+{
+    const or_config *c = &S->c;
+    return or_gen_temperature(S->T[i], x0, x1, yion, S->nH[i], c->chi, c->t_reion, c->alpha_pl, c->z, dt);
 }
 
 static void update_kappa_sub(or_sim *S, int64_t i)
@@ -1116,7 +1188,8 @@ static void or_chem(or_sim *S, double dt, int final, double *y_est, double *ksub
         /* Generalized mode: Gamma of the ionised component (Eq. 17 with
          * ds -> x_ion ds and V -> x_ion V); the screen advances by the photons
          * it absorbed over the atoms it ionises (Eq. 18), the ionised part
-         * loses what recombines beyond its absorptions; isothermal.  The
+         * loses what recombines beyond its absorptions; temperature as
+         * gen_temperature (or fixed when isothermal).  The
          * screen's share of arriving photons for the next pass (or step) is
          * the atoms it has left over the photons that reached it */
         for (int64_t i = 0; i < S->ncell; ++i) {
@@ -1139,6 +1212,8 @@ static void or_chem(or_sim *S, double dt, int final, double *y_est, double *ksub
             if (x1 > 1.0) x1 = 1.0;
             if (x1 < 0.0) x1 = 0.0;
             S->rho[i] = S->fall[i] > (1.0 - x1) * A ? (1.0 - x1) * A / S->fall[i] : 1.0;
+            if (!c->isothermal && x1 > 0.0)
+                S->T[i] = gen_temperature(S, i, x, x1, gen_y_ion(S, i, G), dt);
             S->xion[i] = x1;
             S->gamma[i] = G;
             S->yion[i] = gen_y_ion(S, i, G);

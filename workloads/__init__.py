@@ -89,6 +89,8 @@ class Options:
     gamma_iters: int = 1                # passes of the Gamma - <n_HI> (and lambda - Gamma) iteration
     gen_mode: bool = False              # Generalized Opacity mode (moving-screen I-fronts)
     chi: float = 0.0                    # He/H number ratio (singly ionised helium, Eq. 18)
+    t_reion: float = 2.0e4              # Generalized mode, not isothermal: T of newly ionised gas (K)
+    alpha_pl: float = 1.5               # Generalized mode: spectral index of the Eq. 22 photo-heating
 
 
 @dc.dataclass
