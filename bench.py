@@ -185,7 +185,7 @@ def problem(args):
     if getattr(args, "gamma_iters", 1) > 1:
         p = dc.replace(p, options=dc.replace(p.options, gamma_iters=args.gamma_iters))
     if getattr(args, "gen_mode", False):
-        p = dc.replace(p, options=dc.replace(p.options, gen_mode=True, gamma_iters=max(args.gamma_iters, 2)))
+        p = dc.replace(p, options=dc.replace(p.options, gen_mode=True, gamma_iters=max(args.gamma_iters, 4)))
     return p
 
 
@@ -626,7 +626,7 @@ def main(argv=None):
                     help="passes of the Gamma - <n_HI> iteration per RT step (1 = the plain step)")
     ap.add_argument("--problem", default="cosmo16", choices=["cosmo16", "cosmo20k"],
                     help="single-simulation workload of the default line")
-    ap.add_argument("--gen-mode", action="store_true", help="Generalized Opacity mode (at least 2 passes)")
+    ap.add_argument("--gen-mode", action="store_true", help="Generalized Opacity mode (at least 4 passes)")
     args = ap.parse_args(argv)
     if args.workload == "merge" and args.impl != "reference":
         dist = Dist()

@@ -133,17 +133,33 @@ typedef struct {
      * ionised fraction x_ion, crossed with the sub-grid opacity of its mfp
      * law, and a neutral rest behind an infinitely thin screen that absorbs
      * what reaches it and advances (Eq. 18-19); chemistry is the cell's atom
-     * balance instead of Eq. 7-10.  Needs isothermal = 1 and gamma_iters >= 2
-     * (lambda and Gamma are iterated to self-consistency).  chi: He/H number
-     * ratio, singly ionised helium in Eq. 18. */
+     * balance instead of Eq. 7-10.  Needs gamma_iters >= 4: lambda, Gamma
+     * and each screen's share of the photons reaching it are iterated towards
+     * self-consistency.  A screen's share comes from the previous pass; a
+     * screen first reached in the last pass absorbs all that reaches it, and
+     * what exceeds its atoms is lost (counted as absorbed): on a 32^3
+     * Stromgren sphere's first 40 steps 8e-3 of the emitted photons with 3
+     * passes, 6e-5 with 4, 2e-6 with 5.  chi: He/H number ratio, singly
+     * ionised helium in Eq. 18.
+     * With isothermal = 0 the ionised part's temperature evolves: gas that
+     * ionises enters at t_reion (K; 0 < t_reion < 1e9, -1 < alpha_pl < 20;
+     * E_INVALID otherwise) and mixes by mass with the gas ionised before;
+     * then Eq. 12 at static density with the photo-heating of Eq. 22
+     * (power-law spectrum of index alpha_pl cut at 4 Ryd, case-A
+     * recombinations balanced by ionisations) against the cooling rates, with
+     * n_HI from the ionised part's neutral fraction.  Gas the screen has not
+     * reached keeps its temperature (no pre-heating). */
     int32_t gen_mode;
     double chi;
+    double t_reion;
+    double alpha_pl;
 } flexrt_options;
 
 /* Fill *o with defaults (l_src 0, l_max 12, N_min 3, eps 1e-10, seed 1,
  * rotate 1, isothermal 1, rates 0, 5 iterations, alpha_B 2.59e-13,
  * x_init 1.2e-3, T_init 1e4, automatic capacity, library stream, no merging,
- * l_merge 0, N_ex 16, one pass per step, Standard mode, chi 0). */
+ * l_merge 0, N_ex 16, one pass per step, Standard mode, chi 0,
+ * t_reion 2e4 K, alpha_pl 1.5). */
 void flexrt_default_options(flexrt_options *o);
 
 /* Create one simulation.  n_H: host, nx*ny*nz doubles, physical cm^-3,

@@ -48,6 +48,8 @@ extern "C" void flexrt_default_options(flexrt_options *o) {
     o->gamma_iters = 1;
     o->gen_mode = 0;
     o->chi = 0.0;
+    o->t_reion = 2.0e4;
+    o->alpha_pl = 1.5;
 }
 
 static flexrt_status free_fail(flexrt_status s, const std::string &m) {

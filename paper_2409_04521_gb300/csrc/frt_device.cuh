@@ -529,6 +529,11 @@ __device__ __forceinline__ float alphaB_f(float T) {
     const float lam = 2.0f * T_HI_F / T;
     return 2.753e-14f * fpow(lam, 1.5f) / fpow(1.0f + fpow(lam * (1.0f / 2.740f), 0.407f), 2.242f);
 }
+// case-A recombination coefficient (Hui & Gnedin 1997)
+__device__ __forceinline__ float alphaA_f(float T) {
+    const float lam = 2.0f * T_HI_F / T;
+    return 1.269e-13f * fpow(lam, 1.503f) / fpow(1.0f + fpow(lam * (1.0f / 0.522f), 0.470f), 1.923f);
+}
 __device__ __forceinline__ float collion_f(float T) {
     const float lam = 2.0f * T_HI_F / T;
     if (lam > 180.0f) return 0.0f;                    // exp(-lam/2) below the float range

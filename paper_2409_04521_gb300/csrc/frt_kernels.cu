@@ -51,10 +51,54 @@ __device__ __forceinline__ float2 cell_kappa(const SimDev &S, double nH, double 
 // alpha (1 + chi) n_H / Gamma, else 0 -- and its opacity: n_HI sigma from
 // that fraction plus the sub-grid law's 1/lambda.  A part never lit yet
 // (Gamma = 0) is optically thin (the Eq. 14 guess).
-__device__ __forceinline__ float gen_y_ion(const SimDev &S, double nH, float G) {
+__device__ __forceinline__ float gen_y_ion(const SimDev &S, double nH, float G, float alpha) {
     if (S.mfp_mode != 3 || !(G > 0.0f)) return 0.0f;
     const float g = fmaxf(G, (float)S.gamma_floor);
-    return fminf(1.0f, S.alpha_iso * (float)(1.0 + S.chi) * (float)nH / g);
+    return fminf(1.0f, alpha * (float)(1.0 + S.chi) * (float)nH / g);
+}
+// case-B recombination coefficient of a Generalized-mode cell at T
+__device__ __forceinline__ float gen_alpha(const SimDev &S, float T) {
+    if (S.isothermal) return S.alpha_iso;
+    return S.rates ? alphaB_f(T) : (float)S.alpha_const;
+}
+
+// Generalized mode with evolving temperature (Sec. 4.2): dT/dt of the
+// ionised part from Eq. 12 at static density -- the photo-heating of Eq. 22,
+// E_pl alpha_A n_e n_HII (photo-ionisations balance case-A recombinations),
+// less the cooling rates with n_HI = y_ion n_H and n_e = n_HII + chi n_H.
+// Per n_H^2 inside, pref = 2 n_H / (3 k_B n_tot / n_H).
+__device__ __forceinline__ float gen_dTdt_f(const SimDev &S, float T, float yion, float xe, float pref, float cc) {
+    const float heat = S.pl_heat * alphaA_f(T) * xe * (1.0f - yion);
+    return pref * (heat - cooling_f(T, xe, yion, 1.0f - yion, cc, S.Tcmb));
+}
+// Newly ionised gas enters at T_reion and mixes by mass with the gas ionised
+// before; then sub-steps of the two-stage Rosenbrock scheme ROS2 (Verwer,
+// Spee, Blom & Hundsdorfer 1999, gamma = 1 + 1/sqrt 2; second order for any
+// Jacobian: here a one-sided difference over 10^-3 T, clipped at 0), each at
+// most the step that would move T by 5% explicitly, at most 1000 (the last
+// takes what is left).  L-stable: a step much longer than the relaxation
+// time ends at the equilibrium temperature.
+__device__ float gen_temperature_f(const SimDev &S, float T0, double x0, double x1, float yion, double nH) {
+    float T = x1 > x0 ? (float)((x0 * (double)T0 + (x1 - x0) * (double)S.t_reion) / x1) : T0;
+    const float nHf = (float)nH;
+    const float xe = 1.0f - yion + (float)S.chi;
+    const float pref = 2.0f * nHf / (3.0f * KB_F * (1.0f + (float)S.chi + xe));
+    const float cc = S.compton_c / nHf;
+    const float gam = 1.70710678f;
+    float left = (float)S.dt;
+    for (int k = 0; k < 1000 && left > 0.0f; ++k) {
+        const float f = gen_dTdt_f(S, T, yion, xe, pref, cc);
+        if (f == 0.0f) break;
+        const float J = fminf((gen_dTdt_f(S, T * 1.001f, yion, xe, pref, cc) - f) / (0.001f * T), 0.0f);
+        float h = left;
+        if (k < 999) h = fminf(h, 0.05f * T / fabsf(f));
+        const float w = 1.0f / (1.0f - gam * h * J);
+        const float k1 = w * f;
+        const float k2 = w * (gen_dTdt_f(S, T + h * k1, yion, xe, pref, cc) - 2.0f * k1);
+        T += h * (1.5f * k1 + 0.5f * k2);
+        left -= h;
+    }
+    return T;
 }
 __device__ __forceinline__ float2 gen_kappa(const SimDev &S, double nH, float yion, float G) {
     const float kx = (float)nH * yion * (float)S.ksc;
@@ -211,15 +255,24 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                     const double Acell = (1.0 + SG.chi) * nH * V;                // atoms of a whole cell
                     const float Gf = x > 0.0 ? (float)((double)d.y * SG.gscale / x) : 0.0f;
                     const double fall = (double)fs.y * SG.nref;
+                    const float T0 = A.cells.T[g];
+                    const float alpha = gen_alpha(SG, T0);
                     if (!A.final_pass) {
                         A.cells.rho[g] = fall > (1.0 - x) * Acell ? (float)((1.0 - x) * Acell / fall) : 1.0f;
-                        A.cells.kap[g] = gen_kappa(SG, nH, gen_y_ion(SG, nH, Gf), Gf);
+                        A.cells.kap[g] = gen_kappa(SG, nH, gen_y_ion(SG, nH, Gf, alpha), Gf);
                     } else {
-                        const double rec = (double)SG.alpha_iso * (1.0 + SG.chi) * nH * nH * x * V * SG.dt;
+                        const double rec = (double)alpha * (1.0 + SG.chi) * nH * nH * x * V * SG.dt;
                         double x1 = x + ((double)fs.x * SG.nref + (double)d.x * SG.nref - rec) / Acell;
                         x1 = fmin(fmax(x1, 0.0), 1.0);
                         A.cells.rho[g] = fall > (1.0 - x1) * Acell ? (float)((1.0 - x1) * Acell / fall) : 1.0f;
-                        const float yi = gen_y_ion(SG, nH, Gf);
+                        // the temperature moves with the start-of-step neutral
+                        // fraction; the committed one is that of the new T
+                        float yi = gen_y_ion(SG, nH, Gf, alpha);
+                        if (!SG.isothermal && x1 > 0.0) {
+                            const float T1 = gen_temperature_f(SG, T0, x, x1, yi, nH);
+                            A.cells.T[g] = T1;
+                            yi = gen_y_ion(SG, nH, Gf, gen_alpha(SG, T1));
+                        }
                         A.cells.xion[g] = x1;
                         A.cells.y[g] = (1.0 - x1) + x1 * (double)yi;
                         A.cells.x[g] = (float)(x1 * (1.0 - (double)yi));

@@ -67,6 +67,9 @@ struct SimDev {
     int32_t gamma_iters;    // passes of the Gamma - <n_HI> iteration per step (Sec. 4.1, Eq. 11)
     int32_t gen_mode;       // Generalized Opacity mode (Sec. 4.2): ionised fraction + moving screen
     double chi;             // He/H number ratio (Eq. 18)
+    // Generalized mode with evolving temperature: T of newly ionised gas (K)
+    // and the Eq. 22 mean excess energy per photo-ionisation (erg)
+    float t_reion, pl_heat;
 };
 
 // Per-simulation accumulators, code photons (double) and counters.

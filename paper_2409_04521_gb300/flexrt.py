@@ -53,7 +53,8 @@ class Options(C.Structure):
                 ("chem_iters", C.c_int32), ("alpha_B_const", C.c_double), ("x_init", C.c_double),
                 ("T_init", C.c_double), ("ray_capacity", C.c_int64), ("keep_diagnostics", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double),
-                ("gamma_iters", C.c_int32), ("gen_mode", C.c_int32), ("chi", C.c_double)]
+                ("gamma_iters", C.c_int32), ("gen_mode", C.c_int32), ("chi", C.c_double),
+                ("t_reion", C.c_double), ("alpha_pl", C.c_double)]
 
 
 class BatchConfig(C.Structure):
@@ -174,6 +175,8 @@ def _merge_options(o, po):
     o.gamma_iters = int(getattr(po, "gamma_iters", 1))
     o.gen_mode = int(getattr(po, "gen_mode", False))
     o.chi = float(getattr(po, "chi", 0.0))
+    o.t_reion = float(getattr(po, "t_reion", 2.0e4))
+    o.alpha_pl = float(getattr(po, "alpha_pl", 1.5))
 
 
 def _merged_fields(getter, out, m):

@@ -102,7 +102,7 @@ def test_stromgren_with_temperature():
     # isothermal analytic one; the gas ahead of the screen is not heated
     p = W.stromgren(n=32, nsteps=200)
     p = dc.replace(p, mfp=dc.replace(p.mfp, mode=3),
-                   options=dc.replace(p.options, gen_mode=True, gamma_iters=3, isothermal=False, rates=1,
+                   options=dc.replace(p.options, gen_mode=True, gamma_iters=4, isothermal=False, rates=1,
                                       T_init=100.0, t_reion=2e4))
     o = oracle.OracleSim(p)
     for _ in range(p.nsteps):
