@@ -447,8 +447,8 @@ __device__ __forceinline__ bool run_sum(int key, float (&v)[NV]) {
 }
 
 // Sum NV values over the whole warp (butterfly); every lane gets the sum.
-template <int NV>
-__device__ __forceinline__ void warp_sum(float (&v)[NV]) {
+template <int NV, typename T>
+__device__ __forceinline__ void warp_sum(T (&v)[NV]) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
 #pragma unroll

@@ -78,9 +78,8 @@ __device__ __forceinline__ float gen_dTdt_f(const SimDev &S, float T, float yion
 // most the step that would move T by 5% explicitly, at most 1000 (the last
 // takes what is left).  L-stable: a step much longer than the relaxation
 // time ends at the equilibrium temperature.
-__device__ float gen_temperature_f(const SimDev &S, float T0, double x0, double x1, float yion, double nH) {
-    float T = x1 > x0 ? (float)((x0 * (double)T0 + (x1 - x0) * (double)S.t_reion) / x1) : T0;
-    const float nHf = (float)nH;
+__device__ float gen_temperature_f(const SimDev &S, float T0, float x0, float dx, float x1, float yion, float nHf) {
+    float T = dx > 0.0f ? (x0 * T0 + dx * S.t_reion) / x1 : T0;
     const float xe = 1.0f - yion + (float)S.chi;
     const float pref = 2.0f * nHf / (3.0f * KB_F * (1.0f + (float)S.chi + xe));
     const float cc = S.compton_c / nHf;
@@ -213,9 +212,18 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
     long long *s_pref = reinterpret_cast<long long *>(sh_abs + A.nsims);
     long long *s_cell0 = s_pref + A.nsims + 1;
     int *s_sim = reinterpret_cast<int *>(s_cell0 + A.nsims);
+    // Generalized mode: its flag and the atoms of a cell per unit n_H, in
+    // code photons
+    float *s_apn = reinterpret_cast<float *>(s_sim + A.nsims);
+    int *s_gen = reinterpret_cast<int *>(s_apn + A.nsims);
     const Ctl *C = A.ctl;
     const int nrng = C->n_ranges;
-    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) sh_abs[i] = 0.0;
+    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) {
+        sh_abs[i] = 0.0;
+        const SimDev &S = A.sims[i];
+        s_apn[i] = (float)((1.0 + S.chi) * S.dx_phys * S.dx_phys * S.dx_phys / S.nref);
+        s_gen[i] = S.gen_mode;
+    }
     for (int i = threadIdx.x; i <= nrng; i += blockDim.x) s_pref[i] = A.rg.pref[i];
     for (int i = threadIdx.x; i < nrng; i += blockDim.x) { s_cell0[i] = A.rg.cell0[i]; s_sim[i] = A.rg.sim[i]; }
     __syncthreads();
@@ -223,6 +231,12 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
     const long long n = C->ncell_active;
     const long long nr = (n + 31) & ~31LL;
     const int lane = lane_id();
+    // absorbed photons: each thread sums its cells of one simulation in a
+    // register and adds the sum to the block's total when the simulation
+    // changes and at the end (one shared-memory atomic per run of cells, not
+    // one per warp and cell)
+    double t_abs = 0.0;
+    int t_sim = -1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += (long long)gridDim.x * blockDim.x) {
         int sim = -1;
         float a_abs = 0.0f;
@@ -234,48 +248,64 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
             }
             sim = s_sim[lo];
             const long long g = s_cell0[lo] + (i - s_pref[lo]);
+            // every load of the cell first: the stores below would otherwise
+            // hold the later loads back, one memory round trip each
+            const bool gen = s_gen[sim] != 0;
             const float4 d = A.cells.dep[g];
+            const double nH = A.cells.nH[g];
+            const float T0 = A.cells.T[g];
+            float2 fs = make_float2(0.f, 0.f);
+            double xs;                     // Generalized: x_ion; Standard: neutral fraction y
+            float x0f = 0.0f;
+            if (gen) {
+                fs = A.cells.fscr[g];
+                xs = A.cells.xion[g];
+            } else {
+                xs = A.cells.y[g];
+                x0f = A.cells.x[g];
+            }
             A.cells.dep[g] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (A.cells.segcnt) A.cells.segcnt[g] = (int)d.w;
+            if (gen) A.cells.fscr[g] = make_float2(0.f, 0.f);
             const SimDev &SG = A.sims[sim];
-            if (SG.gen_mode) {
+            if (gen) {
                 // Generalized mode (Sec. 4.2): Gamma of the ionised part (Eq. 17
                 // with ds -> x ds, V -> x V); the cell's atom balance -- photons
                 // absorbed at the screen and in the ionised part less the
                 // recombinations there, alpha (1 + chi) n_H^2 x V dt (Eq. 22's
                 // approximation) -- moves x (Eq. 18 when the last two cancel);
                 // the screen's share rho for the next pass or step
-                const float2 fs = A.cells.fscr[g];
-                A.cells.fscr[g] = make_float2(0.f, 0.f);
                 if (!err) {
+                    // single precision except the state x_ion and its
+                    // complement (FP64 is a narrow pipe on this part): the
+                    // atoms of the cell Ac and the photons in code units, and
+                    // the recombinations per atom alpha n_H x dt
                     a_abs = d.x + fs.x;
-                    const double nH = A.cells.nH[g];
-                    const double x = A.cells.xion[g];
-                    const double V = SG.dx_phys * SG.dx_phys * SG.dx_phys;
-                    const double Acell = (1.0 + SG.chi) * nH * V;                // atoms of a whole cell
-                    const float Gf = x > 0.0 ? (float)((double)d.y * SG.gscale / x) : 0.0f;
-                    const double fall = (double)fs.y * SG.nref;
-                    const float T0 = A.cells.T[g];
+                    const double x = xs;
+                    const float xf = (float)x, omx = (float)(1.0 - x);
+                    const float nHf = (float)nH;
+                    const float Ac = nHf * s_apn[sim];                           // atoms of a whole cell
+                    const float Gf = xf > 0.0f ? d.y * (float)SG.gscale / xf : 0.0f;
                     const float alpha = gen_alpha(SG, T0);
                     if (!A.final_pass) {
-                        A.cells.rho[g] = fall > (1.0 - x) * Acell ? (float)((1.0 - x) * Acell / fall) : 1.0f;
+                        A.cells.rho[g] = fs.y > omx * Ac ? omx * Ac / fs.y : 1.0f;
                         A.cells.kap[g] = gen_kappa(SG, nH, gen_y_ion(SG, nH, Gf, alpha), Gf);
                     } else {
-                        const double rec = (double)alpha * (1.0 + SG.chi) * nH * nH * x * V * SG.dt;
-                        double x1 = x + ((double)fs.x * SG.nref + (double)d.x * SG.nref - rec) / Acell;
-                        x1 = fmin(fmax(x1, 0.0), 1.0);
-                        A.cells.rho[g] = fall > (1.0 - x1) * Acell ? (float)((1.0 - x1) * Acell / fall) : 1.0f;
+                        const float dxf = (fs.x + d.x) / Ac - alpha * nHf * xf * (float)SG.dt;
+                        const double x1 = fmin(fmax(x + (double)dxf, 0.0), 1.0);
+                        const float om1 = (float)(1.0 - x1), x1f = (float)x1;
+                        A.cells.rho[g] = fs.y > om1 * Ac ? om1 * Ac / fs.y : 1.0f;
                         // the temperature moves with the start-of-step neutral
                         // fraction; the committed one is that of the new T
                         float yi = gen_y_ion(SG, nH, Gf, alpha);
                         if (!SG.isothermal && x1 > 0.0) {
-                            const float T1 = gen_temperature_f(SG, T0, x, x1, yi, nH);
+                            const float T1 = gen_temperature_f(SG, T0, xf, (float)(x1 - x), x1f, yi, nHf);
                             A.cells.T[g] = T1;
                             yi = gen_y_ion(SG, nH, Gf, gen_alpha(SG, T1));
                         }
                         A.cells.xion[g] = x1;
-                        A.cells.y[g] = (1.0 - x1) + x1 * (double)yi;
-                        A.cells.x[g] = (float)(x1 * (1.0 - (double)yi));
+                        A.cells.y[g] = fma(x1, (double)yi, 1.0 - x1);
+                        A.cells.x[g] = x1f * (1.0f - yi);
                         A.cells.gamma[g] = Gf;
                         A.cells.kap[g] = gen_kappa(SG, nH, yi, Gf);
                     }
@@ -284,11 +314,9 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                 a_abs = d.x;
                 const SimDev &S = A.sims[sim];
                 const float Gf = d.y * (float)S.gscale;               // Eq. 17, 1/s
-                const double nH = A.cells.nH[g];
                 const float nHf = (float)nH;
-                const double y0 = A.cells.y[g];
-                const float y0f = (float)y0, x0f = A.cells.x[g];
-                const float T0 = A.cells.T[g];
+                const double y0 = xs;
+                const float y0f = (float)y0;
                 const float dtf = (float)S.dt;
                 float alpha = S.alpha_iso, Cc = S.coll_iso;
                 if (!S.isothermal && S.rates) { alpha = alphaB_f(T0); Cc = collion_f(T0); }
@@ -347,10 +375,25 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                 }
             }
         }
-        const unsigned peers = __match_any_sync(FULL, sim);
-        float v[1] = {a_abs};
-        if (__any_sync(FULL, __popc(peers) > 1)) peer_sum<1>(peers, v);
-        if (sim >= 0 && (peers & ((1u << lane) - 1u)) == 0u && v[0] != 0.0f) atomicAdd(&sh_abs[sim], (double)v[0]);
+        if (sim >= 0 && a_abs != 0.0f) {
+            if (sim != t_sim) {
+                if (t_sim >= 0 && t_abs != 0.0) atomicAdd(&sh_abs[t_sim], t_abs);
+                t_sim = sim;
+                t_abs = 0.0;
+            }
+            t_abs += (double)a_abs;
+        }
+    }
+    {
+        // the warp's sums: one atomic when its lanes share a simulation
+        const int kref = __reduce_max_sync(FULL, t_sim);
+        if (kref >= 0 && __all_sync(FULL, t_sim < 0 || t_sim == kref)) {
+            double v[1] = {t_sim == kref ? t_abs : 0.0};
+            warp_sum<1>(v);
+            if (lane == 0 && v[0] != 0.0) atomicAdd(&sh_abs[kref], v[0]);
+        } else if (t_sim >= 0 && t_abs != 0.0) {
+            atomicAdd(&sh_abs[t_sim], t_abs);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < A.nsims; i += blockDim.x)
@@ -536,7 +579,7 @@ int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims, b
 }
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st) {
     const size_t sh = (size_t)a.nsims * sizeof(double) + (size_t)(2 * a.nsims + 1) * sizeof(long long) +
-                      (size_t)a.nsims * sizeof(int);
+                      (size_t)a.nsims * (2 * sizeof(int) + sizeof(float));
     k_chem<<<blocks, 256, sh, st>>>(a);
     return cudaGetLastError();
 }
