@@ -343,7 +343,6 @@ struct Walk {
     unsigned Dx, Dy, Dz;     // distance along each axis to the next face ahead (<= 2^22)
     unsigned ax, ay, az;     // |d| (<= 2^21)
     int sx, sy, sz;          // sign of d
-    unsigned tn, td;         // segment start, t = tn/td
 };
 
 // cell index (floor) and distance to the next face for one axis; a ray on a
@@ -363,35 +362,70 @@ __device__ __forceinline__ void walk_init(Walk &w, long long px, long long py, l
     axis_init(px, dx, w.cx, w.Dx, w.ax, w.sx);
     axis_init(py, dy, w.cy, w.Dy, w.ay, w.sy);
     axis_init(pz, dz, w.cz, w.Dz, w.az, w.sz);
-    w.tn = 0u; w.td = 1u;
 }
 __device__ __forceinline__ bool walk_outside(const Walk &w, int nx, int ny, int nz) {
     return (unsigned)w.cx >= (unsigned)nx || (unsigned)w.cy >= (unsigned)ny || (unsigned)w.cz >= (unsigned)nz;
 }
-// Emit the segment in the current (inside) cell: its length ds (cells) and
-// whether the ray goes on to another cell in this step.  Advances the walk.
-// Face crossings t_a = D_a/|d_a| are compared as exact cross products.
-__device__ __forceinline__ bool walk_segment(Walk &w, float &ds) {
+// The segments of one step.  |d_a| is at most one cell, so each axis is
+// crossed at most once, at t_a = D_a/|d_a| < 1 (D_a < |d_a|); the segments
+// end at these times in increasing order and at t = 1.  The times are
+// ordered once per step by exact cross-multiplied comparisons (the rank of
+// an axis: the crossing axes strictly earlier); axes crossed at the same t
+// step together.  A segment's length is the exact fraction t_k - t_(k-1),
+// rounded once.  Outputs by fixed slot, so that they stay in registers: slot
+// r < 3 holds the segment that ends at the crossing of rank r, slot 3 the one
+// that ends the step; the bits of the returned mask mark the slots in use
+// (none after the ray leaves the grid: esc), in order along the ray.  A
+// slot's cell is key = coff + (z ny + y) nx + x (-1 for an empty slot).
+__device__ __forceinline__ float seg_len(unsigned un, unsigned ud, unsigned tn, unsigned td) {
+    const unsigned long long num = wmul(un, td) - wmul(tn, ud);
+    const unsigned long long den = wmul(ud, td);
+    return __fdividef(u64_to_float(num), u64_to_float(den));
+}
+__device__ __forceinline__ unsigned walk_step(const Walk &w, int nx, int ny, int nz, int coff, int (&key)[4],
+                                              float (&ds)[4], bool &esc) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { key[r] = -1; ds[r] = 0.0f; }
+    esc = walk_outside(w, nx, ny, nz);
+    if (esc) return 0u;
     const bool crx = w.sx != 0 && w.Dx < w.ax;
     const bool cry = w.sy != 0 && w.Dy < w.ay;
     const bool crz = w.sz != 0 && w.Dz < w.az;
-    unsigned un = 1u, ud = 1u;
-    bool cross = false;
-    if (crx) { un = w.Dx; ud = w.ax; cross = true; }
-    if (cry && (!cross || wmul(w.Dy, ud) < wmul(un, w.ay))) { un = w.Dy; ud = w.ay; cross = true; }
-    if (crz && (!cross || wmul(w.Dz, ud) < wmul(un, w.az))) { un = w.Dz; ud = w.az; cross = true; }
-    // ds = un/ud - tn/td as one exact integer fraction
-    const unsigned long long num = wmul(un, w.td) - wmul(w.tn, ud);
-    const unsigned long long den = wmul(ud, w.td);
-    ds = __fdividef(u64_to_float(num), u64_to_float(den));
-    if (cross) {
-        // every axis crossing at the same t steps together
-        if (crx && wmul(w.Dx, ud) == wmul(un, w.ax)) { w.cx += w.sx; w.Dx += (unsigned)ONE_CELL; }
-        if (cry && wmul(w.Dy, ud) == wmul(un, w.ay)) { w.cy += w.sy; w.Dy += (unsigned)ONE_CELL; }
-        if (crz && wmul(w.Dz, ud) == wmul(un, w.az)) { w.cz += w.sz; w.Dz += (unsigned)ONE_CELL; }
-        w.tn = un; w.td = ud;
+    // t_i < t_j  <=>  D_i |d_j| < D_j |d_i|
+    const unsigned long long xy = wmul(w.Dx, w.ay), yx = wmul(w.Dy, w.ax);
+    const unsigned long long xz = wmul(w.Dx, w.az), zx = wmul(w.Dz, w.ax);
+    const unsigned long long yz = wmul(w.Dy, w.az), zy = wmul(w.Dz, w.ay);
+    const int rx = (cry && yx < xy) + (crz && zx < xz);
+    const int ry = (crx && xy < yx) + (crz && zy < yz);
+    const int rz = (crx && xz < zx) + (cry && yz < zy);
+    int x = w.cx, y = w.cy, z = w.cz;
+    unsigned tn = 0u, td = 1u, mask = 0u;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const bool bx = crx && rx == r, by = cry && ry == r, bz = crz && rz == r;
+        key[r] = -1;
+        ds[r] = 0.0f;
+        if (!esc && (bx || by || bz)) {
+            key[r] = coff + (z * ny + y) * nx + x;
+            const unsigned un = bx ? w.Dx : (by ? w.Dy : w.Dz);
+            const unsigned ud = bx ? w.ax : (by ? w.ay : w.az);
+            ds[r] = seg_len(un, ud, tn, td);
+            mask |= 1u << r;
+            if (bx) x += w.sx;
+            if (by) y += w.sy;
+            if (bz) z += w.sz;
+            tn = un; td = ud;
+            esc = (unsigned)x >= (unsigned)nx || (unsigned)y >= (unsigned)ny || (unsigned)z >= (unsigned)nz;
+        }
     }
-    return cross;
+    key[3] = -1;
+    ds[3] = 0.0f;
+    if (!esc) {
+        key[3] = coff + (z * ny + y) * nx + x;
+        ds[3] = seg_len(1u, 1u, tn, td);
+        mask |= 8u;
+    }
+    return mask;
 }
 
 // ---------------------------------------------------------------------------

@@ -482,20 +482,22 @@ __global__ void k_probe_traverse(long long n, const long long *p0, const int32_t
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         Walk w;
         walk_init(w, p0[3 * i], p0[3 * i + 1], p0[3 * i + 2], d[3 * i], d[3 * i + 1], d[3 * i + 2]);
-        int k = 0, e = 0;
-        bool live = true;
-        if (walk_outside(w, gx, gy, gz)) { e = 1; live = false; }
-        while (live && k < 4) {
-            cells[12 * i + 3 * k] = w.cx; cells[12 * i + 3 * k + 1] = w.cy; cells[12 * i + 3 * k + 2] = w.cz;
-            float s;
-            bool more = walk_segment(w, s);
-            ds[4 * i + k] = s;
+        int key[4];
+        float s[4];
+        bool e = false;
+        const unsigned m = walk_step(w, gx, gy, gz, 0, key, s, e);
+        int k = 0;
+        for (int j = 0; j < 4; ++j) {
+            if (!(m & (1u << j))) continue;
+            const int c = key[j];
+            cells[12 * i + 3 * k] = c % gx;
+            cells[12 * i + 3 * k + 1] = (c / gx) % gy;
+            cells[12 * i + 3 * k + 2] = c / (gx * gy);
+            ds[4 * i + k] = s[j];
             ++k;
-            if (!more) live = false;
-            else if (walk_outside(w, gx, gy, gz)) { e = 1; live = false; }
         }
-        nseg[i] = live ? -1 : k;
-        esc[i] = e;
+        nseg[i] = k;
+        esc[i] = e ? 1 : 0;
     }
 }
 

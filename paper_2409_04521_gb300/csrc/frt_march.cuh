@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             float ds[4];
             bool esc = false;
             int nseg = 0;
+            unsigned vmask = 0u;
             {
                 Walk w;
                 long long px, py, pz;
@@ -186,24 +187,12 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     pz = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + (long long)age * dz;
                 }
                 walk_init(w, px, py, pz, dx, dy, dz);
-                bool live = valid;
-                if (live && walk_outside(w, S.nx, S.ny, S.nz)) { esc = true; live = false; }
+                // slots may be empty (tied crossings): every later phase
+                // visits the four slots in order and skips the empty ones
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    key[j] = -1;
-                    ds[j] = 0.0f;
-                    if (live) {
-                        key[j] = (int)(S.coff + ((long long)w.cz * S.ny + w.cy) * S.nx + w.cx);
-                        const bool more = walk_segment(w, ds[j]);
-                        ++nseg;
-                        if (!more) live = false;
-                        else if (walk_outside(w, S.nx, S.ny, S.nz)) { esc = true; live = false; }
-                    }
-                }
-                if (live) {  // more than four segments: impossible for |d| <= 2^21
-                    atomicOr(&C->err, 4);
-                    valid = false;
-                }
+                for (int j = 0; j < 4; ++j) { key[j] = -1; ds[j] = 0.0f; }
+                if (valid) vmask = walk_step(w, S.nx, S.ny, S.nz, (int)S.coff, key, ds, esc);
+                nseg = __popc(vmask);
             }
             // (2) opacities of the crossed cells (Generalized mode: also the
             // ionised fraction and the screen's share)
@@ -253,14 +242,14 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                         for (int b = 0; b < NB; ++b) ph[b] *= keep;
                         if (rg[j] >= 1.0f) {
                             screened = true;
-                            nseg = j + 1;
+                            nseg = __popc(vmask & ((2u << j) - 1u));
                         }
                     }
                 }
                 if (AGG == 0) {
                     if (key[j] >= 0) red_add_v4(A.cells.dep + key[j], v[0], v[1], v[2], v[3]);
                 } else {
-                    if (__ballot_sync(FULL, key[j] >= 0) == 0u) break;
+                    if (__ballot_sync(FULL, key[j] >= 0) == 0u) continue;
                     if (AGG == 1) {
                         const unsigned peers = __match_any_sync(FULL, key[j]);
                         if (__any_sync(FULL, key[j] >= 0 && __popc(peers) > 1)) peer_sum<4>(peers, v);
