@@ -522,6 +522,26 @@ __device__ __forceinline__ void absorb_transmit(float t, float &a, float &tr) {
     tr = small ? 1.0f - series : ex;
 }
 
+// absorb_transmit on two bins at once: the polynomial in the paired
+// single-precision units (same operations, same rounding per bin).
+__device__ __forceinline__ void absorb_transmit2(float2 t, float2 &a, float2 &tr) {
+    const float2 u = make_float2(fminf(t.x, 0.125f), fminf(t.y, 0.125f));
+    const float2 nu = make_float2(-u.x, -u.y);
+    float2 q = make_float2(1.0f / 5040.0f, 1.0f / 5040.0f);
+    q = __ffma2_rn(q, nu, make_float2(1.0f / 720.0f, 1.0f / 720.0f));
+    q = __ffma2_rn(q, nu, make_float2(1.0f / 120.0f, 1.0f / 120.0f));
+    q = __ffma2_rn(q, nu, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
+    q = __ffma2_rn(q, nu, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+    q = __ffma2_rn(q, nu, make_float2(0.5f, 0.5f));
+    q = __ffma2_rn(q, nu, make_float2(1.0f, 1.0f));
+    const float2 series = __fmul2_rn(q, u);
+    const float2 one_m = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-series.x, -series.y));
+    const float ex0 = __expf(-t.x), ex1 = __expf(-t.y);
+    const bool s0 = t.x < 0.125f, s1 = t.y < 0.125f;
+    a = make_float2(s0 ? series.x : 1.0f - ex0, s1 ? series.y : 1.0f - ex1);
+    tr = make_float2(s0 ? one_m.x : ex0, s1 ? one_m.y : ex1);
+}
+
 // exact 2^-k for 0 <= k < 126
 __device__ __forceinline__ float pow2_neg(int k) { return __int_as_float((127 - k) << 23); }
 

@@ -217,8 +217,34 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 if (EXT && screened) key[j] = -1;
                 if (key[j] >= 0) {
                     const float dse = EXT ? xg[j] * ds[j] : ds[j];
+                    // bins in pairs on the paired single-precision units
+                    float2 w0 = make_float2(0.f, 0.f), w1 = w0, w2 = w0;
+                    const float2 kx2 = make_float2(kc[j].x, kc[j].x), ky2 = make_float2(kc[j].y, kc[j].y);
+                    const float2 ds2 = make_float2(dse, dse);
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
+                    for (int b = 0; b + 1 < NB; b += 2) {
+                        const float2 sg = make_float2(S.sig[b], S.sig[b + 1]);
+                        const float2 se = make_float2(S.sige[b], S.sige[b + 1]);
+                        const float2 kb = __ffma2_rn(kx2, sg, ky2);
+                        float2 tr, ab;
+                        absorb_transmit2(__fmul2_rn(kb, ds2), ab, tr);
+                        const float2 p2 = make_float2(ph[b], ph[b + 1]);
+                        const float2 a = __fmul2_rn(p2, ab);
+                        const float2 pd = __fmul2_rn(p2, ds2);
+                        const float2 phin = make_float2(kb.x > 0.0f ? __fdividef(a.x, kb.x) : pd.x,
+                                                        kb.y > 0.0f ? __fdividef(a.y, kb.y) : pd.y);
+                        const float2 pn = __fmul2_rn(p2, tr);
+                        ph[b] = pn.x;
+                        ph[b + 1] = pn.y;
+                        w0 = __fadd2_rn(w0, a);
+                        w1 = __ffma2_rn(sg, phin, w1);
+                        w2 = __ffma2_rn(se, phin, w2);
+                    }
+                    v[0] = w0.x + w0.y;
+                    v[1] = w1.x + w1.y;
+                    v[2] = w2.x + w2.y;
+                    if (NB & 1) {
+                        const int b = NB - 1;
                         const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
                         float tr, ab;
                         absorb_transmit(kb * dse, ab, tr);
