@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         float t_esc = 0.0f, t_out = 0.0f;
         unsigned t_cnt = 0u, t_rout = 0u;
         int t_sim = -1, t_n = 0;
-        // the next ray's words are loaded one iteration ahead
+        // the ray's words, loaded at the top of its iteration (loading the next
+        // ray's one iteration ahead cost more in spilled registers than it hid)
         uint32_t npl = DEAD_RAY, ne_ = 0;
         int nbi = 0, ndx = 0, ndy = 0, ndz = 0;
         float nph[NB];
@@ -135,8 +136,8 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 for (int b = 0; b < NB; ++b) nph[b] = 0.0f;
             }
         };
-        load_ray(blockIdx.x * (long long)blockDim.x + threadIdx.x);
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += stride) {
+            load_ray(i);
             const uint32_t pl = npl, e = ne_;
             const int bi = nbi, dx = ndx, dy = ndy, dz = ndz;
             const int mx = nmx, my = nmy, mz = nmz;
@@ -145,7 +146,6 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             float ph[NB];
 #pragma unroll
             for (int b = 0; b < NB; ++b) ph[b] = nph[b];
-            load_ray(i + stride);
             bool valid = pl != DEAD_RAY;
             const bool mrg = EXT && valid && (e & MERGED_BIT);
             int sim = 0;
