@@ -314,11 +314,11 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 }
             }
             // per-simulation tallies: each lane accumulates the rays of one
-            // simulation for up to four iterations, then the warp reduces them
+            // simulation for up to sixteen iterations, then the warp reduces them
             // into the block's fixed-point totals
             {
                 const bool clash = valid && t_sim >= 0 && t_sim != sim;
-                if (__any_sync(FULL, clash) || t_n == 4) {
+                if (__any_sync(FULL, clash) || t_n == 16) {
                     flush_tallies(t_esc, t_out, t_cnt, t_rout, t_sim, sh_acc);
                     t_n = 0;
                 }
