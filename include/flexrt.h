@@ -307,9 +307,10 @@ typedef struct {
 
 /* The merge step (Sec. 3.3) alone: the very kernels of a step's merge run on
  * n host-given live rays (const in) of one simulation as they stand after the
- * march of step p->step.  Writes up to cap rays to out and their number to
- * *n_out, in the order the kernels leave them in the queue.  Allocates and
- * frees its own device scratch.  Synchronous. */
+ * march of step p->step.  Writes up to cap of the rays left live to out and
+ * their number to *n_out, in the order the kernels leave them in the queue
+ * (merged rays in their leaders' slots; the followers' slots, empty, are
+ * skipped).  Allocates and frees its own device scratch.  Synchronous. */
 flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t n, const flexrt_probe_rays *in,
                                  int64_t cap, flexrt_probe_rays *out, int64_t *n_out);
 

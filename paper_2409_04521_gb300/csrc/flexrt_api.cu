@@ -384,24 +384,23 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     DevBuf<Ctl> dctl;
     DevBuf<SimDev> dsim;
     DevBuf<SimAcc> dacc;
-    DevBuf<uint32_t> qpl[2], qem[2], qma[2], hist, sel, tkey, gid, gcnt;
+    DevBuf<uint32_t> qpl[2], qem[2], qma[2], hist, sel, tkey, gcnt, lead_i, lead_slot;
     DevBuf<int32_t> qbi[2], qd[2], qm[2], tsim, rsim;
     DevBuf<float> qph[2], qthr[2], grp, n0;
     DevBuf<int4> ecell, rot;
-    DevBuf<long long> pref, cell0, boff;
-    DevBuf<uint32_t> bcount, hole, mover;
+    DevBuf<long long> pref, cell0;
     bool ok = dctl.alloc(1) == cudaSuccess && dsim.alloc(1) == cudaSuccess && dacc.alloc(1) == cudaSuccess;
     for (int k = 0; k < 2 && ok; ++k)
         ok = qpl[k].alloc(m) == cudaSuccess && qem[k].alloc(m) == cudaSuccess && qma[k].alloc(m) == cudaSuccess &&
              qbi[k].alloc(m) == cudaSuccess && qd[k].alloc(3 * m) == cudaSuccess && qm[k].alloc(3 * m) == cudaSuccess &&
              qph[k].alloc(nb * m) == cudaSuccess && qthr[k].alloc(m) == cudaSuccess;
     ok = ok && hist.alloc(HIST_BINS) == cudaSuccess && sel.alloc(8) == cudaSuccess && tkey.alloc(m) == cudaSuccess &&
-         tsim.alloc(m) == cudaSuccess && gid.alloc(m) == cudaSuccess && gcnt.alloc(ncell * ndir) == cudaSuccess &&
+         tsim.alloc(m) == cudaSuccess && gcnt.alloc(ncell * ndir) == cudaSuccess &&
          grp.alloc(ncell * ndir * gw) == cudaSuccess && rot.alloc(3 * ncell) == cudaSuccess &&
          ecell.alloc(std::max(p->n_emitters, 1)) == cudaSuccess && n0.alloc(std::max(p->n_emitters, 1)) == cudaSuccess &&
          pref.alloc(2) == cudaSuccess && cell0.alloc(1) == cudaSuccess && rsim.alloc(1) == cudaSuccess &&
-         bcount.alloc(MERGE_MAX_BLOCKS * 8) == cudaSuccess && boff.alloc(MERGE_MAX_BLOCKS * 8) == cudaSuccess &&
-         hole.alloc(m) == cudaSuccess && mover.alloc(m) == cudaSuccess;
+         lead_i.alloc(m + MERGE_MAX_BLOCKS * 8 * 128) == cudaSuccess &&
+         lead_slot.alloc(m + MERGE_MAX_BLOCKS * 8 * 128) == cudaSuccess;
     if (!ok) return free_fail(FLEXRT_E_OOM, "probe_merge: device allocation failed");
     // queue layout: structure of arrays, photons bin-major
     auto queue = [&](int k) {
@@ -444,41 +443,50 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     em.cell = ecell.p; em.n0 = n0.p;
     Ranges rg{pref.p, cell0.p, rsim.p};
     MergeWork w{};
-    w.hist = hist.p; w.sel = sel.p; w.tkey = tkey.p; w.tsim = tsim.p; w.gid = gid.p;
+    w.hist = hist.p; w.sel = sel.p; w.tkey = tkey.p; w.tsim = tsim.p;
     w.grp = grp.p; w.gcnt = gcnt.p; w.rot = rot.p; w.ndir = ndir; w.grp_w = gw;
-    w.bcount = bcount.p; w.boff = boff.p; w.hrep = 1; w.hole = hole.p; w.mover = mover.p;
+    w.hrep = 1; w.lead_i = lead_i.p; w.lead_slot = lead_slot.p;
+    w.lead_cap = m + MERGE_MAX_BLOCKS * 8 * 128;
     MergeArgs a{dctl.p, dsim.p, dacc.p, 1, {q0, q1}, em, rg, tab, lt, w, nb};
     if (launch_merge(a, sms, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
         return free_fail(FLEXRT_E_CUDA, "probe_merge: kernels failed");
     Ctl hc;
     if (cudaMemcpy(&hc, dctl.p, sizeof(hc), cudaMemcpyDeviceToHost) != cudaSuccess)
         return free_fail(FLEXRT_E_CUDA, "probe_merge: read-back failed");
-    // the rays stay in queue 1, compacted to mlive slots when merged
+    // the rays stay in queue 1; the merge leaves holes where its followers
+    // were, skipped here
     const int k = 1;
-    const long long cnt = hc.merged ? hc.mlive : hc.cnt[1];
-    *n_out = cnt;
-    const long long c = std::min<long long>(cnt, cap);
-    std::vector<int32_t> od(3 * m), om(3 * m);
-    std::vector<float> oph(nb * m);
-    std::vector<uint32_t> oma(m);
+    const long long cnt = std::min<long long>(hc.cnt[1], m);
+    std::vector<uint32_t> opl(m), oem(m), oma(m);
+    std::vector<int32_t> obi(m), od(3 * m), om(3 * m);
+    std::vector<float> oph(nb * m), othr(m);
     auto down = [](void *dst, const void *src, size_t bytes) {
         return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
     };
     const Queue qq = k ? q1 : q0;
-    ok = down(out->pixlev, qq.pl, c * 4) && down(out->emitter, qq.em, c * 4) && down(out->birth, qq.bi, c * 4) &&
+    ok = down(opl.data(), qq.pl, m * 4) && down(oem.data(), qq.em, m * 4) && down(obi.data(), qq.bi, m * 4) &&
          down(od.data(), qd[k].p, 3 * m * 4) && down(om.data(), qm[k].p, 3 * m * 4) &&
-         down(oph.data(), qph[k].p, nb * m * 4) && down(oma.data(), qq.ma, m * 4) && down(out->thr, qq.mthr, c * 4);
+         down(oph.data(), qph[k].p, nb * m * 4) && down(oma.data(), qq.ma, m * 4) && down(othr.data(), qq.mthr, m * 4);
     if (!ok) return free_fail(FLEXRT_E_CUDA, "probe_merge: read-back failed");
-    for (long long i = 0; i < c; ++i) {
-        const bool mg = (out->emitter[i] & 0x80000000u) != 0;
-        for (int a2 = 0; a2 < 3; ++a2) {
-            out->dir[3 * i + a2] = od[a2 * m + i];
-            out->pos[3 * i + a2] = mg ? om[a2 * m + i] : 0;
+    long long o = 0;
+    for (long long i = 0; i < cnt; ++i) {
+        if (opl[i] == DEAD_RAY) continue;
+        if (o < cap) {
+            const bool mg = (oem[i] & 0x80000000u) != 0;
+            out->pixlev[o] = opl[i];
+            out->emitter[o] = oem[i];
+            out->birth[o] = obi[i];
+            for (int a2 = 0; a2 < 3; ++a2) {
+                out->dir[3 * o + a2] = od[a2 * m + i];
+                out->pos[3 * o + a2] = mg ? om[a2 * m + i] : 0;
+            }
+            for (int b = 0; b < nb; ++b) out->photons[(size_t)nb * o + b] = oph[b * m + i];
+            out->aux[o] = mg ? (oma[i] & 0x8000ffffu) : 0u;
+            out->thr[o] = mg ? othr[i] : 0.0f;
         }
-        for (int b = 0; b < nb; ++b) out->photons[(size_t)nb * i + b] = oph[b * m + i];
-        out->aux[i] = mg ? (oma[i] & 0x8000ffffu) : 0u;
-        if (!mg) out->thr[i] = 0.0f;
+        ++o;
     }
+    *n_out = o;
     return FLEXRT_OK;
 }
 

@@ -216,25 +216,28 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
 #undef ALLOC
     if (mrg) {
         // merge scratch (Sec. 3.3): histograms and selections per slot, rank
-        // content / simulation / group per queue slot, group sums and sizes
-        // per (cell, merge pixel), rotation rows per cell
+        // content / simulation per queue slot, group sums and sizes per
+        // (cell, merge pixel), rotation rows per cell, the list of leaders
         mw_.ndir = 12 << (2 * cfg_.merge_l_max);
         mw_.grp_w = 12 + 4 * ((cfg_.nb + 4) / 4);   // 6 integer sums, photons and threshold
         const long long ngrp = nc * (long long)mw_.ndir;
         if (ngrp >= (1LL << 31)) return fail(FLEXRT_E_INVALID, "cells x merge directions must stay below 2^31");
         mw_.hrep = std::max(1, std::min(32, 64 / ms));
+        // leader list: at most one entry per queue slot plus each group-pass
+        // warp's unused run
+        mw_.lead_cap = cap + (long long)MERGE_MAX_BLOCKS * 8 * 128;
         const size_t sz[] = {(size_t)ms * mw_.hrep * HIST_BINS * 4, (size_t)ms * 32, (size_t)cap * 4,
-                             (size_t)cap * 4, (size_t)cap * 4, (size_t)ngrp * mw_.grp_w * 4, (size_t)ngrp * 4,
-                             (size_t)nc * 48, (size_t)MERGE_MAX_BLOCKS * 8 * 4, (size_t)MERGE_MAX_BLOCKS * 8 * 8,
-                             (size_t)cap * 4, (size_t)cap * 4};
+                             (size_t)cap * 4, (size_t)ngrp * mw_.grp_w * 4, (size_t)ngrp * 4,
+                             (size_t)nc * 48, (size_t)mw_.lead_cap * 4, (size_t)mw_.lead_cap * 4};
         size_t tot = 0;
         for (size_t v : sz) tot += (v + 255) & ~(size_t)255;
         if (cudaMalloc(&mwmem_, tot) != cudaSuccess) return fail(FLEXRT_E_OOM, "merge scratch allocation failed");
         char *p = (char *)mwmem_;
         void **dst[] = {(void **)&mw_.hist, (void **)&mw_.sel, (void **)&mw_.tkey, (void **)&mw_.tsim,
-                        (void **)&mw_.gid, (void **)&mw_.grp, (void **)&mw_.gcnt, (void **)&mw_.rot,
-                        (void **)&mw_.bcount, (void **)&mw_.boff, (void **)&mw_.hole, (void **)&mw_.mover};
-        for (int k = 0; k < 12; ++k) { *dst[k] = p; p += (sz[k] + 255) & ~(size_t)255; }
+                        (void **)&mw_.grp, (void **)&mw_.gcnt, (void **)&mw_.rot, (void **)&mw_.lead_i,
+                        (void **)&mw_.lead_slot};
+        static_assert(sizeof(sz) / sizeof(sz[0]) == sizeof(dst) / sizeof(dst[0]), "merge scratch layout");
+        for (size_t k = 0; k < sizeof(sz) / sizeof(sz[0]); ++k) { *dst[k] = p; p += (sz[k] + 255) & ~(size_t)255; }
         if (cap >= (1LL << 32)) return fail(FLEXRT_E_INVALID, "merging needs fewer than 2^32 queue slots");
         CK(cudaMemsetAsync(mwmem_, 0, tot, st_));
     }

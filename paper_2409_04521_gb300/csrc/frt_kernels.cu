@@ -425,11 +425,10 @@ __global__ void k_end(Ctl *C, SimDev *sims, SimAcc *acc, int nsims) {
     __syncthreads();
     if (threadIdx.x == 0) {
         // the march wrote the live rays to the other queue (a merge step
-        // compacted them there to mlive slots)
+        // left holes there, which the next march skips)
         const int par = C->par;
         if (err) C->cnt[par ^ 1] = 0;
         else {
-            if (C->merged) C->cnt[par ^ 1] = C->mlive;
             C->cnt[par] = 0;
             C->par = par ^ 1;
         }

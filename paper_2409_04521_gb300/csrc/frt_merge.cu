@@ -14,16 +14,15 @@
 //   k_mgroup : per non-exempt ray, its end cell and merge pixel; a group slot
 //              per (cell, pixel) takes its photons and threshold (vector
 //              reductions), its weighted position, distance and level as
-//              exact 64-bit integer sums, and the ray's arrival rank (rank 0
-//              leads the group).  The weight is the content on a grid of
-//              2^-26 of the power of two above T_ref (at least 1), so the
-//              means are exact quotients, independent of summation order;
-//   k_mscan  : the new queue length L (rays left: exempt, lone, one per group)
-//              and the number H of holes below it;
-//   k_memit  : in place: each group's leader overwrites its own slot with the
-//              merged ray and clears the group; holes below L and live rays
-//              at or above L are listed;
-//   k_mmove  : the H live rays at or above L move down into the H holes.
+//              exact 64-bit integer sums, and the ray's arrival rank: rank 0
+//              leads the group and is listed, the others leave the queue
+//              (their slots become holes).  The weight is the content on a
+//              grid of 2^-26 of the power of two above T_ref (at least 1), so
+//              the means are exact quotients, independent of summation order;
+//   k_memit  : per listed leader: it overwrites its own slot with the merged
+//              ray and clears the group.
+// The holes stay in the queue: the next march skips them and writes its
+// survivors densely into the other queue, so no compaction pass is needed.
 // Contents are non-negative floats, so their bit patterns order as unsigned
 // integers and the select works on the bits.
 #include "frt_march.cuh"
@@ -69,6 +68,8 @@ constexpr int SEL_STATE = 0, SEL_HIGH = 1, SEL_ABOVE = 2, SEL_T = 3, SEL_EXEMPT 
 constexpr uint32_t SEL_OFF = 0, SEL_PASS2 = 1, SEL_DONE = 2;
 constexpr int WBITS = 26;                    // merge weights below 2^26
 constexpr int GSUMS = 6;                     // integer sums: weight, weighted x, y, z, distance, level
+constexpr int LEAD_SLAB = 128;               // leader-list entries a warp takes at once
+constexpr uint32_t NO_LEADER = 0xffffffffu;  // an unused leader-list entry
 
 // num / den rounded to nearest, ties to even
 __device__ __forceinline__ unsigned long long div_rne(unsigned long long num, unsigned long long den) {
@@ -94,8 +95,9 @@ __device__ __forceinline__ int ray_sim(const Queue &q, const Emitters &em, long 
     return (e & MERGED_BIT) ? (int)((q.ma[i] >> 16) & 0x7fffu) : __ldg(&em.cell[e]).w;
 }
 
-// The contiguous queue slots [c0, c1) a warp owns in the group and emit
-// passes (the same for both, so per-warp prefix counts follow slot order).
+// The contiguous queue slots [c0, c1) a warp owns in the group pass (the
+// march writes a parent's children next to each other: one warp sees them
+// together and combines their group sums).
 __device__ __forceinline__ long long warp_chunk_len(long long n, long long nwarps) {
     return ((n + 31) / 32 + nwarps - 1) / nwarps * 32;
 }
@@ -105,11 +107,6 @@ __device__ __forceinline__ void warp_chunk(long long n, long long &c0, long long
     const long long per = warp_chunk_len(n, nw);
     c0 = min(w * per, n);
     c1 = min(c0 + per, n);
-}
-
-// a ray that stays live after the merge: exempt, alone in its group, or a leader
-__device__ __forceinline__ bool stays(uint32_t pl, uint32_t gid) {
-    return pl != DEAD_RAY && (gid == MERGE_KEEP || !(gid & MERGE_FOLLOWER));
 }
 
 // inclusive scan of one value per thread over a block of 1024 threads
@@ -176,6 +173,7 @@ __global__ void __launch_bounds__(256) k_mrot(MergeArgs A) {
     for (int i = threadIdx.x; i <= nrng; i += blockDim.x) s_pref[i] = A.rg.pref[i];
     for (int i = threadIdx.x; i < nrng; i += blockDim.x) { s_cell0[i] = A.rg.cell0[i]; s_sim[i] = A.rg.sim[i]; }
     __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->mlead = 0ull;
     if (C->err) return;
     const long long n = C->ncell_active;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -325,212 +323,179 @@ __global__ void __launch_bounds__(256) k_mhist2(MergeArgs A) {
 // ---------------------------------------------------------------------------
 // Sums of equal groups are combined within the warp first (the march writes
 // a parent's split children next to each other, and they usually share cell
-// and pixel).  Every ray's fate is known here -- exempt, lone and group
-// leaders go to the merged queue, followers do not -- so the pass also
-// counts each warp's outputs for the exact compaction of k_memit (both
-// kernels give a warp the same queue slots).
-__global__ void __launch_bounds__(256, 5) k_mgroup(MergeArgs A) {
-    const Ctl *C = A.ctl;
-    const bool on = !C->err && C->merged;
-    uint32_t outs = 0;
-    if (on) {
-        const int par = C->par;
-        const Queue q = A.q[par ^ 1];
-        const long long n = C->cnt[par ^ 1];
-        const int ndir = A.w.ndir, gw = A.w.grp_w;
-        const int lane = lane_id();
-        long long c0, c1;
-        warp_chunk(n, c0, c1);
-        for (long long base = c0; base < c1; base += 32) {
-            const long long i = base + lane;
-            uint32_t gid = MERGE_KEEP;
-            long long slot = -1;
-            unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
-            float f[MAXB + 4];
+// and pixel).  Exempt rays are decided from two words and left untouched;
+// a non-exempt ray's words are all loaded before its emitter and the cell's
+// rotation, which depend on them.
+__global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
+    Ctl *C = A.ctl;
+    if (C->err || !C->merged) return;
+    const int par = C->par;
+    const Queue q = A.q[par ^ 1];
+    const long long n = C->cnt[par ^ 1];
+    const int ndir = A.w.ndir, gw = A.w.grp_w;
+    const int lane = lane_id();
+    // this warp's run of leader-list entries [lslab, lslab + lleft), taken
+    // LEAD_SLAB at a time with one atomic (a single shared counter per warp
+    // iteration serialises the kernel)
+    unsigned long long lslab = 0;
+    int lleft = 0;
+    long long c0, c1;
+    warp_chunk(n, c0, c1);
+    for (long long base = c0; base < c1; base += 32) {
+        const long long i = base + lane;
+        long long slot = -1;
+        unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
+        float f[MAXB + 4];
 #pragma unroll
-            for (int k = 0; k < MAXB + 4; ++k) f[k] = 0.0f;
-            int nbf = 0;
-            bool live = false;
-            if (i < c1) {
-                live = q.pl[i] != DEAD_RAY;
-                const int sim = A.w.tsim[i];
-                if (sim >= 0) {
-                    const uint32_t *sel = A.w.sel + SEL_W * sim;
-                    const uint32_t key = A.w.tkey[i];
-                    const uint32_t tref = sel[SEL_T];
-                    if (sel[SEL_STATE] == SEL_DONE && !(sel[SEL_EXEMPT] && key >= tref)) {
-                        const SimDev &S = A.sims[sim];
-                        const uint32_t e = q.em[i], pl = q.pl[i];
-                        const int bi = q.bi[i];
-                        const int dx = q.dx[i], dy = q.dy[i], dz = q.dz[i];
-                        const int lev = (int)(pl >> LEVEL_SHIFT);
-                        // end point of this step's march and the distance travelled
-                        long long p[3];
-                        int dist;
-                        float thr;
-                        if (e & MERGED_BIT) {
-                            const long long k = S.step - bi;
-                            p[0] = q.mx[i] + k * dx; p[1] = q.my[i] + k * dy; p[2] = q.mz[i] + k * dz;
-                            dist = (int)(q.ma[i] & 0xffffu) + (int)k;
-                            thr = q.mthr[i];
-                        } else {
-                            const int4 ec = __ldg(&A.em.cell[e]);
-                            const long long k = S.step - bi + 1;
-                            p[0] = ((2LL * ec.x + 1) << (FRAC_BITS - 1)) + k * dx;
-                            p[1] = ((2LL * ec.y + 1) << (FRAC_BITS - 1)) + k * dy;
-                            p[2] = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + k * dz;
-                            dist = (int)k;
-                            thr = S.eps_term * __ldg(&A.em.n0[e]) * pow2_neg(2 * (lev - S.l_src));
-                        }
-                        const long long cx = p[0] >> FRAC_BITS, cy = p[1] >> FRAC_BITS, cz = p[2] >> FRAC_BITS;
-                        if (cx >= 0 && cy >= 0 && cz >= 0 && cx < S.nx && cy < S.ny && cz < S.nz) {
-                            const long long g = S.cell_off + (cz * S.ny + cy) * S.nx + cx;
-                            const int4 *rp = A.w.rot + 3 * g;
-                            const int4 rows[3] = {rp[0], rp[1], rp[2]};
-                            slot = g * ndir + merge_pixel(S.l_merge, rows, dx, dy, dz);
-                            // weight: the content times 2^(26 - e), T_ref < 2^e
-                            // (exact power-of-two scaling), truncated, at least 1
-                            const int eref = (int)((tref >> 23) & 0xffu) - 126;
-                            const float wscale = __int_as_float((127 + WBITS - eref) << 23);
-                            const unsigned long long qw =
-                                max(__float2ull_rz(__fmul_rn(__uint_as_float(key), wscale)), 1ull);
-                            v[0] = qw;
-                            v[1] = qw * (unsigned long long)(p[0] - (cx << FRAC_BITS));
-                            v[2] = qw * (unsigned long long)(p[1] - (cy << FRAC_BITS));
-                            v[3] = qw * (unsigned long long)(p[2] - (cz << FRAC_BITS));
-                            v[4] = qw * (unsigned long long)dist;
-                            v[5] = qw * (unsigned long long)lev;
-                            nbf = S.nb;
+        for (int k = 0; k < MAXB + 4; ++k) f[k] = 0.0f;
+        int nbf = 0;
+        int sim = -1;
+        uint32_t key = 0;
+        if (i < c1) {
+            sim = A.w.tsim[i];
+            key = A.w.tkey[i];
+        }
+        if (sim >= 0) {
+            const uint32_t *sel = A.w.sel + SEL_W * sim;
+            const uint32_t tref = sel[SEL_T];
+            if (sel[SEL_STATE] == SEL_DONE && !(sel[SEL_EXEMPT] && key >= tref)) {
+                const SimDev &S = A.sims[sim];
+                const uint32_t e = q.em[i], pl = q.pl[i];
+                const int bi = q.bi[i];
+                const int dx = q.dx[i], dy = q.dy[i], dz = q.dz[i];
+                const int nbs = S.nb;
 #pragma unroll
-                            for (int b = 0; b < MAXB; ++b) {
-                                if (b < S.nb) f[b] = q.ph[b][i];
-                                if (b == S.nb) f[b] = thr;
-                            }
-                            if (S.nb == MAXB) f[MAXB] = thr;
-                        }
-                    }
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < nbs) f[b] = q.ph[b][i];
+                const int lev = (int)(pl >> LEVEL_SHIFT);
+                // end point of this step's march and the distance travelled
+                long long p[3];
+                int dist;
+                float thr;
+                if (e & MERGED_BIT) {
+                    const long long k = S.step - bi;
+                    p[0] = q.mx[i] + k * dx; p[1] = q.my[i] + k * dy; p[2] = q.mz[i] + k * dz;
+                    dist = (int)(q.ma[i] & 0xffffu) + (int)k;
+                    thr = q.mthr[i];
+                } else {
+                    const int4 ec = __ldg(&A.em.cell[e]);
+                    const long long k = S.step - bi + 1;
+                    p[0] = ((2LL * ec.x + 1) << (FRAC_BITS - 1)) + k * dx;
+                    p[1] = ((2LL * ec.y + 1) << (FRAC_BITS - 1)) + k * dy;
+                    p[2] = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + k * dz;
+                    dist = (int)k;
+                    thr = S.eps_term * __ldg(&A.em.n0[e]) * pow2_neg(2 * (lev - S.l_src));
+                }
+                const long long cx = p[0] >> FRAC_BITS, cy = p[1] >> FRAC_BITS, cz = p[2] >> FRAC_BITS;
+                if (cx >= 0 && cy >= 0 && cz >= 0 && cx < S.nx && cy < S.ny && cz < S.nz) {
+                    const long long g = S.cell_off + (cz * S.ny + cy) * S.nx + cx;
+                    const int4 *rp = A.w.rot + 3 * g;
+                    const int4 rows[3] = {rp[0], rp[1], rp[2]};
+                    slot = g * ndir + merge_pixel(S.l_merge, rows, dx, dy, dz);
+                    // weight: the content times 2^(26 - e), T_ref < 2^e
+                    // (exact power-of-two scaling), truncated, at least 1
+                    const int eref = (int)((tref >> 23) & 0xffu) - 126;
+                    const float wscale = __int_as_float((127 + WBITS - eref) << 23);
+                    const unsigned long long qw =
+                        max(__float2ull_rz(__fmul_rn(__uint_as_float(key), wscale)), 1ull);
+                    v[0] = qw;
+                    v[1] = qw * (unsigned long long)(p[0] - (cx << FRAC_BITS));
+                    v[2] = qw * (unsigned long long)(p[1] - (cy << FRAC_BITS));
+                    v[3] = qw * (unsigned long long)(p[2] - (cz << FRAC_BITS));
+                    v[4] = qw * (unsigned long long)dist;
+                    v[5] = qw * (unsigned long long)lev;
+                    nbf = nbs;
+#pragma unroll
+                    for (int b = 0; b <= MAXB; ++b)
+                        if (b == nbs) f[b] = thr;
                 }
             }
-            // combine equal groups in the warp, then one set of atomics per group
-            const unsigned peers = __match_any_sync(FULL, slot);
-            const unsigned below = peers & ((1u << lane) - 1u);
-            if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) {
-                peer_sum<GSUMS, unsigned long long>(peers, v);
-                peer_sum<MAXB + 4, float>(peers, f);
-            }
-            if (slot >= 0) {
-                uint32_t base = 0;
-                if (below == 0u) {
-                    base = atomicAdd(A.w.gcnt + slot, (uint32_t)__popc(peers));
-                    float *gp = A.w.grp + slot * gw;
-                    unsigned long long *gs = reinterpret_cast<unsigned long long *>(gp);
-                    for (int k = 0; k < GSUMS; ++k) atomicAdd(gs + k, v[k]);
-                    float4 *gf = reinterpret_cast<float4 *>(gp + 2 * GSUMS);
+        }
+        // combine equal groups in the warp, then one set of atomics per group
+        const unsigned peers = __match_any_sync(FULL, slot);
+        const unsigned below = peers & ((1u << lane) - 1u);
+        if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) {
+            peer_sum<GSUMS, unsigned long long>(peers, v);
+            peer_sum<MAXB + 4, float>(peers, f);
+        }
+        bool leads = false;
+        if (slot >= 0) {
+            uint32_t gbase = 0;
+            if (below == 0u) {
+                gbase = atomicAdd(A.w.gcnt + slot, (uint32_t)__popc(peers));
+                float *gp = A.w.grp + slot * gw;
+                unsigned long long *gs = reinterpret_cast<unsigned long long *>(gp);
+                for (int k = 0; k < GSUMS; ++k) atomicAdd(gs + k, v[k]);
+                float4 *gf = reinterpret_cast<float4 *>(gp + 2 * GSUMS);
 #pragma unroll
-                    for (int b = 0; b <= MAXB; b += 4)
-                        if (b <= nbf) red_add_v4(gf + b / 4, f[b], f[b + 1], f[b + 2], f[b + 3]);
-                }
-                // the group's first member in arrival order leads it
-                const int lead = __ffs(peers) - 1;
-                base = __shfl_sync(peers, base, lead);
-                const uint32_t rank = base + (uint32_t)__popc(below);
-                gid = (uint32_t)slot | (rank ? MERGE_FOLLOWER : 0u);
+                for (int b = 0; b <= MAXB; b += 4)
+                    if (b <= nbf) red_add_v4(gf + b / 4, f[b], f[b + 1], f[b + 2], f[b + 3]);
             }
-            if (i < c1) {
-                A.w.gid[i] = gid;
-                outs += live && (gid == MERGE_KEEP || !(gid & MERGE_FOLLOWER)) ? 1u : 0u;
+            // the group's first member in arrival order leads it; the
+            // others leave the queue
+            const int lead = __ffs(peers) - 1;
+            gbase = __shfl_sync(peers, gbase, lead);
+            const uint32_t rank = gbase + (uint32_t)__popc(below);
+            leads = rank == 0u;
+            if (!leads) q.pl[i] = DEAD_RAY;
+        }
+        // list the leaders: the rest of the warp's run first, then a new run
+        const unsigned lm = __ballot_sync(FULL, leads);
+        const int tot = __popc(lm);
+        if (tot) {
+            const unsigned long long s0 = lslab;
+            const int left = lleft;
+            unsigned long long s1 = 0;
+            if (tot > left) {
+                const int need = tot - left;
+                const int want = need > LEAD_SLAB ? need : LEAD_SLAB;
+                unsigned long long nb = 0;
+                if (lane == 0) nb = atomicAdd(&C->mlead, (unsigned long long)want);
+                nb = __shfl_sync(FULL, nb, 0);
+                s1 = nb;
+                lslab = nb + need;
+                lleft = want - need;
+            } else {
+                lslab = s0 + tot;
+                lleft = left - tot;
+            }
+            if (leads) {
+                const int k = __popc(lm & ((1u << lane) - 1u));
+                const unsigned long long o = k < left ? s0 + k : s1 + (k - left);
+                if (o < (unsigned long long)A.w.lead_cap) {
+                    A.w.lead_i[o] = (uint32_t)i;
+                    A.w.lead_slot[o] = (uint32_t)slot;
+                } else {
+                    atomicOr(&C->err, 1);
+                }
             }
         }
     }
-    // this warp's outputs
-    uint32_t t = outs;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-    if (lane_id() == 0) A.w.bcount[blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)] = t;
-}
-
-// exclusive prefix of the per-warp counts of rays that stay; the new queue
-// length L and the number H of holes below it
-__global__ void __launch_bounds__(1024) k_mscan(MergeArgs A, int nwarps) {
-    __shared__ unsigned long long sh[32];
-    Ctl *C = A.ctl;
-    if (C->err || !C->merged) return;
-    unsigned long long run = 0;
-    for (int b0 = 0; b0 < nwarps; b0 += blockDim.x) {
-        const int b = b0 + threadIdx.x;
-        const unsigned long long v = b < nwarps ? A.w.bcount[b] : 0ull;
-        const unsigned long long incl = block_incl_scan(v, sh);
-        if (b < nwarps) A.w.boff[b] = (long long)(run + incl - v);
-        if (threadIdx.x == blockDim.x - 1) sh[0] = incl;     // block_incl_scan's last barrier has passed
-        __syncthreads();
-        run += sh[0];
-        __syncthreads();
-    }
-    // rays that stay below L: the prefix of L's warp plus its own below L
-    const int par = C->par;
-    const long long n = C->cnt[par ^ 1];
-    const long long L = (long long)run;
-    const long long per = warp_chunk_len(n, nwarps);
-    unsigned long long below = 0;
-    if (L < n) {
-        const long long w = L / per;
-        const Queue q = A.q[par ^ 1];
-        unsigned long long c = 0;
-        for (long long i = w * per + threadIdx.x; i < L; i += blockDim.x) c += stays(q.pl[i], A.w.gid[i]) ? 1ull : 0ull;
-        const unsigned long long tot = block_incl_scan(c, sh);
-        if (threadIdx.x == blockDim.x - 1) sh[0] = tot;
-        __syncthreads();
-        below = (unsigned long long)A.w.boff[w] + sh[0];
-    } else {
-        below = run;
-    }
-    if (threadIdx.x == 0) {
-        C->mlive = L;
-        C->mmoves = L - (long long)below;
-    }
+    // the unused end of the warp's run
+    for (int k = lane; k < lleft; k += 32)
+        if (lslab + k < (unsigned long long)A.w.lead_cap) A.w.lead_i[lslab + k] = NO_LEADER;
 }
 
 // ---------------------------------------------------------------------------
-// in place: merged rays into their leaders' slots; holes and movers listed
+// in place: merged rays into their leaders' slots
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
+__global__ void __launch_bounds__(256) k_memit(MergeArgs A) {
     extern __shared__ int sh_drop[];              // per simulation: rays removed by merging
-    __shared__ int s_done;                        // warps of this block that have finished
     for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) sh_drop[k] = 0;
-    if (threadIdx.x == 0) s_done = 0;
     __syncthreads();
-    Ctl *C = A.ctl;
+    const Ctl *C = A.ctl;
     if (!C->err && C->merged) {
-        const int par = C->par;
-        const Queue q = A.q[par ^ 1];
-        const long long n = C->cnt[par ^ 1];
-        const long long L = C->mlive;
+        const Queue q = A.q[C->par ^ 1];
+        const long long nl = min((long long)C->mlead, A.w.lead_cap);
         const int ndir = A.w.ndir, gw = A.w.grp_w, nbq = A.nbq;
-        const int lane = lane_id();
-        long long c0, c1;
-        warp_chunk(n, c0, c1);
-        long long rank0 = A.w.boff[blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)];
-        for (long long base = c0; base < c1; base += 32) {
-            const long long i = base + lane;
-            bool stay = false, leader = false;
-            uint32_t slot = 0, gsize = 0;
-            if (i < c1) {
-                const uint32_t pl = q.pl[i], gid = A.w.gid[i];
-                stay = stays(pl, gid);
-                if (stay && gid != MERGE_KEEP) {
-                    leader = true;
-                    slot = gid;
-                    gsize = A.w.gcnt[slot];
-                }
-            }
-            const unsigned has = __ballot_sync(FULL, stay);
-            const long long rank = rank0 + __popc(has & ((1u << lane) - 1u));   // live rays before slot i
-            rank0 += __popc(has);
-            if (i < c1) {
-                if (!stay && i < L) A.w.hole[i - rank] = (uint32_t)i;
-                if (stay && i >= L) A.w.mover[L - 1 - rank] = (uint32_t)i;
-            }
-            if (leader && gsize > 1) {
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nl;
+             k += (long long)gridDim.x * blockDim.x) {
+            const uint32_t li = A.w.lead_i[k];
+            if (li == NO_LEADER) continue;
+            const long long i = li;
+            const uint32_t slot = A.w.lead_slot[k];
+            const uint32_t gsize = A.w.gcnt[slot];
+            if (gsize > 1) {
                 const int sim = A.w.tsim[i];
                 const SimDev &S = A.sims[sim];
                 const float *gp = A.w.grp + (long long)slot * gw;
@@ -542,7 +507,7 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
                 const long long cell[3] = {local % S.nx, (local / S.nx) % S.ny, local / ((long long)S.nx * S.ny)};
                 int P[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) P[k] = (int)(cell[k] << FRAC_BITS) + (int)div_rne(gs[1 + k], W);
+                for (int a = 0; a < 3; ++a) P[a] = (int)(cell[a] << FRAC_BITS) + (int)div_rne(gs[1 + a], W);
                 const int Adist = (int)min(div_rne(gs[4], W), 65535ull);
                 const int L2 = min(max((int)div_rne(gs[5], W), S.l_merge), S.l_max);
                 const float *gph = gp + 2 * GSUMS;
@@ -557,56 +522,22 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
                 q.bi[i] = S.step;
                 q.dx[i] = dx; q.dy[i] = dy; q.dz[i] = dz;
 #pragma unroll
-                for (int k = 0; k < MAXB; ++k)
-                    if (k < nbq) q.ph[k][i] = k < S.nb ? gph[k] : 0.0f;
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < nbq) q.ph[b][i] = b < S.nb ? gph[b] : 0.0f;
                 q.mx[i] = P[0]; q.my[i] = P[1]; q.mz[i] = P[2];
                 q.ma[i] = (L2 > S.l_merge ? 0x80000000u : 0u) | ((uint32_t)sim << 16) | (uint32_t)Adist;
                 q.mthr[i] = gph[S.nb];
                 atomicAdd(&sh_drop[sim], (int)gsize - 1);
             }
-            if (leader) {
-                // the leader clears its group for the next step
-                float4 *gz = reinterpret_cast<float4 *>(A.w.grp + (long long)slot * gw);
-                for (int k = 0; k < gw / 4; ++k) gz[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                A.w.gcnt[slot] = 0u;
-            }
+            // the leader clears its group for the next step
+            float4 *gz = reinterpret_cast<float4 *>(A.w.grp + (long long)slot * gw);
+            for (int b = 0; b < gw / 4; ++b) gz[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+            A.w.gcnt[slot] = 0u;
         }
     }
-    // the block's last warp to finish adds the block's counts (no barrier:
-    // warps of unequal work do not wait for each other)
-    __threadfence_block();
-    int last = 0;
-    if (lane_id() == 0) last = atomicAdd(&s_done, 1) == (int)(blockDim.x >> 5) - 1;
-    last = __shfl_sync(FULL, last, 0);
-    if (last) {
-        __threadfence_block();
-        for (int k = lane_id(); k < A.nsims; k += 32) {
-            const int d = atomicAdd(&sh_drop[k], 0);
-            if (d) atomicAdd(&A.acc[k].p_rays_out, -(double)d);
-        }
-    }
-}
-
-// the live rays at or above L move into the holes below it
-__global__ void __launch_bounds__(256) k_mmove(MergeArgs A) {
-    const Ctl *C = A.ctl;
-    if (C->err || !C->merged) return;
-    const Queue q = A.q[C->par ^ 1];
-    const long long H = C->mmoves;
-    const int nbq = A.nbq;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < H; k += (long long)gridDim.x * blockDim.x) {
-        const long long i = A.w.mover[k], o = A.w.hole[k];
-        const uint32_t e = q.em[i];
-        q.pl[o] = q.pl[i]; q.em[o] = e; q.bi[o] = q.bi[i];
-        q.dx[o] = q.dx[i]; q.dy[o] = q.dy[i]; q.dz[o] = q.dz[i];
-#pragma unroll
-        for (int b = 0; b < MAXB; ++b)
-            if (b < nbq) q.ph[b][o] = q.ph[b][i];
-        if (e & MERGED_BIT) {
-            q.mx[o] = q.mx[i]; q.my[o] = q.my[i]; q.mz[o] = q.mz[i];
-            q.ma[o] = q.ma[i]; q.mthr[o] = q.mthr[i];
-        }
-    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < A.nsims; k += blockDim.x)
+        if (sh_drop[k]) atomicAdd(&A.acc[k].p_rays_out, -(double)sh_drop[k]);
 }
 
 __global__ void k_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, uint32_t *out) {
@@ -627,9 +558,7 @@ cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st) {
     if (a.w.hrep > 1) k_mreduce<<<rblocks, 256, 0, st>>>(a, 2);
     k_mfind<<<a.nsims, 1024, 0, st>>>(a, 2);
     k_mgroup<<<rblocks, 256, 0, st>>>(a);
-    k_mscan<<<1, 1024, 0, st>>>(a, rblocks * 8);
     k_memit<<<rblocks, 256, (size_t)a.nsims * sizeof(int), st>>>(a);
-    k_mmove<<<rblocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -20,8 +20,6 @@ constexpr uint32_t PIX_MASK = (1u << LEVEL_SHIFT) - 1u;
 constexpr uint32_t DEAD_RAY = 0xffffffffu;         // unused queue slot (level 15 never occurs)
 constexpr int OUT_SLAB = 512;                       // queue slots a warp reserves at once
 constexpr uint32_t MERGED_BIT = 0x80000000u;        // emitter word of a merged ray: bit | local cell
-constexpr uint32_t MERGE_KEEP = 0xffffffffu;        // merge group word: ray not merged
-constexpr uint32_t MERGE_FOLLOWER = 0x80000000u;    // merge group word: not the group's leader
 constexpr int HIST_BINS = 65536;                    // radix-select bins per pass (16 bits)
 constexpr int MERGE_MAX_BLOCKS = 4096;              // blocks of the merge's per-ray passes (8 warps each)
 
@@ -91,8 +89,8 @@ struct Ctl {
     long long ncell_active;  // cells in active simulations
     int32_t merged;          // a simulation merged rays this step
     int32_t pad;
-    long long mlive;         // rays left by the merge (the queue's new length)
-    long long mmoves;        // live rays moved down into holes by the merge
+    unsigned long long mlead;  // groups (their leaders) made by this step's merge
+    long long pad2;
 };
 
 // Structure-of-arrays ray queue.
@@ -141,14 +139,12 @@ struct MergeWork {
     uint32_t *sel;           // [slot][8]: selection state, upper bits, rays above, T_ref bits, any exempt
     uint32_t *tkey;          // per queue slot: rank content (float bits)
     int32_t *tsim;           // per queue slot: simulation taking part, -1 none
-    uint32_t *gid;           // per queue slot: merge group, MERGE_FOLLOWER flag, or MERGE_KEEP
     float *grp;              // [cell * ndir + pixel][grp_w]: 6 uint64 weighted sums, photons, threshold
     uint32_t *gcnt;          // [cell * ndir + pixel] group sizes
     int4 *rot;               // [cell][3] merge-sphere rotation rows of this step
-    uint32_t *bcount;        // per warp of the group pass: rays that stay live after the merge
-    long long *boff;         // their exclusive prefix (warps own contiguous chunks of the queue)
-    uint32_t *hole;          // k-th hole below the new length
-    uint32_t *mover;         // k-th live ray at or above the new length, from the top
+    uint32_t *lead_i;        // k-th group leader: its queue slot (0xffffffff: unused entry)
+    uint32_t *lead_slot;     // and its group slot
+    long long lead_cap;      // entries of the leader list (queue slots plus 128 per warp)
     int32_t ndir;            // group slots per cell (12 * 4^l_merge of the deepest allowed level)
     int32_t grp_w;           // floats per group
     int32_t hrep;            // copies of each simulation's histogram (spreads hot bins)
