@@ -71,10 +71,18 @@ constexpr int GSUMS = 6;                     // integer sums: weight, weighted x
 constexpr int LEAD_SLAB = 128;               // leader-list entries a warp takes at once
 constexpr uint32_t NO_LEADER = 0xffffffffu;  // an unused leader-list entry
 
-// num / den rounded to nearest, ties to even
+// num / den rounded to nearest, ties to even, for num < 2^62 and a
+// quotient below 2^40: a double-precision estimate (error well under one)
+// corrected to the exact floor by the integer remainder, without a 64-bit
+// integer division
 __device__ __forceinline__ unsigned long long div_rne(unsigned long long num, unsigned long long den) {
-    unsigned long long q = num / den, r = num - q * den;
-    if (2 * r > den || (2 * r == den && (q & 1ull))) ++q;
+    unsigned long long q = (unsigned long long)__ddiv_rn((double)num, (double)den);
+    long long r = (long long)(num - q * den);
+    if (r < 0) { --q; r += (long long)den; }
+    if (r < 0) { --q; r += (long long)den; }
+    if (r >= (long long)den) { ++q; r -= (long long)den; }
+    if (r >= (long long)den) { ++q; r -= (long long)den; }
+    if (2 * (unsigned long long)r > den || (2 * (unsigned long long)r == den && (q & 1ull))) ++q;
     return q;
 }
 
@@ -479,7 +487,7 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
 // ---------------------------------------------------------------------------
 // in place: merged rays into their leaders' slots
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_memit(MergeArgs A) {
+__global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
     extern __shared__ int sh_drop[];              // per simulation: rays removed by merging
     for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) sh_drop[k] = 0;
     __syncthreads();
@@ -503,11 +511,11 @@ __global__ void __launch_bounds__(256) k_memit(MergeArgs A) {
                 const unsigned long long W = gs[0];
                 const long long g = (long long)slot / ndir;
                 const uint32_t pm = slot % ndir;
-                const long long local = g - S.cell_off;
-                const long long cell[3] = {local % S.nx, (local / S.nx) % S.ny, local / ((long long)S.nx * S.ny)};
+                const int local = (int)(g - S.cell_off);          // below 2^31 cells
+                const int cell[3] = {local % S.nx, (local / S.nx) % S.ny, local / (S.nx * S.ny)};
                 int P[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) P[a] = (int)(cell[a] << FRAC_BITS) + (int)div_rne(gs[1 + a], W);
+                for (int a = 0; a < 3; ++a) P[a] = (cell[a] << FRAC_BITS) + (int)div_rne(gs[1 + a], W);
                 const int Adist = (int)min(div_rne(gs[4], W), 65535ull);
                 const int L2 = min(max((int)div_rne(gs[5], W), S.l_merge), S.l_max);
                 const float *gph = gp + 2 * GSUMS;
