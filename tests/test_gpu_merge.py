@@ -234,3 +234,41 @@ def test_batch_members_with_merging_equal_alone():
         assert np.allclose(B.budget(s), a.budget(), rtol=1e-5)
         a.close()
     B.close()
+
+
+def test_merge_in_generalized_mode_matches_oracle():
+    # merged rays and moving screens in the same march (Sec. 3.3 with
+    # Sec. 4.2): cell by cell up to and including the first merge, then the
+    # quantities Sec. 7.1 validates merging on -- ionised volume, mean Gamma,
+    # ray count, photon budget -- (measured: volume within 4e-5, Gamma 7e-5,
+    # budget 3e-5 of emitted, rays within 1)
+    p = W.stromgren(n=32, nsteps=30)
+    p = dc.replace(p, mfp=dc.replace(p.mfp, mode=3),
+                   options=dc.replace(p.options, gen_mode=True, gamma_iters=5, merge=True, n_ex=0.05, l_merge=0))
+    g = F.Simulation(p, ray_capacity=1 << 21)
+    o = oracle.OracleSim(p)
+    first = None
+    for s in range(p.nsteps):
+        g.step(p.dt)
+        o.step(p.dt)
+        gb, ob = g.budget(), o.budget()
+        for b in (gb, ob):
+            assert abs(b[0] - b[1] - b[2] - b[3]) <= BUDGET_RTOL * b[0]
+        xg, (xo, _) = g.ionized_volume(), o.gen_state()
+        gf, of = g.fields(), o.fields()
+        gc, oc = g.counts(), o.counts()
+        if first is None:
+            assert np.max(np.abs(xg - xo)) <= 5e-4
+            if oc["near_threshold"] == 0:
+                assert gc["rays"] == oc["rays"]
+            if o.rays()["merged"].any():
+                first = s
+        assert abs(gc["rays"] - oc["rays"]) <= 0.02 * oc["rays"] + 16
+        assert abs(xg.sum() - xo.sum()) <= 1e-3 * xo.sum()
+        if of["gamma_HI"].mean() > 0:
+            assert abs(gf["gamma_HI"].mean() - of["gamma_HI"].mean()) <= 1e-3 * of["gamma_HI"].mean()
+        assert np.all(np.abs(gb - ob) <= 1e-3 * ob[0])
+    assert first is not None and first < p.nsteps - 5
+    assert g.rays()["merged"].sum() > 100
+    g.close()
+    o.close()
