@@ -164,7 +164,11 @@ __global__ void k_emit(EmitArgs A) {
     }
     const Queue q = A.q[par];
     const int n = C->n_act_emit;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int nr = (n + 31) & ~31;                 // whole warps: the budget sum below is warp-wide
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nr; j += gridDim.x * blockDim.x) {
+        double emitted = 0.0;
+        int esim = -1;
+        if (j < n) {
         const int e = A.em.act[j];
         const long long off = base + A.em.act_off[j];
         const int4 cell = A.em.cell[e];
@@ -196,7 +200,21 @@ __global__ void k_emit(EmitArgs A) {
             q.dx[o] = dx; q.dy[o] = dy; q.dz[o] = dz;
             for (int b = 0; b < A.nb; ++b) q.ph[b][o] = ph[b];
         }
-        atomicAdd(&A.acc[cell.w].p_emit, tot * (double)ncast);
+        emitted = tot * (double)ncast;
+        esim = cell.w;
+        }
+        // photons emitted, summed over the warp when its emitters share a
+        // simulation (one atomic per warp instead of one per emitter)
+        const int kref = __reduce_max_sync(FULL, esim);
+        if (kref >= 0) {
+            if (__all_sync(FULL, esim < 0 || esim == kref)) {
+                double v[1] = {esim == kref ? emitted : 0.0};
+                warp_sum<1>(v);
+                if (lane_id() == 0) atomicAdd(&A.acc[kref].p_emit, v[0]);
+            } else if (esim >= 0) {
+                atomicAdd(&A.acc[esim].p_emit, emitted);
+            }
+        }
     }
 }
 
