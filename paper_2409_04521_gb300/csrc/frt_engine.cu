@@ -15,6 +15,13 @@ namespace frt {
 namespace {
 
 constexpr double EV_ERG = 1.602176634e-12;
+
+// Generalized mode: atoms of a whole cell per unit n_H, in code photons,
+// (1 + chi) V / nref, in single precision (capped at the largest float)
+static float atoms_per_nH(const frt::SimDev &h) {
+    const double v = (1.0 + h.chi) * h.dx_phys * h.dx_phys * h.dx_phys / h.nref;
+    return v < 3.0e38 ? (float)v : 3.0e38f;
+}
 constexpr double MYR_S = 3.15576e13;
 
 // process-wide fixed-point pixel vector tables, one per device, grown on demand
@@ -117,7 +124,7 @@ Engine::~Engine() {
     if (st_) cudaStreamSynchronize(st_);
     if (graph_) cudaGraphExecDestroy(graph_);
     cudaFree(ctl_); cudaFree(sims_); cudaFree(acc_); cudaFree(qmem_);
-    cudaFree(cells_.nH); cudaFree(cells_.y); cudaFree(cells_.x); cudaFree(cells_.T); cudaFree(cells_.gamma);
+    cudaFree(cells_.nH); cudaFree(cells_.nHf); cudaFree(cells_.y); cudaFree(cells_.x); cudaFree(cells_.T); cudaFree(cells_.gamma);
     cudaFree(cells_.kap); cudaFree(cells_.dep); cudaFree(cells_.segcnt);
     cudaFree(cells_.xion); cudaFree(cells_.rho); cudaFree(cells_.fscr);
     cudaFree(em_.cell); cudaFree(em_.local); cudaFree(em_.ndot); cudaFree(em_.n0);
@@ -200,6 +207,7 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     ALLOC(sims_, ms);
     ALLOC(acc_, ms);
     ALLOC(cells_.nH, nc);
+    ALLOC(cells_.nHf, nc);
     ALLOC(cells_.y, nc);
     ALLOC(cells_.x, nc);
     ALLOC(cells_.T, nc);
@@ -242,7 +250,7 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
         CK(cudaMemsetAsync(mwmem_, 0, tot, st_));
     }
     if (cudaMallocHost(&h_err_, 64) != cudaSuccess) return fail(FLEXRT_E_OOM, "pinned allocation failed");
-    if (cudaMallocHost(&h_stage_, (size_t)(ms + 1) * 4 * sizeof(double)) != cudaSuccess)
+    if (cudaMallocHost(&h_stage_, (size_t)(ms + 1) * 6 * sizeof(double)) != cudaSuccess)
         return fail(FLEXRT_E_OOM, "pinned allocation failed");
     CK(cudaEventCreateWithFlags(&ev_err_, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_stage_, cudaEventDisableTiming));
@@ -419,6 +427,22 @@ flexrt_status Engine::make_sim(const flexrt_grid *grid, const flexrt_box *box, c
         h.alpha_iso = (float)(opt.rates ? aB : opt.alpha_B_const);
         h.coll_iso = (float)(opt.rates ? ci : 0.0);
     }
+    {
+        // single-precision copies for the chemistry kernel
+        h.ksc_f = (float)h.ksc;
+        h.inv_nH_mean_f = (float)h.inv_nH_mean;
+        h.inv_gamma_ref_f = (float)h.inv_gamma_ref;
+        h.neg_delta_exp_f = (float)(-h.delta_exp);
+        h.gamma_exp_f = (float)h.gamma_exp;
+        h.gamma_floor_f = (float)h.gamma_floor;
+        float t = (float)h.y_thr;
+        if ((double)t > h.y_thr) t = std::nextafter(t, -INFINITY);
+        h.y_thr_dn = t;
+        h.alpha_const_f = (float)h.alpha_const;
+        h.chi_f = (float)h.chi;
+        h.chi1_f = (float)(1.0 + h.chi);
+        h.apn_f = atoms_per_nH(h);
+    }
     return FLEXRT_OK;
 }
 
@@ -514,6 +538,9 @@ flexrt_status Engine::add_sources(int s, int32_t n, const int32_t *ijk, const do
             sl.nref_set = true;
             CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, nref), &sl.h.nref, sizeof(double),
                           cudaMemcpyHostToDevice));
+            sl.h.apn_f = atoms_per_nH(sl.h);
+            CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, apn_f), &sl.h.apn_f, sizeof(float),
+                          cudaMemcpyHostToDevice));
             if (sl.h.dt > 0) {
                 const double dt = sl.h.dt;
                 sl.h.dt = 0.0;
@@ -580,11 +607,18 @@ flexrt_status Engine::set_dt(int s, double dt) {
     h.dt = dt;
     h.gscale = h.nref * h.sigma_ref / (h.dx_phys * h.dx_phys * dt);
     h.hscale = h.gscale * EV_ERG;
-    double *st = h_stage_ + 4 * s;
+    h.dt_f = (float)h.dt; h.gscale_f = (float)h.gscale; h.hscale_f = (float)h.hscale;
+    double *st = h_stage_ + 6 * s;
     st[0] = h.dt; st[1] = h.gscale; st[2] = h.hscale;
+    float *sf = reinterpret_cast<float *>(st + 3);
+    sf[0] = h.dt_f; sf[1] = h.gscale_f; sf[2] = h.hscale_f; sf[3] = 0.0f;
     static_assert(offsetof(SimDev, gscale) == offsetof(SimDev, dt) + sizeof(double), "dt/gscale layout");
     static_assert(offsetof(SimDev, hscale) == offsetof(SimDev, dt) + 2 * sizeof(double), "dt/hscale layout");
+    static_assert(offsetof(SimDev, gscale_f) == offsetof(SimDev, dt_f) + sizeof(float), "dt_f layout");
+    static_assert(offsetof(SimDev, hscale_f) == offsetof(SimDev, dt_f) + 2 * sizeof(float), "dt_f layout");
     CK(cudaMemcpyAsync((char *)(sims_ + s) + offsetof(SimDev, dt), st, 3 * sizeof(double), cudaMemcpyHostToDevice,
+                       st_));
+    CK(cudaMemcpyAsync((char *)(sims_ + s) + offsetof(SimDev, dt_f), sf, 3 * sizeof(float), cudaMemcpyHostToDevice,
                        st_));
     CK(cudaEventRecord(ev_stage_, st_));
     return FLEXRT_OK;

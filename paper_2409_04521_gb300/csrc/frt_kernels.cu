@@ -32,15 +32,16 @@ __global__ void k_pixtab(int4 *tab, int L) {
 // ---------------------------------------------------------------------------
 // kappa of a cell for the next step (Sec. 4.2, Eq. 13 and the sub-grid law)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cell_kappa(const SimDev &S, double nH, double y, float G) {
-    const float kx = (float)(nH * y) * (float)S.ksc;
+// (single precision throughout; `ionised`: the cell's neutral fraction is at
+// most 1 - the ionised threshold of the sub-grid law)
+__device__ __forceinline__ float2 cell_kappa(const SimDev &S, float nHf, float yf, bool ionised, float G) {
+    const float kx = nHf * yf * S.ksc_f;
     float ks = 0.0f;
     if (S.mfp_mode == 1) {
         ks = S.kap_sub0;
-    } else if (S.mfp_mode == 2 && y <= S.y_thr) {
-        const float g = fmaxf(G, (float)S.gamma_floor);
-        const float f = powf((float)nH * (float)S.inv_nH_mean, (float)(-S.delta_exp)) *
-                        powf(g * (float)S.inv_gamma_ref, (float)S.gamma_exp);
+    } else if (S.mfp_mode == 2 && ionised) {
+        const float g = fmaxf(G, S.gamma_floor_f);
+        const float f = powf(nHf * S.inv_nH_mean_f, S.neg_delta_exp_f) * powf(g * S.inv_gamma_ref_f, S.gamma_exp_f);
         ks = __fdividef(S.kap_sub0, f);
     }
     return make_float2(kx, ks);
@@ -51,15 +52,15 @@ __device__ __forceinline__ float2 cell_kappa(const SimDev &S, double nH, double 
 // alpha (1 + chi) n_H / Gamma, else 0 -- and its opacity: n_HI sigma from
 // that fraction plus the sub-grid law's 1/lambda.  A part never lit yet
 // (Gamma = 0) is optically thin (the Eq. 14 guess).
-__device__ __forceinline__ float gen_y_ion(const SimDev &S, double nH, float G, float alpha) {
+__device__ __forceinline__ float gen_y_ion(const SimDev &S, float nHf, float G, float alpha) {
     if (S.mfp_mode != 3 || !(G > 0.0f)) return 0.0f;
-    const float g = fmaxf(G, (float)S.gamma_floor);
-    return fminf(1.0f, alpha * (float)(1.0 + S.chi) * (float)nH / g);
+    const float g = fmaxf(G, S.gamma_floor_f);
+    return fminf(1.0f, alpha * S.chi1_f * nHf / g);
 }
 // case-B recombination coefficient of a Generalized-mode cell at T
 __device__ __forceinline__ float gen_alpha(const SimDev &S, float T) {
     if (S.isothermal) return S.alpha_iso;
-    return S.rates ? alphaB_f(T) : (float)S.alpha_const;
+    return S.rates ? alphaB_f(T) : S.alpha_const_f;
 }
 
 // Generalized mode with evolving temperature (Sec. 4.2): dT/dt of the
@@ -80,11 +81,11 @@ __device__ __forceinline__ float gen_dTdt_f(const SimDev &S, float T, float yion
 // time ends at the equilibrium temperature.
 __device__ float gen_temperature_f(const SimDev &S, float T0, float x0, float dx, float x1, float yion, float nHf) {
     float T = dx > 0.0f ? (x0 * T0 + dx * S.t_reion) / x1 : T0;
-    const float xe = 1.0f - yion + (float)S.chi;
-    const float pref = 2.0f * nHf / (3.0f * KB_F * (1.0f + (float)S.chi + xe));
+    const float xe = 1.0f - yion + S.chi_f;
+    const float pref = 2.0f * nHf / (3.0f * KB_F * (S.chi1_f + xe));
     const float cc = S.compton_c / nHf;
     const float gam = 1.70710678f;
-    float left = (float)S.dt;
+    float left = S.dt_f;
     for (int k = 0; k < 1000 && left > 0.0f; ++k) {
         const float f = gen_dTdt_f(S, T, yion, xe, pref, cc);
         if (f == 0.0f) break;
@@ -99,15 +100,14 @@ __device__ float gen_temperature_f(const SimDev &S, float T0, float x0, float dx
     }
     return T;
 }
-__device__ __forceinline__ float2 gen_kappa(const SimDev &S, double nH, float yion, float G) {
-    const float kx = (float)nH * yion * (float)S.ksc;
+__device__ __forceinline__ float2 gen_kappa(const SimDev &S, float nHf, float yion, float G) {
+    const float kx = nHf * yion * S.ksc_f;
     float ks = 0.0f;
     if (S.mfp_mode == 1) {
         ks = S.kap_sub0;
     } else if (S.mfp_mode == 2 && G > 0.0f) {
-        const float g = fmaxf(G, (float)S.gamma_floor);
-        const float f = powf((float)nH * (float)S.inv_nH_mean, (float)(-S.delta_exp)) *
-                        powf(g * (float)S.inv_gamma_ref, (float)S.gamma_exp);
+        const float g = fmaxf(G, S.gamma_floor_f);
+        const float f = powf(nHf * S.inv_nH_mean_f, S.neg_delta_exp_f) * powf(g * S.inv_gamma_ref_f, S.gamma_exp_f);
         ks = __fdividef(S.kap_sub0, f);
     }
     return make_float2(kx, ks);
@@ -145,7 +145,9 @@ __global__ void k_init_cells(const SimDev *sims, int sim, Cells c) {
         c.xion[g] = 0.0;
         c.rho[g] = 1.0f;
         c.fscr[g] = make_float2(0.f, 0.f);
-        c.kap[g] = S.gen_mode ? gen_kappa(S, c.nH[g], 0.0f, 0.0f) : cell_kappa(S, c.nH[g], y, 0.0f);
+        const float nHf = (float)c.nH[g];
+        c.nHf[g] = nHf;
+        c.kap[g] = S.gen_mode ? gen_kappa(S, nHf, 0.0f, 0.0f) : cell_kappa(S, nHf, (float)y, y <= S.y_thr, 0.0f);
     }
 }
 
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
     for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) {
         sh_abs[i] = 0.0;
         const SimDev &S = A.sims[i];
-        s_apn[i] = (float)((1.0 + S.chi) * S.dx_phys * S.dx_phys * S.dx_phys / S.nref);
+        s_apn[i] = S.apn_f;
         s_gen[i] = S.gen_mode;
     }
     for (int i = threadIdx.x; i <= nrng; i += blockDim.x) s_pref[i] = A.rg.pref[i];
@@ -250,10 +252,11 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
     const long long nr = (n + 31) & ~31LL;
     const int lane = lane_id();
     // absorbed photons: each thread sums its cells of one simulation in a
-    // register and adds the sum to the block's total when the simulation
-    // changes and at the end (one shared-memory atomic per run of cells, not
-    // one per warp and cell)
-    double t_abs = 0.0;
+    // register pair (a single-precision sum and its exact rounding error,
+    // Knuth's two-sum: no FP64 per cell) and adds the sum to the block's
+    // total when the simulation changes and at the end (one shared-memory
+    // atomic per run of cells, not one per warp and cell)
+    float t_hi = 0.0f, t_lo = 0.0f;
     int t_sim = -1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += (long long)gridDim.x * blockDim.x) {
         int sim = -1;
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
             // hold the later loads back, one memory round trip each
             const bool gen = s_gen[sim] != 0;
             const float4 d = A.cells.dep[g];
-            const double nH = A.cells.nH[g];
+            const float nHf = A.cells.nHf[g];
             const float T0 = A.cells.T[g];
             float2 fs = make_float2(0.f, 0.f);
             double xs;                     // Generalized: x_ion; Standard: neutral fraction y
@@ -301,44 +304,42 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                     a_abs = d.x + fs.x;
                     const double x = xs;
                     const float xf = (float)x, omx = (float)(1.0 - x);
-                    const float nHf = (float)nH;
                     const float Ac = nHf * s_apn[sim];                           // atoms of a whole cell
-                    const float Gf = xf > 0.0f ? d.y * (float)SG.gscale / xf : 0.0f;
+                    const float Gf = xf > 0.0f ? d.y * SG.gscale_f / xf : 0.0f;
                     const float alpha = gen_alpha(SG, T0);
                     if (!A.final_pass) {
                         A.cells.rho[g] = fs.y > omx * Ac ? omx * Ac / fs.y : 1.0f;
-                        A.cells.kap[g] = gen_kappa(SG, nH, gen_y_ion(SG, nH, Gf, alpha), Gf);
+                        A.cells.kap[g] = gen_kappa(SG, nHf, gen_y_ion(SG, nHf, Gf, alpha), Gf);
                     } else {
-                        const float dxf = (fs.x + d.x) / Ac - alpha * nHf * xf * (float)SG.dt;
+                        const float dxf = (fs.x + d.x) / Ac - alpha * nHf * xf * SG.dt_f;
                         const double x1 = fmin(fmax(x + (double)dxf, 0.0), 1.0);
                         const float om1 = (float)(1.0 - x1), x1f = (float)x1;
                         A.cells.rho[g] = fs.y > om1 * Ac ? om1 * Ac / fs.y : 1.0f;
                         // the temperature moves with the start-of-step neutral
                         // fraction; the committed one is that of the new T
-                        float yi = gen_y_ion(SG, nH, Gf, alpha);
+                        float yi = gen_y_ion(SG, nHf, Gf, alpha);
                         if (!SG.isothermal && x1 > 0.0) {
                             const float T1 = gen_temperature_f(SG, T0, xf, (float)(x1 - x), x1f, yi, nHf);
                             A.cells.T[g] = T1;
-                            yi = gen_y_ion(SG, nH, Gf, gen_alpha(SG, T1));
+                            yi = gen_y_ion(SG, nHf, Gf, gen_alpha(SG, T1));
                         }
                         A.cells.xion[g] = x1;
                         A.cells.y[g] = fma(x1, (double)yi, 1.0 - x1);
                         A.cells.x[g] = x1f * (1.0f - yi);
                         A.cells.gamma[g] = Gf;
-                        A.cells.kap[g] = gen_kappa(SG, nH, yi, Gf);
+                        A.cells.kap[g] = gen_kappa(SG, nHf, yi, Gf);
                     }
                 }
             } else if (!err) {
                 a_abs = d.x;
                 const SimDev &S = A.sims[sim];
-                const float Gf = d.y * (float)S.gscale;               // Eq. 17, 1/s
-                const float nHf = (float)nH;
+                const float Gf = d.y * S.gscale_f;                    // Eq. 17, 1/s
                 const double y0 = xs;
                 const float y0f = (float)y0;
-                const float dtf = (float)S.dt;
+                const float dtf = S.dt_f;
                 float alpha = S.alpha_iso, Cc = S.coll_iso;
                 if (!S.isothermal && S.rates) { alpha = alphaB_f(T0); Cc = collion_f(T0); }
-                else if (!S.isothermal) alpha = (float)S.alpha_const;
+                else if (!S.isothermal) alpha = S.alpha_const_f;
                 // Eq. 7-10 with n_e re-evaluated from <x>.  With i = Gamma + C n_e,
                 // b = alpha n_e, r = dt (i + b), e = e^-r, g = (1 - e)/r and
                 // h = (1 - g)/r, the solution x(t) = x_eq + (x0 - x_eq) e^{-t/t_i}
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                     // a trial pass of the Gamma - <n_HI> iteration (Eq. 11; with
                     // the sub-grid law lambda - Gamma): the next march sees the
                     // opacity of the time-averaged state; the state is kept
-                    A.cells.kap[g] = cell_kappa(S, nH, (double)yb, Gf);
+                    A.cells.kap[g] = cell_kappa(S, nHf, yb, yb <= S.y_thr_dn, Gf);
                 } else {
                 // x1 + y1 = 1 holds to rounding: keep x1 in [0, 1]
                 const float x1 = fminf(fmaf(x0f, ef, gf * idt), 1.0f);
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                     // Eq. 12 with static density: particle-number term, then
                     // sub-stepped heating minus cooling (per n_H^2)
                     T = T0 * (1.0f + x0f) / (1.0f + x1);
-                    const float heat = d.z * (float)S.hscale * yb / nHf;
+                    const float heat = d.z * S.hscale_f * yb / nHf;
                     const float pref = 2.0f * nHf / (3.0f * KB_F * (1.0f + xb));
                     const float cc = S.compton_c / nHf;
                     float left = dtf;
@@ -389,21 +390,24 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                 A.cells.x[g] = x1;
                 A.cells.T[g] = T;
                 A.cells.gamma[g] = Gf;
-                A.cells.kap[g] = cell_kappa(S, nH, y1, Gf);
+                A.cells.kap[g] = cell_kappa(S, nHf, (float)y1, y1 <= S.y_thr, Gf);
                 }
             }
         }
         if (sim >= 0 && a_abs != 0.0f) {
             if (sim != t_sim) {
-                if (t_sim >= 0 && t_abs != 0.0) atomicAdd(&sh_abs[t_sim], t_abs);
+                if (t_sim >= 0) atomicAdd(&sh_abs[t_sim], (double)t_hi + (double)t_lo);
                 t_sim = sim;
-                t_abs = 0.0;
+                t_hi = t_lo = 0.0f;
             }
-            t_abs += (double)a_abs;
+            const float s = t_hi + a_abs, bp = s - t_hi;
+            t_lo += (t_hi - (s - bp)) + (a_abs - bp);
+            t_hi = s;
         }
     }
     {
         // the warp's sums: one atomic when its lanes share a simulation
+        const double t_abs = (double)t_hi + (double)t_lo;
         const int kref = __reduce_max_sync(FULL, t_sim);
         if (kref >= 0 && __all_sync(FULL, t_sim < 0 || t_sim == kref)) {
             double v[1] = {t_sim == kref ? t_abs : 0.0};

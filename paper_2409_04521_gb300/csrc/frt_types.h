@@ -68,6 +68,13 @@ struct SimDev {
     // Generalized mode with evolving temperature: T of newly ionised gas (K)
     // and the Eq. 22 mean excess energy per photo-ionisation (erg)
     float t_reion, pl_heat;
+    // single-precision copies for the per-cell chemistry (converting the
+    // double fields above in every cell kept the narrow FP64 pipe busy)
+    float dt_f, gscale_f, hscale_f, pad_f;       // with dt
+    float ksc_f, inv_nH_mean_f, inv_gamma_ref_f, neg_delta_exp_f, gamma_exp_f, gamma_floor_f;
+    float y_thr_dn;                              // largest float <= y_thr (same decisions for float y)
+    float alpha_const_f, chi_f, chi1_f;          // alpha_const, chi, 1 + chi
+    float apn_f;                                 // (1 + chi) V / nref: atoms of a cell per unit n_H
 };
 
 // Per-simulation accumulators, code photons (double) and counters.
@@ -108,6 +115,7 @@ struct Queue {
 
 struct Cells {
     double *nH;              // cm^-3 physical
+    float *nHf;              // the same in single precision (chemistry)
     double *y;               // neutral fraction x_HI
     float *x;                // ionised fraction x_HII (kept separately: accurate when small)
     float *T;                // K
