@@ -72,11 +72,12 @@ constexpr int LEAD_SLAB = 128;               // leader-list entries a warp takes
 constexpr uint32_t NO_LEADER = 0xffffffffu;  // an unused leader-list entry
 
 // num / den rounded to nearest, ties to even, for num < 2^62 and a
-// quotient below 2^40: a double-precision estimate (error well under one)
+// quotient below 2^22 (positions within a cell, distances, levels): a
+// single-precision estimate (relative error below 2^-22, so under one here)
 // corrected to the exact floor by the integer remainder, without a 64-bit
-// integer division
+// integer division or the FP64 pipe
 __device__ __forceinline__ unsigned long long div_rne(unsigned long long num, unsigned long long den) {
-    unsigned long long q = (unsigned long long)__ddiv_rn((double)num, (double)den);
+    unsigned long long q = (unsigned long long)__fdiv_rn((float)num, (float)den);
     long long r = (long long)(num - q * den);
     if (r < 0) { --q; r += (long long)den; }
     if (r < 0) { --q; r += (long long)den; }
