@@ -94,3 +94,21 @@ def test_temperature_relaxes_to_heating_equilibrium():
     for _ in range(50):
         T = oracle.temperature(T, nH, xb, xb, xb, lam, z, 3e15)
     assert T == pytest.approx(T_eq, rel=1e-2)
+
+
+@pytest.mark.parametrize("nH,xb,T0,heat_ratio", [(1e-1, 0.99, 8e4, 0.3), (1.0, 0.9, 5e3, 2.0), (1e-3, 0.999, 2e4, 0.5)])
+def test_temperature_follows_the_energy_equation(nH, xb, T0, heat_ratio):
+    # Eq. 12 at fixed ionisation: 3/2 k_B n_tot dT/dt = H - Lambda(T), n_tot =
+    # n_H (1 + x) (atoms and ions plus one electron per ion); the explicit
+    # sub-steps follow an accurate solution of it (scipy's LSODA) within
+    # their first-order accuracy over up to two cooling times (measured at
+    # most 2 %)
+    integrate = pytest.importorskip("scipy.integrate")
+    kB, z = 1.380649e-16, 6.0
+    ne, nHII, nHI, ntot = nH * xb, nH * xb, nH * (1 - xb), nH * (1 + xb)
+    heat = heat_ratio * oracle.cooling(T0, ne, nHI, nHII, z)
+    rhs = lambda t, T: [2.0 / (3.0 * kB * ntot) * (heat - oracle.cooling(T[0], ne, nHI, nHII, z))]
+    tc = T0 / abs(rhs(0.0, [T0])[0])
+    for f in (0.1, 0.5, 2.0):
+        ref = integrate.solve_ivp(rhs, (0.0, f * tc), [T0], method="LSODA", rtol=1e-10, atol=1e-8).y[0, -1]
+        assert oracle.temperature(T0, nH, xb, xb, xb, heat, z, f * tc) == pytest.approx(ref, rel=0.03)
