@@ -31,6 +31,11 @@
  *                       highly ionised fraction x_ion with the sub-grid
  *                       opacity and a neutral rest behind an infinitely thin
  *                       moving screen that the photons reaching it advance.
+ *   Sec. 4.2, Eq. 20-22 -- in that mode the photo-ionisation-equilibrium
+ *                       opacity law and, with evolving temperature, newly
+ *                       ionised gas at T_reion heated by the power-law
+ *                       photo-heating of Eq. 22 (helium singly ionised with
+ *                       hydrogen through chi, Eq. 18).
  * Where the paper is silent the reading taken is stated at the spot
  * (fixed-point geometry, termination, rotation sampler, rate fits ...).
  *
