@@ -152,3 +152,23 @@ def test_generalized_temperature_stromgren():
     assert np.all((T[ion] > 8e3) & (T[ion] < 6e4)) and np.median(T[ion]) > 1e4
     assert np.all(T[x == 0] == np.float32(100.0))
     g.close()
+
+
+def test_generalized_temperature_ragged_grid():
+    # a 24 x 16 x 9 grid with the source near a corner: the screens, the
+    # temperature and the escapes through three faces, cell by cell
+    p = W.stromgren(n=32, nsteps=20)
+    nx, ny, nz = 24, 16, 9
+    p = dc.replace(p, grid=(nx, ny, nz), nH=np.full(nx * ny * nz, 1e-3), source_cells=np.array([[1, 14, 4]], np.int32),
+                   mfp=dc.replace(p.mfp, mode=3),
+                   options=dc.replace(p.options, gen_mode=True, gamma_iters=5, isothermal=False, rates=1,
+                                      T_init=100.0, t_reion=2e4))
+    _run_gen_pair(p, x_atol=5e-4, vol_rtol=2e-5, bud_rtol=2e-6, g_rtol=5e-3, T_rtol=1e-3)
+
+
+def test_generalized_subgrid_law_with_temperature():
+    # the sub-grid opacity law with helium and evolving temperature
+    p = W.cosmo20k(n=24, nsteps=8, nsrc=40)
+    p = dc.replace(p, options=dc.replace(p.options, gen_mode=True, gamma_iters=4, chi=0.08, isothermal=False,
+                                         T_init=100.0, t_reion=2e4))
+    _run_gen_pair(p, x_atol=1e-4, vol_rtol=1e-5, bud_rtol=1e-6, g_rtol=1e-3, T_rtol=1e-3)

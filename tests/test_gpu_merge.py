@@ -272,3 +272,36 @@ def test_merge_in_generalized_mode_matches_oracle():
     assert g.rays()["merged"].sum() > 100
     g.close()
     o.close()
+
+
+def test_merge_with_iteration_matches_oracle():
+    # three passes of the Gamma - <n_HI> iteration and a merge after the last:
+    # element by element up to the first merge, then Sec. 7.1's global criteria
+    prob = _prob(1.0, 0, seed=2)
+    prob = dc.replace(prob, options=dc.replace(prob.options, gamma_iters=3))
+    g = F.Simulation(prob, ray_capacity=1 << 22)
+    o = oracle.OracleSim(prob)
+    n0_max = float(np.max(prob.source_ndot)) * prob.dt / 12
+    first = None
+    for s in range(prob.nsteps):
+        g.step(prob.dt)
+        o.step(prob.dt)
+        gb, ob = g.budget(), o.budget()
+        for b in (gb, ob):
+            assert abs(b[0] - b[1] - b[2] - b[3]) <= BUDGET_RTOL * b[0]
+        oc, gc = o.counts(), g.counts()
+        gf, of = g.fields(), o.fields()
+        orr = o.rays()
+        if first is None:
+            compare_merged_rays(g.rays(), orr, n0_max, allow=64 * oc["near_threshold"])
+            compare_fields(gf, of)
+            if orr["merged"].any():
+                first = s
+        else:
+            assert abs(gc["rays"] - oc["rays"]) <= 0.02 * oc["rays"] + 16
+            assert abs(gf["x_HII"].mean() - of["x_HII"].mean()) <= 0.01 * of["x_HII"].mean()
+            assert abs(gf["gamma_HI"].mean() - of["gamma_HI"].mean()) <= 0.02 * of["gamma_HI"].mean()
+            assert np.all(np.abs(gb - ob) <= 0.01 * ob[0])
+    assert first is not None and first < prob.nsteps - 1
+    g.close()
+    o.close()
