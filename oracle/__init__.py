@@ -130,8 +130,6 @@ def lib():
             L.or_merge_pixel.restype = C.c_int64
             L.or_vertex_child.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int64]
             L.or_vertex_child.restype = C.c_int64
-            L.or_rank_content.argtypes = [P(C.c_double), C.c_int, C.c_int]
-            L.or_rank_content.restype = C.c_float
             L.or_num_emitters.argtypes = [C.c_void_p]
             L.or_num_emitters.restype = C.c_int32
             L.or_config_size.restype = C.c_int64
@@ -173,8 +171,8 @@ def rotation(seed: int, emitter: int, step: int, rotate: bool = True):
 
 
 def merge_rotation(seed: int, cell: int, step: int, rotate: bool = True) -> np.ndarray:
-    """Rotation of a cell's merge sphere (Sec. 3.3), single precision:
-    Rq int32[3,3] = round(R * 2^24)."""
+    """Rotation of a cell's merge sphere (Sec. 3.3), drawn like an emitter's
+    sphere with the key 2^31 + cell: Rq int32[3,3] = round(R * 2^24)."""
     Rq = np.zeros(9, np.int32)
     lib().or_merge_rotation(seed, cell, step, int(rotate), _p(Rq, C.c_int32))
     return Rq.reshape(3, 3)
@@ -214,7 +212,7 @@ def traverse(p0, d, n):
 
 def merge_pixel(level: int, Rq, d) -> int:
     """Pixel at `level` of the fixed-point direction d on the merge sphere
-    rotated by Rq (Sec. 3.3), decided in single precision."""
+    rotated by Rq (Sec. 3.3): double-precision NESTED ang2pix of Rq^T d."""
     Rq = np.ascontiguousarray(np.asarray(Rq, np.int32).reshape(9))
     d = np.ascontiguousarray(np.asarray(d, np.int32).reshape(3))
     return int(lib().or_merge_pixel(level, _p(Rq, C.c_int32), _p(d, C.c_int32)))
@@ -224,13 +222,6 @@ def vertex_child(l_merge: int, pm: int, level: int, m: int, c: int) -> int:
     """Pixel (level + m) of child c of a merged ray of `level` centred on
     merge pixel pm of level l_merge."""
     return int(lib().or_vertex_child(l_merge, pm, level, m, c))
-
-
-def rank_content(N, E: int = 0) -> float:
-    """A ray's photons as the merge ranks them: the single-precision sum of
-    its bins, in bin order, in units of 2^E photons."""
-    N = np.ascontiguousarray(np.asarray(N, np.float64).reshape(-1))
-    return float(lib().or_rank_content(_p(N, C.c_double), len(N), E))
 
 
 def alpha_B(T: float) -> float:

@@ -251,49 +251,16 @@ void or_rotation(uint64_t seed, int64_t e, int64_t s, int rotate, double R[9], i
 
 /* Fixed-point direction of pixel (l,p) under rotation Rq:
  * vq = round(v * 2^24), d = round(Rq . vq / 2^27), |d| <= 2^21 per axis. */
-/* Random rotation of a cell's merge sphere (Sec. 3.3: one randomly oriented
- * HEALPix sphere per cell and merge).  The same counter-based stream and
- * Marsaglia quaternion as the emitters' rotations, evaluated in single
- * precision (24-bit uniforms, correctly rounded float operations in a fixed
- * order): these spheres are drawn for every cell at every merge, and the
- * result only has to be one identical random rotation on both sides.
- * Rq = round(R * 2^24). */
+/* Random rotation of a cell's merge sphere (Sec. 3.3: "in each cell, we
+ * throw down a randomly oriented HealPix sphere").  Drawn exactly like an
+ * emitter's sphere (or_rotation: the same counter-based stream and Marsaglia
+ * quaternion in double precision) with the key 2^31 + local cell index, one
+ * per (cell, step).  Rq = round(R * 2^24). */
+#define OR_MERGE_KEY ((int64_t)1 << 31)
 void or_merge_rotation(uint64_t seed, int64_t cell, int64_t s, int rotate, int32_t Rq[9])
 {
-    float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
-    if (rotate) {
-        const uint64_t key = rot_key(seed, ((int64_t)1 << 31) + cell, s);
-        int draw = 0;
-        float a = 0.0f, b = 0.0f, s1 = 2.0f, c = 0.0f, d = 0.0f, s2 = 2.0f;
-        int ok1 = 0, ok2 = 0;
-        for (int t = 0; t < 64 && !ok1; ++t) {
-            a = 2.0f * ((float)(or_sm_draw(key, draw++) >> 40) * 0x1p-24f) - 1.0f;
-            b = 2.0f * ((float)(or_sm_draw(key, draw++) >> 40) * 0x1p-24f) - 1.0f;
-            s1 = a * a + b * b;
-            ok1 = s1 < 1.0f;
-        }
-        for (int t = 0; t < 64 && ok1 && !ok2; ++t) {
-            c = 2.0f * ((float)(or_sm_draw(key, draw++) >> 40) * 0x1p-24f) - 1.0f;
-            d = 2.0f * ((float)(or_sm_draw(key, draw++) >> 40) * 0x1p-24f) - 1.0f;
-            s2 = c * c + d * d;
-            ok2 = s2 < 1.0f && s2 > 0.0f;
-        }
-        if (ok1 && ok2) {
-            float f = sqrtf((1.0f - s1) / s2);
-            w = a; x = b; y = c * f; z = d * f;
-        }
-    }
-    float R[9];
-    R[0] = 1.0f - 2.0f * (y * y + z * z);
-    R[1] = 2.0f * (x * y - w * z);
-    R[2] = 2.0f * (x * z + w * y);
-    R[3] = 2.0f * (x * y + w * z);
-    R[4] = 1.0f - 2.0f * (x * x + z * z);
-    R[5] = 2.0f * (y * z - w * x);
-    R[6] = 2.0f * (x * z - w * y);
-    R[7] = 2.0f * (y * z + w * x);
-    R[8] = 1.0f - 2.0f * (x * x + y * y);
-    for (int k = 0; k < 9; ++k) Rq[k] = (int32_t)rintf(R[k] * 16777216.0f);
+    double R[9];
+    or_rotation(seed, OR_MERGE_KEY + cell, s, rotate, R, Rq);
 }
 
 int or_direction(int level, int64_t p, const int32_t Rq[9], int32_t d[3])
@@ -339,14 +306,10 @@ void or_split_table(double n_min, int32_t K[OR_MAXL])
 /* ------------------------------------------------------------------------- */
 /* Merge-sphere pixel of a direction (Sec. 3.3)                               */
 /* ------------------------------------------------------------------------- */
-/* Which rays merge is decided by the pixel each falls in on the randomly
- * oriented level-l_merge sphere of its cell.  That is an integer decided by
- * floating point, so it is evaluated in single precision as one fixed
- * sequence of correctly rounded operations (the GPU evaluates the same
- * sequence): v = Rq^T d with the quantised rotation (entries below 2^24 in
- * magnitude, exact in float) and the fixed-point direction, then the NESTED
- * ang2pix of Gorski et al. (2005), with the azimuth from an arctangent
- * series instead of a library atan2. */
+/* The pixel a ray "occupies" on the randomly oriented level-l_merge sphere
+ * of its cell: the NESTED ang2pix of Gorski et al. (2005) of the direction
+ * expressed in the sphere's own frame, v = Rq^T d (the sphere's pixel
+ * vectors are Rq . v), in double precision with the library atan2. */
 
 static int64_t spread_bits(int64_t v) /* bit i of v to bit 2i */
 {
@@ -356,77 +319,37 @@ static int64_t spread_bits(int64_t v) /* bit i of v to bit 2i */
     return out;
 }
 
-/* arctan(t) / (pi/2) for 0 <= t <= 1.  Above tan(pi/8), arctan t = pi/4 +
- * arctan u with u = (t-1)/(t+1); then the Taylor series of arctan u to the
- * u^19 term (|u| <= tan(pi/8): the next term is below 1e-9 relative). */
-static float f_atan_quarter(float t)
-{
-    static const float c[10] = {1.0f, -0.333333343f, 0.200000003f, -0.142857149f, 0.111111112f,
-                                -0.0909090936f, 0.0769230798f, -0.0666666701f, 0.0588235296f,
-                                -0.0526315793f};
-    float base = 0.0f, u = t;
-    if (t > 0.414213568f) {
-        u = (t - 1.0f) / (t + 1.0f);
-        base = 0.5f;
-    }
-    float s2 = u * u;
-    float p = c[9];
-    for (int k = 8; k >= 0; --k) p = p * s2 + c[k];
-    float a = u * p;
-    return base + a * 0.636619747f;
-}
-
-/* azimuth of (x, y) in quarter turns, in [0, 4) */
-static float f_phi_quarter(float x, float y)
-{
-    float ax = fabsf(x), ay = fabsf(y);
-    if (ax == 0.0f && ay == 0.0f) return 0.0f;
-    float a = ax >= ay ? f_atan_quarter(ay / ax) : 1.0f - f_atan_quarter(ax / ay);
-    float tt;
-    if (x >= 0.0f) tt = y >= 0.0f ? a : 4.0f - a;
-    else tt = y >= 0.0f ? 2.0f - a : 2.0f + a;
-    if (tt >= 4.0f) tt = tt - 4.0f;
-    return tt;
-}
-
-/* NESTED pixel at `level` of direction d (fixed point) on the sphere rotated
- * by Rq (direction = Rq . pixel vector, so the pixel vector is Rq^T d). */
 int64_t or_merge_pixel(int level, const int32_t Rq[9], const int32_t d[3])
 {
-    const float df0 = (float)d[0], df1 = (float)d[1], df2 = (float)d[2];
-    float v[3];
-    for (int j = 0; j < 3; ++j) {
-        float a = (float)Rq[j] * df0;
-        float b = (float)Rq[3 + j] * df1;
-        float c = (float)Rq[6 + j] * df2;
-        v[j] = (a + b) + c;
-    }
+    double v[3];
+    for (int j = 0; j < 3; ++j)    /* integers below 2^47: exact */
+        v[j] = (double)Rq[j] * (double)d[0] + (double)Rq[3 + j] * (double)d[1] + (double)Rq[6 + j] * (double)d[2];
     const int64_t nside = (int64_t)1 << level;
-    const float ns = (float)nside;
-    float s2 = v[0] * v[0] + v[1] * v[1];
-    float r = sqrtf(s2 + v[2] * v[2]);
-    float z = v[2] / r;
-    float za = fabsf(z);
-    float tt = f_phi_quarter(v[0], v[1]);
+    const double ns = (double)nside;
+    const double s2 = v[0] * v[0] + v[1] * v[1];
+    const double r = sqrt(s2 + v[2] * v[2]);
+    const double z = v[2] / r, za = fabs(z);
+    double tt = atan2(v[1], v[0]) / (0.5 * OR_PI);   /* azimuth in quarter turns */
+    if (tt < 0.0) tt += 4.0;
+    if (tt >= 4.0) tt -= 4.0;
     int64_t face, ix, iy;
-    if (za <= 0.666666687f) {                       /* equatorial belt */
-        float t1 = ns * (0.5f + tt);
-        float t2 = ns * (z * 0.75f);
-        int64_t jp = (int64_t)(t1 - t2), jm = (int64_t)(t1 + t2);
-        int64_t ifp = jp >> level, ifm = jm >> level;
+    if (za <= 2.0 / 3.0) {                          /* equatorial belt */
+        const double t1 = ns * (0.5 + tt), t2 = ns * z * 0.75;
+        const int64_t jp = (int64_t)(t1 - t2), jm = (int64_t)(t1 + t2);
+        const int64_t ifp = jp >> level, ifm = jm >> level;
         face = ifp == ifm ? (ifp | 4) : (ifp < ifm ? ifp : ifm + 8);
         ix = jm & (nside - 1);
         iy = nside - (jp & (nside - 1)) - 1;
     } else {                                         /* polar caps */
         int64_t ntt = (int64_t)tt;
         if (ntt > 3) ntt = 3;
-        float tp = tt - (float)ntt;
-        float omz = s2 / (r * (r + fabsf(v[2])));    /* 1 - |z| without cancellation */
-        float tmp = ns * sqrtf(3.0f * omz);
-        int64_t jp = (int64_t)(tp * tmp), jm = (int64_t)((1.0f - tp) * tmp);
+        const double tp = tt - (double)ntt;
+        const double omz = s2 / (r * (r + fabs(v[2])));   /* 1 - |z| */
+        const double tmp = ns * sqrt(3.0 * omz);
+        int64_t jp = (int64_t)(tp * tmp), jm = (int64_t)((1.0 - tp) * tmp);
         if (jp > nside - 1) jp = nside - 1;
         if (jm > nside - 1) jm = nside - 1;
-        if (z >= 0.0f) { face = ntt; ix = nside - jm - 1; iy = nside - jp - 1; }
+        if (z >= 0.0) { face = ntt; ix = nside - jm - 1; iy = nside - jp - 1; }
         else { face = ntt + 8; ix = jp; iy = jm; }
     }
     return face * nside * nside + spread_bits(ix) + 2 * spread_bits(iy);
@@ -884,38 +807,21 @@ static void deposit_all(or_sim *S, int64_t cell, const double *N, const double *
 /* Ray merging at the end of a step (Sec. 3.3, Eq. 4)                         */
 /* ------------------------------------------------------------------------- */
 /* Readings where the section is silent:
- *  - rank: a ray's photon content is the sum over bins in single precision
- *    (an integer decision taken in the precision of the GPU path); with
+ *  - rank: a ray's photon content is the sum of its bins; with
  *    K = floor(N_ex * N_RT), every ray whose content is at least the K-th
- *    largest, T_ref, is exempt (ties at the K-th value are all exempt; with
- *    K = 0 nothing is exempt and T_ref is the largest content);
+ *    largest, T_ref, is exempt (ties at the K-th value are all exempt; K = 0
+ *    exempts nothing; K >= the number of rays merges nothing);
  *  - cell: the cell holding the ray's end point (floor per axis); a ray whose
  *    end point is on the far face of the box is not merged;
  *  - sphere: one random rotation per (cell, step), drawn like an emitter's
- *    with the key 2^31 + local cell index, in single precision
  *    (or_merge_rotation);
  *  - merged ray: photons summed per bin; position, distance travelled and
- *    level are photon-weighted means of the constituents' (rounded half to
- *    even to the fixed-point grid, whole cells and whole levels; the level
- *    at least l_merge); direction the centre of the merge pixel; termination
- *    threshold the sum of the constituents'.  A group of one ray keeps the
- *    ray.  The means are exact integer quotients: a ray's weight is its
- *    content on a grid of 2^-26 of the power of two above T_ref (truncated,
- *    at least 1), so the position is an integer decided identically in any
- *    summation order. */
-#define OR_MERGE_KEY ((int64_t)1 << 31)
-
-#define OR_WBITS 26                          /* merge weights below 2^26 */
-
+ *    HEALPix level are the photon-weighted means of the constituents'
+ *    (weight: the ray's content), each rounded once to nearest (the
+ *    fixed-point grid, whole cells, whole levels; the level at least
+ *    l_merge); direction the centre of the merge pixel; termination threshold
+ *    the sum of the constituents'.  A group of one ray keeps the ray. */
 typedef struct { int64_t key, idx; } or_mkey;
-
-/* num / den rounded to nearest, ties to even */
-static uint64_t div_rne(uint64_t num, uint64_t den)
-{
-    uint64_t q = num / den, r = num - q * den;
-    if (2 * r > den || (2 * r == den && (q & 1))) q++;
-    return q;
-}
 
 static int cmp_mkey(const void *a, const void *b)
 {
@@ -924,21 +830,10 @@ static int cmp_mkey(const void *a, const void *b)
     return x->idx < y->idx ? -1 : (x->idx > y->idx);
 }
 
-static int cmp_float_desc(const void *a, const void *b)
+static int cmp_double_desc(const void *a, const void *b)
 {
-    float x = *(const float *)a, y = *(const float *)b;
+    double x = *(const double *)a, y = *(const double *)b;
     return x > y ? -1 : (x < y);
-}
-
-/* Photons of a ray as the merge ranks them: the single-precision sum, in bin
- * order, of its bins in units of 2^E photons.  Rounding commutes with a
- * power-of-two unit, so the order (and its ties) is the same for any unit
- * that keeps the values in the normal single-precision range. */
-float or_rank_content(const double *N, int nb, int E)
-{
-    float t = (float)ldexp(N[0], -E);
-    for (int b = 1; b < nb; ++b) t = t + (float)ldexp(N[b], -E);
-    return t;
 }
 
 static int or_merge(or_sim *S, double dt, int64_t s, int64_t Kin)
@@ -950,26 +845,23 @@ static int or_merge(or_sim *S, double dt, int64_t s, int64_t Kin)
     const int64_t K = (int64_t)Kd;
     const int64_t ncast = 12LL << (2 * c->l_src);
     const int64_t ndir = 12LL << (2 * c->l_merge);
-    float *T = malloc((size_t)n * sizeof(float)), *Ts = malloc((size_t)n * sizeof(float));
+    double *T = malloc((size_t)n * sizeof(double)), *Ts = malloc((size_t)n * sizeof(double));
     or_mkey *mk = malloc((size_t)n * sizeof(or_mkey));
     int64_t (*p1) = malloc((size_t)n * 3 * sizeof(int64_t));
     char *dead = calloc((size_t)n, 1);
     if (!T || !Ts || !mk || !p1 || !dead) return -1;
-    double nmax = 0.0;
+    /* rank by photon content (Sec. 3.3: "rank-ordered by the number of
+     * photons they contain") */
     for (int64_t i = 0; i < n; ++i) {
         double t = 0.0;
         for (int b = 0; b < c->nb; ++b) t += S->rays[i].N[b];
-        if (t > nmax) nmax = t;
+        Ts[i] = T[i] = t;
     }
-    int E = 0;
-    frexp(nmax, &E);                                   /* unit: the largest content is below 1 */
-    for (int64_t i = 0; i < n; ++i) Ts[i] = T[i] = or_rank_content(S->rays[i].N, c->nb, E);
-    qsort(Ts, (size_t)n, sizeof(float), cmp_float_desc);
-    const float Tref = Ts[(K > 0 ? K : 1) - 1];
-    const float Tstar = K > 0 ? Tref : INFINITY;
-    int eref = 0;
-    frexpf(Tref, &eref);                               /* Tref < 2^eref */
-    const float wscale = ldexpf(1.0f, OR_WBITS - eref);
+    double Tstar = INFINITY;
+    if (K > 0) {
+        qsort(Ts, (size_t)n, sizeof(double), cmp_double_desc);
+        Tstar = Ts[K - 1];
+    }
     int64_t nm = 0;
     const int64_t nn[3] = {c->nx, c->ny, c->nz};
     for (int64_t i = 0; i < n; ++i) {
@@ -1002,28 +894,31 @@ static int or_merge(or_sim *S, double dt, int64_t s, int64_t Kin)
             memset(&m, 0, sizeof(m));
             const int64_t local = mk[g0].key / ndir, pm = mk[g0].key % ndir;
             const int64_t cell[3] = {local % c->nx, (local / c->nx) % c->ny, local / ((int64_t)c->nx * c->ny)};
-            uint64_t W = 0, wp[3] = {0, 0, 0}, wa = 0, wl = 0;
-            double thr = 0.0;
+            /* photon-weighted sums; positions relative to the cell's corner */
+            double W = 0.0, wp[3] = {0.0, 0.0, 0.0}, wa = 0.0, wl = 0.0, thr = 0.0;
             for (int64_t k = g0; k < g1; ++k) {
                 const int64_t i = mk[k].idx;
                 const or_ray *r = &S->rays[i];
+                const double w = T[i];
                 for (int b = 0; b < c->nb; ++b) m.N[b] += r->N[b];
-                float qf = T[i] * wscale;                      /* exact unless below 2^-126 */
-                uint64_t q = (uint64_t)qf;
-                if (q < 1) q = 1;
-                for (int a = 0; a < 3; ++a) wp[a] += q * (uint64_t)(p1[3 * i + a] - cell[a] * OR_S);
-                int64_t dist = r->kind == 0 ? s - r->b + 1 : r->A + (s - r->b);
-                wa += q * (uint64_t)dist;
-                wl += q * (uint64_t)r->l;
+                for (int a = 0; a < 3; ++a) wp[a] += w * (double)(p1[3 * i + a] - cell[a] * OR_S);
+                const int64_t dist = r->kind == 0 ? s - r->b + 1 : r->A + (s - r->b);
+                wa += w * (double)dist;
+                wl += w * (double)r->l;
                 thr += r->kind == 0 ? c->eps_term * S->endot[r->e] * dt / (double)ncast * ldexp(1.0, -2 * (r->l - c->l_src))
                                     : r->thr;
-                W += q;
+                W += w;
                 dead[i] = 1;
             }
-            for (int a = 0; a < 3; ++a) m.P[a] = cell[a] * OR_S + (int64_t)div_rne(wp[a], W);
-            uint64_t A = div_rne(wa, W);
-            m.A = (int32_t)(A > 65535 ? 65535 : A);
-            int64_t L = (int64_t)div_rne(wl, W);
+            for (int a = 0; a < 3; ++a) {
+                int64_t v = W > 0.0 ? (int64_t)nearbyint(wp[a] / W) : 0;
+                if (v < 0) v = 0;
+                if (v > OR_S - 1) v = OR_S - 1;
+                m.P[a] = cell[a] * OR_S + v;
+            }
+            const double Am = W > 0.0 ? nearbyint(wa / W) : 0.0;
+            m.A = (int32_t)(Am < 0.0 ? 0.0 : (Am > 65535.0 ? 65535.0 : Am));
+            int64_t L = W > 0.0 ? (int64_t)nearbyint(wl / W) : c->l_merge;
             if (L < c->l_merge) L = c->l_merge;
             if (L > c->l_max) L = c->l_max;
             m.l = (int32_t)L;
