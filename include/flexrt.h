@@ -54,7 +54,7 @@ typedef enum {
     FLEXRT_E_OOM = 2,       /* device or host allocation failed              */
     FLEXRT_E_CAPACITY = 3,  /* ray queue, emitter or cell arena full         */
     FLEXRT_E_CUDA = 4,      /* CUDA runtime error                            */
-    FLEXRT_E_TIMEOUT = 5,   /* a bounded device wait expired                 */
+    FLEXRT_E_TIMEOUT = 5,   /* reserved: no call waits on the device with a limit */
     FLEXRT_E_STATE = 6      /* call not valid in the current state           */
 } flexrt_status;
 
@@ -153,6 +153,12 @@ typedef struct {
     double chi;
     double t_reion;
     double alpha_pl;
+    /* Cap on the device memory the context allocates (bytes; 0 = none).  An
+     * allocation that would pass it fails as if the device were full:
+     * flexrt_create returns FLEXRT_E_OOM, frees whatever it had allocated
+     * and leaves *out NULL; flexrt_add_sources returns FLEXRT_E_OOM and the
+     * context keeps its previous sources. */
+    int64_t device_bytes_max;
 } flexrt_options;
 
 /* Fill *o with defaults (l_src 0, l_max 12, N_min 3, eps 1e-10, seed 1,
@@ -179,7 +185,9 @@ flexrt_status flexrt_add_sources(flexrt_ctx *ctx, int32_t n, const int32_t *cell
 /* Enqueue one RT step of length dt_s seconds (asynchronous). */
 flexrt_status flexrt_step(flexrt_ctx *ctx, double dt_s);
 
-/* Wait for all enqueued work; returns a latched device error if any. */
+/* Wait for all enqueued work; returns a latched device error if any.  No
+ * call of this library waits on the device with a time limit, so
+ * FLEXRT_E_TIMEOUT is reserved and never returned. */
 flexrt_status flexrt_sync(flexrt_ctx *ctx);
 
 /* Restore the state right after flexrt_create + flexrt_add_sources (fields,
@@ -226,6 +234,27 @@ flexrt_status flexrt_get_ionized_volume(flexrt_ctx *ctx, double *x_ion);
 flexrt_status flexrt_get_rays_merged(flexrt_ctx *ctx, int64_t cap, int32_t *merged, int32_t *vertex,
                                      int32_t *dist, int64_t *pos, double *thr, int64_t *n);
 
+/* Checkpoint and restart (no counterpart in the paper: a facility for long
+ * runs).  flexrt_save_state writes the state a later step reads -- per-cell
+ * neutral fraction, ionised fraction, temperature, Gamma, opacity and
+ * Generalized-mode state, the live rays, the emitters' photons per ray and
+ * rotation ring, the step counter, dt and the photon budget -- into the
+ * caller's host buffer buf of cap bytes; with buf == NULL it only stores the
+ * size needed in *bytes (FLEXRT_E_CAPACITY if cap is too small).  It waits
+ * for enqueued work.  flexrt_load_state restores such a buffer into a
+ * context created with the same grid, spectrum bins, sources, queue layout
+ * (merging on or off) and a ray capacity that holds its rays; FLEXRT_E_INVALID
+ * for a buffer of another simulation, with the context unchanged.  A restored
+ * context continues exactly as the saved one would: the next step marches the
+ * same rays through the same opacities.  Options (N_ex, passes ...) are those
+ * of the context it is loaded into. */
+flexrt_status flexrt_save_state(flexrt_ctx *ctx, void *buf, int64_t cap, int64_t *bytes);
+flexrt_status flexrt_load_state(flexrt_ctx *ctx, const void *buf, int64_t bytes);
+
+/* Device memory the context has allocated, in bytes (the quantity
+ * flexrt_options.device_bytes_max caps). */
+flexrt_status flexrt_get_device_bytes(flexrt_ctx *ctx, int64_t *bytes);
+
 /* Per-kernel device time accumulated since the last call (CUDA events on
  * the context stream): "emit", "march", "chem" and "merge" (all kernels of
  * the merge step); ms[k], launches[k].  Timing is only recorded when enabled
@@ -266,11 +295,13 @@ flexrt_status flexrt_probe_direction(int32_t level, int64_t p0, int64_t n,
                                      const int32_t *Rq, int32_t *out);
 
 /* Merge-sphere pixel (Sec. 3.3) of n fixed-point directions d int32[3n] on
- * the sphere rotated by Rq int32[9] at `level` (0..12): out int32[n].  The
- * decision is taken in single precision by one fixed sequence of correctly
- * rounded operations (v = Rq^T d, NESTED ang2pix). */
+ * the sphere rotated by Rq at `level` (0..12): out int32[n].  Rq holds
+ * n_rot rotations int32[9 * n_rot]: n_rot == 1, one sphere for every
+ * direction; n_rot == n, direction i on sphere i.  The step's decision:
+ * single precision, one fixed sequence of correctly rounded operations
+ * (v = Rq^T d, NESTED ang2pix). */
 flexrt_status flexrt_probe_merge_pixel(int32_t level, int64_t n, const int32_t *d, const int32_t *Rq,
-                                       int32_t *out);
+                                       int64_t n_rot, int32_t *out);
 
 /* Rays as the merge step sees them (flexrt_probe_merge): n rays, caller-owned
  * host arrays.  pixlev = level << 28 | NESTED pixel (merge pixel of a vertex
@@ -343,6 +374,9 @@ typedef struct {
                                 cell_capacity * 12 * 4^merge_l_max groups);
                                 -1: members cannot merge                       */
     int32_t gen_capable;     /* 1: members may run Generalized mode            */
+    int64_t device_bytes_max;/* cap on the batch's device allocations (0 = none);
+                                flexrt_batch_create fails with FLEXRT_E_OOM and
+                                frees everything when the arenas exceed it     */
 } flexrt_batch_config;
 
 void flexrt_default_batch_config(flexrt_batch_config *c);
@@ -371,6 +405,7 @@ flexrt_status flexrt_batch_retire(flexrt_batch *b, int32_t slot);
 flexrt_status flexrt_batch_get_fields(flexrt_batch *b, int32_t slot, flexrt_fields *f);
 flexrt_status flexrt_batch_get_budget(flexrt_batch *b, int32_t slot, double out[4]);
 flexrt_status flexrt_batch_get_counts(flexrt_batch *b, int32_t slot, int64_t out[6]);
+flexrt_status flexrt_batch_get_segment_counts(flexrt_batch *b, int32_t slot, int32_t *out);
 flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *level,
                                     int64_t *pixel, int32_t *emitter, int32_t *birth, int32_t *dir,
                                     double *photons, int64_t *n);
@@ -401,8 +436,10 @@ void flexrt_batch_destroy(flexrt_batch *b);
  * (FLEXRT_STATIC_MAX_RAYS rays), present on every GPU that loads the library
  * until the process exits.  n > FLEXRT_STATIC_MAX_RAYS returns
  * FLEXRT_E_CAPACITY with a message in flexrt_last_error(NULL).  The first call
- * on each device looks up the array's device address; make that first call
- * before any stream capture.  Every call reuses the same array: calls that
+ * on each device looks up the array's device address and keeps it for the
+ * life of the process; make that first call before any stream capture.  A
+ * device reset (cudaDeviceReset, or a reset of the primary context) between
+ * calls is not supported: the kept address would be stale.  Every call reuses the same array: calls that
  * overlap on the GPU (e.g. from two host threads) race, so serialise them.
  * Synchronous; runs on the legacy default stream; allocates nothing. */
 flexrt_status flexrt_probe_traverse_static(int64_t n, const int64_t *p0, const int32_t *d,

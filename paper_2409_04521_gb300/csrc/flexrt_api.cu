@@ -84,6 +84,7 @@ extern "C" flexrt_status flexrt_create(const flexrt_grid *grid, const flexrt_box
     cfg.stream = opt.cuda_stream;
     cfg.merge_l_max = opt.merge ? opt.l_merge : -1;
     cfg.gen_capable = opt.gen_mode != 0;
+    cfg.device_bytes_max = opt.device_bytes_max;
     s = c->eng.init(cfg);
     if (s == FLEXRT_OK) s = c->eng.add_sim(h, n_H, &c->slot);
     if (s != FLEXRT_OK) {
@@ -132,6 +133,17 @@ extern "C" flexrt_status flexrt_get_ionized_volume(flexrt_ctx *c, double *x_ion)
 extern "C" flexrt_status flexrt_get_rays_merged(flexrt_ctx *c, int64_t cap, int32_t *merged, int32_t *vertex,
                                                 int32_t *dist, int64_t *pos, double *thr, int64_t *n) {
     return c ? c->eng.rays_merged(c->slot, cap, merged, vertex, dist, pos, thr, n) : FLEXRT_E_INVALID;
+}
+extern "C" flexrt_status flexrt_save_state(flexrt_ctx *c, void *buf, int64_t cap, int64_t *bytes) {
+    return c ? c->eng.save_state(c->slot, buf, cap, bytes) : FLEXRT_E_INVALID;
+}
+extern "C" flexrt_status flexrt_load_state(flexrt_ctx *c, const void *buf, int64_t bytes) {
+    return c ? c->eng.load_state(c->slot, buf, bytes) : FLEXRT_E_INVALID;
+}
+extern "C" flexrt_status flexrt_get_device_bytes(flexrt_ctx *c, int64_t *bytes) {
+    if (!c || !bytes) return FLEXRT_E_INVALID;
+    *bytes = c->eng.device_bytes();
+    return FLEXRT_OK;
 }
 extern "C" flexrt_status flexrt_profile(flexrt_ctx *c, int32_t enable) {
     return c ? c->eng.profile(enable != 0) : FLEXRT_E_INVALID;
@@ -184,6 +196,7 @@ extern "C" flexrt_status flexrt_batch_create(const flexrt_batch_config *bc, flex
     cfg.stream = bc->cuda_stream;
     cfg.merge_l_max = bc->merge_l_max;
     cfg.gen_capable = bc->gen_capable != 0;
+    cfg.device_bytes_max = bc->device_bytes_max;
     flexrt_status s = b->eng.init(cfg);
     if (s != FLEXRT_OK) {
         free_fail(s, "flexrt_batch_create: " + b->eng.error());
@@ -224,6 +237,9 @@ extern "C" flexrt_status flexrt_batch_retire(flexrt_batch *b, int32_t slot) {
 }
 extern "C" flexrt_status flexrt_batch_get_fields(flexrt_batch *b, int32_t slot, flexrt_fields *f) {
     return b ? b->eng.fields(slot, f) : FLEXRT_E_INVALID;
+}
+extern "C" flexrt_status flexrt_batch_get_segment_counts(flexrt_batch *b, int32_t slot, int32_t *out) {
+    return b ? b->eng.segment_counts(slot, out) : FLEXRT_E_INVALID;
 }
 extern "C" flexrt_status flexrt_batch_get_budget(flexrt_batch *b, int32_t slot, double out[4]) {
     return b ? b->eng.budget(slot, out) : FLEXRT_E_INVALID;
@@ -315,20 +331,21 @@ extern "C" flexrt_status flexrt_probe_direction(int32_t level, int64_t p0, int64
 }
 
 extern "C" flexrt_status flexrt_probe_merge_pixel(int32_t level, int64_t n, const int32_t *d, const int32_t *Rq,
-                                                  int32_t *out) {
-    if (level < 0 || level > FLEXRT_MAX_LEVEL || n < 0 || !Rq || (n && (!d || !out))) return FLEXRT_E_INVALID;
+                                                  int64_t n_rot, int32_t *out) {
+    if (level < 0 || level > FLEXRT_MAX_LEVEL || n < 0 || !Rq || (n && (!d || !out)) || !(n_rot == 1 || n_rot == n))
+        return FLEXRT_E_INVALID;
     for (int64_t i = 0; i < 3 * n; ++i)
         if (d[i] > (1 << 21) || d[i] < -(1 << 21)) return FLEXRT_E_INVALID;
-    for (int k = 0; k < 9; ++k)
+    for (int64_t k = 0; k < 9 * n_rot; ++k)
         if (Rq[k] > (1 << 24) || Rq[k] < -(1 << 24)) return FLEXRT_E_INVALID;
     DevBuf<int32_t> dd, dr;
     DevBuf<uint32_t> dout;
-    if (dd.alloc(3 * n) != cudaSuccess || dr.alloc(9) != cudaSuccess || dout.alloc(n) != cudaSuccess)
+    if (dd.alloc(3 * n) != cudaSuccess || dr.alloc(9 * n_rot) != cudaSuccess || dout.alloc(n) != cudaSuccess)
         return FLEXRT_E_OOM;
     if (cudaMemcpy(dd.p, d, 3 * n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(dr.p, Rq, 9 * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(dr.p, Rq, 9 * n_rot * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
         return FLEXRT_E_CUDA;
-    if (launch_probe_merge_pixel(level, n, dd.p, dr.p, dout.p, 0) != cudaSuccess) return FLEXRT_E_CUDA;
+    if (launch_probe_merge_pixel(level, n, dd.p, dr.p, n_rot > 1, dout.p, 0) != cudaSuccess) return FLEXRT_E_CUDA;
     if (cudaMemcpy(out, dout.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return FLEXRT_E_CUDA;
     return FLEXRT_OK;
 }
@@ -384,7 +401,8 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     DevBuf<Ctl> dctl;
     DevBuf<SimDev> dsim;
     DevBuf<SimAcc> dacc;
-    DevBuf<uint32_t> qpl[2], qem[2], qma[2], hist, sel, tkey, gcnt, lead_i, lead_slot;
+    DevBuf<uint32_t> qpl[2], qem[2], qma[2], hist, sel, tkey, gcnt, gmax, lead_i, lead_slot;
+    DevBuf<uint4> tgrp;
     DevBuf<int32_t> qbi[2], qd[2], qm[2], tsim, rsim;
     DevBuf<float> qph[2], qthr[2], grp, n0;
     DevBuf<int4> ecell, rot;
@@ -396,6 +414,7 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
              qph[k].alloc(nb * m) == cudaSuccess && qthr[k].alloc(m) == cudaSuccess;
     ok = ok && hist.alloc(HIST_BINS) == cudaSuccess && sel.alloc(8) == cudaSuccess && tkey.alloc(m) == cudaSuccess &&
          tsim.alloc(m) == cudaSuccess && gcnt.alloc(ncell * ndir) == cudaSuccess &&
+         gmax.alloc(ncell * ndir) == cudaSuccess && tgrp.alloc(m) == cudaSuccess &&
          grp.alloc(ncell * ndir * gw) == cudaSuccess && rot.alloc(3 * ncell) == cudaSuccess &&
          ecell.alloc(std::max(p->n_emitters, 1)) == cudaSuccess && n0.alloc(std::max(p->n_emitters, 1)) == cudaSuccess &&
          pref.alloc(2) == cudaSuccess && cell0.alloc(1) == cudaSuccess && rsim.alloc(1) == cudaSuccess &&
@@ -436,7 +455,7 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
          up(n0.p, p->emitter_n0, p->n_emitters * sizeof(float)) && up(pref.p, pr, sizeof(pr)) &&
          up(cell0.p, &c0, sizeof(c0)) && up(rsim.p, &s0, sizeof(s0));
     ok = ok && cudaMemset(hist.p, 0, HIST_BINS * 4) == cudaSuccess && cudaMemset(sel.p, 0, 32) == cudaSuccess &&
-         cudaMemset(gcnt.p, 0, ncell * ndir * 4) == cudaSuccess &&
+         cudaMemset(gcnt.p, 0, ncell * ndir * 4) == cudaSuccess && cudaMemset(gmax.p, 0, ncell * ndir * 4) == cudaSuccess &&
          cudaMemset(grp.p, 0, (size_t)ncell * ndir * gw * 4) == cudaSuccess;
     if (!ok) return free_fail(FLEXRT_E_CUDA, "probe_merge: upload failed");
     Emitters em{};
@@ -444,7 +463,7 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     Ranges rg{pref.p, cell0.p, rsim.p};
     MergeWork w{};
     w.hist = hist.p; w.sel = sel.p; w.tkey = tkey.p; w.tsim = tsim.p;
-    w.grp = grp.p; w.gcnt = gcnt.p; w.rot = rot.p; w.ndir = ndir; w.grp_w = gw;
+    w.grp = grp.p; w.gcnt = gcnt.p; w.gmax = gmax.p; w.tgrp = tgrp.p; w.rot = rot.p; w.ndir = ndir; w.grp_w = gw;
     w.hrep = 1; w.lead_i = lead_i.p; w.lead_slot = lead_slot.p;
     w.lead_cap = m + MERGE_MAX_BLOCKS * 8 * 128;
     MergeArgs a{dctl.p, dsim.p, dacc.p, 1, {q0, q1}, em, rg, tab, lt, w, nb};

@@ -113,7 +113,8 @@ __host__ __device__ __forceinline__ long long level_offset(int l) {  // sum_{j<l
 // ---------------------------------------------------------------------------
 // Per-(emitter, step) random rotation (Sec. 3.1).  SplitMix64 (Steele, Lea &
 // Flood 2014) as a counter-based stream; Marsaglia (1972) uniform unit
-// quaternion.  Rows returned as round(R * 2^24).
+// quaternion.  Rows returned as round(R * 2^24).  A cell's merge sphere
+// (Sec. 3.3) is drawn the same way with the key 2^31 + local cell index.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t sm64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -167,57 +168,6 @@ __device__ inline void rotation_rows(uint64_t seed, long long e, long long s, in
     for (int r = 0; r < 3; ++r)
         rows[r] = make_int4(__double2int_rn(__dmul_rn(R[3 * r], Q)), __double2int_rn(__dmul_rn(R[3 * r + 1], Q)),
                             __double2int_rn(__dmul_rn(R[3 * r + 2], Q)), 0);
-}
-
-// Rotation of a cell's merge sphere (Sec. 3.3) for (seed, local cell, step):
-// the same counter-based stream (key 2^31 + cell) and Marsaglia quaternion,
-// in single precision -- 24-bit uniforms and correctly rounded float
-// operations in a fixed order (explicit _rn intrinsics).  Rows round(R * 2^24).
-__device__ inline void merge_rotation_rows(uint64_t seed, long long cell, long long s, int rotate, int4 rows[3]) {
-    float w = 1.0f, x = 0.0f, y = 0.0f, zz = 0.0f;
-    if (rotate) {
-        uint64_t h = sm64(seed + GOLD);
-        h = sm64(h + GOLD * (uint64_t)((1LL << 31) + cell + 1));
-        h = sm64(h + GOLD * (uint64_t)(s + 1));
-        int draw = 0;
-        auto uni = [&](void) -> float {
-            const uint64_t u = sm64(h + GOLD * (uint64_t)(draw + 1));
-            ++draw;
-            return __fmul_rn((float)(uint32_t)(u >> 40), 5.9604644775390625e-08f);   // 2^-24
-        };
-        float a = 0, b = 0, s1 = 0, c = 0, d = 0, s2 = 0;
-        bool ok1 = false, ok2 = false;
-        for (int t = 0; t < 64 && !ok1; ++t) {
-            a = __fadd_rn(__fmul_rn(2.0f, uni()), -1.0f);
-            b = __fadd_rn(__fmul_rn(2.0f, uni()), -1.0f);
-            s1 = __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b));
-            ok1 = s1 < 1.0f;
-        }
-        for (int t = 0; t < 64 && ok1 && !ok2; ++t) {
-            c = __fadd_rn(__fmul_rn(2.0f, uni()), -1.0f);
-            d = __fadd_rn(__fmul_rn(2.0f, uni()), -1.0f);
-            s2 = __fadd_rn(__fmul_rn(c, c), __fmul_rn(d, d));
-            ok2 = (s2 < 1.0f) && (s2 > 0.0f);
-        }
-        if (ok1 && ok2) {
-            const float f = __fsqrt_rn(__fdiv_rn(__fadd_rn(1.0f, -s1), s2));
-            w = a; x = b; y = __fmul_rn(c, f); zz = __fmul_rn(d, f);
-        }
-    }
-    float R[9];
-    R[0] = __fadd_rn(1.0f, -__fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, y), __fmul_rn(zz, zz))));
-    R[1] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, y), -__fmul_rn(w, zz)));
-    R[2] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, zz), __fmul_rn(w, y)));
-    R[3] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, y), __fmul_rn(w, zz)));
-    R[4] = __fadd_rn(1.0f, -__fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(zz, zz))));
-    R[5] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, zz), -__fmul_rn(w, x)));
-    R[6] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, zz), -__fmul_rn(w, y)));
-    R[7] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, zz), __fmul_rn(w, x)));
-    R[8] = __fadd_rn(1.0f, -__fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y))));
-    for (int r = 0; r < 3; ++r)
-        rows[r] = make_int4(__float2int_rn(__fmul_rn(R[3 * r], 16777216.0f)),
-                            __float2int_rn(__fmul_rn(R[3 * r + 1], 16777216.0f)),
-                            __float2int_rn(__fmul_rn(R[3 * r + 2], 16777216.0f)), 0);
 }
 
 // round(X / 2^27), ties to even (X = Rq . vq, 2^48 scale -> 2^21 scale)

@@ -114,6 +114,29 @@ flexrt_status Engine::cuda(cudaError_t e, const char *what) {
     return FLEXRT_E_CUDA;
 }
 
+// Device allocations of the engine: counted against the context's cap
+// (device_bytes_max; 0 = none); an allocation beyond it fails like a
+// cudaMalloc that found no memory.
+cudaError_t Engine::dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (cfg_.device_bytes_max > 0 && (long long)(alloc_bytes_ + bytes) > cfg_.device_bytes_max)
+        return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    alloc_sizes_[*p] = bytes;
+    alloc_bytes_ += bytes;
+    return cudaSuccess;
+}
+void Engine::dev_free(void *p) {
+    if (!p) return;
+    auto it = alloc_sizes_.find(p);
+    if (it != alloc_sizes_.end()) {
+        alloc_bytes_ -= it->second;
+        alloc_sizes_.erase(it);
+    }
+    cudaFree(p);
+}
+
 #define CK(call)                                          \
     do {                                                  \
         cudaError_t e__ = (call);                         \
@@ -123,14 +146,9 @@ flexrt_status Engine::cuda(cudaError_t e, const char *what) {
 Engine::~Engine() {
     if (st_) cudaStreamSynchronize(st_);
     if (graph_) cudaGraphExecDestroy(graph_);
-    cudaFree(ctl_); cudaFree(sims_); cudaFree(acc_); cudaFree(qmem_);
-    cudaFree(cells_.nH); cudaFree(cells_.nHf); cudaFree(cells_.y); cudaFree(cells_.x); cudaFree(cells_.T); cudaFree(cells_.gamma);
-    cudaFree(cells_.kap); cudaFree(cells_.dep); cudaFree(cells_.segcnt);
-    cudaFree(cells_.xion); cudaFree(cells_.rho); cudaFree(cells_.fscr);
-    cudaFree(em_.cell); cudaFree(em_.local); cudaFree(em_.ndot); cudaFree(em_.n0);
-    cudaFree(em_.ring); cudaFree(em_.act); cudaFree(em_.act_off);
-    cudaFree(rg_.pref); cudaFree(rg_.cell0); cudaFree(rg_.sim);
-    cudaFree(mwmem_);
+    // every device allocation of the engine, whether or not init completed
+    for (auto &kv : alloc_sizes_) cudaFree(kv.first);
+    alloc_sizes_.clear();
     if (h_err_) cudaFreeHost(h_err_);
     if (h_stage_) cudaFreeHost(h_stage_);
     if (ev_err_) cudaEventDestroy(ev_err_);
@@ -175,7 +193,7 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     {
         const size_t a = (size_t)cap * 4, per = ray_bytes(cfg_.nb, mrg) * (size_t)cap;
         char *base = nullptr;
-        if (cudaMalloc(&base, 2 * per + 256) != cudaSuccess) return fail(FLEXRT_E_OOM, "ray queue allocation failed");
+        if (dev_alloc((void **)&base, 2 * per + 256) != cudaSuccess) return fail(FLEXRT_E_OOM, "ray queue allocation failed");
         qmem_ = base;
         for (int k = 0; k < 2; ++k) {
             char *p = base + k * per;
@@ -201,7 +219,7 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     const long long nc = cfg_.cell_capacity;
     const int ms = cfg_.max_sims;
 #define ALLOC(ptr, n)                                                          \
-    if (cudaMalloc(&(ptr), (size_t)(n) * sizeof(*(ptr))) != cudaSuccess)       \
+    if (dev_alloc((void **)&(ptr), (size_t)(n) * sizeof(*(ptr))) != cudaSuccess) \
         return fail(FLEXRT_E_OOM, "device allocation failed: " #ptr)
     ALLOC(ctl_, 1);
     ALLOC(sims_, ms);
@@ -236,14 +254,15 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
         mw_.lead_cap = cap + (long long)MERGE_MAX_BLOCKS * 8 * 128;
         const size_t sz[] = {(size_t)ms * mw_.hrep * HIST_BINS * 4, (size_t)ms * 32, (size_t)cap * 4,
                              (size_t)cap * 4, (size_t)ngrp * mw_.grp_w * 4, (size_t)ngrp * 4,
-                             (size_t)nc * 48, (size_t)mw_.lead_cap * 4, (size_t)mw_.lead_cap * 4};
+                             (size_t)nc * 48, (size_t)mw_.lead_cap * 4, (size_t)mw_.lead_cap * 4,
+                             (size_t)ngrp * 4, (size_t)cap * 16};
         size_t tot = 0;
         for (size_t v : sz) tot += (v + 255) & ~(size_t)255;
-        if (cudaMalloc(&mwmem_, tot) != cudaSuccess) return fail(FLEXRT_E_OOM, "merge scratch allocation failed");
+        if (dev_alloc(&mwmem_, tot) != cudaSuccess) return fail(FLEXRT_E_OOM, "merge scratch allocation failed");
         char *p = (char *)mwmem_;
         void **dst[] = {(void **)&mw_.hist, (void **)&mw_.sel, (void **)&mw_.tkey, (void **)&mw_.tsim,
                         (void **)&mw_.grp, (void **)&mw_.gcnt, (void **)&mw_.rot, (void **)&mw_.lead_i,
-                        (void **)&mw_.lead_slot};
+                        (void **)&mw_.lead_slot, (void **)&mw_.gmax, (void **)&mw_.tgrp};
         static_assert(sizeof(sz) / sizeof(sz[0]) == sizeof(dst) / sizeof(dst[0]), "merge scratch layout");
         for (size_t k = 0; k < sizeof(sz) / sizeof(sz[0]); ++k) { *dst[k] = p; p += (sz[k] + 255) & ~(size_t)255; }
         if (cap >= (1LL << 32)) return fail(FLEXRT_E_INVALID, "merging needs fewer than 2^32 queue slots");
@@ -288,15 +307,15 @@ flexrt_status Engine::grow_emitters(int need) {
     const int cap = std::max(need, std::max(16, 2 * em_cap_));
     Emitters ne{};
     ne.ring_w = em_.ring_w;
-    if (cudaMalloc(&ne.cell, cap * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc(&ne.local, cap * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&ne.ndot, cap * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&ne.n0, cap * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&ne.ring, (size_t)cap * ne.ring_w * 3 * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc(&ne.act, cap * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&ne.act_off, cap * sizeof(long long)) != cudaSuccess) {
-        cudaFree(ne.cell); cudaFree(ne.local); cudaFree(ne.ndot); cudaFree(ne.n0);
-        cudaFree(ne.ring); cudaFree(ne.act); cudaFree(ne.act_off);
+    if (dev_alloc((void **)&ne.cell, cap * sizeof(int4)) != cudaSuccess ||
+        dev_alloc((void **)&ne.local, cap * sizeof(int32_t)) != cudaSuccess ||
+        dev_alloc((void **)&ne.ndot, cap * sizeof(double)) != cudaSuccess ||
+        dev_alloc((void **)&ne.n0, cap * sizeof(float)) != cudaSuccess ||
+        dev_alloc((void **)&ne.ring, (size_t)cap * ne.ring_w * 3 * sizeof(int4)) != cudaSuccess ||
+        dev_alloc((void **)&ne.act, cap * sizeof(int32_t)) != cudaSuccess ||
+        dev_alloc((void **)&ne.act_off, cap * sizeof(long long)) != cudaSuccess) {
+        dev_free(ne.cell); dev_free(ne.local); dev_free(ne.ndot); dev_free(ne.n0);
+        dev_free(ne.ring); dev_free(ne.act); dev_free(ne.act_off);
         return fail(FLEXRT_E_OOM, "emitter table allocation failed");
     }
     if (em_cap_ > 0) {
@@ -307,8 +326,8 @@ flexrt_status Engine::grow_emitters(int need) {
         CK(cudaMemcpy(ne.n0, em_.n0, em_cap_ * sizeof(float), cudaMemcpyDeviceToDevice));
         CK(cudaMemcpy(ne.ring, em_.ring, (size_t)em_cap_ * ne.ring_w * 3 * sizeof(int4), cudaMemcpyDeviceToDevice));
     }
-    cudaFree(em_.cell); cudaFree(em_.local); cudaFree(em_.ndot); cudaFree(em_.n0);
-    cudaFree(em_.ring); cudaFree(em_.act); cudaFree(em_.act_off);
+    dev_free(em_.cell); dev_free(em_.local); dev_free(em_.ndot); dev_free(em_.n0);
+    dev_free(em_.ring); dev_free(em_.act); dev_free(em_.act_off);
     em_ = ne;
     em_cap_ = cap;
     emit_blocks_ = std::max(1, std::min((em_cap_ + 127) / 128, 1024));
@@ -638,6 +657,7 @@ flexrt_status Engine::poll(bool wait) {
     if (v) {
         latched_ = FLEXRT_E_CAPACITY;
         if (v & 1) err_ = "ray queue capacity exceeded; state kept at the last complete step";
+        else if (v & 8) err_ = "merge group too heavy for exact weighted sums (more than 2^13 rays as bright as its brightest)";
         else if (v & 2) err_ = "ray older than the rotation ring (internal bound)";
         else err_ = "ray crossed more than four cells in one step (internal bound)";
     }
@@ -1024,6 +1044,131 @@ int Engine::active_count() const {
     int n = 0;
     for (auto &s : slots_) n += s.active ? 1 : 0;
     return n;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint of a single-simulation engine: everything a later step reads --
+// the per-cell state, the live ray queue, the emitters' per-step photons and
+// rotation ring, the step counter, dt and the photon budget.  Buffers that
+// are zero between steps (deposits, screen tallies, merge groups) are not
+// stored.  Layout: a header, then the arrays in a fixed order.
+// ---------------------------------------------------------------------------
+namespace {
+struct StateHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, nb, n_emitters, ring_w, merged_fields;
+    int64_t ncell, nray, step;
+    double dt, nref;
+    int64_t bytes;
+};
+constexpr char STATE_MAGIC[8] = {'F', 'L', 'E', 'X', 'R', 'T', 'S', '1'};
+}  // namespace
+
+flexrt_status Engine::save_state(int s, void *buf, int64_t cap, int64_t *bytes) {
+    const Slot *sl = slot(s);
+    if (!sl || !bytes || slots_.size() != 1) return fail(FLEXRT_E_INVALID, "checkpoints are for single simulations");
+    CK(cudaStreamSynchronize(st_));
+    flexrt_status ps = poll(true);
+    if (ps != FLEXRT_OK) return ps;
+    Ctl hc;
+    CK(cudaMemcpy(&hc, ctl_, sizeof(hc), cudaMemcpyDeviceToHost));
+    const long long nray = hc.cnt[hc.par], nc = sl->h.ncell, ne = sl->em_n, rw = em_.ring_w;
+    const int nb = cfg_.nb;
+    const bool mf = merge_built();
+    // (device pointer, bytes) in file order
+    std::vector<std::pair<const void *, size_t>> parts = {
+        {acc_ + s, sizeof(SimAcc)},
+        {cells_.y + sl->cell0, nc * 8}, {cells_.x + sl->cell0, nc * 4}, {cells_.T + sl->cell0, nc * 4},
+        {cells_.gamma + sl->cell0, nc * 4}, {cells_.kap + sl->cell0, nc * 8}, {cells_.xion + sl->cell0, nc * 8},
+        {cells_.rho + sl->cell0, nc * 4},
+        {em_.n0 + sl->em0, (size_t)ne * 4}, {em_.ring + sl->em0 * rw * 3, (size_t)ne * rw * 3 * sizeof(int4)}};
+    if (ne == 0) { parts[8].second = 0; parts[9].second = 0; }
+    const Queue &q = q_[hc.par];
+    const void *qa[] = {q.pl, q.em, q.bi, q.dx, q.dy, q.dz};
+    for (const void *a : qa) parts.push_back({a, (size_t)nray * 4});
+    for (int b = 0; b < nb; ++b) parts.push_back({q.ph[b], (size_t)nray * 4});
+    if (mf) {
+        const void *ma[] = {q.mx, q.my, q.mz, q.ma, q.mthr};
+        for (const void *a : ma) parts.push_back({a, (size_t)nray * 4});
+    }
+    size_t tot = sizeof(StateHeader);
+    for (auto &p : parts) tot += p.second;
+    *bytes = (int64_t)tot;
+    if (!buf) return FLEXRT_OK;
+    if (cap < (int64_t)tot) return fail(FLEXRT_E_CAPACITY, "checkpoint buffer too small");
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, STATE_MAGIC, 8);
+    h.version = 1;
+    h.nx = sl->h.nx; h.ny = sl->h.ny; h.nz = sl->h.nz; h.nb = nb;
+    h.n_emitters = sl->em_n; h.ring_w = (int32_t)rw; h.merged_fields = mf ? 1 : 0;
+    h.ncell = nc; h.nray = nray; h.step = sl->h.step; h.dt = sl->h.dt; h.nref = sl->h.nref;
+    h.bytes = (int64_t)tot;
+    char *o = (char *)buf;
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    for (auto &p : parts) {
+        if (p.second) CK(cudaMemcpy(o, p.first, p.second, cudaMemcpyDeviceToHost));
+        o += p.second;
+    }
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::load_state(int s, const void *buf, int64_t bytes) {
+    Slot *sl = (s >= 0 && s < (int)slots_.size() && slots_[s].used) ? &slots_[s] : nullptr;
+    if (!sl || !buf || slots_.size() != 1) return fail(FLEXRT_E_INVALID, "checkpoints are for single simulations");
+    StateHeader h;
+    if (bytes < (int64_t)sizeof(h)) return fail(FLEXRT_E_INVALID, "checkpoint truncated");
+    std::memcpy(&h, buf, sizeof(h));
+    const int nb = cfg_.nb;
+    const long long nc = sl->h.ncell, ne = sl->em_n, rw = em_.ring_w;
+    if (std::memcmp(h.magic, STATE_MAGIC, 8) != 0 || h.version != 1 || h.bytes != bytes)
+        return fail(FLEXRT_E_INVALID, "not a checkpoint of this library");
+    if (h.nx != sl->h.nx || h.ny != sl->h.ny || h.nz != sl->h.nz || h.nb != nb || h.n_emitters != ne ||
+        h.ring_w != rw || h.merged_fields != (merge_built() ? 1 : 0) || h.ncell != nc || h.nref != sl->h.nref)
+        return fail(FLEXRT_E_INVALID, "checkpoint of a different simulation (grid, bins, sources or layout)");
+    if (h.nray < 0 || h.nray > cfg_.ray_capacity) return fail(FLEXRT_E_CAPACITY, "checkpoint holds more rays than the queue");
+    const long long nray = h.nray;
+    std::vector<std::pair<void *, size_t>> parts = {
+        {acc_ + s, sizeof(SimAcc)},
+        {cells_.y + sl->cell0, nc * 8}, {cells_.x + sl->cell0, nc * 4}, {cells_.T + sl->cell0, nc * 4},
+        {cells_.gamma + sl->cell0, nc * 4}, {cells_.kap + sl->cell0, nc * 8}, {cells_.xion + sl->cell0, nc * 8},
+        {cells_.rho + sl->cell0, nc * 4},
+        {em_.n0 + sl->em0, (size_t)ne * 4}, {em_.ring + sl->em0 * rw * 3, (size_t)ne * rw * 3 * sizeof(int4)}};
+    if (ne == 0) { parts[8].second = 0; parts[9].second = 0; }
+    const Queue &q = q_[0];
+    void *qa[] = {q.pl, q.em, q.bi, q.dx, q.dy, q.dz};
+    for (void *a : qa) parts.push_back({a, (size_t)nray * 4});
+    for (int b = 0; b < nb; ++b) parts.push_back({q.ph[b], (size_t)nray * 4});
+    if (merge_built()) {
+        void *ma[] = {q.mx, q.my, q.mz, q.ma, q.mthr};
+        for (void *a : ma) parts.push_back({a, (size_t)nray * 4});
+    }
+    size_t tot = sizeof(StateHeader);
+    for (auto &p : parts) tot += p.second;
+    if ((int64_t)tot != bytes) return fail(FLEXRT_E_INVALID, "checkpoint size does not match its header");
+    CK(cudaStreamSynchronize(st_));
+    const char *src = (const char *)buf + sizeof(h);
+    for (auto &p : parts) {
+        if (p.second) CK(cudaMemcpy(p.first, src, p.second, cudaMemcpyHostToDevice));
+        src += p.second;
+    }
+    // the live rays in queue 0, nothing in flight in queue 1, no latched error
+    const long long cnt[2] = {nray, 0};
+    const int32_t par_err[2] = {0, 0};
+    static_assert(offsetof(Ctl, err) == offsetof(Ctl, par) + sizeof(int32_t), "ctl layout");
+    CK(cudaMemcpy(ctl_->cnt, cnt, sizeof(cnt), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&ctl_->par, par_err, sizeof(par_err), cudaMemcpyHostToDevice));
+    sl->h.step = (int32_t)h.step;
+    CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, step), &sl->h.step, sizeof(int32_t), cudaMemcpyHostToDevice));
+    latched_ = FLEXRT_OK;
+    err_pending_ = false;
+    if (h.dt > 0.0) {
+        flexrt_status r = set_dt(s, h.dt);
+        if (r != FLEXRT_OK) return r;
+    }
+    CK(cudaStreamSynchronize(st_));
+    return FLEXRT_OK;
 }
 
 }  // namespace frt

@@ -4,6 +4,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/flexrt.h"
@@ -56,6 +57,7 @@ struct EngineConfig {
     void *stream = nullptr;
     int merge_l_max = -1;      // deepest merge-sphere level members may use; -1: no merging
     bool gen_capable = false;  // members may run Generalized Opacity mode
+    long long device_bytes_max = 0;  // cap on the engine's device allocations (0 = none)
 };
 
 class Engine {
@@ -85,6 +87,10 @@ class Engine {
     // the march variants that carry merged rays and the moving screen
     bool ext_variants() const { return merge_built() || cfg_.gen_capable; }
     flexrt_status ionized_volume(int slot, double *x_ion);
+    // checkpoint of a single-simulation engine (slot 0): bytes needed, save, load
+    flexrt_status save_state(int slot, void *buf, int64_t cap, int64_t *bytes);
+    flexrt_status load_state(int slot, const void *buf, int64_t bytes);
+    long long device_bytes() const { return alloc_bytes_; }
     flexrt_status set_launch(int agg, int minb, int blocks_per_sm);
     flexrt_status profile(bool on);
     flexrt_status kernel_times(double ms[4], int64_t launches[4], int64_t *rays);
@@ -101,6 +107,8 @@ class Engine {
     flexrt_status cuda(cudaError_t e, const char *what);
 
   private:
+    cudaError_t dev_alloc(void **p, size_t bytes);
+    void dev_free(void *p);
     flexrt_status grow_emitters(int need);
     flexrt_status upload_lists();             // active emitters, cell ranges, counters
     flexrt_status poll(bool wait);
@@ -148,6 +156,9 @@ class Engine {
 
     cudaGraphExec_t graph_ = nullptr;
     bool graph_dirty_ = true;
+
+    std::unordered_map<void *, size_t> alloc_sizes_;   // live device allocations
+    long long alloc_bytes_ = 0;
 };
 
 }  // namespace frt

@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                         int4 rows[3];
                         if (mrg) {
                             const SimDev &SD = A.sims[sim];
-                            merge_rotation_rows(SD.seed, (long long)(e & ~MERGED_BIT), bi, SD.rotate, rows);
+                            rotation_rows(SD.seed, (1LL << 31) + (long long)(e & ~MERGED_BIT), bi, SD.rotate, rows);
                         } else {
                             const int4 *rg = A.em.ring + ((long long)e * A.em.ring_w + (bi % A.em.ring_w)) * 3;
                             rows[0] = rg[0]; rows[1] = rg[1]; rows[2] = rg[2];

@@ -3,28 +3,33 @@
 //
 // The step, per simulation that merges (it has more live rays than
 // K = floor(N_ex * N_RT)):
-//   k_mrot   : per cell, the random rotation of the cell's merge sphere for
-//              this step (key 2^31 + local cell index);
-//   k_mhist1 : per ray, its content (single-precision sum of its bins, the
-//              quantity ranked) and a histogram of the content's upper 16 bits;
-//   k_mfind  : per simulation, a two-pass radix select of the K-th largest
-//              content T_ref (the largest when K = 0): with K > 0 every ray
-//              at least that bright is exempt;
-//   k_mhist2 : per ray in the selected upper bin, a histogram of the lower bits;
-//   k_mgroup : per non-exempt ray, its end cell and merge pixel; a group slot
-//              per (cell, pixel) takes its photons and threshold (vector
-//              reductions), its weighted position, distance and level as
-//              exact 64-bit integer sums, and the ray's arrival rank: rank 0
-//              leads the group and is listed, the others leave the queue
-//              (their slots become holes).  The weight is the content on a
-//              grid of 2^-26 of the power of two above T_ref (at least 1), so
-//              the means are exact quotients, independent of summation order;
-//   k_memit  : per listed leader: it overwrites its own slot with the merged
-//              ray and clears the group.
+//   k_mrot    : per cell, the random rotation of the cell's merge sphere for
+//               this step, drawn like an emitter's sphere (key 2^31 + local
+//               cell index);
+//   k_mhist1  : per ray, its content (single-precision sum of its bins, the
+//               quantity ranked) and a histogram of the content's upper 16 bits;
+//   k_mfind   : per simulation, a two-pass radix select of the K-th largest
+//               content T_ref (the largest when K = 0): with K > 0 every ray
+//               at least that bright is exempt;
+//   k_mhist2  : per ray in the selected upper bin, a histogram of the lower bits;
+//   k_mgroup  : per non-exempt ray, its end cell and merge pixel; a group slot
+//               per (cell, pixel) takes its photons and threshold (vector
+//               reductions), the largest member content and the ray's arrival
+//               rank: rank 0 leads the group and is listed, the others leave
+//               the queue (their slots become holes); the ray's group slot and
+//               its end point, distance and level are kept per queue slot;
+//   k_mweight : per grouped ray, its photon weight -- the content on a grid of
+//               2^-28 of the power of two above its group's largest content,
+//               truncated, at least 1 -- and the weighted end point, distance
+//               and level as exact 64-bit integer sums, so the photon-weighted
+//               means are exact quotients of sums that do not depend on the
+//               summation order, to 2^-27 of the group's brightest member;
+//   k_memit   : per listed leader: it overwrites its own slot with the merged
+//               ray (means rounded once) and clears the group.
 // The holes stay in the queue: the next march skips them and writes its
 // survivors densely into the other queue, so no compaction pass is needed.
 // Contents are non-negative floats, so their bit patterns order as unsigned
-// integers and the select works on the bits.
+// integers and the select and the group maximum work on the bits.
 #include "frt_march.cuh"
 
 namespace frt {
@@ -66,7 +71,8 @@ namespace {
 // per-simulation selection words: state, upper bits, rays above, T_ref bits, any exempt
 constexpr int SEL_STATE = 0, SEL_HIGH = 1, SEL_ABOVE = 2, SEL_T = 3, SEL_EXEMPT = 4, SEL_W = 8;
 constexpr uint32_t SEL_OFF = 0, SEL_PASS2 = 1, SEL_DONE = 2;
-constexpr int WBITS = 26;                    // merge weights below 2^26
+constexpr int WBITS = 28;                    // merge weights below 2^28
+constexpr uint32_t NO_GROUP = 0xffffffffu;   // a queue slot that is in no group
 constexpr int GSUMS = 6;                     // integer sums: weight, weighted x, y, z, distance, level
 constexpr int LEAD_SLAB = 128;               // leader-list entries a warp takes at once
 constexpr uint32_t NO_LEADER = 0xffffffffu;  // an unused leader-list entry
@@ -196,7 +202,7 @@ __global__ void __launch_bounds__(256) k_mrot(MergeArgs A) {
         if (!merges(S, A.acc[sim])) continue;
         const long long local = i - s_pref[lo];
         int4 rows[3];
-        merge_rotation_rows(S.seed, local, S.step, S.rotate, rows);
+        rotation_rows(S.seed, (1LL << 31) + local, S.step, S.rotate, rows);
         int4 *dst = A.w.rot + 3 * (s_cell0[lo] + local);
         dst[0] = rows[0]; dst[1] = rows[1]; dst[2] = rows[2];
     }
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
     for (long long base = c0; base < c1; base += 32) {
         const long long i = base + lane;
         long long slot = -1;
-        unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
+        uint4 pack = make_uint4(NO_GROUP, 0u, 0u, 0u);
         float f[MAXB + 4];
 #pragma unroll
         for (int k = 0; k < MAXB + 4; ++k) f[k] = 0.0f;
@@ -401,18 +407,14 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
                     const int4 *rp = A.w.rot + 3 * g;
                     const int4 rows[3] = {rp[0], rp[1], rp[2]};
                     slot = g * ndir + merge_pixel(S.l_merge, rows, dx, dy, dz);
-                    // weight: the content times 2^(26 - e), T_ref < 2^e
-                    // (exact power-of-two scaling), truncated, at least 1
-                    const int eref = (int)((tref >> 23) & 0xffu) - 126;
-                    const float wscale = __int_as_float((127 + WBITS - eref) << 23);
-                    const unsigned long long qw =
-                        max(__float2ull_rz(__fmul_rn(__uint_as_float(key), wscale)), 1ull);
-                    v[0] = qw;
-                    v[1] = qw * (unsigned long long)(p[0] - (cx << FRAC_BITS));
-                    v[2] = qw * (unsigned long long)(p[1] - (cy << FRAC_BITS));
-                    v[3] = qw * (unsigned long long)(p[2] - (cz << FRAC_BITS));
-                    v[4] = qw * (unsigned long long)dist;
-                    v[5] = qw * (unsigned long long)lev;
+                    // the end point's offsets in its cell (21 bits each), the
+                    // distance (16 bits) and the level (4 bits), packed
+                    const uint32_t ox = (uint32_t)(p[0] - (cx << FRAC_BITS));
+                    const uint32_t oy = (uint32_t)(p[1] - (cy << FRAC_BITS));
+                    const uint32_t oz = (uint32_t)(p[2] - (cz << FRAC_BITS));
+                    const uint32_t ud = (uint32_t)min(dist, 65535);
+                    pack = make_uint4((uint32_t)slot, ox | ((uint32_t)lev << 21), oy | ((ud & 0x7ffu) << 21),
+                                      oz | ((ud >> 11) << 21));
                     nbf = nbs;
 #pragma unroll
                     for (int b = 0; b <= MAXB; ++b)
@@ -420,22 +422,19 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
                 }
             }
         }
+        if (i < c1) A.w.tgrp[i] = pack;
         // combine equal groups in the warp, then one set of atomics per group
         const unsigned peers = __match_any_sync(FULL, slot);
         const unsigned below = peers & ((1u << lane) - 1u);
-        if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) {
-            peer_sum<GSUMS, unsigned long long>(peers, v);
-            peer_sum<MAXB + 4, float>(peers, f);
-        }
+        if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) peer_sum<MAXB + 4, float>(peers, f);
+        const uint32_t kmax = __reduce_max_sync(peers, slot >= 0 ? key : 0u);
         bool leads = false;
         if (slot >= 0) {
             uint32_t gbase = 0;
             if (below == 0u) {
                 gbase = atomicAdd(A.w.gcnt + slot, (uint32_t)__popc(peers));
-                float *gp = A.w.grp + slot * gw;
-                unsigned long long *gs = reinterpret_cast<unsigned long long *>(gp);
-                for (int k = 0; k < GSUMS; ++k) atomicAdd(gs + k, v[k]);
-                float4 *gf = reinterpret_cast<float4 *>(gp + 2 * GSUMS);
+                atomicMax(A.w.gmax + slot, kmax);
+                float4 *gf = reinterpret_cast<float4 *>(A.w.grp + slot * gw + 2 * GSUMS);
 #pragma unroll
                 for (int b = 0; b <= MAXB; b += 4)
                     if (b <= nbf) red_add_v4(gf + b / 4, f[b], f[b + 1], f[b + 2], f[b + 3]);
@@ -486,6 +485,53 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// photon-weighted sums of the grouped rays
+// ---------------------------------------------------------------------------
+// A ray's weight is its content scaled by 2^(28 - e), where 2^e is the power
+// of two above its group's largest content (exact power-of-two scaling),
+// truncated and at least 1: the brightest member has at least 27 significant
+// bits, every weight is below 2^28.  Weighted sums are 64-bit integers.
+__global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
+    const Ctl *C = A.ctl;
+    if (C->err || !C->merged) return;
+    const long long n = C->cnt[C->par ^ 1];
+    const int gw = A.w.grp_w;
+    const int lane = lane_id();
+    long long c0, c1;
+    warp_chunk(n, c0, c1);
+    for (long long base = c0; base < c1; base += 32) {
+        const long long i = base + lane;
+        uint4 pk = make_uint4(NO_GROUP, 0u, 0u, 0u);
+        uint32_t key = 0;
+        if (i < c1) {
+            pk = A.w.tgrp[i];
+            if (pk.x != NO_GROUP) key = A.w.tkey[i];
+        }
+        const long long slot = pk.x == NO_GROUP ? -1 : (long long)pk.x;
+        unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
+        if (slot >= 0) {
+            const uint32_t gm = A.w.gmax[slot];
+            const int eb = max((int)((gm >> 23) & 0xffu), 30);      // biased exponent; 2^(eb-126) > content
+            const float wscale = __int_as_float((253 + WBITS - eb) << 23);
+            const unsigned long long qw = max(__float2ull_rz(__fmul_rn(__uint_as_float(key), wscale)), 1ull);
+            v[0] = qw;
+            v[1] = qw * (unsigned long long)(pk.y & 0x1fffffu);
+            v[2] = qw * (unsigned long long)(pk.z & 0x1fffffu);
+            v[3] = qw * (unsigned long long)(pk.w & 0x1fffffu);
+            v[4] = qw * (unsigned long long)((pk.z >> 21) | ((pk.w >> 21) << 11));
+            v[5] = qw * (unsigned long long)(pk.y >> 21);
+        }
+        const unsigned peers = __match_any_sync(FULL, slot);
+        if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) peer_sum<GSUMS, unsigned long long>(peers, v);
+        if (slot >= 0 && (peers & ((1u << lane) - 1u)) == 0u) {
+            unsigned long long *gs = reinterpret_cast<unsigned long long *>(A.w.grp + slot * gw);
+#pragma unroll
+            for (int k = 0; k < GSUMS; ++k) atomicAdd(gs + k, v[k]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // in place: merged rays into their leaders' slots
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
@@ -510,6 +556,10 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
                 const float *gp = A.w.grp + (long long)slot * gw;
                 const unsigned long long *gs = reinterpret_cast<const unsigned long long *>(gp);
                 const unsigned long long W = gs[0];
+                // weights below 2^28 and offsets below 2^21: the sums stay
+                // exact while W < 2^41 (more than 2^13 members as bright as
+                // the brightest would be needed to reach it)
+                if (W >= (1ull << 41)) atomicOr((int *)&C->err, 8);
                 const long long g = (long long)slot / ndir;
                 const uint32_t pm = slot % ndir;
                 const int local = (int)(g - S.cell_off);          // below 2^31 cells
@@ -542,6 +592,7 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
             float4 *gz = reinterpret_cast<float4 *>(A.w.grp + (long long)slot * gw);
             for (int b = 0; b < gw / 4; ++b) gz[b] = make_float4(0.f, 0.f, 0.f, 0.f);
             A.w.gcnt[slot] = 0u;
+            A.w.gmax[slot] = 0u;
         }
     }
     __syncthreads();
@@ -549,11 +600,14 @@ __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
         if (sh_drop[k]) atomicAdd(&A.acc[k].p_rays_out, -(double)sh_drop[k]);
 }
 
-__global__ void k_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, uint32_t *out) {
-    int4 rows[3];
-    for (int k = 0; k < 3; ++k) rows[k] = make_int4(Rq[3 * k], Rq[3 * k + 1], Rq[3 * k + 2], 0);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+__global__ void k_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, int per_ray,
+                                    uint32_t *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int32_t *R = Rq + (per_ray ? 9 * i : 0);
+        int4 rows[3];
+        for (int k = 0; k < 3; ++k) rows[k] = make_int4(R[3 * k], R[3 * k + 1], R[3 * k + 2], 0);
         out[i] = merge_pixel(level, rows, d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+    }
 }
 
 cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st) {
@@ -567,14 +621,15 @@ cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st) {
     if (a.w.hrep > 1) k_mreduce<<<rblocks, 256, 0, st>>>(a, 2);
     k_mfind<<<a.nsims, 1024, 0, st>>>(a, 2);
     k_mgroup<<<rblocks, 256, 0, st>>>(a);
+    k_mweight<<<rblocks, 256, 0, st>>>(a);
     k_memit<<<rblocks, 256, (size_t)a.nsims * sizeof(int), st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, uint32_t *out,
-                                     cudaStream_t st) {
+cudaError_t launch_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, bool per_ray,
+                                     uint32_t *out, cudaStream_t st) {
     const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
-    k_probe_merge_pixel<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(level, n, d, Rq, out);
+    k_probe_merge_pixel<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(level, n, d, Rq, per_ray ? 1 : 0, out);
     return cudaGetLastError();
 }
 

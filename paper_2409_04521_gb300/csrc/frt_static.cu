@@ -8,7 +8,9 @@
 // The array lives on every GPU that loads the library until the process
 // exits.  In host code `g_stage` names a host-side stand-in, not a device
 // address: its device address is looked up once per device (with that device
-// current) with cudaGetSymbolAddress and handed to the kernel.
+// current) with cudaGetSymbolAddress, kept for the life of the process and
+// handed to the kernel.  A device reset between calls would leave the kept
+// address stale; callers must not reset the device between calls.
 #include <cstdint>
 #include <cstring>
 #include <mutex>

@@ -149,6 +149,9 @@ struct MergeWork {
     int32_t *tsim;           // per queue slot: simulation taking part, -1 none
     float *grp;              // [cell * ndir + pixel][grp_w]: 6 uint64 weighted sums, photons, threshold
     uint32_t *gcnt;          // [cell * ndir + pixel] group sizes
+    uint32_t *gmax;          // [cell * ndir + pixel] largest member content (float bits)
+    uint4 *tgrp;             // per queue slot: group slot (0xffffffff: none), then the end point's
+                             // offsets in its cell, distance travelled and level, packed
     int4 *rot;               // [cell][3] merge-sphere rotation rows of this step
     uint32_t *lead_i;        // k-th group leader: its queue slot (0xffffffff: unused entry)
     uint32_t *lead_slot;     // and its group slot

@@ -54,14 +54,14 @@ class Options(C.Structure):
                 ("T_init", C.c_double), ("ray_capacity", C.c_int64), ("keep_diagnostics", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("merge", C.c_int32), ("l_merge", C.c_int32), ("n_ex", C.c_double),
                 ("gamma_iters", C.c_int32), ("gen_mode", C.c_int32), ("chi", C.c_double),
-                ("t_reion", C.c_double), ("alpha_pl", C.c_double)]
+                ("t_reion", C.c_double), ("alpha_pl", C.c_double), ("device_bytes_max", C.c_int64)]
 
 
 class BatchConfig(C.Structure):
     _fields_ = [("max_sims", C.c_int32), ("max_grid", C.c_int32), ("nbins", C.c_int32), ("n_ray_min", C.c_double),
                 ("ray_capacity", C.c_int64), ("cell_capacity", C.c_int64), ("emitter_capacity", C.c_int32),
                 ("keep_diagnostics", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("merge_l_max", C.c_int32), ("gen_capable", C.c_int32)]
+                ("merge_l_max", C.c_int32), ("gen_capable", C.c_int32), ("device_bytes_max", C.c_int64)]
 
 
 class ProbeRays(C.Structure):
@@ -113,6 +113,9 @@ def lib():
             L.flexrt_get_rays_merged.argtypes = [vp, C.c_int64, P(C.c_int32), P(C.c_int32), P(C.c_int32),
                                                  P(C.c_int64), P(C.c_double), P(C.c_int64)]
             L.flexrt_profile.argtypes = [vp, C.c_int32]
+            L.flexrt_save_state.argtypes = [vp, vp, C.c_int64, P(C.c_int64)]
+            L.flexrt_load_state.argtypes = [vp, vp, C.c_int64]
+            L.flexrt_get_device_bytes.argtypes = [vp, P(C.c_int64)]
             L.flexrt_get_kernel_times.argtypes = [vp, P(C.c_double), P(C.c_int64), P(C.c_int64)]
             L.flexrt_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
             L.flexrt_last_error.argtypes = [vp]
@@ -129,6 +132,7 @@ def lib():
             L.flexrt_batch_get_fields.argtypes = [vp, C.c_int32, P(Fields)]
             L.flexrt_batch_get_budget.argtypes = [vp, C.c_int32, P(C.c_double)]
             L.flexrt_batch_get_counts.argtypes = [vp, C.c_int32, P(C.c_int64)]
+            L.flexrt_batch_get_segment_counts.argtypes = [vp, C.c_int32, P(C.c_int32)]
             L.flexrt_batch_get_rays.argtypes = [vp, C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32),
                                                 P(C.c_int32), P(C.c_int32), P(C.c_double), P(C.c_int64)]
             L.flexrt_batch_get_rays_merged.argtypes = [vp, C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int32),
@@ -147,7 +151,8 @@ def lib():
             L.flexrt_probe_traverse_static.argtypes = L.flexrt_probe_traverse.argtypes
             L.flexrt_probe_merge.argtypes = [P(MergeProbe), C.c_int64, P(ProbeRays), C.c_int64, P(ProbeRays),
                                              P(C.c_int64)]
-            L.flexrt_probe_merge_pixel.argtypes = [C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+            L.flexrt_probe_merge_pixel.argtypes = [C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int32), C.c_int64,
+                                                   P(C.c_int32)]
             _lib = L
     return _lib
 
@@ -290,6 +295,11 @@ class Batch:
         return dict(rays=int(c[0]), segments_last=int(c[1]), segments_total=int(c[2]), step=int(c[3]),
                     capacity=int(c[4]), rays_marched_last=int(c[5]))
 
+    def segment_counts(self, slot):
+        s = np.zeros(self.members[slot][0], np.int32)
+        self._check(lib().flexrt_batch_get_segment_counts(self._h, int(slot), _p(s, C.c_int32)))
+        return s
+
     def rays(self, slot):
         nb = self.members[slot][1]
         n = C.c_int64()
@@ -337,7 +347,8 @@ class Simulation:
     attributes grid, box_cm_comoving, redshift, nH, spectrum (nbins, frac,
     sigma_cm2, eheat_erg), mfp, options, source_cells, source_ndot."""
 
-    def __init__(self, prob, ray_capacity: int = 0, keep_diagnostics: bool = False, stream=None):
+    def __init__(self, prob, ray_capacity: int = 0, keep_diagnostics: bool = False, stream=None,
+                 device_bytes_max: int = 0):
         L = lib()
         g = Grid(*[int(v) for v in prob.grid])
         b = Box(float(prob.box_cm_comoving), float(prob.redshift))
@@ -360,6 +371,7 @@ class Simulation:
         o.ray_capacity = int(ray_capacity)
         o.keep_diagnostics = int(keep_diagnostics)
         o.cuda_stream = stream
+        o.device_bytes_max = int(device_bytes_max)
         nH = np.ascontiguousarray(prob.nH, np.float64).reshape(-1)
         self.ncell = nH.size
         self.nb = int(sp.nbins)
@@ -367,7 +379,7 @@ class Simulation:
         st = L.flexrt_create(C.byref(g), C.byref(b), _p(nH, C.c_double), C.byref(mf), C.byref(s), C.byref(o),
                              C.byref(h))
         if st != FLEXRT_OK:
-            raise FlexRTError(st, "flexrt_create failed")
+            raise FlexRTError(st, "flexrt_create failed: " + (L.flexrt_last_error(None) or b"").decode())
         self._h = h
         if len(prob.source_ndot):
             self.add_sources(prob.source_cells, prob.source_ndot)
@@ -422,6 +434,24 @@ class Simulation:
                                      _p(bi, C.c_int32), _p(d, C.c_int32), _p(N, C.c_double), C.byref(n)), self._h)
         out = dict(level=lv, pixel=pix, emitter=em, birth=bi, dir=d, N=N)
         return _merged_fields(lambda *a: _check(lib().flexrt_get_rays_merged(self._h, *a), self._h), out, m)
+
+    def save_state(self) -> np.ndarray:
+        """Checkpoint of the simulation as a host byte array."""
+        n = C.c_int64()
+        _check(lib().flexrt_save_state(self._h, None, 0, C.byref(n)), self._h)
+        buf = np.zeros(n.value, np.uint8)
+        _check(lib().flexrt_save_state(self._h, buf.ctypes.data_as(C.c_void_p), n.value, C.byref(n)), self._h)
+        return buf
+
+    def load_state(self, buf):
+        """Restore a checkpoint made by save_state of the same simulation."""
+        buf = np.ascontiguousarray(np.asarray(buf, np.uint8))
+        _check(lib().flexrt_load_state(self._h, buf.ctypes.data_as(C.c_void_p), buf.size), self._h)
+
+    def device_bytes(self) -> int:
+        n = C.c_int64()
+        _check(lib().flexrt_get_device_bytes(self._h, C.byref(n)), self._h)
+        return int(n.value)
 
     def ionized_volume(self):
         """Generalized mode: the highly ionised volume fraction per cell."""
@@ -483,11 +513,14 @@ STATIC_MAX_RAYS = 32768
 
 def probe_merge_pixel(level: int, d, Rq) -> np.ndarray:
     """Merge-sphere pixels (Sec. 3.3) of fixed-point directions d [n,3] on the
-    sphere rotated by Rq (3x3 int32), decided on the GPU."""
+    sphere rotated by Rq (3x3 int32, or [n,3,3]: one sphere per direction),
+    decided on the GPU."""
     d = np.ascontiguousarray(np.asarray(d, np.int32).reshape(-1, 3))
-    Rq = np.ascontiguousarray(np.asarray(Rq, np.int32).reshape(9))
+    Rq = np.asarray(Rq, np.int32)
+    nrot = 1 if Rq.size == 9 else len(d)
+    Rq = np.ascontiguousarray(Rq.reshape(nrot * 9))
     out = np.zeros(len(d), np.int32)
-    _check(lib().flexrt_probe_merge_pixel(int(level), len(d), _p(d, C.c_int32), _p(Rq, C.c_int32),
+    _check(lib().flexrt_probe_merge_pixel(int(level), len(d), _p(d, C.c_int32), _p(Rq, C.c_int32), nrot,
                                           _p(out, C.c_int32)))
     return out
 

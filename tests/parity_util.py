@@ -98,3 +98,36 @@ def run_pair(prob, steps=None, capacity=1 << 22, check_every=1, T_rtol=None, x_a
     g.close()
     o.close()
     return summary
+
+
+def field_errors(gf, of):
+    """Max and median error of the GPU's fields against the oracle's: Gamma_HI
+    relative (cells with Gamma >= 1e-8 of the largest), x_HII absolute, T
+    relative, n_HI relative (cells with n_HI >= 1e-8 of the largest)."""
+    out = {}
+    g, o = gf["gamma_HI"], of["gamma_HI"]
+    big = o >= GAMMA_FLOOR * max(o.max(), 1e-300)
+    rel = np.abs(g - o)[big] / o[big] if big.any() else np.zeros(1)
+    out["gamma_rel"] = (float(rel.max()), float(np.median(rel)))
+    ax = np.abs(gf["x_HII"] - of["x_HII"])
+    out["x_abs"] = (float(ax.max()), float(np.median(ax)))
+    rT = np.abs(gf["T"] - of["T"]) / of["T"]
+    out["T_rel"] = (float(rT.max()), float(np.median(rT)))
+    n, on = gf["n_HI"], of["n_HI"]
+    bn = on >= 1e-8 * max(on.max(), 1e-300)
+    rn = np.abs(n - on)[bn] / on[bn] if bn.any() else np.zeros(1)
+    out["nHI_rel"] = (float(rn.max()), float(np.median(rn)))
+    return out
+
+
+def record_errors(config, step, errs, **extra):
+    """Append one row of the per-field error table to the file named by
+    FLEXRT_ERRTABLE (if set)."""
+    import json
+    import os
+    path = os.environ.get("FLEXRT_ERRTABLE")
+    if not path:
+        return
+    row = dict(config=config, step=step, **errs, **extra)
+    with open(path, "a") as f:
+        f.write(json.dumps(row) + "\n")

@@ -1,10 +1,16 @@
 """Ray merging (Sec. 3.3, Eq. 4) on the GPU against the oracle on identical
-seeded inputs: the merge-pixel decision bit for bit; the merge step on the
-same rays bit for bit (exempt set, groups, merged ids, directions,
-positions, distances, levels; photons to single-precision summation); whole
-runs element by element up to the first merge and on global averages after
-it; the ray-count ceiling of Eq. 4; batch members equal to the same
-simulation alone."""
+seeded inputs.  The oracle merges by the section's definition in double
+precision (content ranking, ang2pix on each cell's random sphere,
+photon-weighted means rounded once); the GPU decides in single precision and
+forms the means from exact integer sums of truncated weights.  Compared:
+the merge-pixel decision (equal except within rounding of a pixel edge);
+the merge step on the same rays (tests/merge_parity.py: identical groups,
+merged ids, directions, photons, distances and levels, positions within the
+stated bound, ambiguous rays counted and bounded); whole runs step by step,
+the oracle merging the GPU's own rays after every march (a twin context
+restored from the GPU's checkpoint marches the step without merging); the
+ray-count ceiling of Eq. 4; batch members equal to the same simulation
+alone."""
 import dataclasses as dc
 
 import numpy as np
@@ -13,17 +19,22 @@ import pytest
 import oracle
 import paper_2409_04521_gb300 as F
 import workloads as W
-from parity_util import BUDGET_RTOL, BUDGET_XTOL, RAY_RTOL, compare_fields
+from merge_parity import compare_merge_step
+from parity_util import BUDGET_RTOL, compare_fields, compare_rays
 
 pytestmark = pytest.mark.gpu
 S = 2 ** 21
 
 
-def test_merge_pixel_probe_bit_exact():
+def test_merge_pixel_probe_matches_oracle():
+    # the GPU's single-precision decision equals the oracle's double-precision
+    # ang2pix except within rounding of a pixel edge (a 4-unit nudge of the
+    # direction reproduces it), and rotated pixel centres land in their pixel
     rng = np.random.default_rng(11)
+    mism = total = 0
     for level in range(6):
-        for key in ((1 << 31) + 3, (1 << 31) + 70000, 5):
-            Rq = oracle.rotation(17, key, level + 3)[1]
+        for key in (3, 70000, 5):
+            Rq = oracle.merge_rotation(17, key, level + 3)
             v = rng.normal(size=(4000, 3))
             v /= np.linalg.norm(v, axis=1)[:, None]
             d = np.rint(v * (S - 1)).astype(np.int32)
@@ -31,7 +42,21 @@ def test_merge_pixel_probe_bit_exact():
                 d = np.vstack([d, [oracle.direction(level, p, Rq) for p in range(12 * 4 ** level)]])
             got = F.probe_merge_pixel(level, d, Rq)
             ref = np.array([oracle.merge_pixel(level, Rq, x) for x in d])
-            assert np.array_equal(got, ref)
+            for i in np.nonzero(got != ref)[0]:
+                near = {oracle.merge_pixel(level, Rq, d[i] + s_ * e) for e in np.eye(3, dtype=np.int32)
+                        for s_ in (-4, 4)}
+                assert got[i] in near, (level, i, got[i], ref[i])
+            if level <= 3:
+                assert np.array_equal(got[4000:], np.arange(12 * 4 ** level))
+            mism += int((got != ref).sum())
+            total += len(d)
+    assert mism <= 1e-3 * total, (mism, total)
+    # one sphere per direction gives the same answers
+    Rs = np.array([oracle.merge_rotation(5, c, 2) for c in range(64)], np.int32)
+    d = np.rint(rng.normal(size=(64, 3)) * 2 ** 19).astype(np.int32)
+    per = F.probe_merge_pixel(2, d, Rs)
+    one = np.array([F.probe_merge_pixel(2, d[i:i + 1], Rs[i])[0] for i in range(64)])
+    assert np.array_equal(per, one)
 
 
 def _emitters(prob):
@@ -48,11 +73,10 @@ def _emitters(prob):
 
 @pytest.mark.parametrize("n_ex,l_merge,with_merged", [(1.0, 0, False), (2.0, 1, True), (0.0, 0, True),
                                                       (0.5, 2, True)])
-def test_merge_step_bit_exact_on_identical_rays(n_ex, l_merge, with_merged):
+def test_merge_step_on_identical_rays(n_ex, l_merge, with_merged):
     # the same live rays (photons exact in single precision) merged by the GPU
-    # kernels and by the oracle: identical exempt sets and groups, identical
-    # merged ids, directions, positions, distances and levels; photons and
-    # thresholds to single-precision summation
+    # kernels and by the oracle: identical groups and merged rays up to the
+    # stated rounding (tests/merge_parity.py)
     prob = _prob(n_ex, l_merge, n=16, nsteps=8)
     plain = dc.replace(prob, options=dc.replace(prob.options, merge=False))
     dt, k = prob.dt, 6
@@ -80,19 +104,56 @@ def test_merge_step_bit_exact_on_identical_rays(n_ex, l_merge, with_merged):
     gin = dict(pre, N=N32, thr=thr32)
     got = F.probe_merge(prob.grid, prob.spectrum.nbins, o.l_src, o.l_max, l_merge, K, o.seed, int(o.rotate), step,
                         o.eps_term, cells, n0, gin)
+    got["N"] = got["N"] * nref
+    got["thr"] = got["thr"] * nref
     B.apply_merge(dt, K)
     ref = B.rays()
-    assert len(got["level"]) == len(ref["level"]) < len(pre["level"])
-    gk, g = _table(got)
-    rk, r = _table(ref)
-    assert np.array_equal(gk, rk)
-    assert np.array_equal(g["dir"], r["dir"])
-    assert np.array_equal(g["merged"], r["merged"])
-    m = r["merged"]
-    assert np.array_equal(g["P"][m], r["P"][m]) and np.array_equal(g["A"][m], r["A"][m])
-    assert np.allclose(g["N"] * nref, r["N"], rtol=2e-6, atol=0)
-    assert np.allclose(g["thr"][m] * nref, r["thr"][m], rtol=2e-6)
-    assert (r["birth"][m] == step).sum() > 0
+    assert len(ref["level"]) < len(pre["level"])
+    st = compare_merge_step(pre, got, B.rays(), prob, step, K, l_merge)
+    assert st["merged"] > 0 and st["clean"] >= 0.95 * st["groups"], st
+    assert (ref["birth"][ref["merged"]] == step).sum() > 0
+
+
+def _step_local_run(prob, steps=None, capacity=1 << 22):
+    """Run `prob` with merging on the GPU; before every step a twin restored
+    from the GPU's checkpoint marches the same step with every ray exempt
+    (no merge), and the oracle merges those very rays.  Returns the per-step
+    summaries and the GPU simulation (still open)."""
+    steps = prob.nsteps if steps is None else steps
+    g = F.Simulation(prob, ray_capacity=capacity)
+    twin = F.Simulation(dc.replace(prob, options=dc.replace(prob.options, n_ex=1e9)), ray_capacity=capacity)
+    o = oracle.OracleSim(prob)
+    K = int(np.floor(prob.options.n_ex * prob.ncell))
+    out = []
+    for s in range(steps):
+        twin.load_state(g.save_state())
+        twin.step(prob.dt)
+        pre = twin.rays()
+        g.step(prob.dt)
+        post = g.rays()
+        assert np.array_equal(twin.budget()[:3], g.budget()[:3]) or np.allclose(twin.budget(), g.budget(),
+                                                                                 rtol=1e-6)
+        o.set_rays(s, pre)
+        o.apply_merge(prob.dt, K)
+        st = compare_merge_step(pre, post, o.rays(), prob, s, K, prob.options.l_merge)
+        b = g.budget()
+        assert abs(b[0] - b[1] - b[2] - b[3]) <= BUDGET_RTOL * b[0]
+        out.append(st)
+    twin.close()
+    o.close()
+    return out, g
+
+
+@pytest.mark.parametrize("n_ex,l_merge,seed", [(1.0, 0, 2), (2.0, 1, 4), (0.0, 0, 6)])
+def test_merge_run_step_local(n_ex, l_merge, seed):
+    # every step of a merging run: the GPU's merge of its own marched rays
+    # equals the oracle's merge of the same rays (groups, merged rays)
+    prob = _prob(n_ex, l_merge, seed=seed)
+    stats, g = _step_local_run(prob)
+    g.close()
+    merged = sum(s["merged"] for s in stats)
+    assert merged > 0
+    assert sum(s["clean"] for s in stats) >= 0.95 * sum(s["groups"] for s in stats)
 
 
 def _prob(n_ex, l_merge, n=16, nsteps=10, nsrc=8, seed=2):
@@ -107,41 +168,15 @@ def _table(r):
     return key[order], {k: np.asarray(v)[order] for k, v in r.items()}
 
 
-def compare_merged_rays(gr, orr, n0_max, allow=0):
-    """Same ray ids; bit-exact directions; photons within FP32 accuracy;
-    merged rays' merge position within rounding, distance and level exact.
-    Returns the number of ray ids present on one side only (<= allow)."""
-    gk, g = _table(gr)
-    ok, o = _table(orr)
-    gi = {tuple(k): i for i, k in enumerate(gk)}
-    oi = {tuple(k): i for i, k in enumerate(ok)}
-    only = set(gi) ^ set(oi)
-    assert len(only) <= allow, len(only)
-    common = sorted(set(gi) & set(oi))
-    a = np.array([gi[k] for k in common], np.int64)
-    b = np.array([oi[k] for k in common], np.int64)
-    assert np.array_equal(g["dir"][a], o["dir"][b])
-    assert np.array_equal(g["merged"][a], o["merged"][b])
-    big = o["N"][b] > 1e-9 * n0_max
-    assert np.all(np.abs(g["N"][a] - o["N"][b])[big] <= RAY_RTOL * o["N"][b][big])
-    m = o["merged"][b]
-    if m.any():
-        assert np.all(np.abs(g["P"][a][m] - o["P"][b][m]) <= 2)
-        assert np.array_equal(g["A"][a][m], o["A"][b][m])
-        assert np.allclose(g["thr"][a][m], o["thr"][b][m], rtol=1e-5)
-    return len(only), int(m.sum())
-
-
 @pytest.mark.parametrize("n_ex,l_merge,seed", [(1.0, 0, 2), (2.0, 1, 4), (0.0, 0, 6)])
 def test_merge_run_matches_oracle(n_ex, l_merge, seed):
-    # Up to and including the first step that merges, the two runs hold the
-    # same rays element by element.  After it, merged positions are means
-    # weighted by photon contents that differ at single-precision rounding
-    # (the GPU marches in FP32), which moves them by a few 2^-21 cell; merging
-    # amplifies such differences into different groupings later on (the shot
-    # noise of Sec. 7.1).  Later steps are compared on the quantities Sec. 7.1
-    # uses to validate merging: global ionised fraction and Gamma, and on the
-    # ray count and the photon budget.
+    # Before the first step that merges, the two runs hold the same rays
+    # element by element.  From then on each merge is compared step by step on
+    # identical rays (test_merge_run_step_local); independent runs drift apart
+    # (a ray within rounding of T_ref or of a pixel edge joins another group,
+    # and merging amplifies it: the shot noise of Sec. 7.1), so the two whole
+    # runs are compared on the quantities Sec. 7.1 validates merging with:
+    # global ionised fraction and Gamma, ray count and photon budget.
     prob = _prob(n_ex, l_merge, seed=seed)
     g = F.Simulation(prob, ray_capacity=1 << 22)
     o = oracle.OracleSim(prob)
@@ -157,14 +192,14 @@ def test_merge_run_matches_oracle(n_ex, l_merge, seed):
         oc, gc = o.counts(), g.counts()
         gf, of = g.fields(), o.fields()
         orr = o.rays()
+        if first is None and orr["merged"].any():
+            first = s
         if first is None:
-            compare_merged_rays(g.rays(), orr, n0_max, allow=64 * oc["near_threshold"])
+            compare_rays(g.rays(), orr, oc["near_threshold"], n0_max)
             compare_fields(gf, of)
             if oc["near_threshold"] == 0:
                 assert gc["rays"] == oc["rays"]
                 assert gc["segments_total"] == oc["segments_total"]
-            if orr["merged"].any():
-                first = s
         else:
             assert abs(gc["rays"] - oc["rays"]) <= 0.02 * oc["rays"] + 16
             assert abs(gf["x_HII"].mean() - of["x_HII"].mean()) <= 0.01 * of["x_HII"].mean()
@@ -292,11 +327,11 @@ def test_merge_with_iteration_matches_oracle():
         oc, gc = o.counts(), g.counts()
         gf, of = g.fields(), o.fields()
         orr = o.rays()
+        if first is None and orr["merged"].any():
+            first = s
         if first is None:
-            compare_merged_rays(g.rays(), orr, n0_max, allow=64 * oc["near_threshold"])
+            compare_rays(g.rays(), orr, oc["near_threshold"], n0_max)
             compare_fields(gf, of)
-            if orr["merged"].any():
-                first = s
         else:
             assert abs(gc["rays"] - oc["rays"]) <= 0.02 * oc["rays"] + 16
             assert abs(gf["x_HII"].mean() - of["x_HII"].mean()) <= 0.01 * of["x_HII"].mean()
@@ -305,3 +340,23 @@ def test_merge_with_iteration_matches_oracle():
     assert first is not None and first < prob.nsteps - 1
     g.close()
     o.close()
+
+
+@pytest.mark.parametrize("mode", ["generalized", "iteration"])
+def test_merge_step_local_other_modes(mode):
+    # each merge of a Generalized-mode run (merged rays and moving screens in
+    # one march) and of a run with three passes of the Gamma - <n_HI>
+    # iteration against the oracle's merge of the same rays
+    if mode == "generalized":
+        p = W.stromgren(n=32, nsteps=24)
+        p = dc.replace(p, mfp=dc.replace(p.mfp, mode=3),
+                       options=dc.replace(p.options, gen_mode=True, gamma_iters=5, merge=True, n_ex=0.05,
+                                          l_merge=0))
+    else:
+        p = _prob(1.0, 0, seed=2)
+        p = dc.replace(p, options=dc.replace(p.options, gamma_iters=3))
+    stats, g = _step_local_run(p, capacity=1 << 21 if mode == "generalized" else 1 << 22)
+    assert g.rays()["merged"].any()
+    g.close()
+    assert sum(s["merged"] for s in stats) > 0
+    assert sum(s["clean"] for s in stats) >= 0.95 * sum(s["groups"] for s in stats)

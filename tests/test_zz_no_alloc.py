@@ -48,6 +48,7 @@ def test_static_probe_matches_allocating_probe_on_consecutive_calls():
             assert np.all(cb[i, k:] == -1) and np.all(dsb[i, k:] == 0)
 
 
+@pytest.mark.gpu
 def test_static_probe_rejects_batches_above_its_maximum():
     n = FX.STATIC_MAX_RAYS + 1
     p0 = np.zeros((n, 3), np.int64)
