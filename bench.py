@@ -200,9 +200,9 @@ def workload_desc(args):
     return d
 
 
-def run_oracle_sample(prob, budget_s):
+def run_oracle_sample(prob, budget_s, keep=False):
     """Oracle on the first RT steps of the workload until `budget_s` seconds
-    of CPU work; returns (segments, seconds, steps)."""
+    of CPU work; returns (segments, seconds, steps[, fields, budget])."""
     import oracle
     t0 = time.perf_counter()
     o = oracle.OracleSim(prob)
@@ -214,8 +214,37 @@ def run_oracle_sample(prob, budget_s):
             break
     dt = time.perf_counter() - t0
     seg = o.counts()["segments_total"]
+    extra = (o.fields(), o.budget()) if keep else ()
     o.close()
-    return seg, dt, steps
+    return (seg, dt, steps) + extra
+
+
+def oracle_parity(prob, steps, of, ob, capacity, variant):
+    """The GPU path over the same first RT steps as the oracle sample: max
+    and median error per field (Gamma_HI and n_HI relative on cells above
+    1e-8 of their largest value, x_HII absolute, T relative) and the budget."""
+    import paper_2409_04521_gb300 as F
+    g = F.Simulation(prob, ray_capacity=capacity)
+    if variant:
+        g.set_launch(variant["agg"], variant["minb"], variant["blocks_per_sm"])
+    for _ in range(steps):
+        g.step(prob.dt)
+    gf, gb = g.fields(), g.budget()
+    g.close()
+
+    def stats(a, b, rel, floor=1e-8):
+        if rel:
+            m = b >= floor * max(float(b.max()), 1e-300)
+            e = np.abs(a - b)[m] / b[m] if m.any() else np.zeros(1)
+        else:
+            e = np.abs(a - b)
+        return [float(e.max()), float(np.median(e))]
+    return {"rt_steps": steps, "stat": "[max, median]",
+            "gamma_HI_rel": stats(gf["gamma_HI"], of["gamma_HI"], True),
+            "x_HII_abs": stats(gf["x_HII"], of["x_HII"], False),
+            "T_rel": stats(gf["T"] / of["T"], np.ones_like(of["T"]), False),
+            "n_HI_rel": stats(gf["n_HI"], of["n_HI"], True),
+            "budget_rel_of_emitted": float(np.max(np.abs(gb - ob)) / ob[0])}
 
 
 def impl_reference(args, dist):
@@ -325,7 +354,7 @@ def impl_gpu(args, dist):
     if not args.no_e2e:
         e2e_segs, e2e_t = 0, 0.0
         h2d = d2h = 0
-        for _ in range(max(1, min(args.steps, 2))):
+        for _ in range(max(1, args.steps)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s2 = F.Simulation(prob, ray_capacity=args.capacity)
@@ -339,20 +368,33 @@ def impl_gpu(args, dist):
             e2e_segs += s2.counts()["segments_total"]
             e2e_t += t1 - t0
             s2.close()
-            h2d = ncell * 8 + len(prob.source_ndot) * (12 + 8) + 3 * nb * 8
-            d2h = ncell * (4 + 8 + 8 + 4 + 4)   # x, y and n_H (for n_HI), T, Gamma
+            # host buffers the C ABI copies: the density, the sources and the
+            # spectrum tables in; the per-cell state flexrt_get_fields reads
+            # back (x f32, neutral fraction f64 and n_H f64 for n_HI, T f32,
+            # Gamma f32)
+            h2d = (np.asarray(prob.nH, np.float64).nbytes + np.asarray(prob.source_cells, np.int32).nbytes
+                   + np.asarray(prob.source_ndot, np.float64).nbytes + 3 * nb * 8)
+            d2h = ncell * (4 + 8 + 8 + 4 + 4)
             del f
         e2e = {"value": dist.sum(e2e_segs) / dist.max(e2e_t), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "note": "create+sources+100 RT steps+fields per step, host wall clock"}
+               "note": "create+sources+100 RT steps+fields per step, host wall clock", "runs": max(1, args.steps)}
 
-    # oracle baseline on the host cores (rank 0 only, N=1 only)
-    cpu = None
+    # oracle baseline on the host cores (rank 0 only, N=1 only), and the
+    # GPU's error against it over the same RT steps
+    cpu = parity = None
     if dist.rank == 0 and dist.ws == 1 and not args.no_cpu:
-        s, t, k = run_oracle_sample(prob, args.ref_budget)
+        s, t, k, of, ob = run_oracle_sample(prob, args.ref_budget, keep=True)
         cpu = {"value": s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {k} of {prob.nsteps} RT steps of the same workload, single-thread FP64 C "
                          f"({t:.1f} s)"}
+        parity = oracle_parity(prob, k, of, ob, args.capacity, tuned["variant"] if tuned else None)
+
+    # the batched and served forms against the plain path (N=1 only)
+    batch = serve_line = None
+    if dist.rank == 0 and dist.ws == 1 and not args.no_extra:
+        batch = run_batch(args)
+        serve_line = run_serve(args)
 
     launches_per_sim = 1 + prob.nsteps * (3 + (1 if len(prob.source_ndot) else 0)
                                           + 3 * (prob.options.gamma_iters - 1))
@@ -371,7 +413,8 @@ def impl_gpu(args, dist):
                 "sims_per_hour": 3600.0 / (t_max * 1e-3 / args.steps) * dist.ws,
                 "segments_per_sim": segs_all / args.steps / dist.ws,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches_per_sim * args.steps}
+                "gpu_launches": launches_per_sim * args.steps,
+                "oracle_parity": parity, "batch": batch, "serve": serve_line}
         print(json.dumps(line), flush=True)
 
 
@@ -392,15 +435,14 @@ def _calibrate_capacity(prob):
     return peak
 
 
-def impl_batch(args, dist):
+def run_batch(args):
     """64 uneven simulations (32..96^3, 50 steps each): one batch with one
     launch per kernel per step for all members, against looping the
     single-simulation path over the same members; both from host inputs to
-    fields on the host."""
+    fields on the host.  Returns a summary dict."""
     import torch
     import paper_2409_04521_gb300 as F
     import workloads as W
-    torch.cuda.set_device(dist.local)
     probs = W.batch64(count=args.batch_count, nsteps=args.batch_steps)
     peaks = [_calibrate_capacity(p) for p in probs]
     caps = [int(1.25 * p) + 4096 for p in peaks]
@@ -459,54 +501,68 @@ def impl_batch(args, dist):
         tb.append(time.perf_counter() - t0)
     plain()
     tp = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sp = plain()
         tp.append(time.perf_counter() - t0)
     B.close()
-    t_b, t_p = min(tb), min(tp)
-    line = {"metric": "sims/hour", "value": 3600 * len(probs) / t_b, "unit": "sims/hour", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_b, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batch{len(probs)}: uneven {sorted(set(p.grid[0] for p in probs))}^3, "
-                                   f"{args.batch_steps} RT steps each, 3 bins, mfp law, z=7",
-                       "members": len(probs), "cells": ncell, "emitters": nem,
-                       "march_launch": {"agg": best[0], "minb": best[1], "blocks_per_sm": best[2]}},
-            "segments_per_s": sb / t_b,
-            "plain_loop": {"sims_per_hour": 3600 * len(probs) / t_p, "segments_per_s": sp / t_p,
-                           "seconds": t_p},
-            "speedup_vs_plain": t_p / t_b,
-            "e2e": {"value": 3600 * len(probs) / t_b, "unit": "sims/hour",
-                    "h2d_bytes_per_step": ncell * 8, "d2h_bytes_per_step": ncell * 28}}
+    t_b, t_p = statistics.median(tb), statistics.median(tp)
+    return {"workload": f"batch{len(probs)}: uneven {sorted(set(p.grid[0] for p in probs))}^3, "
+                        f"{args.batch_steps} RT steps each, 3 bins, mfp law, z=7; host inputs to host fields",
+            "members": len(probs), "cells": ncell, "emitters": nem,
+            "march_launch": {"agg": best[0], "minb": best[1], "blocks_per_sm": best[2]},
+            "batched": {"sims_per_hour": 3600 * len(probs) / t_b, "seconds": t_b, "segments_per_s": sb / t_b,
+                        "runs": len(tb)},
+            "plain_loop": {"sims_per_hour": 3600 * len(probs) / t_p, "seconds": t_p, "segments_per_s": sp / t_p,
+                           "runs": len(tp)},
+            "speedup_vs_plain": t_p / t_b}
+
+
+def impl_batch(args, dist):
+    import torch
+    torch.cuda.set_device(dist.local)
+    r = run_batch(args)
+    line = {"metric": "sims/hour", "value": r["batched"]["sims_per_hour"], "unit": "sims/hour", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["batched"]["seconds"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": r["workload"]}, "batch": r,
+            "e2e": {"value": r["batched"]["sims_per_hour"], "unit": "sims/hour",
+                    "h2d_bytes_per_step": r["cells"] * 8, "d2h_bytes_per_step": r["cells"] * 28}}
     print(json.dumps(line), flush=True)
 
 
-def impl_serve(args, dist):
+def run_serve(args):
     """Poisson request stream served by continuous batching under an HBM
-    budget, against serving the same stream one simulation at a time."""
-    import torch
+    budget, against serving the same stream one simulation at a time; then
+    the same requests offered faster than either path serves them."""
     from paper_2409_04521_gb300 import serve
     import workloads as W
-    torch.cuda.set_device(dist.local)
     reqs = W.request_stream(count=args.requests, mean_gap_s=args.mean_gap)
     res_b, st_b = serve.serve(reqs, hbm_budget_bytes=args.hbm_budget)
     res_s, st_s = serve.serve_sequential(reqs)
-    # the same requests offered faster than either path can serve them
     sat = [(t * args.saturate_gap / args.mean_gap, p) for t, p in reqs]
     _, sat_b = serve.serve(sat, hbm_budget_bytes=args.hbm_budget)
     _, sat_s = serve.serve_sequential(sat)
-    line = {"metric": "sims/hour", "value": st_b["sims_per_hour"], "unit": "sims/hour", "n_gpus": 1,
-            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * st_b["wall_s"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serve: {args.requests} Poisson requests (mean gap {args.mean_gap} s), "
-                                   "grids {32,64,96,128,160}^3, 50-200 RT steps, 3 bins, mfp law",
-                       "hbm_budget_bytes": args.hbm_budget},
-            "served": st_b, "sequential": st_s,
-            "p50_s": st_b["p50_s"], "p99_s": st_b["p99_s"],
+    return {"workload": f"serve: {args.requests} Poisson requests (mean gap {args.mean_gap} s), "
+                        "grids {32,64,96,128,160}^3, 50-200 RT steps, 3 bins, mfp law",
+            "hbm_budget_bytes": args.hbm_budget,
+            "served": st_b, "sequential": st_s, "p50_s": st_b["p50_s"], "p99_s": st_b["p99_s"],
+            "sequential_p50_s": st_s["p50_s"], "sequential_p99_s": st_s["p99_s"],
             "speedup_sims_per_hour": st_b["sims_per_hour"] / st_s["sims_per_hour"],
             "saturated": {"mean_gap_s": args.saturate_gap, "served": sat_b, "sequential": sat_s,
                           "speedup_sims_per_hour": sat_b["sims_per_hour"] / sat_s["sims_per_hour"]}}
+
+
+def impl_serve(args, dist):
+    import torch
+    torch.cuda.set_device(dist.local)
+    r = run_serve(args)
+    st_b = r["served"]
+    line = {"metric": "sims/hour", "value": st_b["sims_per_hour"], "unit": "sims/hour", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * st_b["wall_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": r["workload"], "hbm_budget_bytes": args.hbm_budget}, "serve": r}
     print(json.dumps(line), flush=True)
 
 
@@ -613,6 +669,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--workload", default="cosmo16", choices=["cosmo16", "batch64", "serve", "merge"])
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=50)

@@ -185,6 +185,14 @@ flexrt_status flexrt_add_sources(flexrt_ctx *ctx, int32_t n, const int32_t *cell
 /* Enqueue one RT step of length dt_s seconds (asynchronous). */
 flexrt_status flexrt_step(flexrt_ctx *ctx, double dt_s);
 
+/* The same step in two stages, for inspecting the rays the merge takes
+ * (diagnostics): stage 1 enqueues the emission and the marches of the step
+ * of length dt_s; stage 2 (dt_s ignored) the merge, the chemistry and the
+ * commit.  Between the two, flexrt_get_rays and flexrt_get_rays_merged
+ * return the march's output, before merging; flexrt_step, the checkpoint
+ * calls and another stage 1 return FLEXRT_E_STATE. */
+flexrt_status flexrt_step_stage(flexrt_ctx *ctx, double dt_s, int32_t stage);
+
 /* Wait for all enqueued work; returns a latched device error if any.  No
  * call of this library waits on the device with a time limit, so
  * FLEXRT_E_TIMEOUT is reserved and never returned. */
@@ -346,8 +354,9 @@ flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t n, const f
                                  int64_t cap, flexrt_probe_rays *out, int64_t *n_out);
 
 /* One-step cell traversal (Sec. 3.1) of n rays from p0 (int64[3n], 2^-21
- * cell) along d (int32[3n]) in grid g: cells int32[n*4*3], ds float[n*4]
- * (cells), nseg int32[n], escaped int32[n]. */
+ * cell, |p0| < 2^31 - 2^22) along d (int32[3n], |d| <= 2^21) in grid g:
+ * cells int32[n*4*3], ds float[n*4] (cells), nseg int32[n], escaped
+ * int32[n].  FLEXRT_E_INVALID for coordinates out of range. */
 flexrt_status flexrt_probe_traverse(int64_t n, const int64_t *p0, const int32_t *d,
                                     const flexrt_grid *g, int32_t *cells, float *ds,
                                     int32_t *nseg, int32_t *escaped);

@@ -108,6 +108,15 @@ extern "C" flexrt_status flexrt_step(flexrt_ctx *c, double dt) {
     return c->eng.step();
 }
 
+extern "C" flexrt_status flexrt_step_stage(flexrt_ctx *c, double dt, int32_t stage) {
+    if (!c) return FLEXRT_E_INVALID;
+    if (stage == 1) {
+        flexrt_status s = c->eng.set_dt(c->slot, dt);
+        if (s != FLEXRT_OK) return s;
+    }
+    return c->eng.step_stage(stage);
+}
+
 extern "C" flexrt_status flexrt_sync(flexrt_ctx *c) { return c ? c->eng.sync() : FLEXRT_E_INVALID; }
 extern "C" flexrt_status flexrt_reset(flexrt_ctx *c) { return c ? c->eng.reset_all() : FLEXRT_E_INVALID; }
 extern "C" flexrt_status flexrt_get_fields(flexrt_ctx *c, flexrt_fields *f) {
@@ -514,7 +523,9 @@ extern "C" flexrt_status flexrt_probe_traverse(int64_t n, const int64_t *p0, con
                                                int32_t *escaped) {
     if (n < 0 || !g || (n && (!p0 || !dir || !cells || !ds || !nseg || !escaped))) return FLEXRT_E_INVALID;
     for (int64_t i = 0; i < 3 * n; ++i)
-        if (dir[i] > (1 << 21) || dir[i] < -(1 << 21)) return FLEXRT_E_INVALID;
+        if (dir[i] > (1 << 21) || dir[i] < -(1 << 21) || p0[i] > (1LL << 31) - (1LL << 22) ||
+            p0[i] < -(1LL << 31) + (1LL << 22))
+            return FLEXRT_E_INVALID;
     DevBuf<long long> dp;
     DevBuf<int32_t> dd, dc, dn, de;
     DevBuf<float> dsb;

@@ -279,36 +279,41 @@ __device__ __forceinline__ uint32_t vertex_child(int lm, uint32_t pm, int l, int
 // ---------------------------------------------------------------------------
 // One-step traversal (Sec. 3.1): the segment p0 -> p0 + d through unit cells.
 // Integer state; a ray on a face belongs to the cell it moves into; tied face
-// crossings step together; crossings are compared as exact fractions.
+// crossings step together; the order of the crossings is decided by exact
+// integer comparisons.
 // ---------------------------------------------------------------------------
 // exact 32x32 -> 64-bit unsigned product (one wide multiply)
 __device__ __forceinline__ unsigned long long wmul(unsigned a, unsigned b) { return (unsigned long long)a * b; }
 
-__device__ __forceinline__ float u64_to_float(unsigned long long x) {
-    return fmaf((float)(unsigned)(x >> 32), 4294967296.0f, (float)(unsigned)x);
+// exact single-precision value of an unsigned integer below 2^23, on the
+// integer and FMA pipes (no conversion instruction)
+__device__ __forceinline__ float u23_to_float(unsigned u) {
+    return __fadd_rn(__uint_as_float(0x4B000000u | u), -8388608.0f);
 }
 
 struct Walk {
     int cx, cy, cz;          // current cell
-    unsigned Dx, Dy, Dz;     // distance along each axis to the next face ahead (<= 2^22)
+    unsigned Dx, Dy, Dz;     // distance along each axis to the next face ahead (<= 2^21)
     unsigned ax, ay, az;     // |d| (<= 2^21)
     int sx, sy, sz;          // sign of d
 };
 
 // cell index (floor) and distance to the next face for one axis; a ray on a
 // face belongs to the cell it moves into
-__device__ __forceinline__ void axis_init(long long p, int d, int &c, unsigned &D, unsigned &a, int &s) {
+__device__ __forceinline__ void axis_init(int p, int d, int &c, unsigned &D, unsigned &a, int &s) {
     const unsigned MASK = (unsigned)ONE_CELL - 1u;
     if (d > 0) {
-        c = (int)(p >> FRAC_BITS); D = (unsigned)ONE_CELL - ((unsigned)p & MASK); a = (unsigned)d; s = 1;
+        c = p >> FRAC_BITS; D = (unsigned)ONE_CELL - ((unsigned)p & MASK); a = (unsigned)d; s = 1;
     } else if (d < 0) {
-        const long long q = p - 1;
-        c = (int)(q >> FRAC_BITS); D = ((unsigned)q & MASK) + 1u; a = (unsigned)(-d); s = -1;
+        const int q = p - 1;
+        c = q >> FRAC_BITS; D = ((unsigned)q & MASK) + 1u; a = (unsigned)(-d); s = -1;
     } else {
-        c = (int)(p >> FRAC_BITS); D = 0u; a = 0u; s = 0;
+        c = p >> FRAC_BITS; D = 0u; a = 0u; s = 0;
     }
 }
-__device__ __forceinline__ void walk_init(Walk &w, long long px, long long py, long long pz, int dx, int dy, int dz) {
+// positions in 2^-21 cell, |p| < 2^31 - 2^21 (a ray within 1000 cells of the
+// box; arithmetic right shifts are floors)
+__device__ __forceinline__ void walk_init(Walk &w, int px, int py, int pz, int dx, int dy, int dz) {
     axis_init(px, dx, w.cx, w.Dx, w.ax, w.sx);
     axis_init(py, dy, w.cy, w.Dy, w.ay, w.sy);
     axis_init(pz, dz, w.cz, w.Dz, w.az, w.sz);
@@ -318,19 +323,25 @@ __device__ __forceinline__ bool walk_outside(const Walk &w, int nx, int ny, int 
 }
 // The segments of one step.  |d_a| is at most one cell, so each axis is
 // crossed at most once, at t_a = D_a/|d_a| < 1 (D_a < |d_a|); the segments
-// end at these times in increasing order and at t = 1.  The times are
-// ordered once per step by exact cross-multiplied comparisons (the rank of
-// an axis: the crossing axes strictly earlier); axes crossed at the same t
-// step together.  A segment's length is the exact fraction t_k - t_(k-1),
-// rounded once.  Outputs by fixed slot, so that they stay in registers: slot
-// r < 3 holds the segment that ends at the crossing of rank r, slot 3 the one
-// that ends the step; the bits of the returned mask mark the slots in use
-// (none after the ray leaves the grid: esc), in order along the ray.  A
-// slot's cell is key = coff + (z ny + y) nx + x (-1 for an empty slot).
-__device__ __forceinline__ float seg_len(unsigned un, unsigned ud, unsigned tn, unsigned td) {
-    const unsigned long long num = wmul(un, td) - wmul(tn, ud);
-    const unsigned long long den = wmul(ud, td);
-    return __fdividef(u64_to_float(num), u64_to_float(den));
+// end at these times in increasing order and at t = 1.  The order is decided
+// once per step by exact cross-multiplied comparisons (the rank of an axis:
+// the crossing axes strictly earlier); axes crossed at the same t step
+// together.  A segment from t_p = D_p/a_p to t_c = D_c/a_c has the length
+// (D_c a_p - D_p a_c) / (a_c a_p): the numerator, an integer below 2^44, is
+// formed in single precision with the exact rounding errors of its two
+// products (fma), so it is within an ulp; times the approximate
+// reciprocals of a_c and a_p the length is within a few ulp of the exact
+// fraction, however short it is (D, a <= 2^21 are exact floats, converted
+// on the integer and FMA pipes).  Outputs by fixed slot, so that they stay
+// in registers: slot r < 3 holds the segment that ends at the crossing of
+// rank r, slot 3 the one that ends the step; the bits of the returned mask
+// mark the slots in use (none after the ray leaves the grid: esc), in order
+// along the ray.  A slot's cell is key = coff + (z ny + y) nx + x (-1 for an
+// empty slot).
+__device__ __forceinline__ float cross_diff(float dc, float ap, float dp, float ac) {
+    const float p1 = __fmul_rn(dc, ap), p2 = __fmul_rn(dp, ac);
+    const float e1 = __fmaf_rn(dc, ap, -p1), e2 = __fmaf_rn(dp, ac, -p2);
+    return __fadd_rn(__fadd_rn(p1, -p2), __fadd_rn(e1, -e2));
 }
 __device__ __forceinline__ unsigned walk_step(const Walk &w, int nx, int ny, int nz, int coff, int (&key)[4],
                                               float (&ds)[4], bool &esc) {
@@ -348,8 +359,15 @@ __device__ __forceinline__ unsigned walk_step(const Walk &w, int nx, int ny, int
     const int rx = (cry && yx < xy) + (crz && zx < xz);
     const int ry = (crx && xy < yx) + (crz && zy < yz);
     const int rz = (crx && xz < zx) + (cry && yz < zy);
+    // the crossing axes' D, |d| and 1/|d| in single precision
+    const float fDx = u23_to_float(w.Dx), fDy = u23_to_float(w.Dy), fDz = u23_to_float(w.Dz);
+    const float fax = u23_to_float(w.ax), fay = u23_to_float(w.ay), faz = u23_to_float(w.az);
+    const float rax = crx ? __fdividef(1.0f, fax) : 0.0f;
+    const float ray = cry ? __fdividef(1.0f, fay) : 0.0f;
+    const float raz = crz ? __fdividef(1.0f, faz) : 0.0f;
     int x = w.cx, y = w.cy, z = w.cz;
-    unsigned tn = 0u, td = 1u, mask = 0u;
+    float dp = 0.0f, ap = 1.0f, rp = 1.0f;     // end of the previous segment: t = dp / ap
+    unsigned mask = 0u;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const bool bx = crx && rx == r, by = cry && ry == r, bz = crz && rz == r;
@@ -357,14 +375,15 @@ __device__ __forceinline__ unsigned walk_step(const Walk &w, int nx, int ny, int
         ds[r] = 0.0f;
         if (!esc && (bx || by || bz)) {
             key[r] = coff + (z * ny + y) * nx + x;
-            const unsigned un = bx ? w.Dx : (by ? w.Dy : w.Dz);
-            const unsigned ud = bx ? w.ax : (by ? w.ay : w.az);
-            ds[r] = seg_len(un, ud, tn, td);
+            const float dc = bx ? fDx : (by ? fDy : fDz);
+            const float ac = bx ? fax : (by ? fay : faz);
+            const float rc = bx ? rax : (by ? ray : raz);
+            ds[r] = __fmul_rn(__fmul_rn(cross_diff(dc, ap, dp, ac), rc), rp);
             mask |= 1u << r;
             if (bx) x += w.sx;
             if (by) y += w.sy;
             if (bz) z += w.sz;
-            tn = un; td = ud;
+            dp = dc; ap = ac; rp = rc;
             esc = (unsigned)x >= (unsigned)nx || (unsigned)y >= (unsigned)ny || (unsigned)z >= (unsigned)nz;
         }
     }
@@ -372,7 +391,7 @@ __device__ __forceinline__ unsigned walk_step(const Walk &w, int nx, int ny, int
     ds[3] = 0.0f;
     if (!esc) {
         key[3] = coff + (z * ny + y) * nx + x;
-        ds[3] = seg_len(1u, 1u, tn, td);
+        ds[3] = __fmul_rn(__fadd_rn(ap, -dp), rp);      // (a_p - D_p) / a_p, exact numerator
         mask |= 8u;
     }
     return mask;
@@ -449,44 +468,6 @@ __device__ __forceinline__ int warp_incl_scan(int x) {
         if (lane >= o) x += t;
     }
     return x;
-}
-
-// Absorbed fraction a = 1 - e^-t and transmission e^-t of an optical depth
-// t >= 0 in single precision without cancellation: below t = 1/8 the Taylor
-// series of 1 - e^-t through t^5 (truncation below t^5/720 <= 4.2e-8
-// relative, under the single-precision epsilon), above it the
-// hardware exponential (1 - e^-t then loses at most a factor 8 of its
-// relative accuracy, ~2e-6).
-__device__ __forceinline__ void absorb_transmit(float t, float &a, float &tr) {
-    const float u = fminf(t, 0.125f);
-    float q = 1.0f / 120.0f;                     // 1/5!
-    q = fmaf(q, -u, 1.0f / 24.0f);
-    q = fmaf(q, -u, 1.0f / 6.0f);
-    q = fmaf(q, -u, 0.5f);
-    q = fmaf(q, -u, 1.0f);
-    const float series = q * u;                  // 1 - e^-u
-    const float ex = __expf(-t);
-    const bool small = t < 0.125f;
-    a = small ? series : 1.0f - ex;
-    tr = small ? 1.0f - series : ex;
-}
-
-// absorb_transmit on two bins at once: the polynomial in the paired
-// single-precision units (same operations, same rounding per bin).
-__device__ __forceinline__ void absorb_transmit2(float2 t, float2 &a, float2 &tr) {
-    const float2 u = make_float2(fminf(t.x, 0.125f), fminf(t.y, 0.125f));
-    const float2 nu = make_float2(-u.x, -u.y);
-    float2 q = make_float2(1.0f / 120.0f, 1.0f / 120.0f);
-    q = __ffma2_rn(q, nu, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
-    q = __ffma2_rn(q, nu, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
-    q = __ffma2_rn(q, nu, make_float2(0.5f, 0.5f));
-    q = __ffma2_rn(q, nu, make_float2(1.0f, 1.0f));
-    const float2 series = __fmul2_rn(q, u);
-    const float2 one_m = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-series.x, -series.y));
-    const float ex0 = __expf(-t.x), ex1 = __expf(-t.y);
-    const bool s0 = t.x < 0.125f, s1 = t.y < 0.125f;
-    a = make_float2(s0 ? series.x : 1.0f - ex0, s1 ? series.y : 1.0f - ex1);
-    tr = make_float2(s0 ? one_m.x : ex0, s1 ? one_m.y : ex1);
 }
 
 // exact 2^-k for 0 <= k < 126

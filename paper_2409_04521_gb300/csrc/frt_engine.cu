@@ -182,11 +182,13 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     const bool mrg = cfg_.merge_l_max >= 0;
     if (cfg_.merge_l_max > 11) return fail(FLEXRT_E_INVALID, "merge level above 11");
     long long cap = cfg_.ray_capacity;
-    if (cap <= 0) cap = (long long)(0.3 * (double)freeb / (2.0 * ray_bytes(cfg_.nb, mrg)));
+    if (cap <= 0) cap = std::min((long long)(0.3 * (double)freeb / (2.0 * ray_bytes(cfg_.nb, mrg))), 1600000000LL);
     cfg_.ray_capacity = cap = std::max(cap, 1024LL);
     // queue slots beyond the live-ray capacity for the unused tails of the
     // march's warp-private output runs
     cap += cap / 4 + 4096;
+    // the kernels index the queue with 32-bit integers
+    if (cap >= (1LL << 31) - (1LL << 24)) return fail(FLEXRT_E_INVALID, "ray capacity above the 32-bit queue index");
     qcap_ = cap;
 
     // ray queues: one allocation, structure of arrays, two buffers
@@ -676,6 +678,13 @@ static cudaEvent_t take_event(std::vector<cudaEvent_t> &pool) {
 }
 
 flexrt_status Engine::launch_step() {
+    flexrt_status r = launch_stage(1);
+    return r == FLEXRT_OK ? launch_stage(2) : r;
+}
+
+// stage 1: emission and the marches (the trial passes and the committed
+// one); stage 2: merge, chemistry and the budget's commit
+flexrt_status Engine::launch_stage(int stage) {
     const int ms = (int)slots_.size();
     EmitArgs ea{ctl_, sims_, acc_, {q_[0], q_[1]}, qcap_, em_, pixtab_, ltab_, cfg_.nb};
     MarchArgs ma{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, qcap_, em_, cells_, pixtab_, ltab_};
@@ -688,29 +697,32 @@ flexrt_status Engine::launch_step() {
     auto toc = [&](int k) {
         if (prof) { cudaEvent_t e1 = take_event(ev_pool_); cudaEventRecord(e1, st_); ev_k_[k].push_back({e0, e1}); }
     };
-    tic();
-    CK(launch_emit(ea, emit_blocks_, st_));
-    toc(0);
-    // passes of the Gamma - <n_HI> iteration before the committed one: march,
-    // trial chemistry (opacity of the time-averaged state), reset of the
-    // step's march output and tallies
-    int iters = 1;
-    for (const Slot &sl : slots_)
-        if (sl.used) iters = std::max(iters, (int)sl.h.gamma_iters);
-    for (int it = 0; it + 1 < iters; ++it) {
+    if (stage == 1) {
+        tic();
+        CK(launch_emit(ea, emit_blocks_, st_));
+        toc(0);
+        // passes of the Gamma - <n_HI> iteration before the committed one: march,
+        // trial chemistry (opacity of the time-averaged state), reset of the
+        // step's march output and tallies
+        int iters = 1;
+        for (const Slot &sl : slots_)
+            if (sl.used) iters = std::max(iters, (int)sl.h.gamma_iters);
+        for (int it = 0; it + 1 < iters; ++it) {
+            tic();
+            CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, ext_variants()));
+            toc(1);
+            ChemArgs ct = ca;
+            ct.final_pass = 0;
+            tic();
+            CK(launch_chem(ct, chem_blocks_, st_));
+            toc(2);
+            CK(launch_iter_reset(ctl_, acc_, ms, st_));
+    }
         tic();
         CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, ext_variants()));
         toc(1);
-        ChemArgs ct = ca;
-        ct.final_pass = 0;
-        tic();
-        CK(launch_chem(ct, chem_blocks_, st_));
-        toc(2);
-        CK(launch_iter_reset(ctl_, acc_, ms, st_));
+        return FLEXRT_OK;
     }
-    tic();
-    CK(launch_march(ma, cfg_.nb, march_agg_, march_minb_, march_blocks_, march_threads_, st_, ext_variants()));
-    toc(1);
     if (merge_built()) {
         MergeArgs ga{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, em_, rg_, pixtab_, ltab_, mw_, cfg_.nb};
         tic();
@@ -734,6 +746,7 @@ void Engine::free_retired() {
 }
 
 flexrt_status Engine::step() {
+    if (mid_step_) return fail(FLEXRT_E_STATE, "finish the staged step first");
     flexrt_status s = poll(false);
     if (s != FLEXRT_OK) return s;
     free_retired();
@@ -766,6 +779,30 @@ flexrt_status Engine::step() {
     // the step just enqueued drops the rays of members retired before it;
     // work enqueued later runs after it, so their emitters can be reused
     free_retired();
+    return FLEXRT_OK;
+}
+
+flexrt_status Engine::step_stage(int stage) {
+    if (cfg_.use_graph || slots_.size() != 1) return fail(FLEXRT_E_STATE, "staged steps are for single simulations");
+    if (stage == 1) {
+        if (mid_step_) return fail(FLEXRT_E_STATE, "a staged step is already open");
+        flexrt_status s = poll(false);
+        if (s != FLEXRT_OK) return s;
+        s = launch_stage(1);
+        if (s != FLEXRT_OK) return s;
+        mid_step_ = true;
+        return FLEXRT_OK;
+    }
+    if (stage != 2 || !mid_step_) return fail(FLEXRT_E_STATE, "no staged step to finish");
+    mid_step_ = false;
+    flexrt_status s = launch_stage(2);
+    if (s != FLEXRT_OK) return s;
+    CK(cudaMemcpyAsync(h_err_, (char *)ctl_ + offsetof(Ctl, err), sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    CK(cudaEventRecord(ev_err_, st_));
+    err_pending_ = true;
+    ++steps_taken_;
+    for (auto &sl : slots_)
+        if (sl.active) ++sl.h.step;
     return FLEXRT_OK;
 }
 
@@ -902,9 +939,20 @@ flexrt_status Engine::rays(int s, int64_t cap, int32_t *level, int64_t *pixel, i
     *n = (int64_t)a.rays_live;
     Ctl hc;
     CK(cudaMemcpy(&hc, ctl_, sizeof(hc), cudaMemcpyDeviceToHost));
-    const long long m = hc.cnt[hc.par];
-    if (m == 0 || cap == 0) return FLEXRT_OK;
-    const Queue &q = q_[hc.par];
+    const int qs = mid_step_ ? hc.par ^ 1 : hc.par;     // between the stages: the march's output
+    const long long m = hc.cnt[qs];
+    if (mid_step_) *n = 0;
+    if (m == 0 || cap == 0) {
+        if (mid_step_ && m > 0) {
+            std::vector<uint32_t> pl(m), em(m), ma(merge_built() ? m : 0);
+            CK(cudaMemcpy(pl.data(), q_[qs].pl, m * 4, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(em.data(), q_[qs].em, m * 4, cudaMemcpyDeviceToHost));
+            if (!ma.empty()) CK(cudaMemcpy(ma.data(), q_[qs].ma, m * 4, cudaMemcpyDeviceToHost));
+            *n = (int64_t)member_rays(pl, em, ma, s, sl->em0, sl->em_n).size();
+        }
+        return FLEXRT_OK;
+    }
+    const Queue &q = q_[qs];
     std::vector<uint32_t> pl(m), em(m), ma(merge_built() ? m : 0);
     std::vector<int32_t> bi(m), d(3 * m);
     CK(cudaMemcpy(pl.data(), q.pl, m * 4, cudaMemcpyDeviceToHost));
@@ -917,6 +965,7 @@ flexrt_status Engine::rays(int s, int64_t cap, int32_t *level, int64_t *pixel, i
     std::vector<std::vector<float>> ph(photons ? sl->h.nb : 0, std::vector<float>(m));
     for (int b = 0; b < (int)ph.size(); ++b) CK(cudaMemcpy(ph[b].data(), q.ph[b], m * 4, cudaMemcpyDeviceToHost));
     const std::vector<long long> idx = member_rays(pl, em, ma, s, sl->em0, sl->em_n);
+    if (mid_step_) *n = (int64_t)idx.size();
     for (long long k = 0; k < (long long)idx.size() && k < cap; ++k) {
         const long long i = idx[k];
         if (level) level[k] = (int32_t)(pl[i] >> LEVEL_SHIFT);
@@ -937,8 +986,9 @@ flexrt_status Engine::rays_merged(int s, int64_t cap, int32_t *merged, int32_t *
     CK(cudaStreamSynchronize(st_));
     Ctl hc;
     CK(cudaMemcpy(&hc, ctl_, sizeof(hc), cudaMemcpyDeviceToHost));
-    const long long m = hc.cnt[hc.par];
-    const Queue &q = q_[hc.par];
+    const int qs = mid_step_ ? hc.par ^ 1 : hc.par;
+    const long long m = hc.cnt[qs];
+    const Queue &q = q_[qs];
     std::vector<uint32_t> pl(m), em(m), ma(merge_built() ? m : 0);
     std::vector<int32_t> mx(ma.size()), my(ma.size()), mz(ma.size());
     std::vector<float> mt(ma.size());
@@ -1067,6 +1117,7 @@ constexpr char STATE_MAGIC[8] = {'F', 'L', 'E', 'X', 'R', 'T', 'S', '1'};
 flexrt_status Engine::save_state(int s, void *buf, int64_t cap, int64_t *bytes) {
     const Slot *sl = slot(s);
     if (!sl || !bytes || slots_.size() != 1) return fail(FLEXRT_E_INVALID, "checkpoints are for single simulations");
+    if (mid_step_) return fail(FLEXRT_E_STATE, "finish the staged step first");
     CK(cudaStreamSynchronize(st_));
     flexrt_status ps = poll(true);
     if (ps != FLEXRT_OK) return ps;
@@ -1117,6 +1168,7 @@ flexrt_status Engine::save_state(int s, void *buf, int64_t cap, int64_t *bytes) 
 flexrt_status Engine::load_state(int s, const void *buf, int64_t bytes) {
     Slot *sl = (s >= 0 && s < (int)slots_.size() && slots_[s].used) ? &slots_[s] : nullptr;
     if (!sl || !buf || slots_.size() != 1) return fail(FLEXRT_E_INVALID, "checkpoints are for single simulations");
+    if (mid_step_) return fail(FLEXRT_E_STATE, "finish the staged step first");
     StateHeader h;
     if (bytes < (int64_t)sizeof(h)) return fail(FLEXRT_E_INVALID, "checkpoint truncated");
     std::memcpy(&h, buf, sizeof(h));

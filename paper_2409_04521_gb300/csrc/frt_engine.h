@@ -72,6 +72,10 @@ class Engine {
     flexrt_status add_sources(int slot, int32_t n, const int32_t *ijk, const double *ndot);
     flexrt_status set_dt(int slot, double dt);
     flexrt_status step();                     // one RT step of every active simulation
+    // a single simulation's step in two stages: 1 = emission and marches,
+    // 2 = merge, chemistry, commit (the rays getters read the march's output
+    // in between)
+    flexrt_status step_stage(int stage);
     flexrt_status sync();
     flexrt_status retire(int slot);
     flexrt_status reset_all();                // single-simulation reset
@@ -113,6 +117,7 @@ class Engine {
     flexrt_status upload_lists();             // active emitters, cell ranges, counters
     flexrt_status poll(bool wait);
     flexrt_status launch_step();
+    flexrt_status launch_stage(int stage);
     flexrt_status read_acc(int slot, SimAcc &a);
     void free_retired();
 
@@ -156,6 +161,7 @@ class Engine {
 
     cudaGraphExec_t graph_ = nullptr;
     bool graph_dirty_ = true;
+    bool mid_step_ = false;                 // between the two stages of a staged step
 
     std::unordered_map<void *, size_t> alloc_sizes_;   // live device allocations
     long long alloc_bytes_ = 0;

@@ -502,7 +502,7 @@ __global__ void k_probe_traverse(long long n, const long long *p0, const int32_t
                                  int32_t *cells, float *ds, int32_t *nseg, int32_t *esc) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         Walk w;
-        walk_init(w, p0[3 * i], p0[3 * i + 1], p0[3 * i + 2], d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+        walk_init(w, (int)p0[3 * i], (int)p0[3 * i + 1], (int)p0[3 * i + 2], d[3 * i], d[3 * i + 1], d[3 * i + 2]);
         int key[4];
         float s[4];
         bool e = false;

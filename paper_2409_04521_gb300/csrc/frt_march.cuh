@@ -53,12 +53,106 @@ struct MarchSim {
     int nx, ny, nz, step, l_src, l_max, active, l_merge, gen, pad0, pad1, pad2;
     long long coff;
     float eps;
+    float sig_max;          // largest sigma_b / sigma_ref of the bins
     int K[MAXL];
     float sig[MAXB], sige[MAXB], eh[MAXB];
 };
 
 __host__ __device__ constexpr size_t march_shared_bytes(int nsims) {
     return (size_t)nsims * (NACC * sizeof(unsigned long long) + sizeof(MarchSim));
+}
+
+// (1 - e^-t)/t for 0 <= t < 1/8: its Taylor series through t^4 (the next
+// term, t^5/720, is under the single-precision epsilon there)
+__device__ __forceinline__ float2 series_q2(float2 t) {
+    const float2 nt = make_float2(-t.x, -t.y);
+    float2 q = make_float2(1.0f / 120.0f, 1.0f / 120.0f);
+    q = __ffma2_rn(q, nt, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
+    q = __ffma2_rn(q, nt, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+    q = __ffma2_rn(q, nt, make_float2(0.5f, 0.5f));
+    return __ffma2_rn(q, nt, make_float2(1.0f, 1.0f));
+}
+__device__ __forceinline__ float series_q(float t) {
+    float q = 1.0f / 120.0f;
+    q = fmaf(q, -t, 1.0f / 24.0f);
+    q = fmaf(q, -t, 1.0f / 6.0f);
+    q = fmaf(q, -t, 0.5f);
+    return fmaf(q, -t, 1.0f);
+}
+
+// Attenuation of the photons ph[b] entering a segment of length dse (cells)
+// through a cell of optical depth per cell k = (HI at sigma_ref, sub-grid),
+// with its deposits (Eq. 13, Eq. 17): v[0] += absorbed photons, v[1] +=
+// sum_b sigma_b N_b (1 - e^-tau_b)/kappa_b, v[2] the same weighted by the
+// excess energy.  A bin with tau < 1/8 takes 1 - e^-tau = tau q(tau) with
+// the series q, so (1 - e^-tau)/kappa = dse q (no exponential, no
+// division) and keeps N - N tau q; a thicker bin takes the hardware
+// exponential and the division by kappa (N dse when kappa = 0).  SMALL:
+// every bin of every lane of the warp is thin, and only the series is
+// evaluated; the per-bin results are the same either way, so a ray's photons
+// do not depend on the rays it shares a warp with.  Bins go in pairs on the
+// paired single-precision units.
+template <int NB, bool SMALL>
+__device__ __forceinline__ void seg_attenuate(float2 k, float dse, const float *sig, const float *sige, float (&ph)[NB],
+                                              float (&v)[4]) {
+    float2 w0 = make_float2(0.f, 0.f), w1 = w0, w2 = w0;
+    const float2 kx2 = make_float2(k.x, k.x), ky2 = make_float2(k.y, k.y), ds2 = make_float2(dse, dse);
+#pragma unroll
+    for (int b = 0; b + 1 < NB; b += 2) {
+        const float2 sg = make_float2(sig[b], sig[b + 1]);
+        const float2 se = make_float2(sige[b], sige[b + 1]);
+        const float2 kb = __ffma2_rn(kx2, sg, ky2);
+        const float2 tau = __fmul2_rn(kb, ds2);
+        const float2 p2 = make_float2(ph[b], ph[b + 1]);
+        const float2 pd = __fmul2_rn(p2, ds2);
+        float2 a, phin, pn;
+        if (SMALL) {
+            const float2 q = series_q2(tau);
+            a = __fmul2_rn(p2, __fmul2_rn(q, tau));
+            phin = __fmul2_rn(pd, q);
+            pn = __fadd2_rn(p2, make_float2(-a.x, -a.y));
+        } else {
+            const float2 u = make_float2(fminf(tau.x, 0.125f), fminf(tau.y, 0.125f));
+            const float2 q = series_q2(u);
+            const float2 as = __fmul2_rn(p2, __fmul2_rn(q, u));
+            const float2 ps = __fmul2_rn(pd, q);
+            const float ex0 = __expf(-tau.x), ex1 = __expf(-tau.y);
+            const bool s0 = tau.x < 0.125f, s1 = tau.y < 0.125f;
+            a = make_float2(s0 ? as.x : p2.x * (1.0f - ex0), s1 ? as.y : p2.y * (1.0f - ex1));
+            pn = make_float2(s0 ? p2.x - as.x : p2.x * ex0, s1 ? p2.y - as.y : p2.y * ex1);
+            phin = make_float2(s0 ? ps.x : (kb.x > 0.0f ? __fdividef(a.x, kb.x) : pd.x),
+                               s1 ? ps.y : (kb.y > 0.0f ? __fdividef(a.y, kb.y) : pd.y));
+        }
+        ph[b] = pn.x;
+        ph[b + 1] = pn.y;
+        w0 = __fadd2_rn(w0, a);
+        w1 = __ffma2_rn(sg, phin, w1);
+        w2 = __ffma2_rn(se, phin, w2);
+    }
+    v[0] = w0.x + w0.y;
+    v[1] = w1.x + w1.y;
+    v[2] = w2.x + w2.y;
+    if (NB & 1) {
+        const int b = NB - 1;
+        const float kb = fmaf(k.x, sig[b], k.y);
+        const float tau = kb * dse;
+        const float pd = ph[b] * dse;
+        float a, phin;
+        if (SMALL || tau < 0.125f) {
+            const float q = series_q(tau);
+            a = ph[b] * (q * tau);
+            phin = pd * q;
+            ph[b] -= a;
+        } else {
+            const float ex = __expf(-tau);
+            a = ph[b] * (1.0f - ex);
+            phin = kb > 0.0f ? __fdividef(a, kb) : pd;
+            ph[b] *= ex;
+        }
+        v[0] += a;
+        v[1] = fmaf(sig[b], phin, v[1]);
+        v[2] = fmaf(sige[b], phin, v[2]);
+    }
 }
 
 // Phases per ray: (1) the integer walk of the whole step, (2) the opacity
@@ -86,7 +180,11 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         m.active = S.active; m.l_merge = S.l_merge; m.coff = S.cell_off; m.eps = S.eps_term;
         m.gen = S.gen_mode; m.pad0 = m.pad1 = m.pad2 = 0;
         for (int l = 0; l < MAXL; ++l) m.K[l] = S.K[l];
-        for (int b = 0; b < MAXB; ++b) { m.sig[b] = S.sig[b]; m.sige[b] = S.sige[b]; m.eh[b] = S.eh[b]; }
+        m.sig_max = 0.0f;
+        for (int b = 0; b < MAXB; ++b) {
+            m.sig[b] = S.sig[b]; m.sige[b] = S.sige[b]; m.eh[b] = S.eh[b];
+            if (b < S.nb) m.sig_max = fmaxf(m.sig_max, S.sig[b]);
+        }
     }
     __syncthreads();
     Ctl *C = A.ctl;
@@ -95,12 +193,13 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         const int par = C->par;
         const Queue qi = A.q[par], qo = A.q[par ^ 1];
         unsigned long long *out_cnt = (unsigned long long *)&C->cnt[par ^ 1];
-        const long long n = C->cnt[par] + C->emit_total;
-        const long long nr = (n + 31) & ~31LL;
-        const long long stride = (long long)gridDim.x * blockDim.x;
+        // queue slots stay below 2^31 (the engine's bound), so 32-bit indices
+        const unsigned n = (unsigned)(C->cnt[par] + C->emit_total);
+        const unsigned nr = (n + 31u) & ~31u;
+        const unsigned stride = gridDim.x * blockDim.x;
         // warp-private run of output slots [slab, slab + slab_left), and this
         // warp's outputs and iterations so far (its output rate)
-        unsigned long long slab = 0;
+        unsigned slab = 0;
         int slab_left = 0;
         int w_out = 0, w_it = 0;
         // lane-private tallies of one simulation, flushed by the warp:
@@ -116,7 +215,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
         int nmx = 0, nmy = 0, nmz = 0;
         uint32_t nma = 0;
         float nmthr = 0.0f;
-        auto load_ray = [&](long long j) {
+        auto load_ray = [&](unsigned j) {
             // the queue streams through once per step: evict-first loads keep
             // the cells' opacities and deposit buffers resident in L2
             npl = DEAD_RAY;
@@ -136,7 +235,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 for (int b = 0; b < NB; ++b) nph[b] = 0.0f;
             }
         };
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += stride) {
+        for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
             load_ray(i);
             const uint32_t pl = npl, e = ne_;
             const int bi = nbi, dx = ndx, dy = ndy, dz = ndz;
@@ -176,15 +275,17 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             unsigned vmask = 0u;
             {
                 Walk w;
-                long long px, py, pz;
+                // a queued ray is inside the box at the start of its step, so
+                // its position (at most 1000 cells of 2^21) fits 32 bits
+                int px, py, pz;
                 if (mrg) {
-                    px = (long long)mx + (long long)since * dx;
-                    py = (long long)my + (long long)since * dy;
-                    pz = (long long)mz + (long long)since * dz;
+                    px = mx + since * dx;
+                    py = my + since * dy;
+                    pz = mz + since * dz;
                 } else {
-                    px = ((2LL * ec.x + 1) << (FRAC_BITS - 1)) + (long long)age * dx;
-                    py = ((2LL * ec.y + 1) << (FRAC_BITS - 1)) + (long long)age * dy;
-                    pz = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + (long long)age * dz;
+                    px = ((2 * ec.x + 1) << (FRAC_BITS - 1)) + age * dx;
+                    py = ((2 * ec.y + 1) << (FRAC_BITS - 1)) + age * dy;
+                    pz = ((2 * ec.z + 1) << (FRAC_BITS - 1)) + age * dz;
                 }
                 walk_init(w, px, py, pz, dx, dy, dz);
                 // slots may be empty (tied crossings): every later phase
@@ -215,46 +316,13 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             for (int j = 0; j < 4; ++j) {
                 float v[4] = {0.f, 0.f, 0.f, 1.0f};
                 if (EXT && screened) key[j] = -1;
+                const float dse = EXT ? xg[j] * ds[j] : ds[j];
+                // every segment of this slot in the warp optically thin (all
+                // bins' tau below 1/8): the series path, warp-uniform
+                const bool thin = __all_sync(FULL, key[j] < 0 || fmaf(kc[j].x, S.sig_max, kc[j].y) * dse < 0.125f);
                 if (key[j] >= 0) {
-                    const float dse = EXT ? xg[j] * ds[j] : ds[j];
-                    // bins in pairs on the paired single-precision units
-                    float2 w0 = make_float2(0.f, 0.f), w1 = w0, w2 = w0;
-                    const float2 kx2 = make_float2(kc[j].x, kc[j].x), ky2 = make_float2(kc[j].y, kc[j].y);
-                    const float2 ds2 = make_float2(dse, dse);
-#pragma unroll
-                    for (int b = 0; b + 1 < NB; b += 2) {
-                        const float2 sg = make_float2(S.sig[b], S.sig[b + 1]);
-                        const float2 se = make_float2(S.sige[b], S.sige[b + 1]);
-                        const float2 kb = __ffma2_rn(kx2, sg, ky2);
-                        float2 tr, ab;
-                        absorb_transmit2(__fmul2_rn(kb, ds2), ab, tr);
-                        const float2 p2 = make_float2(ph[b], ph[b + 1]);
-                        const float2 a = __fmul2_rn(p2, ab);
-                        const float2 pd = __fmul2_rn(p2, ds2);
-                        const float2 phin = make_float2(kb.x > 0.0f ? __fdividef(a.x, kb.x) : pd.x,
-                                                        kb.y > 0.0f ? __fdividef(a.y, kb.y) : pd.y);
-                        const float2 pn = __fmul2_rn(p2, tr);
-                        ph[b] = pn.x;
-                        ph[b + 1] = pn.y;
-                        w0 = __fadd2_rn(w0, a);
-                        w1 = __ffma2_rn(sg, phin, w1);
-                        w2 = __ffma2_rn(se, phin, w2);
-                    }
-                    v[0] = w0.x + w0.y;
-                    v[1] = w1.x + w1.y;
-                    v[2] = w2.x + w2.y;
-                    if (NB & 1) {
-                        const int b = NB - 1;
-                        const float kb = fmaf(kc[j].x, S.sig[b], kc[j].y);
-                        float tr, ab;
-                        absorb_transmit(kb * dse, ab, tr);
-                        const float a = ph[b] * ab;
-                        const float phin = kb > 0.0f ? __fdividef(a, kb) : ph[b] * dse;
-                        ph[b] *= tr;
-                        v[0] += a;
-                        v[1] = fmaf(S.sig[b], phin, v[1]);
-                        v[2] = fmaf(S.sige[b], phin, v[2]);
-                    }
+                    if (thin) seg_attenuate<NB, true>(kc[j], dse, S.sig, S.sige, ph, v);
+                    else seg_attenuate<NB, false>(kc[j], dse, S.sig, S.sige, ph, v);
                     last = key[j];
                     lastk = kc[j];
                     if (EXT && xg[j] < 1.0f) {
@@ -336,24 +404,25 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
             const int incl = warp_incl_scan(nout);
             const int tot = __shfl_sync(FULL, incl, 31);
             if (tot > 0) {
-                const unsigned long long s0 = slab;
+                const unsigned s0 = slab;
                 const int left = slab_left;
-                unsigned long long s1 = 0;
+                unsigned s1 = 0;
                 bool fits = true;
                 if (tot > left) {
                     // reserve for this warp's next iterations at its own output
                     // rate (at most 16 iterations ahead and OUT_SLAB slots), so the
                     // unused tail stays small whatever the queue's dead fraction
                     const int need = tot - left;
-                    const long long iters_left = (nr - i + stride - 1) / stride;
-                    const int ahead = iters_left < 16 ? (int)iters_left : 16;
+                    const unsigned iters_left = (nr - i + stride - 1u) / stride;
+                    const int ahead = iters_left < 16u ? (int)iters_left : 16;
                     const int rate = (w_out + tot + w_it) / (w_it + 1);
                     const int guess = rate * ahead < OUT_SLAB ? rate * ahead : OUT_SLAB;
                     const int want = need > guess ? need : guess;
-                    unsigned long long nbase = 0;
-                    if (lane == 0) nbase = atomicAdd(out_cnt, (unsigned long long)want);
-                    nbase = __shfl_sync(FULL, nbase, 0);
-                    if ((long long)(nbase + want) > A.cap) {
+                    unsigned long long nb64 = 0;
+                    if (lane == 0) nb64 = atomicAdd(out_cnt, (unsigned long long)want);
+                    nb64 = __shfl_sync(FULL, nb64, 0);
+                    const unsigned nbase = (unsigned)nb64;
+                    if ((long long)(nb64 + want) > A.cap) {
                         if (lane == 0) atomicOr(&C->err, 1);
                         fits = false;
                         slab_left = 0;
@@ -369,11 +438,11 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                 w_out += tot;
                 if (fits && nout > 0) {
                     const int k0 = incl - nout;  // this lane's first output position
-                    auto slot_of = [&](int k) -> long long {
-                        return k < left ? (long long)(s0 + k) : (long long)(s1 + (k - left));
+                    auto slot_of = [&](int k) -> unsigned {
+                        return k < left ? s0 + (unsigned)k : s1 + (unsigned)(k - left);
                     };
                     if (nout == 1) {
-                        const long long o = slot_of(k0);
+                        const unsigned o = slot_of(k0);
                         __stcs(qo.pl + o, pl); __stcs(qo.em + o, e); __stcs(qo.bi + o, bi);
                         __stcs(qo.dx + o, dx); __stcs(qo.dy + o, dy); __stcs(qo.dz + o, dz);
 #pragma unroll
@@ -406,7 +475,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                             const int4 vq = L <= A.ltab ? __ldg(&A.pixtab[level_offset(L) + pix]) : healpix_vq(L, pix);
                             int32_t cx, cy, cz;
                             rotate_dir(rows, vq, cx, cy, cz);
-                            const long long oc = slot_of(k0 + c);
+                            const unsigned oc = slot_of(k0 + c);
                             qo.pl[oc] = ((uint32_t)L << LEVEL_SHIFT) | pix;
                             qo.em[oc] = e; qo.bi[oc] = bi;
                             qo.dx[oc] = cx; qo.dy[oc] = cy; qo.dz[oc] = cz;

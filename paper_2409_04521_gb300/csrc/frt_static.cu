@@ -73,8 +73,9 @@ extern "C" flexrt_status flexrt_probe_traverse_static(int64_t n, const int64_t *
                                            " exceeds the fixed maximum of " + std::to_string(kMaxRays) +
                                            " rays per call (FLEXRT_STATIC_MAX_RAYS)");
     for (int64_t i = 0; i < 3 * n; ++i)
-        if (dir[i] > (1 << 21) || dir[i] < -(1 << 21))
-            return fail(FLEXRT_E_INVALID, "flexrt_probe_traverse_static: |d| > 2^21");
+        if (dir[i] > (1 << 21) || dir[i] < -(1 << 21) || p0[i] > (1LL << 31) - (1LL << 22) ||
+            p0[i] < -(1LL << 31) + (1LL << 22))
+            return fail(FLEXRT_E_INVALID, "flexrt_probe_traverse_static: |d| > 2^21 or |p0| >= 2^31 - 2^22");
     if (n == 0) return FLEXRT_OK;
     unsigned char *base = nullptr;
     cudaError_t e = stage_address(&base);

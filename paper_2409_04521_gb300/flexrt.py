@@ -100,6 +100,7 @@ def lib():
             L.flexrt_create.argtypes = [P(Grid), P(Box), P(C.c_double), P(Mfp), P(Spectrum), P(Options), P(vp)]
             L.flexrt_add_sources.argtypes = [vp, C.c_int32, P(C.c_int32), P(C.c_double)]
             L.flexrt_step.argtypes = [vp, C.c_double]
+            L.flexrt_step_stage.argtypes = [vp, C.c_double, C.c_int32]
             L.flexrt_sync.argtypes = [vp]
             L.flexrt_reset.argtypes = [vp]
             L.flexrt_get_fields.argtypes = [vp, P(Fields)]
@@ -391,6 +392,11 @@ class Simulation:
 
     def step(self, dt: float):
         _check(lib().flexrt_step(self._h, float(dt)), self._h)
+
+    def step_stage(self, dt: float, stage: int):
+        """One step in two stages (1: emission and marches; 2: merge,
+        chemistry, commit); rays() in between returns the march's output."""
+        _check(lib().flexrt_step_stage(self._h, float(dt), int(stage)), self._h)
 
     def sync(self):
         _check(lib().flexrt_sync(self._h), self._h)

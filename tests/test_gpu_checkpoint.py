@@ -54,8 +54,13 @@ def test_checkpoint_round_trip_and_resume(kw):
     # the next step marches the same rays through the same opacities
     b.step(prob.dt)
     c.step(prob.dt)
-    if not kw.get("merge"):
+    if not kw:
+        # one pass: the march reads only the restored state
         _same_rays(b.rays(), c.rays(), exact=True)
+    elif not kw.get("merge"):
+        # trial passes feed Gamma (single-precision reductions) back into the
+        # opacity: equal to rounding
+        _same_rays(b.rays(), c.rays(), exact=False)
     compare_fields(c.fields(), b.fields(), x_atol=1e-6, g_rtol=1e-5, T_rtol=1e-5)
     # and the resumed run follows the uninterrupted one
     a.step(prob.dt)
@@ -67,10 +72,17 @@ def test_checkpoint_round_trip_and_resume(kw):
     if not kw.get("merge"):
         assert cc["rays"] == ca["rays"] and cc["segments_total"] == ca["segments_total"]
         _same_rays(a.rays(), c.rays(), exact=False)
+        compare_fields(c.fields(), a.fields(), x_atol=1e-4, g_rtol=1e-4, T_rtol=1e-3)
+        assert np.allclose(c.budget(), a.budget(), rtol=1e-5)
     else:
+        # merging runs, resumed or not, drift apart from rounding (rays
+        # within rounding of T_ref or a pixel edge change groups): Sec. 7.1's
+        # criteria
+        fc, fa = c.fields(), a.fields()
         assert abs(cc["rays"] - ca["rays"]) <= 0.02 * ca["rays"] + 16
-    compare_fields(c.fields(), a.fields(), x_atol=1e-4, g_rtol=1e-3 if kw.get("merge") else 1e-4, T_rtol=1e-3)
-    assert np.allclose(c.budget(), a.budget(), rtol=1e-5)
+        assert abs(fc["x_HII"].mean() - fa["x_HII"].mean()) <= 0.01 * fa["x_HII"].mean()
+        assert abs(fc["gamma_HI"].mean() - fa["gamma_HI"].mean()) <= 0.02 * fa["gamma_HI"].mean()
+        assert np.all(np.abs(c.budget() - a.budget()) <= 0.01 * a.budget()[0])
     for s in (a, b, c):
         s.close()
 
@@ -81,7 +93,9 @@ def test_checkpoint_rejects_another_simulation():
     a = F.Simulation(prob, ray_capacity=1 << 20)
     o = F.Simulation(other, ray_capacity=1 << 20)
     o.step(other.dt)
-    a.step(prob.dt)
+    for _ in range(5):
+        a.step(prob.dt)
+    assert a.counts()["rays"] > 4096
     before = a.save_state()
     with pytest.raises(F.FlexRTError) as e:
         a.load_state(o.save_state())
@@ -94,7 +108,7 @@ def test_checkpoint_rejects_another_simulation():
         a.load_state(bad)
     assert np.array_equal(a.save_state(), before)             # unchanged
     a.step(prob.dt)
-    assert a.counts()["step"] == 2
+    assert a.counts()["step"] == 6
     # a checkpoint with more live rays than the queue holds
     small = F.Simulation(prob, ray_capacity=1024)
     with pytest.raises(F.FlexRTError) as e:
