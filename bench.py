@@ -286,7 +286,11 @@ def impl_gpu(args, dist):
     sim = F.Simulation(prob, ray_capacity=args.capacity, stream=stream.cuda_stream)
     max_rays = 0
     tuned = None
-    if not args.no_tune:
+    if args.variant:
+        v = tuple(int(x) for x in args.variant.split(","))
+        sim.set_launch(*v)
+        tuned = {"variant": {"agg": v[0], "minb": v[1], "blocks_per_sm": v[2]}, "candidates": 0}
+    elif not args.no_tune:
         from paper_2409_04521_gb300 import autotune
         best, table = autotune.tune(sim, prob)
         tuned = {"variant": {"agg": best[0], "minb": best[1], "blocks_per_sm": best[2]},
@@ -670,6 +674,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--variant", default="", help="march launch agg,minb,blocks_per_sm (no autotuning)")
     ap.add_argument("--workload", default="cosmo16", choices=["cosmo16", "batch64", "serve", "merge"])
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=50)
