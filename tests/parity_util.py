@@ -92,7 +92,11 @@ def run_pair(prob, steps=None, capacity=1 << 22, check_every=1, T_rtol=None, x_a
             assert gc["segments_total"] == oc["segments_total"]
             assert np.array_equal(g.segment_counts(), o.segment_counts())
         summary["straddles"] = oc["near_threshold"]
-        summary.update(compare_fields(g.fields(), o.fields(), x_atol=x_atol, T_rtol=T_rtol))
+        gf, of = g.fields(), o.fields()
+        summary.update(compare_fields(gf, of, x_atol=x_atol, T_rtol=T_rtol))
+        if s + 1 == steps:
+            record_errors(f"{prob.name} {'x'.join(str(v) for v in prob.grid)}", steps, field_errors(gf, of),
+                          gamma_iters=int(getattr(prob.options, "gamma_iters", 1)), rays=gc["rays"])
     summary["rays"] = g.counts()["rays"]
     summary["segments_total"] = g.counts()["segments_total"]
     g.close()
