@@ -139,7 +139,8 @@ typedef struct {
      * screen first reached in the last pass absorbs all that reaches it, and
      * what exceeds its atoms is lost (counted as absorbed): on a 32^3
      * Stromgren sphere's first 40 steps 8e-3 of the emitted photons with 3
-     * passes, 6e-5 with 4, 2e-6 with 5.  chi: He/H number ratio, singly
+     * passes, 2e-3 with 4, 2e-6 with 5 (how fast the cascade of newly
+     * reached screens settles depends on the random spheres).  chi: He/H number ratio, singly
      * ionised helium in Eq. 18.
      * With isothermal = 0 the ionised part's temperature evolves: gas that
      * ionises enters at t_reion (K; 0 < t_reion < 1e9, -1 < alpha_pl < 20;

@@ -183,10 +183,16 @@ int or_pix2vec(int level, int64_t p, double v[3])
 
 /* ------------------------------------------------------------------------- */
 /* Random rotation of a source's HEALPix sphere (Sec. 3.1).                   */
-/* Reading: one uniform rotation per (seed, emitter, step).  Uniforms come    */
+/* Reading: one uniform rotation per (seed, emitter, step).  The draws come   */
 /* from SplitMix64 (Steele, Lea & Flood 2014) used as a counter-based stream; */
-/* the rotation is Marsaglia's (1972) uniform point on S^3 read as a unit     */
-/* quaternion.                                                                */
+/* each 64-bit draw is read as four signed 16-bit integers (w, x, y, z), and  */
+/* draws are rejected until 0 < w^2+x^2+y^2+z^2 <= 2^30: a uniform integer    */
+/* point of the 4-ball, whose direction is a uniform unit quaternion (the     */
+/* rejection idea of Marsaglia 1972, in integers).  The rotation matrix of    */
+/* that quaternion has the exact rational entries Q_ij / n, n = |q|^2, which  */
+/* are rounded half to even to 2^-24 in exact integer arithmetic: no step     */
+/* rounds anything but that last one, so the sphere is the same on every      */
+/* machine.                                                                   */
 /* ------------------------------------------------------------------------- */
 static const uint64_t SM_GAMMA = 0x9E3779B97F4A7C15ULL;
 static uint64_t sm_mix(uint64_t z)
@@ -202,55 +208,44 @@ static uint64_t rot_key(uint64_t seed, int64_t e, int64_t s)
     h = sm_mix(h + SM_GAMMA * (uint64_t)(s + 1));
     return h;
 }
-static double rot_uniform(uint64_t key, int i) /* i-th draw, in [0,1) */
-{
-    uint64_t u = sm_mix(key + SM_GAMMA * (uint64_t)(i + 1));
-    return (double)(u >> 11) * (1.0 / 9007199254740992.0);
-}
 
 /* raw 64-bit draw i of the stream keyed by `key` (exposed for tests) */
 uint64_t or_sm_draw(uint64_t key, int32_t i) { return sm_mix(key + SM_GAMMA * (uint64_t)(i + 1)); }
 uint64_t or_rot_key(uint64_t seed, int64_t e, int64_t s) { return rot_key(seed, e, s); }
 
-/* rotation matrix R (row major) and its 2^24 fixed-point copy */
-void or_rotation(uint64_t seed, int64_t e, int64_t s, int rotate, double R[9], int32_t Rq[9])
+/* num / den rounded to nearest, ties to even, for den > 0 */
+static int64_t div_round_even(int64_t num, int64_t den)
 {
-    double w = 1.0, x = 0.0, y = 0.0, z = 0.0;
-    if (rotate) {
-        uint64_t key = rot_key(seed, e, s);
-        int draw = 0, ok1 = 0, ok2 = 0;
-        double a = 0, b = 0, s1 = 0, c = 0, d = 0, s2 = 0;
-        for (int t = 0; t < 64 && !ok1; ++t) {
-            a = 2.0 * rot_uniform(key, draw++) - 1.0;
-            b = 2.0 * rot_uniform(key, draw++) - 1.0;
-            s1 = a * a + b * b;
-            ok1 = s1 < 1.0;
-        }
-        for (int t = 0; t < 64 && ok1 && !ok2; ++t) {
-            c = 2.0 * rot_uniform(key, draw++) - 1.0;
-            d = 2.0 * rot_uniform(key, draw++) - 1.0;
-            s2 = c * c + d * d;
-            ok2 = (s2 < 1.0) && (s2 > 0.0);
-        }
-        if (ok1 && ok2) {
-            double f = sqrt((1.0 - s1) / s2);
-            w = a; x = b; y = c * f; z = d * f;
-        }
-    }
-    R[0] = 1.0 - 2.0 * (y * y + z * z);
-    R[1] = 2.0 * (x * y - w * z);
-    R[2] = 2.0 * (x * z + w * y);
-    R[3] = 2.0 * (x * y + w * z);
-    R[4] = 1.0 - 2.0 * (x * x + z * z);
-    R[5] = 2.0 * (y * z - w * x);
-    R[6] = 2.0 * (x * z - w * y);
-    R[7] = 2.0 * (y * z + w * x);
-    R[8] = 1.0 - 2.0 * (x * x + y * y);
-    for (int i = 0; i < 9; ++i) Rq[i] = (int32_t)nearbyint(R[i] * 16777216.0);
+    int64_t q = num / den, r = num % den;          /* C: truncation toward zero */
+    if (r < 0) { q -= 1; r += den; }               /* floor and 0 <= r < den     */
+    if (2 * r > den || (2 * r == den && (q & 1))) q += 1;
+    return q;
 }
 
-/* Fixed-point direction of pixel (l,p) under rotation Rq:
- * vq = round(v * 2^24), d = round(Rq . vq / 2^27), |d| <= 2^21 per axis. */
+/* rotation matrix R (row major, Q_ij / n) and its 2^24 fixed-point copy */
+void or_rotation(uint64_t seed, int64_t e, int64_t s, int rotate, double R[9], int32_t Rq[9])
+{
+    int64_t w = 1, x = 0, y = 0, z = 0;
+    if (rotate) {
+        const uint64_t key = rot_key(seed, e, s);
+        for (int t = 0; t < 64; ++t) {
+            const uint64_t u = or_sm_draw(key, t);
+            const int64_t a = (int64_t)((u >> 0) & 0xFFFF) - 32768, b = (int64_t)((u >> 16) & 0xFFFF) - 32768;
+            const int64_t c = (int64_t)((u >> 32) & 0xFFFF) - 32768, d = (int64_t)((u >> 48) & 0xFFFF) - 32768;
+            const int64_t n2 = a * a + b * b + c * c + d * d;
+            if (n2 > 0 && n2 <= ((int64_t)1 << 30)) { w = a; x = b; y = c; z = d; break; }
+        }
+    }
+    const int64_t n = w * w + x * x + y * y + z * z;
+    const int64_t Q[9] = {w * w + x * x - y * y - z * z, 2 * (x * y - w * z), 2 * (x * z + w * y),
+                          2 * (x * y + w * z), w * w - x * x + y * y - z * z, 2 * (y * z - w * x),
+                          2 * (x * z - w * y), 2 * (y * z + w * x), w * w - x * x - y * y + z * z};
+    for (int i = 0; i < 9; ++i) {
+        R[i] = (double)Q[i] / (double)n;
+        Rq[i] = (int32_t)div_round_even(Q[i] * ((int64_t)1 << OR_VQ_BITS), n);
+    }
+}
+
 /* Random rotation of a cell's merge sphere (Sec. 3.3: "in each cell, we
  * throw down a randomly oriented HealPix sphere").  Drawn exactly like an
  * emitter's sphere (or_rotation: the same counter-based stream and Marsaglia

@@ -1,10 +1,11 @@
 // frt_device.cuh -- device functions of the RT step.
 //
-// The HEALPix vectors and sphere rotations are computed in double precision
-// with explicitly rounded intrinsics (no FMA contraction), so their 2^-24
-// fixed-point copies are the same integers on every IEEE-754 machine that
-// evaluates the same expressions in the same order.  Everything that decides
-// an integer (directions, crossed cells, splits) is integer arithmetic.
+// The HEALPix vectors are computed in double precision with explicitly
+// rounded intrinsics (no FMA contraction), so their 2^-24 fixed-point copies
+// are the same integers on every IEEE-754 machine that evaluates the same
+// expressions in the same order; the sphere rotations are exact integer
+// arithmetic.  Everything that decides an integer (directions, crossed
+// cells, splits) is integer arithmetic.
 #pragma once
 #include <cstdint>
 #include "frt_types.h"
@@ -111,10 +112,14 @@ __host__ __device__ __forceinline__ long long level_offset(int l) {  // sum_{j<l
 }
 
 // ---------------------------------------------------------------------------
-// Per-(emitter, step) random rotation (Sec. 3.1).  SplitMix64 (Steele, Lea &
-// Flood 2014) as a counter-based stream; Marsaglia (1972) uniform unit
-// quaternion.  Rows returned as round(R * 2^24).  A cell's merge sphere
-// (Sec. 3.3) is drawn the same way with the key 2^31 + local cell index.
+// Per-(emitter, step) random rotation (Sec. 3.1), and a cell's merge sphere
+// (Sec. 3.3) with the key 2^31 + local cell index.  SplitMix64 (Steele, Lea &
+// Flood 2014) as a counter-based stream; each 64-bit draw is read as four
+// signed 16-bit integers (w, x, y, z), rejected until 0 < |q|^2 <= 2^30 (a
+// uniform integer point of the 4-ball: a uniform unit quaternion by
+// direction); the rotation matrix's exact rational entries Q_ij / |q|^2 are
+// rounded half to even to 2^-24.  Integer arithmetic only: the same integers
+// on every machine, and no double-precision pipe.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t sm64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -123,51 +128,40 @@ __device__ __forceinline__ uint64_t sm64(uint64_t z) {
 }
 constexpr uint64_t GOLD = 0x9E3779B97F4A7C15ULL;
 
+// num / den rounded half to even, for 0 < den <= 2^30 and |num / den| <= 2^24:
+// a single-precision estimate (within a few units) corrected exactly by the
+// remainder
+__device__ __forceinline__ int32_t div_round_even(long long num, long long den) {
+    long long q = __float2ll_rz(__fdividef((float)num, (float)den));
+    long long r = num - q * den;
+    for (int k = 0; k < 16 && r < 0; ++k) { --q; r += den; }
+    for (int k = 0; k < 16 && r >= den; ++k) { ++q; r -= den; }
+    if (2 * r > den || (2 * r == den && (q & 1))) ++q;
+    return (int32_t)q;
+}
+
 __device__ inline void rotation_rows(uint64_t seed, long long e, long long s, int rotate, int4 rows[3]) {
-    double w = 1.0, x = 0.0, y = 0.0, zz = 0.0;
+    long long w = 1, x = 0, y = 0, z = 0;
     if (rotate) {
         uint64_t h = sm64(seed + GOLD);
         h = sm64(h + GOLD * (uint64_t)(e + 1));
         h = sm64(h + GOLD * (uint64_t)(s + 1));
-        int draw = 0;
-        auto uni = [&](void) -> double {
-            uint64_t u = sm64(h + GOLD * (uint64_t)(draw + 1));
-            ++draw;
-            return __dmul_rn(__ull2double_rn(u >> 11), 1.0 / 9007199254740992.0);
-        };
-        double a = 0, b = 0, s1 = 0, c = 0, d = 0, s2 = 0;
-        bool ok1 = false, ok2 = false;
-        for (int t = 0; t < 64 && !ok1; ++t) {
-            a = __dsub_rn(__dmul_rn(2.0, uni()), 1.0);
-            b = __dsub_rn(__dmul_rn(2.0, uni()), 1.0);
-            s1 = __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b));
-            ok1 = s1 < 1.0;
-        }
-        for (int t = 0; t < 64 && ok1 && !ok2; ++t) {
-            c = __dsub_rn(__dmul_rn(2.0, uni()), 1.0);
-            d = __dsub_rn(__dmul_rn(2.0, uni()), 1.0);
-            s2 = __dadd_rn(__dmul_rn(c, c), __dmul_rn(d, d));
-            ok2 = (s2 < 1.0) && (s2 > 0.0);
-        }
-        if (ok1 && ok2) {
-            double f = __dsqrt_rn(__ddiv_rn(__dsub_rn(1.0, s1), s2));
-            w = a; x = b; y = __dmul_rn(c, f); zz = __dmul_rn(d, f);
+        for (int t = 0; t < 64; ++t) {
+            const uint64_t u = sm64(h + GOLD * (uint64_t)(t + 1));
+            const int a = (int)(u & 0xFFFFu) - 32768, b = (int)((u >> 16) & 0xFFFFu) - 32768;
+            const int c = (int)((u >> 32) & 0xFFFFu) - 32768, d = (int)((u >> 48) & 0xFFFFu) - 32768;
+            const unsigned n2 = (unsigned)(a * a) + (unsigned)(b * b) + (unsigned)(c * c) + (unsigned)(d * d);
+            if (n2 > 0u && n2 <= (1u << 30)) { w = a; x = b; y = c; z = d; break; }
         }
     }
-    double R[9];
-    R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(zz, zz))));
-    R[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, zz)));
-    R[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, zz), __dmul_rn(w, y)));
-    R[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, zz)));
-    R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(zz, zz))));
-    R[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(y, zz), __dmul_rn(w, x)));
-    R[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, zz), __dmul_rn(w, y)));
-    R[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, zz), __dmul_rn(w, x)));
-    R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
-    const double Q = 16777216.0;
-    for (int r = 0; r < 3; ++r)
-        rows[r] = make_int4(__double2int_rn(__dmul_rn(R[3 * r], Q)), __double2int_rn(__dmul_rn(R[3 * r + 1], Q)),
-                            __double2int_rn(__dmul_rn(R[3 * r + 2], Q)), 0);
+    const long long n = w * w + x * x + y * y + z * z;
+    const long long Q[9] = {w * w + x * x - y * y - z * z, 2 * (x * y - w * z), 2 * (x * z + w * y),
+                            2 * (x * y + w * z), w * w - x * x + y * y - z * z, 2 * (y * z - w * x),
+                            2 * (x * z - w * y), 2 * (y * z + w * x), w * w - x * x - y * y + z * z};
+    int32_t q[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) q[i] = div_round_even(Q[i] * (1LL << VQ_BITS), n);
+    for (int r = 0; r < 3; ++r) rows[r] = make_int4(q[3 * r], q[3 * r + 1], q[3 * r + 2], 0);
 }
 
 // round(X / 2^27), ties to even (X = Rq . vq, 2^48 scale -> 2^21 scale)

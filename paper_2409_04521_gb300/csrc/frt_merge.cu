@@ -5,7 +5,7 @@
 // K = floor(N_ex * N_RT)):
 //   k_mrot    : per cell, the random rotation of the cell's merge sphere for
 //               this step, drawn like an emitter's sphere (key 2^31 + local
-//               cell index);
+//               cell index; exact integer arithmetic);
 //   k_mhist1  : per ray, its content (single-precision sum of its bins, the
 //               quantity ranked) and a histogram of the content's upper 16 bits;
 //   k_mfind   : per simulation, a two-pass radix select of the K-th largest
