@@ -261,11 +261,15 @@ __global__ void __launch_bounds__(256) k_mreduce(MergeArgs A, int pass) {
         const bool on = pass == 1 ? merges(A.sims[s], A.acc[s]) : A.w.sel[SEL_W * s + SEL_STATE] == SEL_PASS2;
         if (!on) continue;
         uint32_t *h = A.w.hist + (long long)s * hrep * HIST_BINS + (i % HIST_BINS);
-        uint32_t sum = h[0];
-        for (int c = 1; c < hrep; ++c) {
-            sum += h[(long long)c * HIST_BINS];
-            h[(long long)c * HIST_BINS] = 0u;
-        }
+        // every copy's count first (independent loads in flight together),
+        // then the clears
+        uint32_t cnt[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) cnt[c] = c < hrep ? h[(long long)c * HIST_BINS] : 0u;
+        uint32_t sum = 0u;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) sum += cnt[c];
+        for (int c = 1; c < hrep; ++c) h[(long long)c * HIST_BINS] = 0u;
         h[0] = sum;
     }
 }
@@ -507,7 +511,9 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
             pk = A.w.tgrp[i];
             if (pk.x != NO_GROUP) key = A.w.tkey[i];
         }
-        const long long slot = pk.x == NO_GROUP ? -1 : (long long)pk.x;
+        long long slot = pk.x == NO_GROUP ? -1 : (long long)pk.x;
+        // a ray alone in its group stays as it is: its sums are never read
+        if (slot >= 0 && A.w.gcnt[slot] < 2u) slot = -1;
         unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
         if (slot >= 0) {
             const uint32_t gm = A.w.gmax[slot];
