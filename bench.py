@@ -226,7 +226,7 @@ def oracle_parity(prob, steps, of, ob, capacity, variant):
     import paper_2409_04521_gb300 as F
     g = F.Simulation(prob, ray_capacity=capacity)
     if variant:
-        g.set_launch(variant["agg"], variant["minb"], variant["blocks_per_sm"])
+        g.set_launch(variant["agg"], variant["minb"], variant["blocks_per_sm"], variant["threads"], variant["slab"])
     for _ in range(steps):
         g.step(prob.dt)
     gf, gb = g.fields(), g.budget()
@@ -289,12 +289,14 @@ def impl_gpu(args, dist):
     if args.variant:
         v = tuple(int(x) for x in args.variant.split(","))
         sim.set_launch(*v)
-        tuned = {"variant": {"agg": v[0], "minb": v[1], "blocks_per_sm": v[2]}, "candidates": 0}
+        v = v + (256, 512)[len(v) - 3:] if len(v) < 5 else v
+        tuned = {"variant": {"agg": v[0], "minb": v[1], "blocks_per_sm": v[2], "threads": v[3], "slab": v[4]},
+                 "candidates": 0}
     elif not args.no_tune:
         from paper_2409_04521_gb300 import autotune
         best, table = autotune.tune(sim, prob)
-        tuned = {"variant": {"agg": best[0], "minb": best[1], "blocks_per_sm": best[2]},
-                 "candidates": len(table)}
+        tuned = {"variant": {"agg": best[0], "minb": best[1], "blocks_per_sm": best[2], "threads": best[3],
+                             "slab": best[4]}, "candidates": len(table)}
 
     def one_sim():
         nonlocal max_rays
@@ -364,7 +366,7 @@ def impl_gpu(args, dist):
             s2 = F.Simulation(prob, ray_capacity=args.capacity)
             if tuned:
                 v = tuned["variant"]
-                s2.set_launch(v["agg"], v["minb"], v["blocks_per_sm"])
+                s2.set_launch(v["agg"], v["minb"], v["blocks_per_sm"], v["threads"], v["slab"])
             for _ in range(prob.nsteps):
                 s2.step(prob.dt)
             f = s2.fields()
@@ -412,7 +414,10 @@ def impl_gpu(args, dist):
                            "ray_capacity": args.capacity, "max_live_rays": max_rays,
                            "parallelism": f"replicas x{dist.ws}",
                            "l2": "working set larger than L2 (ray queues of several GB)",
-                           "precision": "rays/deposits fp32, ionisation update fp64, temperature fp32",
+                           "precision": "rays, deposits, segment lengths fp32; ionisation update in sums of "
+                                        "positive terms with fp32 factors, neutral fraction combined and stored "
+                                        "in fp64; temperature fp32; photon budget fp64 (error against the fp64 "
+                                        "oracle: oracle_parity)",
                            "march_launch": tuned},
                 "sims_per_hour": 3600.0 / (t_max * 1e-3 / args.steps) * dist.ws,
                 "segments_per_sim": segs_all / args.steps / dist.ws,
@@ -485,14 +490,19 @@ def run_batch(args):
     # the autotuner's candidates, each timed on one whole batched run
     from paper_2409_04521_gb300 import autotune
     table = []
-    for v in autotune.CANDIDATES:
-        try:
-            B.set_launch(*v)
-        except F.FlexRTError:
-            continue
-        t0 = time.perf_counter()
-        batched()
-        table.append((time.perf_counter() - t0, v))
+
+    def timed(vs):
+        for v in vs:
+            try:
+                B.set_launch(*v)
+            except F.FlexRTError:
+                continue
+            t0 = time.perf_counter()
+            batched()
+            table.append((time.perf_counter() - t0, v))
+    timed(autotune.CANDIDATES)
+    b3 = min(table)[1][:3]
+    timed([b3 + sh for sh in autotune.SHAPES if sh != (256, 512)])
     best = min(table)[1]
     B.set_launch(*best)
     for _ in range(args.warmup):
@@ -515,7 +525,8 @@ def run_batch(args):
     return {"workload": f"batch{len(probs)}: uneven {sorted(set(p.grid[0] for p in probs))}^3, "
                         f"{args.batch_steps} RT steps each, 3 bins, mfp law, z=7; host inputs to host fields",
             "members": len(probs), "cells": ncell, "emitters": nem,
-            "march_launch": {"agg": best[0], "minb": best[1], "blocks_per_sm": best[2]},
+            "march_launch": {"agg": best[0], "minb": best[1], "blocks_per_sm": best[2], "threads": best[3],
+                             "slab": best[4]},
             "batched": {"sims_per_hour": 3600 * len(probs) / t_b, "seconds": t_b, "segments_per_s": sb / t_b,
                         "runs": len(tb)},
             "plain_loop": {"sims_per_hour": 3600 * len(probs) / t_p, "seconds": t_p, "segments_per_s": sp / t_p,

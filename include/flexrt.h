@@ -277,8 +277,12 @@ flexrt_status flexrt_get_kernel_times(flexrt_ctx *ctx, double ms[4], int64_t lau
  * vector reduction (0 none, 1 groups of equal cells, 2 runs of equal
  * consecutive cells); minb: resident blocks per SM the register budget
  * targets (2..4); blocks_per_sm: persistent blocks launched per SM
- * (0 = occupancy limit).  FLEXRT_E_INVALID if the variant is not built. */
-flexrt_status flexrt_set_launch(flexrt_ctx *ctx, int32_t agg, int32_t minb, int32_t blocks_per_sm);
+ * (0 = occupancy limit); threads: threads per block, 128 or 256 (0 = 256);
+ * slab: queue slots a warp reserves for its output at a time, 32..4096
+ * (0 = 512).  FLEXRT_E_INVALID if the variant is not built or a value is
+ * out of range. */
+flexrt_status flexrt_set_launch(flexrt_ctx *ctx, int32_t agg, int32_t minb, int32_t blocks_per_sm,
+                                int32_t threads, int32_t slab);
 
 /* Message of the context's last failure; with ctx == NULL, of the last failed
  * call without a context (probes) on this host thread. */
@@ -428,7 +432,8 @@ flexrt_status flexrt_batch_get_rays_merged(flexrt_batch *b, int32_t slot, int64_
  * out[3] ray capacity, out[4] queue slots in use by live rays (waits for
  * enqueued work), out[5] free slots. */
 flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[6]);
-flexrt_status flexrt_batch_set_launch(flexrt_batch *b, int32_t agg, int32_t minb, int32_t blocks_per_sm);
+flexrt_status flexrt_batch_set_launch(flexrt_batch *b, int32_t agg, int32_t minb, int32_t blocks_per_sm,
+                                      int32_t threads, int32_t slab);
 const char *flexrt_batch_last_error(const flexrt_batch *b);
 void flexrt_batch_destroy(flexrt_batch *b);
 

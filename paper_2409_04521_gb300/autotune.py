@@ -2,8 +2,9 @@
 
 For a given workload it runs the first RT steps of the simulation once per
 candidate (deposit aggregation scheme, register budget, persistent blocks
-per SM), times the march kernel with CUDA events on the simulation's
-stream, and keeps the fastest.  Results are cached per workload signature
+per SM), then on the fastest of those once per launch shape (threads per
+block, output run length of a warp in queue slots), times the march kernel
+with CUDA events on the simulation's stream, and keeps the fastest.  Results are cached per workload signature
 and device name in ``_build/tune_cache.json``.
 """
 from __future__ import annotations
@@ -19,9 +20,18 @@ from . import flexrt as _f
 CACHE = os.path.join(_build.BUILD, "tune_cache.json")
 _lock = threading.Lock()
 
-# (aggregation, register budget in resident blocks per SM, blocks per SM;
-# 0 = occupancy limit)
-CANDIDATES = [(a, m, 0) for a in (0, 1, 2) for m in (2, 3, 4)] + [(1, 3, 2), (2, 3, 2), (0, 3, 2)]
+# Stage 1: (aggregation, register budget in resident blocks per SM, blocks
+# per SM; 0 = occupancy limit) with the default launch shape.
+BASES = [(a, m, 0) for a in (0, 1, 2) for m in (2, 3, 4)] + [(1, 3, 2), (2, 3, 2), (0, 3, 2)]
+# Stage 2, on the best base: (threads per block, output run length in queue
+# slots); (256, 512) is the default shape.
+SHAPES = [(256, 512), (128, 512), (256, 128), (128, 128), (256, 2048), (128, 2048)]
+CANDIDATES = [b + (256, 512) for b in BASES]
+
+
+def candidates():
+    """Every launch the two-stage search can return."""
+    return [b + sh for b in BASES for sh in SHAPES]
 
 
 def signature(prob, nsteps: int) -> str:
@@ -79,22 +89,29 @@ def tune(sim, prob, nsteps: int = None, candidates=None, use_cache: bool = True,
     key = f"{_device_name()}|{signature(prob, nsteps)}"
     with _lock:
         cache = _load() if use_cache else {}
-    if key in cache:
+    if key in cache and len(cache[key]["best"]) == 5:
         v = tuple(cache[key]["best"])
         sim.set_launch(*v)
         sim.reset()
         return v, cache[key]["table"]
     table = []
-    for v in candidates or CANDIDATES:
-        try:
-            ms, rays = time_variant(sim, prob, nsteps, v)
-        except _f.FlexRTError:
-            continue
-        table.append([list(v), ms, rays])
-        if verbose:
-            print("variant", v, "march ms %.3f" % ms, flush=True)
+
+    def run(vs):
+        for v in vs:
+            try:
+                ms, rays = time_variant(sim, prob, nsteps, v)
+            except _f.FlexRTError:
+                continue
+            table.append([list(v), ms, rays])
+            if verbose:
+                print("variant", v, "march ms %.3f" % ms, flush=True)
+
+    run(candidates or CANDIDATES)
     if not table:
         raise RuntimeError("no march variant could run")
+    if candidates is None:
+        b = tuple(min(table, key=lambda r: r[1])[0])[:3]
+        run([b + sh for sh in SHAPES if sh != (256, 512)])
     best = tuple(min(table, key=lambda r: r[1])[0])
     sim.set_launch(*best)
     sim.reset()

@@ -162,8 +162,9 @@ extern "C" flexrt_status flexrt_get_kernel_times(flexrt_ctx *c, double ms[4], in
     if (!c || !ms || !launches) return FLEXRT_E_INVALID;
     return c->eng.kernel_times(ms, launches, march_rays);
 }
-extern "C" flexrt_status flexrt_set_launch(flexrt_ctx *c, int32_t agg, int32_t minb, int32_t blocks_per_sm) {
-    return c ? c->eng.set_launch(agg, minb, blocks_per_sm) : FLEXRT_E_INVALID;
+extern "C" flexrt_status flexrt_set_launch(flexrt_ctx *c, int32_t agg, int32_t minb, int32_t blocks_per_sm,
+                                           int32_t threads, int32_t slab) {
+    return c ? c->eng.set_launch(agg, minb, blocks_per_sm, threads, slab) : FLEXRT_E_INVALID;
 }
 extern "C" const char *flexrt_last_error(const flexrt_ctx *c) {
     return c ? c->eng.error().c_str() : frt::g_free_err.c_str();
@@ -282,8 +283,9 @@ extern "C" flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[6]) {
     out[5] = b->eng.free_slots();
     return FLEXRT_OK;
 }
-extern "C" flexrt_status flexrt_batch_set_launch(flexrt_batch *b, int32_t agg, int32_t minb, int32_t bps) {
-    return b ? b->eng.set_launch(agg, minb, bps) : FLEXRT_E_INVALID;
+extern "C" flexrt_status flexrt_batch_set_launch(flexrt_batch *b, int32_t agg, int32_t minb, int32_t bps,
+                                                 int32_t threads, int32_t slab) {
+    return b ? b->eng.set_launch(agg, minb, bps, threads, slab) : FLEXRT_E_INVALID;
 }
 extern "C" const char *flexrt_batch_last_error(const flexrt_batch *b) {
     return b ? b->eng.error().c_str() : frt::g_free_err.c_str();

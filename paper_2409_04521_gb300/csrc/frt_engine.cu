@@ -687,7 +687,7 @@ flexrt_status Engine::launch_step() {
 flexrt_status Engine::launch_stage(int stage) {
     const int ms = (int)slots_.size();
     EmitArgs ea{ctl_, sims_, acc_, {q_[0], q_[1]}, qcap_, em_, pixtab_, ltab_, cfg_.nb};
-    MarchArgs ma{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, qcap_, em_, cells_, pixtab_, ltab_};
+    MarchArgs ma{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, qcap_, em_, cells_, pixtab_, ltab_, march_slab_};
     ChemArgs ca{ctl_, sims_, acc_, ms, cells_, rg_, 1};
     const bool prof = profiling_ && !cfg_.use_graph;
     cudaEvent_t e0 = nullptr;
@@ -1030,15 +1030,20 @@ flexrt_status Engine::ionized_volume(int s, double *x_ion) {
     return FLEXRT_OK;
 }
 
-flexrt_status Engine::set_launch(int agg, int minb, int blocks_per_sm) {
-    if (!march_variant_exists(cfg_.nb, agg, minb, ext_variants()) || blocks_per_sm < 0 || blocks_per_sm > 32)
-        return fail(FLEXRT_E_INVALID, "march kernel variant not built");
+flexrt_status Engine::set_launch(int agg, int minb, int blocks_per_sm, int threads, int slab) {
+    if (threads == 0) threads = 256;
+    if (slab == 0) slab = OUT_SLAB;
+    if (!march_variant_exists(cfg_.nb, agg, minb, ext_variants()) || blocks_per_sm < 0 || blocks_per_sm > 32 ||
+        (threads != 128 && threads != 256) || slab < 32 || slab > 4096)
+        return fail(FLEXRT_E_INVALID, "march kernel variant not built or launch shape out of range");
     CK(march_prepare(cfg_.nb, agg, minb, (int)slots_.size(), ext_variants()));
-    const int lim = march_max_blocks_per_sm(cfg_.nb, agg, minb, march_threads_, (int)slots_.size(), ext_variants());
+    const int lim = march_max_blocks_per_sm(cfg_.nb, agg, minb, threads, (int)slots_.size(), ext_variants());
     if (lim < 1) return fail(FLEXRT_E_INVALID, "variant cannot be resident");
     const int bps = blocks_per_sm == 0 ? lim : std::min(blocks_per_sm, lim);
     march_agg_ = agg;
     march_minb_ = minb;
+    march_threads_ = threads;
+    march_slab_ = slab;
     march_blocks_ = sm_count_ * bps;
     graph_dirty_ = true;
     return FLEXRT_OK;

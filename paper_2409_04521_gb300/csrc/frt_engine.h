@@ -95,7 +95,7 @@ class Engine {
     flexrt_status save_state(int slot, void *buf, int64_t cap, int64_t *bytes);
     flexrt_status load_state(int slot, const void *buf, int64_t bytes);
     long long device_bytes() const { return alloc_bytes_; }
-    flexrt_status set_launch(int agg, int minb, int blocks_per_sm);
+    flexrt_status set_launch(int agg, int minb, int blocks_per_sm, int threads, int slab);
     flexrt_status profile(bool on);
     flexrt_status kernel_times(double ms[4], int64_t launches[4], int64_t *rays);
     int active_count() const;
@@ -146,7 +146,7 @@ class Engine {
     std::vector<Slot> slots_;
     long long steps_taken_ = 0;
 
-    int march_agg_ = 0, march_minb_ = 3, march_blocks_ = 1, march_threads_ = 256;
+    int march_agg_ = 0, march_minb_ = 3, march_blocks_ = 1, march_threads_ = 256, march_slab_ = OUT_SLAB;
     int chem_blocks_ = 1, emit_blocks_ = 1, sm_count_ = 1;
 
     int32_t *h_err_ = nullptr;

@@ -28,6 +28,7 @@ struct MarchArgs {
     Cells cells;
     const int4 *pixtab;
     int ltab;
+    int slab;                // output slots a warp reserves at once (run length, 32..4096)
 };
 
 struct MergeArgs {

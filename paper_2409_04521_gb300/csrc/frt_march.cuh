@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(256, MINB) k_march(MarchArgs A) {
                     const unsigned iters_left = (nr - i + stride - 1u) / stride;
                     const int ahead = iters_left < 16u ? (int)iters_left : 16;
                     const int rate = (w_out + tot + w_it) / (w_it + 1);
-                    const int guess = rate * ahead < OUT_SLAB ? rate * ahead : OUT_SLAB;
+                    const int guess = rate * ahead < A.slab ? rate * ahead : A.slab;
                     const int want = need > guess ? need : guess;
                     unsigned long long nb64 = 0;
                     if (lane == 0) nb64 = atomicAdd(out_cnt, (unsigned long long)want);

@@ -118,7 +118,7 @@ def lib():
             L.flexrt_load_state.argtypes = [vp, vp, C.c_int64]
             L.flexrt_get_device_bytes.argtypes = [vp, P(C.c_int64)]
             L.flexrt_get_kernel_times.argtypes = [vp, P(C.c_double), P(C.c_int64), P(C.c_int64)]
-            L.flexrt_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
+            L.flexrt_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
             L.flexrt_last_error.argtypes = [vp]
             L.flexrt_last_error.restype = C.c_char_p
             L.flexrt_destroy.argtypes = [vp]
@@ -139,7 +139,7 @@ def lib():
             L.flexrt_batch_get_rays_merged.argtypes = [vp, C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int32),
                                                        P(C.c_int32), P(C.c_int64), P(C.c_double), P(C.c_int64)]
             L.flexrt_batch_info.argtypes = [vp, P(C.c_int64)]
-            L.flexrt_batch_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
+            L.flexrt_batch_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
             L.flexrt_batch_last_error.argtypes = [vp]
             L.flexrt_batch_last_error.restype = C.c_char_p
             L.flexrt_batch_destroy.argtypes = [vp]
@@ -328,8 +328,9 @@ class Batch:
         return dict(active=int(o[0]), cells_free=int(o[1]), emitters_free=int(o[2]), ray_capacity=int(o[3]),
                     queue_used=int(o[4]), slots_free=int(o[5]))
 
-    def set_launch(self, agg, minb, blocks_per_sm=0):
-        self._check(lib().flexrt_batch_set_launch(self._h, int(agg), int(minb), int(blocks_per_sm)))
+    def set_launch(self, agg, minb, blocks_per_sm=0, threads=0, slab=0):
+        self._check(lib().flexrt_batch_set_launch(self._h, int(agg), int(minb), int(blocks_per_sm), int(threads),
+                                                  int(slab)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -477,8 +478,9 @@ class Simulation:
         names = ("emit", "march", "chem", "merge")
         return dict(zip(names, ms)), dict(zip(names, ln)), int(rays[0])
 
-    def set_launch(self, agg: int, minb: int, blocks_per_sm: int = 0):
-        _check(lib().flexrt_set_launch(self._h, int(agg), int(minb), int(blocks_per_sm)), self._h)
+    def set_launch(self, agg: int, minb: int, blocks_per_sm: int = 0, threads: int = 0, slab: int = 0):
+        _check(lib().flexrt_set_launch(self._h, int(agg), int(minb), int(blocks_per_sm), int(threads), int(slab)),
+               self._h)
 
     def close(self):
         if getattr(self, "_h", None):

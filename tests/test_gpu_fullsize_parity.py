@@ -50,29 +50,32 @@ def _compare(name, prob, g, ref, step, variant, T_rtol=2e-3):
                   straddles=oc["near_threshold"], rays_one_side=nd)
 
 
-def _variant_run(name, prob, variants, checkpoints, capacity):
+def _variant_run(name, prob, variants, checkpoints, capacity, last_only=()):
     ref = _oracle_checkpoints(prob, checkpoints)
     for v in variants:
         g = F.Simulation(prob, ray_capacity=capacity, keep_diagnostics=True)
         g.set_launch(*v)
         for s in range(1, max(checkpoints) + 1):
             g.step(prob.dt)
-            if s in checkpoints:
+            if s in checkpoints and (v not in last_only or s == max(checkpoints)):
                 _compare(name, prob, g, ref[s], s, v)
         g.close()
 
 
 def test_cosmo16_full_size_matches_oracle():
     # 128^3, 16 sources, 4 bins, temperature evolution: the bench workload,
-    # its first 15 RT steps, every candidate launch of the march
+    # its first 15 RT steps, every launch of the march the autotuner can
+    # choose (the non-default launch shapes at the last checkpoint)
     prob = W.cosmo16()
-    _variant_run("cosmo16 128^3", prob, autotune.CANDIDATES, (5, 10, 15), 40_000_000)
+    shaped = [v for v in autotune.candidates() if v not in autotune.CANDIDATES]
+    _variant_run("cosmo16 128^3", prob, autotune.CANDIDATES + shaped, (5, 10, 15), 40_000_000, last_only=shaped)
 
 
 def test_cosmo20k_full_size_matches_oracle():
     # 200^3, 2e4 sources, sub-grid mean free path law, 3 bins: first 6 steps
     prob = W.cosmo20k()
-    _variant_run("cosmo20k 200^3", prob, [(0, 2, 0), (0, 4, 0), (1, 3, 0)], (3, 6), 30_000_000)
+    _variant_run("cosmo20k 200^3", prob, [(0, 2, 0), (0, 4, 0), (1, 3, 0), (0, 4, 0, 128, 128)], (3, 6),
+                 30_000_000)
 
 
 def test_batch64_member_96_matches_oracle():
@@ -83,7 +86,7 @@ def test_batch64_member_96_matches_oracle():
     assert big
     k = big[0]
     ref = _oracle_checkpoints(members[k], (6, 12))
-    for v in [(0, 2, 0), (0, 4, 0)]:
+    for v in [(0, 2, 0), (0, 4, 0), (0, 3, 2, 128, 2048)]:
         B = F.Batch(max_sims=16, max_grid=96, nbins=3, ray_capacity=1 << 24, emitter_capacity=1024,
                     keep_diagnostics=True)
         B.set_launch(*v)
