@@ -353,7 +353,8 @@ typedef struct {
  * n host-given live rays (const in) of one simulation as they stand after the
  * march of step p->step.  Writes up to cap of the rays left live to out and
  * their number to *n_out, in the order the kernels leave them in the queue
- * (merged rays in their leaders' slots; the followers' slots, empty, are
+ * (the rays that did not merge in their slots, then the merged rays, which
+ * the merge appends; the slots of the rays that merged, empty, are
  * skipped).  Allocates and frees its own device scratch.  Synchronous. */
 flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t n, const flexrt_probe_rays *in,
                                  int64_t cap, flexrt_probe_rays *out, int64_t *n_out);

@@ -407,48 +407,53 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     Ctl ctl;
     std::memset(&ctl, 0, sizeof(ctl));
     ctl.par = 0; ctl.cnt[1] = n; ctl.n_ranges = 1; ctl.ncell_active = ncell;
-    const long long m = std::max<long long>(n, 1);
+    // the queue holds the n rays and the merged rays appended after them
+    // (each stands for two or more of the n)
+    const long long m = std::max<long long>(n, 1), mq = m + m / 2 + 1;
+    // per-block lists of the merge passes: each block's run starts at a
+    // multiple of 256 past its first queue slot
+    const long long ml = m + (long long)MERGE_MAX_BLOCKS * 256;
     const int gw = 12 + 4 * ((nb + 4) / 4);
     DevBuf<Ctl> dctl;
     DevBuf<SimDev> dsim;
     DevBuf<SimAcc> dacc;
-    DevBuf<uint32_t> qpl[2], qem[2], qma[2], hist, sel, tkey, gcnt, gmax, lead_i, lead_slot;
-    DevBuf<uint4> tgrp;
-    DevBuf<int32_t> qbi[2], qd[2], qm[2], tsim, rsim;
+    DevBuf<uint32_t> qpl[2], qem[2], qma[2], hist, sel, tkey, cand, ckey, lead_slot, bcnt, bled;
+    DevBuf<uint4> tgrp, gcm;
+    DevBuf<int32_t> qbi[2], qd[2], qm[2], tsim, rsim, lead_sim;
     DevBuf<float> qph[2], qthr[2], grp, n0;
     DevBuf<int4> ecell, rot;
     DevBuf<long long> pref, cell0;
     bool ok = dctl.alloc(1) == cudaSuccess && dsim.alloc(1) == cudaSuccess && dacc.alloc(1) == cudaSuccess;
     for (int k = 0; k < 2 && ok; ++k)
-        ok = qpl[k].alloc(m) == cudaSuccess && qem[k].alloc(m) == cudaSuccess && qma[k].alloc(m) == cudaSuccess &&
-             qbi[k].alloc(m) == cudaSuccess && qd[k].alloc(3 * m) == cudaSuccess && qm[k].alloc(3 * m) == cudaSuccess &&
-             qph[k].alloc(nb * m) == cudaSuccess && qthr[k].alloc(m) == cudaSuccess;
+        ok = qpl[k].alloc(mq) == cudaSuccess && qem[k].alloc(mq) == cudaSuccess && qma[k].alloc(mq) == cudaSuccess &&
+             qbi[k].alloc(mq) == cudaSuccess && qd[k].alloc(3 * mq) == cudaSuccess && qm[k].alloc(3 * mq) == cudaSuccess &&
+             qph[k].alloc(nb * mq) == cudaSuccess && qthr[k].alloc(mq) == cudaSuccess;
     ok = ok && hist.alloc(HIST_BINS) == cudaSuccess && sel.alloc(8) == cudaSuccess && tkey.alloc(m) == cudaSuccess &&
-         tsim.alloc(m) == cudaSuccess && gcnt.alloc(ncell * ndir) == cudaSuccess &&
-         gmax.alloc(ncell * ndir) == cudaSuccess && tgrp.alloc(m) == cudaSuccess &&
+         tsim.alloc(m) == cudaSuccess && gcm.alloc(ncell * ndir) == cudaSuccess && tgrp.alloc(ml) == cudaSuccess &&
+         cand.alloc(ml) == cudaSuccess && ckey.alloc(ml) == cudaSuccess && bcnt.alloc(MERGE_MAX_BLOCKS) == cudaSuccess &&
+         bled.alloc(MERGE_MAX_BLOCKS) == cudaSuccess &&
          grp.alloc(ncell * ndir * gw) == cudaSuccess && rot.alloc(3 * ncell) == cudaSuccess &&
          ecell.alloc(std::max(p->n_emitters, 1)) == cudaSuccess && n0.alloc(std::max(p->n_emitters, 1)) == cudaSuccess &&
          pref.alloc(2) == cudaSuccess && cell0.alloc(1) == cudaSuccess && rsim.alloc(1) == cudaSuccess &&
-         lead_i.alloc(m + MERGE_MAX_BLOCKS * 8 * 128) == cudaSuccess &&
-         lead_slot.alloc(m + MERGE_MAX_BLOCKS * 8 * 128) == cudaSuccess;
+         lead_slot.alloc(ml) == cudaSuccess && lead_sim.alloc(ml) == cudaSuccess;
     if (!ok) return free_fail(FLEXRT_E_OOM, "probe_merge: device allocation failed");
     // queue layout: structure of arrays, photons bin-major
     auto queue = [&](int k) {
         Queue q{};
         q.pl = qpl[k].p; q.em = qem[k].p; q.bi = qbi[k].p;
-        q.dx = qd[k].p; q.dy = qd[k].p + m; q.dz = qd[k].p + 2 * m;
-        for (int b = 0; b < nb; ++b) q.ph[b] = qph[k].p + b * m;
-        q.mx = qm[k].p; q.my = qm[k].p + m; q.mz = qm[k].p + 2 * m;
+        q.dx = qd[k].p; q.dy = qd[k].p + mq; q.dz = qd[k].p + 2 * mq;
+        for (int b = 0; b < nb; ++b) q.ph[b] = qph[k].p + b * mq;
+        q.mx = qm[k].p; q.my = qm[k].p + mq; q.mz = qm[k].p + 2 * mq;
         q.ma = qma[k].p; q.mthr = qthr[k].p;
         return q;
     };
     const Queue q0 = queue(0), q1 = queue(1);
-    std::vector<int32_t> d3(3 * m), m3(3 * m);
-    std::vector<float> ph(nb * m);
-    std::vector<uint32_t> ma(m);
+    std::vector<int32_t> d3(3 * mq), m3(3 * mq);
+    std::vector<float> ph(nb * mq);
+    std::vector<uint32_t> ma(mq);
     for (int64_t i = 0; i < n; ++i) {
-        for (int a = 0; a < 3; ++a) { d3[a * m + i] = in->dir[3 * i + a]; m3[a * m + i] = in->pos[3 * i + a]; }
-        for (int b = 0; b < nb; ++b) ph[b * m + i] = in->photons[(size_t)nb * i + b];
+        for (int a = 0; a < 3; ++a) { d3[a * mq + i] = in->dir[3 * i + a]; m3[a * mq + i] = in->pos[3 * i + a]; }
+        for (int b = 0; b < nb; ++b) ph[b * mq + i] = in->photons[(size_t)nb * i + b];
         ma[i] = in->aux[i] & 0x8000ffffu;              // simulation 0
     }
     std::vector<int4> ec(std::max(p->n_emitters, 1));
@@ -461,12 +466,12 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     };
     ok = up(dctl.p, &ctl, sizeof(ctl)) && up(dsim.p, &h, sizeof(h)) && up(dacc.p, &acc, sizeof(acc)) &&
          up(q1.pl, in->pixlev, n * 4) && up(q1.em, in->emitter, n * 4) && up(q1.bi, in->birth, n * 4) &&
-         up(qd[1].p, d3.data(), 3 * m * 4) && up(qm[1].p, m3.data(), 3 * m * 4) && up(qph[1].p, ph.data(), nb * m * 4) &&
-         up(q1.ma, ma.data(), m * 4) && up(q1.mthr, in->thr, n * 4) && up(ecell.p, ec.data(), ec.size() * sizeof(int4)) &&
+         up(qd[1].p, d3.data(), 3 * mq * 4) && up(qm[1].p, m3.data(), 3 * mq * 4) &&
+         up(qph[1].p, ph.data(), nb * mq * 4) && up(q1.ma, ma.data(), mq * 4) && up(q1.mthr, in->thr, n * 4) && up(ecell.p, ec.data(), ec.size() * sizeof(int4)) &&
          up(n0.p, p->emitter_n0, p->n_emitters * sizeof(float)) && up(pref.p, pr, sizeof(pr)) &&
          up(cell0.p, &c0, sizeof(c0)) && up(rsim.p, &s0, sizeof(s0));
     ok = ok && cudaMemset(hist.p, 0, HIST_BINS * 4) == cudaSuccess && cudaMemset(sel.p, 0, 32) == cudaSuccess &&
-         cudaMemset(gcnt.p, 0, ncell * ndir * 4) == cudaSuccess && cudaMemset(gmax.p, 0, ncell * ndir * 4) == cudaSuccess &&
+         cudaMemset(gcm.p, 0, ncell * ndir * 16) == cudaSuccess &&
          cudaMemset(grp.p, 0, (size_t)ncell * ndir * gw * 4) == cudaSuccess;
     if (!ok) return free_fail(FLEXRT_E_CUDA, "probe_merge: upload failed");
     Emitters em{};
@@ -474,29 +479,29 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     Ranges rg{pref.p, cell0.p, rsim.p};
     MergeWork w{};
     w.hist = hist.p; w.sel = sel.p; w.tkey = tkey.p; w.tsim = tsim.p;
-    w.grp = grp.p; w.gcnt = gcnt.p; w.gmax = gmax.p; w.tgrp = tgrp.p; w.rot = rot.p; w.ndir = ndir; w.grp_w = gw;
-    w.hrep = 1; w.lead_i = lead_i.p; w.lead_slot = lead_slot.p;
-    w.lead_cap = m + MERGE_MAX_BLOCKS * 8 * 128;
-    MergeArgs a{dctl.p, dsim.p, dacc.p, 1, {q0, q1}, em, rg, tab, lt, w, nb};
+    w.grp = grp.p; w.gcm = gcm.p; w.cand = cand.p; w.ckey = ckey.p; w.tgrp = tgrp.p; w.rot = rot.p; w.ndir = ndir;
+    w.grp_w = gw; w.hrep = 1; w.lead_slot = lead_slot.p; w.lead_sim = lead_sim.p;
+    w.bcnt = bcnt.p; w.bled = bled.p; w.lead_cap = ml;
+    MergeArgs a{dctl.p, dsim.p, dacc.p, 1, {q0, q1}, em, rg, tab, lt, w, nb, mq};
     if (launch_merge(a, sms, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
         return free_fail(FLEXRT_E_CUDA, "probe_merge: kernels failed");
     Ctl hc;
     if (cudaMemcpy(&hc, dctl.p, sizeof(hc), cudaMemcpyDeviceToHost) != cudaSuccess)
         return free_fail(FLEXRT_E_CUDA, "probe_merge: read-back failed");
-    // the rays stay in queue 1; the merge leaves holes where its followers
-    // were, skipped here
+    // the rays stay in queue 1; the merge leaves holes where its groups'
+    // members were (skipped here) and appends the merged rays
     const int k = 1;
-    const long long cnt = std::min<long long>(hc.cnt[1], m);
-    std::vector<uint32_t> opl(m), oem(m), oma(m);
-    std::vector<int32_t> obi(m), od(3 * m), om(3 * m);
-    std::vector<float> oph(nb * m), othr(m);
+    const long long cnt = std::min<long long>(hc.cnt[1], mq);
+    std::vector<uint32_t> opl(mq), oem(mq), oma(mq);
+    std::vector<int32_t> obi(mq), od(3 * mq), om(3 * mq);
+    std::vector<float> oph(nb * mq), othr(mq);
     auto down = [](void *dst, const void *src, size_t bytes) {
         return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
     };
     const Queue qq = k ? q1 : q0;
-    ok = down(opl.data(), qq.pl, m * 4) && down(oem.data(), qq.em, m * 4) && down(obi.data(), qq.bi, m * 4) &&
-         down(od.data(), qd[k].p, 3 * m * 4) && down(om.data(), qm[k].p, 3 * m * 4) &&
-         down(oph.data(), qph[k].p, nb * m * 4) && down(oma.data(), qq.ma, m * 4) && down(othr.data(), qq.mthr, m * 4);
+    ok = down(opl.data(), qq.pl, mq * 4) && down(oem.data(), qq.em, mq * 4) && down(obi.data(), qq.bi, mq * 4) &&
+         down(od.data(), qd[k].p, 3 * mq * 4) && down(om.data(), qm[k].p, 3 * mq * 4) &&
+         down(oph.data(), qph[k].p, nb * mq * 4) && down(oma.data(), qq.ma, mq * 4) && down(othr.data(), qq.mthr, mq * 4);
     if (!ok) return free_fail(FLEXRT_E_CUDA, "probe_merge: read-back failed");
     long long o = 0;
     for (long long i = 0; i < cnt; ++i) {
@@ -507,10 +512,10 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
             out->emitter[o] = oem[i];
             out->birth[o] = obi[i];
             for (int a2 = 0; a2 < 3; ++a2) {
-                out->dir[3 * o + a2] = od[a2 * m + i];
-                out->pos[3 * o + a2] = mg ? om[a2 * m + i] : 0;
+                out->dir[3 * o + a2] = od[a2 * mq + i];
+                out->pos[3 * o + a2] = mg ? om[a2 * mq + i] : 0;
             }
-            for (int b = 0; b < nb; ++b) out->photons[(size_t)nb * o + b] = oph[b * m + i];
+            for (int b = 0; b < nb; ++b) out->photons[(size_t)nb * o + b] = oph[b * mq + i];
             out->aux[o] = mg ? (oma[i] & 0x8000ffffu) : 0u;
             out->thr[o] = mg ? othr[i] : 0.0f;
         }

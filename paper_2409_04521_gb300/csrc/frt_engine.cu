@@ -244,27 +244,29 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
 #undef ALLOC
     if (mrg) {
         // merge scratch (Sec. 3.3): histograms and selections per slot, rank
-        // content / simulation per queue slot, group sums and sizes per
-        // (cell, merge pixel), rotation rows per cell, the list of leaders
+        // content / simulation per queue slot, group sums, sizes, largest
+        // contents and leaders per (cell, merge pixel), rotation rows per
+        // cell, the per-block candidate and merged-ray lists (a block's run
+        // starts at a multiple of 256 past its first queue slot) and counts
         mw_.ndir = 12 << (2 * cfg_.merge_l_max);
         mw_.grp_w = 12 + 4 * ((cfg_.nb + 4) / 4);   // 6 integer sums, photons and threshold
         const long long ngrp = nc * (long long)mw_.ndir;
         if (ngrp >= (1LL << 31)) return fail(FLEXRT_E_INVALID, "cells x merge directions must stay below 2^31");
         mw_.hrep = std::max(1, std::min(32, 64 / ms));
-        // leader list: at most one entry per queue slot plus each group-pass
-        // warp's unused run
-        mw_.lead_cap = cap + (long long)MERGE_MAX_BLOCKS * 8 * 128;
+        mw_.lead_cap = cap + (long long)MERGE_MAX_BLOCKS * 256;
+        const size_t nl = (size_t)mw_.lead_cap;
         const size_t sz[] = {(size_t)ms * mw_.hrep * HIST_BINS * 4, (size_t)ms * 32, (size_t)cap * 4,
-                             (size_t)cap * 4, (size_t)ngrp * mw_.grp_w * 4, (size_t)ngrp * 4,
-                             (size_t)nc * 48, (size_t)mw_.lead_cap * 4, (size_t)mw_.lead_cap * 4,
-                             (size_t)ngrp * 4, (size_t)cap * 16};
+                             (size_t)cap * 4, (size_t)ngrp * mw_.grp_w * 4, (size_t)ngrp * 16,
+                             (size_t)nc * 48, nl * 4, nl * 4, nl * 4, nl * 4, nl * 16,
+                             (size_t)MERGE_MAX_BLOCKS * 4, (size_t)MERGE_MAX_BLOCKS * 4};
         size_t tot = 0;
         for (size_t v : sz) tot += (v + 255) & ~(size_t)255;
         if (dev_alloc(&mwmem_, tot) != cudaSuccess) return fail(FLEXRT_E_OOM, "merge scratch allocation failed");
         char *p = (char *)mwmem_;
         void **dst[] = {(void **)&mw_.hist, (void **)&mw_.sel, (void **)&mw_.tkey, (void **)&mw_.tsim,
-                        (void **)&mw_.grp, (void **)&mw_.gcnt, (void **)&mw_.rot, (void **)&mw_.lead_i,
-                        (void **)&mw_.lead_slot, (void **)&mw_.gmax, (void **)&mw_.tgrp};
+                        (void **)&mw_.grp, (void **)&mw_.gcm, (void **)&mw_.rot, (void **)&mw_.cand,
+                        (void **)&mw_.ckey, (void **)&mw_.lead_slot, (void **)&mw_.lead_sim, (void **)&mw_.tgrp,
+                        (void **)&mw_.bcnt, (void **)&mw_.bled};
         static_assert(sizeof(sz) / sizeof(sz[0]) == sizeof(dst) / sizeof(dst[0]), "merge scratch layout");
         for (size_t k = 0; k < sizeof(sz) / sizeof(sz[0]); ++k) { *dst[k] = p; p += (sz[k] + 255) & ~(size_t)255; }
         if (cap >= (1LL << 32)) return fail(FLEXRT_E_INVALID, "merging needs fewer than 2^32 queue slots");
@@ -724,7 +726,7 @@ flexrt_status Engine::launch_stage(int stage) {
         return FLEXRT_OK;
     }
     if (merge_built()) {
-        MergeArgs ga{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, em_, rg_, pixtab_, ltab_, mw_, cfg_.nb};
+        MergeArgs ga{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, em_, rg_, pixtab_, ltab_, mw_, cfg_.nb, qcap_};
         tic();
         CK(launch_merge(ga, sm_count_, st_));
         toc(3);
@@ -828,6 +830,14 @@ flexrt_status Engine::reset_all() {
     CK(cudaStreamSynchronize(st_));
     latched_ = FLEXRT_OK;
     err_pending_ = false;
+    int32_t derr = 0;
+    CK(cudaMemcpy(&derr, &ctl_->err, sizeof(derr), cudaMemcpyDeviceToHost));
+    if (derr && mwmem_) {
+        // a step that failed may have stopped inside the merge, with groups
+        // not cleared: clear the whole merge scratch
+        auto it = alloc_sizes_.find(mwmem_);
+        if (it != alloc_sizes_.end()) CK(cudaMemset(mwmem_, 0, it->second));
+    }
     CK(cudaMemset(ctl_, 0, offsetof(Ctl, emit_total)));   // counts, parity, error
     for (int s = 0; s < (int)slots_.size(); ++s) {
         Slot &sl = slots_[s];

@@ -43,6 +43,7 @@ struct MergeArgs {
     int ltab;
     MergeWork w;
     int nbq;                 // photon bins of the queue layout
+    long long cap;           // queue slots (merged rays are appended)
 };
 
 struct ChemArgs {

@@ -11,21 +11,28 @@
 //   k_mfind   : per simulation, a two-pass radix select of the K-th largest
 //               content T_ref (the largest when K = 0): with K > 0 every ray
 //               at least that bright is exempt;
-//   k_mhist2  : per ray in the selected upper bin, a histogram of the lower bits;
-//   k_mgroup  : per non-exempt ray, its end cell and merge pixel; a group slot
-//               per (cell, pixel) takes its photons and threshold (vector
-//               reductions), the largest member content and the ray's arrival
-//               rank: rank 0 leads the group and is listed, the others leave
-//               the queue (their slots become holes); the ray's group slot and
-//               its end point, distance and level are kept per queue slot;
-//   k_mweight : per grouped ray, its photon weight -- the content on a grid of
-//               2^-28 of the power of two above its group's largest content,
-//               truncated, at least 1 -- and the weighted end point, distance
-//               and level as exact 64-bit integer sums, so the photon-weighted
-//               means are exact quotients of sums that do not depend on the
-//               summation order, to 2^-27 of the group's brightest member;
-//   k_memit   : per listed leader: it overwrites its own slot with the merged
-//               ray (means rounded once) and clears the group.
+//   k_mhist2  : per ray in the selected upper bin, a histogram of the lower
+//               bits; and the candidate list, the rays that can still merge
+//               (those at most in T_ref's upper bin), so that the passes
+//               below run over candidates only, with whole warps;
+//   k_mgroup  : per non-exempt candidate, its end cell and merge pixel; a
+//               group slot per (cell, pixel) takes its photons and threshold
+//               (vector reductions), the largest member content and the ray's
+//               arrival rank: rank 0 leads the group, the others leave the
+//               queue (their slots become holes); the candidate's group slot,
+//               end point, distance and level are kept per candidate;
+//   k_mweight : per candidate in a group of two or more, its photon weight --
+//               the content on a grid of 2^-28 of the power of two above its
+//               group's largest content, truncated, at least 1 -- and the
+//               weighted end point, distance and level as exact 64-bit
+//               integer sums, so the photon-weighted means are exact quotients
+//               of sums that do not depend on the summation order, to 2^-27 of
+//               the group's brightest member; each group's leader leaves a
+//               hole too and takes the next entry of the merged-ray list; a
+//               ray alone in its group stays and clears the group;
+//   k_memit   : per entry of that list, the merged ray (means rounded once),
+//               appended densely after the march's output, and the group
+//               cleared for the next step.
 // The holes stay in the queue: the next march skips them and writes its
 // survivors densely into the other queue, so no compaction pass is needed.
 // Contents are non-negative floats, so their bit patterns order as unsigned
@@ -68,14 +75,13 @@ MarchFn march_fn_merge(int nb, int agg, int minb) {
 
 namespace {
 
-// per-simulation selection words: state, upper bits, rays above, T_ref bits, any exempt
-constexpr int SEL_STATE = 0, SEL_HIGH = 1, SEL_ABOVE = 2, SEL_T = 3, SEL_EXEMPT = 4, SEL_W = 8;
+// per-simulation selection words: state, upper bits, rays above, T_ref bits,
+// any exempt, rays removed by this step's merge
+constexpr int SEL_STATE = 0, SEL_HIGH = 1, SEL_ABOVE = 2, SEL_T = 3, SEL_EXEMPT = 4, SEL_DROP = 5, SEL_W = 8;
 constexpr uint32_t SEL_OFF = 0, SEL_PASS2 = 1, SEL_DONE = 2;
 constexpr int WBITS = 28;                    // merge weights below 2^28
 constexpr uint32_t NO_GROUP = 0xffffffffu;   // a queue slot that is in no group
 constexpr int GSUMS = 6;                     // integer sums: weight, weighted x, y, z, distance, level
-constexpr int LEAD_SLAB = 128;               // leader-list entries a warp takes at once
-constexpr uint32_t NO_LEADER = 0xffffffffu;  // an unused leader-list entry
 
 // num / den rounded to nearest, ties to even, for num < 2^62 and a
 // quotient below 2^22 (positions within a cell, distances, levels): a
@@ -110,18 +116,13 @@ __device__ __forceinline__ int ray_sim(const Queue &q, const Emitters &em, long 
     return (e & MERGED_BIT) ? (int)((q.ma[i] >> 16) & 0x7fffu) : __ldg(&em.cell[e]).w;
 }
 
-// The contiguous queue slots [c0, c1) a warp owns in the group pass (the
-// march writes a parent's children next to each other: one warp sees them
-// together and combines their group sums).
-__device__ __forceinline__ long long warp_chunk_len(long long n, long long nwarps) {
-    return ((n + 31) / 32 + nwarps - 1) / nwarps * 32;
-}
-__device__ __forceinline__ void warp_chunk(long long n, long long &c0, long long &c1) {
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long long per = warp_chunk_len(n, nw);
-    c0 = min(w * per, n);
-    c1 = min(c0 + per, n);
+// whether a block of a pass with barriers runs: the control words are read
+// once, by one thread, so that every thread of the block takes the same
+// branch (another block may set the error word meanwhile)
+__device__ __forceinline__ bool block_runs(const Ctl *C, bool need_merged, int *s_flag) {
+    if (threadIdx.x == 0) *s_flag = C->err == 0 && (!need_merged || C->merged != 0);
+    __syncthreads();
+    return *s_flag != 0;
 }
 
 // inclusive scan of one value per thread over a block of 1024 threads
@@ -188,7 +189,6 @@ __global__ void __launch_bounds__(256) k_mrot(MergeArgs A) {
     for (int i = threadIdx.x; i <= nrng; i += blockDim.x) s_pref[i] = A.rg.pref[i];
     for (int i = threadIdx.x; i < nrng; i += blockDim.x) { s_cell0[i] = A.rg.cell0[i]; s_sim[i] = A.rg.sim[i]; }
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->mlead = 0ull;
     if (C->err) return;
     const long long n = C->ncell_active;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -316,52 +316,104 @@ __global__ void __launch_bounds__(1024) k_mfind(MergeArgs A, int pass) {
     for (int k = threadIdx.x; k < HIST_BINS; k += blockDim.x) hist[k] = 0u;   // ready for the next pass
 }
 
+// The candidate and merged-ray lists are built without a global counter:
+// block b of the merge passes (all launched with the same grid) owns the
+// queue slots [b ch, (b + 1) ch) and lists their candidates from b ch on, in
+// queue order, and later its merged rays the same way; the per-block counts
+// give each block's place in the queue's appended run.
+__device__ __forceinline__ long long block_chunk(long long n) {
+    const long long g = gridDim.x;
+    return ((n + g - 1) / g + 255) & ~255LL;
+}
+
+// Exclusive positions, within a window of the block's 256 threads, of the
+// threads whose flag is set; *total gets the window's count.  Three barriers:
+// every thread of the block calls it.
+__device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t *s_wofs, uint32_t *total) {
+    const int lane = lane_id(), wid = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(FULL, flag);
+    if (lane == 0) s_wofs[wid] = (uint32_t)__popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t c = s_wofs[k];
+            s_wofs[k] = t;
+            t += c;
+        }
+        s_wofs[8] = t;
+    }
+    __syncthreads();
+    const uint32_t r = s_wofs[wid] + (uint32_t)__popc(m & ((1u << lane) - 1u));
+    *total = s_wofs[8];
+    __syncthreads();                               // the words are reused by the next window
+    return r;
+}
+
+// per ray in the selected upper bin: a histogram of the lower bits; and the
+// block's candidate list (the march writes a parent's children next to each
+// other, and the group pass combines the sums of neighbours in the list)
 __global__ void __launch_bounds__(256) k_mhist2(MergeArgs A) {
-    const Ctl *C = A.ctl;
-    if (C->err) return;
+    __shared__ uint32_t s_wofs[9];
+    __shared__ int s_on;
+    Ctl *C = A.ctl;
+    if (!block_runs(C, false, &s_on)) return;
     const int par = C->par;
     const long long n = C->cnt[par ^ 1];
-    const long long nr = (n + 31) & ~31LL;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += (long long)gridDim.x * blockDim.x) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->mbase = n;
+    const long long ch = block_chunk(n), b0 = blockIdx.x * ch, b1 = min(n, b0 + ch);
+    uint32_t run = 0;                              // candidates listed so far (block-uniform)
+    for (long long w0 = b0; w0 < b1; w0 += 256) {
+        const long long i = w0 + threadIdx.x;
         long long bin = -1;
-        if (i < n) {
+        bool cand = false;
+        uint32_t key = 0;
+        if (i < b1) {
             const int sim = A.w.tsim[i];
             if (sim >= 0) {
                 const uint32_t *sel = A.w.sel + SEL_W * sim;
-                const uint32_t key = A.w.tkey[i];
-                if (sel[SEL_STATE] == SEL_PASS2 && (key >> 16) == sel[SEL_HIGH])
-                    bin = hist_row(A.w, sim) + (key & 0xffffu);
+                key = A.w.tkey[i];
+                if (sel[SEL_STATE] == SEL_PASS2) {
+                    const uint32_t hi = key >> 16, high = sel[SEL_HIGH];
+                    if (hi == high) bin = hist_row(A.w, sim) + (key & 0xffffu);
+                    cand = !sel[SEL_EXEMPT] || hi <= high;
+                }
             }
         }
         hist_add(A.w.hist, bin);
+        uint32_t tot;
+        const uint32_t r = block_rank(cand, s_wofs, &tot);
+        if (cand) {
+            A.w.cand[b0 + run + r] = (uint32_t)i;
+            A.w.ckey[b0 + run + r] = key;
+        }
+        run += tot;
     }
+    if (threadIdx.x == 0) A.w.bcnt[blockIdx.x] = run;
 }
 
 // ---------------------------------------------------------------------------
-// groups: end cell and merge pixel of every non-exempt ray
+// groups: end cell and merge pixel of every non-exempt candidate
 // ---------------------------------------------------------------------------
-// Sums of equal groups are combined within the warp first (the march writes
-// a parent's split children next to each other, and they usually share cell
-// and pixel).  Exempt rays are decided from two words and left untouched;
-// a non-exempt ray's words are all loaded before its emitter and the cell's
-// rotation, which depend on them.
+// Sums of equal groups are combined within the warp first (a parent's split
+// children are neighbours in the list and usually share cell and pixel).
+// Exempt candidates (the rays of T_ref's upper bin at least T_ref) are
+// decided from two words and left untouched; a non-exempt ray's words are
+// all loaded before its emitter and the cell's rotation, which depend on
+// them.  Every group update is a reduction without a returned value: the
+// group's leader is its member with the lowest candidate-list index (kept
+// as its complement, so that a cleared group reads zero).
 __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
     Ctl *C = A.ctl;
     if (C->err || !C->merged) return;
     const int par = C->par;
     const Queue q = A.q[par ^ 1];
-    const long long n = C->cnt[par ^ 1];
+    const long long b0 = blockIdx.x * block_chunk(C->cnt[par ^ 1]);
+    const long long b1 = b0 + A.w.bcnt[blockIdx.x];
     const int ndir = A.w.ndir, gw = A.w.grp_w;
     const int lane = lane_id();
-    // this warp's run of leader-list entries [lslab, lslab + lleft), taken
-    // LEAD_SLAB at a time with one atomic (a single shared counter per warp
-    // iteration serialises the kernel)
-    unsigned long long lslab = 0;
-    int lleft = 0;
-    long long c0, c1;
-    warp_chunk(n, c0, c1);
-    for (long long base = c0; base < c1; base += 32) {
-        const long long i = base + lane;
+    for (long long base = b0 + (threadIdx.x & ~31); base < b1; base += blockDim.x) {
+        const long long c = base + lane;
         long long slot = -1;
         uint4 pack = make_uint4(NO_GROUP, 0u, 0u, 0u);
         float f[MAXB + 4];
@@ -370,9 +422,11 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
         int nbf = 0;
         int sim = -1;
         uint32_t key = 0;
-        if (i < c1) {
+        long long i = 0;
+        if (c < b1) {
+            i = A.w.cand[c];
+            key = A.w.ckey[c];
             sim = A.w.tsim[i];
-            key = A.w.tkey[i];
         }
         if (sim >= 0) {
             const uint32_t *sel = A.w.sel + SEL_W * sim;
@@ -426,66 +480,22 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
                 }
             }
         }
-        if (i < c1) A.w.tgrp[i] = pack;
-        // combine equal groups in the warp, then one set of atomics per group
+        if (c < b1) A.w.tgrp[c] = pack;
+        // combine equal groups in the warp, then one set of reductions per group
         const unsigned peers = __match_any_sync(FULL, slot);
-        const unsigned below = peers & ((1u << lane) - 1u);
         if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) peer_sum<MAXB + 4, float>(peers, f);
         const uint32_t kmax = __reduce_max_sync(peers, slot >= 0 ? key : 0u);
-        bool leads = false;
-        if (slot >= 0) {
-            uint32_t gbase = 0;
-            if (below == 0u) {
-                gbase = atomicAdd(A.w.gcnt + slot, (uint32_t)__popc(peers));
-                atomicMax(A.w.gmax + slot, kmax);
-                float4 *gf = reinterpret_cast<float4 *>(A.w.grp + slot * gw + 2 * GSUMS);
+        if (slot >= 0 && (peers & ((1u << lane) - 1u)) == 0u) {
+            uint4 *gc = A.w.gcm + slot;
+            atomicAdd(&gc->x, (uint32_t)__popc(peers));
+            atomicMax(&gc->y, kmax);
+            atomicMax(&gc->z, ~(uint32_t)c);       // the lowest index of the peers is this lane's
+            float4 *gf = reinterpret_cast<float4 *>(A.w.grp + slot * gw + 2 * GSUMS);
 #pragma unroll
-                for (int b = 0; b <= MAXB; b += 4)
-                    if (b <= nbf) red_add_v4(gf + b / 4, f[b], f[b + 1], f[b + 2], f[b + 3]);
-            }
-            // the group's first member in arrival order leads it; the
-            // others leave the queue
-            const int lead = __ffs(peers) - 1;
-            gbase = __shfl_sync(peers, gbase, lead);
-            const uint32_t rank = gbase + (uint32_t)__popc(below);
-            leads = rank == 0u;
-            if (!leads) q.pl[i] = DEAD_RAY;
-        }
-        // list the leaders: the rest of the warp's run first, then a new run
-        const unsigned lm = __ballot_sync(FULL, leads);
-        const int tot = __popc(lm);
-        if (tot) {
-            const unsigned long long s0 = lslab;
-            const int left = lleft;
-            unsigned long long s1 = 0;
-            if (tot > left) {
-                const int need = tot - left;
-                const int want = need > LEAD_SLAB ? need : LEAD_SLAB;
-                unsigned long long nb = 0;
-                if (lane == 0) nb = atomicAdd(&C->mlead, (unsigned long long)want);
-                nb = __shfl_sync(FULL, nb, 0);
-                s1 = nb;
-                lslab = nb + need;
-                lleft = want - need;
-            } else {
-                lslab = s0 + tot;
-                lleft = left - tot;
-            }
-            if (leads) {
-                const int k = __popc(lm & ((1u << lane) - 1u));
-                const unsigned long long o = k < left ? s0 + k : s1 + (k - left);
-                if (o < (unsigned long long)A.w.lead_cap) {
-                    A.w.lead_i[o] = (uint32_t)i;
-                    A.w.lead_slot[o] = (uint32_t)slot;
-                } else {
-                    atomicOr(&C->err, 1);
-                }
-            }
+            for (int b = 0; b <= MAXB; b += 4)
+                if (b <= nbf) red_add_v4(gf + b / 4, f[b], f[b + 1], f[b + 2], f[b + 3]);
         }
     }
-    // the unused end of the warp's run
-    for (int k = lane; k < lleft; k += 32)
-        if (lslab + k < (unsigned long long)A.w.lead_cap) A.w.lead_i[lslab + k] = NO_LEADER;
 }
 
 // ---------------------------------------------------------------------------
@@ -495,29 +505,53 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
 // of two above its group's largest content (exact power-of-two scaling),
 // truncated and at least 1: the brightest member has at least 27 significant
 // bits, every weight is below 2^28.  Weighted sums are 64-bit integers.
+// Every member of a group of two or more leaves the queue (its slot becomes a
+// hole); the leader lists the group in the block's merged-ray list.
 __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
-    const Ctl *C = A.ctl;
-    if (C->err || !C->merged) return;
-    const long long n = C->cnt[C->par ^ 1];
+    __shared__ uint32_t s_wofs[9];
+    __shared__ int s_on;
+    extern __shared__ uint32_t s_drop[];           // per simulation: rays removed
+    for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) s_drop[k] = 0u;
+    Ctl *C = A.ctl;
+    if (!block_runs(C, true, &s_on)) return;
+    const Queue q = A.q[C->par ^ 1];
+    const long long b0 = blockIdx.x * block_chunk(C->cnt[C->par ^ 1]);
+    const uint32_t bc = A.w.bcnt[blockIdx.x];
     const int gw = A.w.grp_w;
     const int lane = lane_id();
-    long long c0, c1;
-    warp_chunk(n, c0, c1);
-    for (long long base = c0; base < c1; base += 32) {
-        const long long i = base + lane;
+    uint32_t run = 0;                              // merged rays listed so far (block-uniform)
+    for (uint32_t w0 = 0; w0 < bc; w0 += 256) {
+        const long long c = b0 + w0 + threadIdx.x;
+        const bool in = w0 + threadIdx.x < bc;
         uint4 pk = make_uint4(NO_GROUP, 0u, 0u, 0u);
-        uint32_t key = 0;
-        if (i < c1) {
-            pk = A.w.tgrp[i];
-            if (pk.x != NO_GROUP) key = A.w.tkey[i];
+        uint32_t key = 0, qi = 0;
+        if (in) {
+            pk = A.w.tgrp[c];
+            if (pk.x != NO_GROUP) {
+                key = A.w.ckey[c];
+                qi = A.w.cand[c];
+            }
         }
         long long slot = pk.x == NO_GROUP ? -1 : (long long)pk.x;
-        // a ray alone in its group stays as it is: its sums are never read
-        if (slot >= 0 && A.w.gcnt[slot] < 2u) slot = -1;
+        uint4 gm = make_uint4(0u, 0u, 0u, 0u);
+        if (slot >= 0) gm = A.w.gcm[slot];
+        if (slot >= 0 && gm.x < 2u) {
+            // alone in its group: the ray stays as it is, and clears the
+            // group (no other ray touched it)
+            float4 *gz = reinterpret_cast<float4 *>(A.w.grp + slot * gw + 2 * GSUMS);
+            for (int b = 0; b < gw / 4 - GSUMS / 2; ++b) gz[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+            A.w.gcm[slot] = make_uint4(0u, 0u, 0u, 0u);
+            slot = -1;
+        }
+        const bool leads = slot >= 0 && gm.z == ~(uint32_t)c;
+        int sim = -1;
+        if (slot >= 0) {
+            sim = A.w.tsim[qi];
+            q.pl[qi] = DEAD_RAY;
+        }
         unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
         if (slot >= 0) {
-            const uint32_t gm = A.w.gmax[slot];
-            const int eb = max((int)((gm >> 23) & 0xffu), 30);      // biased exponent; 2^(eb-126) > content
+            const int eb = max((int)((gm.y >> 23) & 0xffu), 30);    // biased exponent; 2^(eb-126) > content
             const float wscale = __int_as_float((253 + WBITS - eb) << 23);
             const unsigned long long qw = max(__float2ull_rz(__fmul_rn(__uint_as_float(key), wscale)), 1ull);
             v[0] = qw;
@@ -534,76 +568,121 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
 #pragma unroll
             for (int k = 0; k < GSUMS; ++k) atomicAdd(gs + k, v[k]);
         }
+        // rays removed: every member of a merging group but one
+        const int dsim = slot >= 0 && !leads ? sim : -1;
+        if (__any_sync(FULL, dsim >= 0)) {
+            const unsigned dp = __match_any_sync(FULL, dsim);
+            if (dsim >= 0 && (dp & ((1u << lane) - 1u)) == 0u) atomicAdd(s_drop + dsim, (uint32_t)__popc(dp));
+        }
+        uint32_t tot;
+        const uint32_t r = block_rank(leads, s_wofs, &tot);
+        if (leads) {
+            A.w.lead_slot[b0 + run + r] = (uint32_t)slot;
+            A.w.lead_sim[b0 + run + r] = sim;
+        }
+        run += tot;
     }
+    if (threadIdx.x == 0) A.w.bled[blockIdx.x] = run;
+    __syncthreads();
+    for (int k = threadIdx.x; k < A.nsims; k += blockDim.x)
+        if (s_drop[k]) atomicAdd(A.w.sel + SEL_W * k + SEL_DROP, s_drop[k]);
 }
 
 // ---------------------------------------------------------------------------
-// in place: merged rays into their leaders' slots
+// the merged rays, appended after the march's output
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
-    extern __shared__ int sh_drop[];              // per simulation: rays removed by merging
-    for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) sh_drop[k] = 0;
-    __syncthreads();
-    const Ctl *C = A.ctl;
-    if (!C->err && C->merged) {
-        const Queue q = A.q[C->par ^ 1];
-        const long long nl = min((long long)C->mlead, A.w.lead_cap);
-        const int ndir = A.w.ndir, gw = A.w.grp_w, nbq = A.nbq;
-        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nl;
-             k += (long long)gridDim.x * blockDim.x) {
-            const uint32_t li = A.w.lead_i[k];
-            if (li == NO_LEADER) continue;
-            const long long i = li;
-            const uint32_t slot = A.w.lead_slot[k];
-            const uint32_t gsize = A.w.gcnt[slot];
-            if (gsize > 1) {
-                const int sim = A.w.tsim[i];
-                const SimDev &S = A.sims[sim];
-                const float *gp = A.w.grp + (long long)slot * gw;
-                const unsigned long long *gs = reinterpret_cast<const unsigned long long *>(gp);
-                const unsigned long long W = gs[0];
-                // weights below 2^28 and offsets below 2^21: the sums stay
-                // exact while W < 2^41 (more than 2^13 members as bright as
-                // the brightest would be needed to reach it)
-                if (W >= (1ull << 41)) atomicOr((int *)&C->err, 8);
-                const long long g = (long long)slot / ndir;
-                const uint32_t pm = slot % ndir;
-                const int local = (int)(g - S.cell_off);          // below 2^31 cells
-                const int cell[3] = {local % S.nx, (local / S.nx) % S.ny, local / (S.nx * S.ny)};
-                int P[3];
+    __shared__ unsigned long long s_sum[2][8];
+    __shared__ int s_on;
+    Ctl *C = A.ctl;
+    if (!block_runs(C, true, &s_on)) return;
+    const int par = C->par;
+    const Queue q = A.q[par ^ 1];
+    const long long mbase = C->mbase;
+    // this block's place in the appended run: the merged rays of the blocks
+    // before it; and the run's length
+    unsigned long long pre = 0, tot = 0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        const uint32_t v = A.w.bled[k];
+        tot += v;
+        if (k < (int)blockIdx.x) pre += v;
+    }
 #pragma unroll
-                for (int a = 0; a < 3; ++a) P[a] = (cell[a] << FRAC_BITS) + (int)div_rne(gs[1 + a], W);
-                const int Adist = (int)min(div_rne(gs[4], W), 65535ull);
-                const int L2 = min(max((int)div_rne(gs[5], W), S.l_merge), S.l_max);
-                const float *gph = gp + 2 * GSUMS;
-                const int4 *rp = A.w.rot + 3 * g;
-                const int4 rows[3] = {rp[0], rp[1], rp[2]};
-                const int4 vq = S.l_merge <= A.ltab ? __ldg(&A.pixtab[level_offset(S.l_merge) + pm])
-                                                    : healpix_vq(S.l_merge, pm);
-                int32_t dx, dy, dz;
-                rotate_dir(rows, vq, dx, dy, dz);
-                q.pl[i] = ((uint32_t)L2 << LEVEL_SHIFT) | pm;
-                q.em[i] = MERGED_BIT | (uint32_t)local;
-                q.bi[i] = S.step;
-                q.dx[i] = dx; q.dy[i] = dy; q.dz[i] = dz;
-#pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < nbq) q.ph[b][i] = b < S.nb ? gph[b] : 0.0f;
-                q.mx[i] = P[0]; q.my[i] = P[1]; q.mz[i] = P[2];
-                q.ma[i] = (L2 > S.l_merge ? 0x80000000u : 0u) | ((uint32_t)sim << 16) | (uint32_t)Adist;
-                q.mthr[i] = gph[S.nb];
-                atomicAdd(&sh_drop[sim], (int)gsize - 1);
-            }
-            // the leader clears its group for the next step
-            float4 *gz = reinterpret_cast<float4 *>(A.w.grp + (long long)slot * gw);
-            for (int b = 0; b < gw / 4; ++b) gz[b] = make_float4(0.f, 0.f, 0.f, 0.f);
-            A.w.gcnt[slot] = 0u;
-            A.w.gmax[slot] = 0u;
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        pre += __shfl_xor_sync(FULL, pre, o);
+        tot += __shfl_xor_sync(FULL, tot, o);
+    }
+    if (lane_id() == 0) {
+        s_sum[0][threadIdx.x >> 5] = pre;
+        s_sum[1][threadIdx.x >> 5] = tot;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < A.nsims; k += blockDim.x)
-        if (sh_drop[k]) atomicAdd(&A.acc[k].p_rays_out, -(double)sh_drop[k]);
+    pre = tot = 0;
+    for (int w = 0; w < 8; ++w) {
+        pre += s_sum[0][w];
+        tot += s_sum[1][w];
+    }
+    if ((long long)(mbase + tot) > A.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&C->err, 1);
+        return;
+    }
+    if (blockIdx.x == 0) {
+        // no other thread of this kernel reads the count or the removals
+        if (threadIdx.x == 0) C->cnt[par ^ 1] = mbase + (long long)tot;
+        for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) {
+            uint32_t *d = A.w.sel + SEL_W * k + SEL_DROP;
+            if (*d) {
+                A.acc[k].p_rays_out -= (double)*d;
+                *d = 0u;
+            }
+        }
+    }
+    const long long b0 = blockIdx.x * block_chunk(mbase);
+    const uint32_t bl = A.w.bled[blockIdx.x];
+    const int ndir = A.w.ndir, gw = A.w.grp_w, nbq = A.nbq;
+    for (uint32_t j = threadIdx.x; j < bl; j += blockDim.x) {
+        const uint32_t slot = A.w.lead_slot[b0 + j];
+        const int sim = A.w.lead_sim[b0 + j];
+        const SimDev &S = A.sims[sim];
+        float *gp = A.w.grp + (long long)slot * gw;
+        const unsigned long long *gs = reinterpret_cast<const unsigned long long *>(gp);
+        const unsigned long long W = gs[0];
+        // weights below 2^28 and offsets below 2^21: the sums stay exact
+        // while W < 2^41 (more than 2^13 members as bright as the brightest
+        // would be needed to reach it)
+        if (W >= (1ull << 41)) atomicOr(&C->err, 8);
+        const long long g = (long long)slot / ndir;
+        const uint32_t pm = slot % ndir;
+        const int local = (int)(g - S.cell_off);          // below 2^31 cells
+        const int cell[3] = {local % S.nx, (local / S.nx) % S.ny, local / (S.nx * S.ny)};
+        int P[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) P[a] = (cell[a] << FRAC_BITS) + (int)div_rne(gs[1 + a], W);
+        const int Adist = (int)min(div_rne(gs[4], W), 65535ull);
+        const int L2 = min(max((int)div_rne(gs[5], W), S.l_merge), S.l_max);
+        const float *gph = gp + 2 * GSUMS;
+        const int4 *rp = A.w.rot + 3 * g;
+        const int4 rows[3] = {rp[0], rp[1], rp[2]};
+        const int4 vq = S.l_merge <= A.ltab ? __ldg(&A.pixtab[level_offset(S.l_merge) + pm])
+                                            : healpix_vq(S.l_merge, pm);
+        int32_t dx, dy, dz;
+        rotate_dir(rows, vq, dx, dy, dz);
+        const long long o = mbase + (long long)pre + j;
+        q.pl[o] = ((uint32_t)L2 << LEVEL_SHIFT) | pm;
+        q.em[o] = MERGED_BIT | (uint32_t)local;
+        q.bi[o] = S.step;
+        q.dx[o] = dx; q.dy[o] = dy; q.dz[o] = dz;
+#pragma unroll
+        for (int b = 0; b < MAXB; ++b)
+            if (b < nbq) q.ph[b][o] = b < S.nb ? gph[b] : 0.0f;
+        q.mx[o] = P[0]; q.my[o] = P[1]; q.mz[o] = P[2];
+        q.ma[o] = (L2 > S.l_merge ? 0x80000000u : 0u) | ((uint32_t)sim << 16) | (uint32_t)Adist;
+        q.mthr[o] = gph[S.nb];
+        // the group is cleared for the next step
+        float4 *gz = reinterpret_cast<float4 *>(gp);
+        for (int b = 0; b < gw / 4; ++b) gz[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.w.gcm[slot] = make_uint4(0u, 0u, 0u, 0u);
+    }
 }
 
 __global__ void k_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, int per_ray,
@@ -627,8 +706,8 @@ cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st) {
     if (a.w.hrep > 1) k_mreduce<<<rblocks, 256, 0, st>>>(a, 2);
     k_mfind<<<a.nsims, 1024, 0, st>>>(a, 2);
     k_mgroup<<<rblocks, 256, 0, st>>>(a);
-    k_mweight<<<rblocks, 256, 0, st>>>(a);
-    k_memit<<<rblocks, 256, (size_t)a.nsims * sizeof(int), st>>>(a);
+    k_mweight<<<rblocks, 256, (size_t)a.nsims * sizeof(uint32_t), st>>>(a);
+    k_memit<<<rblocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

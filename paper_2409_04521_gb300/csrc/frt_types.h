@@ -96,7 +96,7 @@ struct Ctl {
     long long ncell_active;  // cells in active simulations
     int32_t merged;          // a simulation merged rays this step
     int32_t pad;
-    unsigned long long mlead;  // groups (their leaders) made by this step's merge
+    long long mbase;         // the march's output count: merged rays are appended from here
     long long pad2;
 };
 
@@ -148,14 +148,20 @@ struct MergeWork {
     uint32_t *tkey;          // per queue slot: rank content (float bits)
     int32_t *tsim;           // per queue slot: simulation taking part, -1 none
     float *grp;              // [cell * ndir + pixel][grp_w]: 6 uint64 weighted sums, photons, threshold
-    uint32_t *gcnt;          // [cell * ndir + pixel] group sizes
-    uint32_t *gmax;          // [cell * ndir + pixel] largest member content (float bits)
-    uint4 *tgrp;             // per queue slot: group slot (0xffffffff: none), then the end point's
+    uint4 *gcm;              // [cell * ndir + pixel] group size, largest member content (float
+                             // bits), complement of the lowest candidate-list index (its
+                             // leader), unused; all zero when the group is empty
+    uint32_t *cand;          // candidate lists, one run per block of the merge passes: the queue
+                             // slot of each ray that may merge
+    uint32_t *ckey;          // and its rank content (float bits)
+    uint4 *tgrp;             // per candidate: group slot (0xffffffff: none), then the end point's
                              // offsets in its cell, distance travelled and level, packed
     int4 *rot;               // [cell][3] merge-sphere rotation rows of this step
-    uint32_t *lead_i;        // k-th group leader: its queue slot (0xffffffff: unused entry)
-    uint32_t *lead_slot;     // and its group slot
-    long long lead_cap;      // entries of the leader list (queue slots plus 128 per warp)
+    uint32_t *lead_slot;     // merged-ray lists, one run per block: the group slot
+    int32_t *lead_sim;       // and the simulation of each merged ray
+    uint32_t *bcnt;          // per block of the merge passes: candidates listed
+    uint32_t *bled;          // and merged rays listed
+    long long lead_cap;      // entries of the candidate and merged-ray lists
     int32_t ndir;            // group slots per cell (12 * 4^l_merge of the deepest allowed level)
     int32_t grp_w;           // floats per group
     int32_t hrep;            // copies of each simulation's histogram (spreads hot bins)
