@@ -125,53 +125,77 @@ __device__ __forceinline__ bool block_runs(const Ctl *C, bool need_merged, int *
     return *s_flag != 0;
 }
 
-// inclusive scan of one value per thread over a block of 1024 threads
-__device__ unsigned long long block_incl_scan(unsigned long long v, unsigned long long *sh) {
-    const int lane = lane_id(), wid = threadIdx.x >> 5;
+// inclusive prefix sum over the lanes of a warp
+__device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long long v) {
+    const int lane = lane_id();
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long t = __shfl_up_sync(FULL, v, o);
         if (lane >= o) v += t;
     }
-    if (lane == 31) sh[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        unsigned long long w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0ull;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long t = __shfl_up_sync(FULL, w, o);
-            if (lane >= o) w += t;
-        }
-        sh[lane] = w;
-    }
-    __syncthreads();
-    const unsigned long long r = v + (wid > 0 ? sh[wid - 1] : 0ull);
-    __syncthreads();
-    return r;
+    return v;
 }
 
 // In hist[0..HIST_BINS) find the largest bin b with above + count(bins >= b)
-// >= K (K > above, and the total reaches K).  Returns b and the count above b.
+// >= K (K > above, and the total reaches K).  Returns b and the count above
+// b.  A block of 1024 threads visits the bins from the top, d = HIST_BINS - 1
+// - bin: warp w owns d in [2048 w, 2048 w + 2048), in rows of 32 bins (128
+// contiguous bytes); lane l sums the rows l and l + 32 of its warp.  The warp
+// holding the K-th ray then finds its row from the row sums, and the bin
+// within the row.
 __device__ void select_bin(const uint32_t *hist, unsigned long long above, unsigned long long K, uint32_t *out_bin,
-                           unsigned long long *out_above, unsigned long long *sh) {
-    constexpr int PER = HIST_BINS / 1024;
-    const int t = threadIdx.x;
-    const int chunk = 1023 - t;           // thread 0 owns the highest bins
-    unsigned long long v = 0;
-    for (int k = 0; k < PER; ++k) v += hist[chunk * PER + k];
-    const unsigned long long incl = above + block_incl_scan(v, sh);
-    const unsigned long long excl = incl - v;
-    if (excl < K && K <= incl) {
-        unsigned long long acc = excl;
-        for (int k = PER - 1; k >= 0; --k) {
-            const unsigned long long c = hist[chunk * PER + k];
-            if (acc + c >= K) {
-                *out_bin = (uint32_t)(chunk * PER + k);
-                *out_above = acc;
-                break;
-            }
-            acc += c;
+                           unsigned long long *out_above, uint32_t (*s_rows)[64], unsigned long long *s_w) {
+    constexpr int WB = HIST_BINS / 32;
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    uint32_t rs[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int d0 = w * WB + 32 * (lane + 32 * h);
+        const uint4 *src = reinterpret_cast<const uint4 *>(hist + (HIST_BINS - 32 - d0));
+        uint4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = src[k];
+        uint32_t t = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += v[k].x + v[k].y + v[k].z + v[k].w;
+        rs[h] = t;
+        s_rows[w][lane + 32 * h] = t;
+    }
+    unsigned long long tw = (unsigned long long)rs[0] + rs[1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tw += __shfl_xor_sync(FULL, tw, o);
+    if (lane == 0) s_w[w] = tw;
+    __syncthreads();
+    if (w == 0) {
+        const unsigned long long v = s_w[lane], inc = warp_incl_scan64(v);
+        s_w[32 + lane] = inc;
+        __syncwarp();
+        s_w[lane] = inc - v;
+    }
+    __syncthreads();
+    unsigned long long acc = above + s_w[w];
+    if (!(acc < K && K <= above + s_w[32 + w])) return;      // warp-uniform
+    int row = -1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (row >= 0) break;
+        const unsigned long long v = s_rows[w][lane + 32 * h], inc = acc + warp_incl_scan64(v);
+        const unsigned hit = __ballot_sync(FULL, inc - v < K && K <= inc);
+        if (hit) {
+            const int src = __ffs(hit) - 1;
+            row = 32 * h + src;
+            acc = __shfl_sync(FULL, inc - v, src);
+        } else {
+            acc = __shfl_sync(FULL, inc, 31);
         }
+    }
+    if (row < 0) return;                                     // not reached: the warp holds the K-th
+    const int d = w * WB + 32 * row + lane;
+    const unsigned long long c = hist[HIST_BINS - 1 - d], inc = acc + warp_incl_scan64(c);
+    const unsigned hit = __ballot_sync(FULL, inc - c < K && K <= inc);
+    if (lane == __ffs(hit) - 1) {
+        *out_bin = (uint32_t)(HIST_BINS - 1 - d);
+        *out_above = inc - c;
     }
 }
 
@@ -278,7 +302,8 @@ __global__ void __launch_bounds__(256) k_mreduce(MergeArgs A, int pass) {
 // per simulation: the threshold's upper 16 bits (pass 1) or all 32 (pass 2)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_mfind(MergeArgs A, int pass) {
-    __shared__ unsigned long long sh[32];
+    __shared__ uint32_t s_rows[32][64];
+    __shared__ unsigned long long s_w[64];
     __shared__ uint32_t s_bin;
     __shared__ unsigned long long s_above;
     Ctl *C = A.ctl;
@@ -292,9 +317,13 @@ __global__ void __launch_bounds__(1024) k_mfind(MergeArgs A, int pass) {
             if (threadIdx.x == 0) sel[SEL_STATE] = SEL_OFF;
             return;
         }
-        if (threadIdx.x == 0) C->merged = 1;
+        if (threadIdx.x == 0) {
+            C->merged = 1;
+            s_bin = 0u;
+            s_above = 0ull;
+        }
         const unsigned long long K = S.k_ex > 0 ? (unsigned long long)S.k_ex : 1ull;
-        select_bin(hist, 0ull, K, &s_bin, &s_above, sh);
+        select_bin(hist, 0ull, K, &s_bin, &s_above, s_rows, s_w);
         __syncthreads();
         if (threadIdx.x == 0) {
             sel[SEL_STATE] = SEL_PASS2;
@@ -304,8 +333,12 @@ __global__ void __launch_bounds__(1024) k_mfind(MergeArgs A, int pass) {
         }
     } else {
         if (sel[SEL_STATE] != SEL_PASS2) return;
+        if (threadIdx.x == 0) {
+            s_bin = 0u;
+            s_above = 0ull;
+        }
         const unsigned long long K = S.k_ex > 0 ? (unsigned long long)S.k_ex : 1ull;
-        select_bin(hist, (unsigned long long)sel[SEL_ABOVE], K, &s_bin, &s_above, sh);
+        select_bin(hist, (unsigned long long)sel[SEL_ABOVE], K, &s_bin, &s_above, s_rows, s_w);
         __syncthreads();
         if (threadIdx.x == 0) {
             sel[SEL_T] = (sel[SEL_HIGH] << 16) | s_bin;
