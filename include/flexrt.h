@@ -298,6 +298,15 @@ void flexrt_destroy(flexrt_ctx *ctx);
  * `level`, out int32[3n] = round(v * 2^24). */
 flexrt_status flexrt_probe_pixvec(int32_t level, int64_t p0, int64_t n, int32_t *out);
 
+/* The chemistry's single-precision rate fits (Sec. 4.1: case-B and case-A
+ * recombination, collisional ionisation of HI, and the cooling rate of
+ * recombination, collisional ionisation and excitation and free-free
+ * emission with unit electron, HI and HII densities, no Compton term) at n
+ * temperatures T float[n] (K, 1 <= T <= 1e9): out float[4n] = (alpha_B,
+ * alpha_A cm^3/s, C_HI cm^3/s, Lambda erg cm^3/s) per temperature.
+ * FLEXRT_E_INVALID for a temperature out of range.  Synchronous. */
+flexrt_status flexrt_probe_rates(int64_t n, const float *T, float *out);
+
 /* Rotation of (seed, emitter, step) quantised to 2^24: out int32[9]. */
 flexrt_status flexrt_probe_rotation(uint64_t seed, int64_t emitter, int64_t step,
                                     int32_t rotate, int32_t *out);

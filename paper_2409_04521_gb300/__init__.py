@@ -5,4 +5,4 @@ The method runs in the CUDA kernels of ``libflexrt.so`` (sources in
 ``csrc/``, C ABI in ``include/flexrt.h``); ``flexrt`` is its ctypes binding.
 """
 from .flexrt import (Batch, FlexRTError, Simulation, default_options, lib, library_path, probe_direction,  # noqa: F401
-                     probe_merge, probe_merge_pixel, probe_pixvec, probe_rotation, probe_traverse)
+                     probe_merge, probe_merge_pixel, probe_pixvec, probe_rates, probe_rotation, probe_traverse)

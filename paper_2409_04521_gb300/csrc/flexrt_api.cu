@@ -314,6 +314,19 @@ extern "C" flexrt_status flexrt_probe_pixvec(int32_t level, int64_t p0, int64_t 
     return FLEXRT_OK;
 }
 
+extern "C" flexrt_status flexrt_probe_rates(int64_t n, const float *T, float *out) {
+    if (n < 0 || (n && (!T || !out))) return FLEXRT_E_INVALID;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(T[i] >= 1.0f && T[i] <= 1.0e9f)) return FLEXRT_E_INVALID;
+    if (n == 0) return FLEXRT_OK;
+    DevBuf<float> dT, dout;
+    if (dT.alloc(n) != cudaSuccess || dout.alloc(4 * n) != cudaSuccess) return FLEXRT_E_OOM;
+    if (cudaMemcpy(dT.p, T, n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return FLEXRT_E_CUDA;
+    if (launch_probe_rates(n, dT.p, dout.p, 0) != cudaSuccess) return FLEXRT_E_CUDA;
+    if (cudaMemcpy(out, dout.p, 4 * n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return FLEXRT_E_CUDA;
+    return FLEXRT_OK;
+}
+
 extern "C" flexrt_status flexrt_probe_rotation(uint64_t seed, int64_t e, int64_t s, int32_t rotate, int32_t *out) {
     if (!out) return FLEXRT_E_INVALID;
     DevBuf<int32_t> d;

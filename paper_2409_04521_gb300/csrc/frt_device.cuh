@@ -498,34 +498,49 @@ __device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float
 constexpr float KB_F = 1.380649e-16f;
 constexpr float T_HI_F = 157807.0f;
 
-// x^p for x > 0 through the hardware log2/exp2 (relative error ~1e-6)
-__device__ __forceinline__ float fpow(float x, float p) { return exp2f(p * __log2f(x)); }
+// The fits are evaluated in log2 space: with t = log2 T and l = log2 lambda
+// (lambda = 2 T_HI / T), every power, quotient and Boltzmann factor is one
+// exp2 of a sum, and T's logarithm is taken once.  Hardware log2/exp2: the
+// exponents stay below ~30 in magnitude (the large constant factors are kept
+// outside), so each rate is within a few 1e-6 relative of the fit.
+constexpr float LOG2_2THI = 18.2678017f;           // log2(2 T_HI)
+constexpr float HALF_LOG2E = 0.721347520f;         // log2(e) / 2
 
+// log2 of (1 + (lambda / b)^c)^d from l = log2 lambda and lb = log2 b
+__device__ __forceinline__ float hg_den(float l, float lb, float c, float d) {
+    return d * __log2f(1.0f + exp2f(c * (l - lb)));
+}
 __device__ __forceinline__ float alphaB_f(float T) {
-    const float lam = 2.0f * T_HI_F / T;
-    return 2.753e-14f * fpow(lam, 1.5f) / fpow(1.0f + fpow(lam * (1.0f / 2.740f), 0.407f), 2.242f);
+    const float l = LOG2_2THI - __log2f(T);
+    return 2.753e-14f * exp2f(1.5f * l - hg_den(l, 1.45417589f, 0.407f, 2.242f));      // b = 2.740
 }
 // case-A recombination coefficient (Hui & Gnedin 1997)
 __device__ __forceinline__ float alphaA_f(float T) {
-    const float lam = 2.0f * T_HI_F / T;
-    return 1.269e-13f * fpow(lam, 1.503f) / fpow(1.0f + fpow(lam * (1.0f / 0.522f), 0.470f), 1.923f);
+    const float l = LOG2_2THI - __log2f(T);
+    return 1.269e-13f * exp2f(1.503f * l - hg_den(l, -0.937878288f, 0.470f, 1.923f));  // b = 0.522
+}
+// collisional ionisation rate from t = log2 T, l = log2 lambda and lambda
+__device__ __forceinline__ float collion_tl(float t, float l, float lam) {
+    if (lam > 180.0f) return 0.0f;                    // exp(-lam/2) below the float range
+    return 21.11f * exp2f(-1.5f * t - HALF_LOG2E * lam - 1.089f * l - hg_den(l, -1.49817873f, 0.874f, 1.101f));
 }
 __device__ __forceinline__ float collion_f(float T) {
-    const float lam = 2.0f * T_HI_F / T;
-    if (lam > 180.0f) return 0.0f;                    // exp(-lam/2) below the float range
-    return 21.11f * fpow(T, -1.5f) * __expf(-0.5f * lam) * fpow(lam, -1.089f) /
-           fpow(1.0f + fpow(lam * (1.0f / 0.354f), 0.874f), 1.101f);
+    const float t = __log2f(T), l = LOG2_2THI - t;
+    return collion_tl(t, l, exp2f(l));
 }
 // net cooling rate per n_H^2 (erg cm^3 s^-1) for electron, HI and HII
 // fractions xe, xHI, xHII; compton_c already divided by n_H
 __device__ __forceinline__ float cooling_f(float T, float xe, float xHI, float xHII, float compton_c, float Tcmb) {
-    const float lam = 2.0f * T_HI_F / T;
-    const float rec = 3.435e-30f * T * fpow(lam, 1.970f) / fpow(1.0f + fpow(lam * (1.0f / 2.250f), 0.376f), 3.720f);
-    const float cion = 2.1789874e-11f * collion_f(T);      // 13.6 eV in erg
-    const float cexc = 7.5e-19f * __expf(-118348.0f / T) / (1.0f + sqrtf(T * 1.0e-5f));
-    const float lt = __log10f(T);
-    const float gff = 1.1f + 0.34f * __expf(-(5.5f - lt) * (5.5f - lt) * (1.0f / 3.0f));
-    const float ff = 1.42e-27f * gff * sqrtf(T);
+    const float t = __log2f(T), l = LOG2_2THI - t, lam = exp2f(l);
+    // recombination cooling: T lambda^1.970 / (1 + (lambda/2.250)^0.376)^3.720
+    const float rec = 3.435e-30f * exp2f(t + 1.970f * l - hg_den(l, 1.169925f, 0.376f, 3.720f));
+    const float cion = 2.1789874e-11f * collion_tl(t, l, lam);     // 13.6 eV in erg
+    // collisional excitation: exp(-118348 / T) / (1 + sqrt(T / 1e5)), and
+    // 118348 / T = 0.374976 lambda
+    const float cexc = 7.5e-19f * exp2f(-0.540977500f * lam - __log2f(1.0f + exp2f(0.5f * (t - 16.6096405f))));
+    const float u = 5.5f - 0.301029996f * t;                         // 5.5 - log10 T
+    const float gff = 1.1f + 0.34f * exp2f(-0.480898347f * u * u);  // exp(-u^2 / 3)
+    const float ff = 1.42e-27f * gff * exp2f(0.5f * t);
     return (rec + ff) * xe * xHII + (cion + cexc) * xe * xHI + compton_c * (T - Tcmb) * xe;
 }
 

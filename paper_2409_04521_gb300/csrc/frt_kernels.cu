@@ -481,6 +481,18 @@ __global__ void k_probe_pixvec(int level, long long p0, long long n, int32_t *ou
         out[3 * i] = v.x; out[3 * i + 1] = v.y; out[3 * i + 2] = v.z;
     }
 }
+// the single-precision rate fits of the chemistry kernel (Sec. 4.1) at n
+// temperatures: alpha_B, alpha_A, C_HI and the cooling rate with unit
+// electron, HI and HII fractions and no Compton term
+__global__ void k_probe_rates(long long n, const float *T, float *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float t = T[i];
+        out[4 * i + 0] = alphaB_f(t);
+        out[4 * i + 1] = alphaA_f(t);
+        out[4 * i + 2] = collion_f(t);
+        out[4 * i + 3] = cooling_f(t, 1.0f, 1.0f, 1.0f, 0.0f, 0.0f);
+    }
+}
 __global__ void k_probe_rotation(uint64_t seed, long long e, long long s, int rotate, int32_t *out) {
     int4 r[3];
     rotation_rows(seed, e, s, rotate, r);
@@ -619,6 +631,11 @@ cudaError_t launch_probe_pixvec(int level, long long p0, long long n, int32_t *o
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
     k_probe_pixvec<<<blocks, 256, 0, st>>>(level, p0, n, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_probe_rates(long long n, const float *T, float *out, cudaStream_t st) {
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+    k_probe_rates<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(n, T, out);
     return cudaGetLastError();
 }
 cudaError_t launch_probe_rotation(uint64_t seed, long long e, long long s, int rotate, int32_t *out, cudaStream_t st) {

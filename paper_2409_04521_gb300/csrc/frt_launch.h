@@ -80,6 +80,7 @@ cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st);
 cudaError_t launch_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, bool per_ray,
                                      uint32_t *out, cudaStream_t st);
 cudaError_t launch_probe_pixvec(int level, long long p0, long long n, int32_t *out, cudaStream_t st);
+cudaError_t launch_probe_rates(long long n, const float *T, float *out, cudaStream_t st);
 cudaError_t launch_probe_rotation(uint64_t seed, long long e, long long s, int rotate, int32_t *out, cudaStream_t st);
 cudaError_t launch_probe_direction(int level, long long p0, long long n, const int32_t *Rq, const int4 *tab, int ltab,
                                    int32_t *out, cudaStream_t st);

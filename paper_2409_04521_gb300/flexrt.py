@@ -146,6 +146,7 @@ def lib():
             L.flexrt_batch_destroy.restype = None
             L.flexrt_probe_pixvec.argtypes = [C.c_int32, C.c_int64, C.c_int64, P(C.c_int32)]
             L.flexrt_probe_rotation.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int32, P(C.c_int32)]
+            L.flexrt_probe_rates.argtypes = [C.c_int64, P(C.c_float), P(C.c_float)]
             L.flexrt_probe_direction.argtypes = [C.c_int32, C.c_int64, C.c_int64, P(C.c_int32), P(C.c_int32)]
             L.flexrt_probe_traverse.argtypes = [C.c_int64, P(C.c_int64), P(C.c_int32), P(Grid), P(C.c_int32),
                                                 P(C.c_float), P(C.c_int32), P(C.c_int32)]
@@ -500,6 +501,15 @@ class Simulation:
 def probe_pixvec(level: int, p0: int, n: int) -> np.ndarray:
     out = np.zeros((n, 3), np.int32)
     _check(lib().flexrt_probe_pixvec(level, p0, n, _p(out, C.c_int32)))
+    return out
+
+
+def probe_rates(T) -> np.ndarray:
+    """The chemistry kernel's rate fits at temperatures T: columns alpha_B,
+    alpha_A, C_HI and the cooling rate (unit densities, no Compton term)."""
+    T = np.ascontiguousarray(np.asarray(T, np.float32).ravel())
+    out = np.zeros((len(T), 4), np.float32)
+    _check(lib().flexrt_probe_rates(len(T), _p(T, C.c_float), _p(out, C.c_float)))
     return out
 
 

@@ -92,3 +92,24 @@ def test_traversal_cells_bit_exact():
         assert np.array_equal(cells[i, :k], oc), i
         # lengths: the exact fractions to a few single-precision ulp
         assert np.allclose(ds[i, :k], ods, rtol=6e-7, atol=0), (i, ds[i, :k], ods)
+
+
+def test_rate_fits_match_oracle():
+    # the chemistry kernel's single-precision fits (evaluated through log2 /
+    # exp2 of sums) against the oracle's double-precision fits, 1 K to 1e9 K.
+    # A rate of the form exp(-c lambda) (lambda = 2 T_HI / T) inherits
+    # lambda's relative error times c lambda: the tolerance grows with lambda.
+    T = np.geomspace(1.0, 1.0e9, 4001).astype(np.float32)
+    g = F.probe_rates(T).astype(np.float64)
+    Td = T.astype(np.float64)
+    lam = 2 * 157807.0 / Td
+    o = np.stack([[oracle.alpha_B(t), oracle.alpha_A(t), oracle.coll_ion(t), oracle.cooling(t, 1.0, 1.0, 1.0, -1.0)]
+                  for t in Td])
+    for k, name in enumerate(("alpha_B", "alpha_A", "C_HI", "cooling")):
+        big = o[:, k] > 1e-35
+        rel = np.abs(g[big, k] / o[big, k] - 1.0)
+        tol = 3e-5 + 3e-6 * lam[big]
+        assert np.all(rel <= tol), (name, float(rel.max()), float(Td[big][np.argmax(rel / tol)]))
+        assert np.all(np.abs(g[~big, k]) <= 1e-34), name
+    with pytest.raises(F.FlexRTError):
+        F.probe_rates(np.array([0.5], np.float32))
