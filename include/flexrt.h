@@ -409,7 +409,9 @@ void flexrt_default_batch_config(flexrt_batch_config *c);
 flexrt_status flexrt_batch_create(const flexrt_batch_config *c, flexrt_batch **out);
 
 /* Admit one simulation (same parameters as flexrt_create plus its sources and
- * step length): host inputs are copied; *slot receives its slot.
+ * step length): host inputs are copied before the call returns (the copies
+ * to the device run in stream order, behind the steps already enqueued: the
+ * call does not wait for them); *slot receives its slot.
  * FLEXRT_E_CAPACITY when no slot, cells or emitters are free. */
 flexrt_status flexrt_batch_add(flexrt_batch *b, const flexrt_grid *grid, const flexrt_box *box,
                                const double *n_H, const flexrt_mfp *mfp, const flexrt_spectrum *spectrum,
@@ -421,8 +423,9 @@ flexrt_status flexrt_batch_add(flexrt_batch *b, const flexrt_grid *grid, const f
 flexrt_status flexrt_batch_step(flexrt_batch *b);
 flexrt_status flexrt_batch_sync(flexrt_batch *b);
 
-/* Remove a member between steps; its cells are reusable at once, its slot
- * and emitters after the next step. */
+/* Remove a member between steps (without waiting for enqueued steps, which
+ * still advance it); its cells are reusable at once, its slot and emitters
+ * after the next step. */
 flexrt_status flexrt_batch_retire(flexrt_batch *b, int32_t slot);
 
 /* Per-member read-back, as the single-simulation getters. */
@@ -439,8 +442,9 @@ flexrt_status flexrt_batch_get_rays_merged(flexrt_batch *b, int32_t slot, int64_
                                            int64_t *n);
 
 /* out[0] active members, out[1] free cells, out[2] free emitters,
- * out[3] ray capacity, out[4] queue slots in use by live rays (waits for
- * enqueued work), out[5] free slots. */
+ * out[3] ray capacity, out[4] queue slots in use by live rays after the last
+ * step seen complete (does not wait for enqueued steps; exact after
+ * flexrt_batch_sync), out[5] free slots. */
 flexrt_status flexrt_batch_info(flexrt_batch *b, int64_t out[6]);
 flexrt_status flexrt_batch_set_launch(flexrt_batch *b, int32_t agg, int32_t minb, int32_t blocks_per_sm,
                                       int32_t threads, int32_t slab);

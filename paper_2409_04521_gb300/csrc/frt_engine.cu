@@ -151,6 +151,8 @@ Engine::~Engine() {
     alloc_sizes_.clear();
     if (h_err_) cudaFreeHost(h_err_);
     if (h_stage_) cudaFreeHost(h_stage_);
+    if (h_nh_) cudaFreeHost(h_nh_);
+    if (ev_nh_) cudaEventDestroy(ev_nh_);
     if (ev_err_) cudaEventDestroy(ev_err_);
     if (ev_stage_) cudaEventDestroy(ev_stage_);
     for (auto e : ev_pool_) cudaEventDestroy(e);
@@ -273,6 +275,13 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
         CK(cudaMemsetAsync(mwmem_, 0, tot, st_));
     }
     if (cudaMallocHost(&h_err_, 64) != cudaSuccess) return fail(FLEXRT_E_OOM, "pinned allocation failed");
+    if (ms > 1) {
+        // members are admitted while others step: their densities go up
+        // through pinned staging, so that admission does not wait for the GPU
+        const size_t nh = (size_t)cfg_.max_grid * cfg_.max_grid * cfg_.max_grid * sizeof(double);
+        if (cudaMallocHost(&h_nh_, nh) != cudaSuccess) return fail(FLEXRT_E_OOM, "pinned allocation failed");
+        CK(cudaEventCreateWithFlags(&ev_nh_, cudaEventDisableTiming));
+    }
     if (cudaMallocHost(&h_stage_, (size_t)(ms + 1) * 6 * sizeof(double)) != cudaSuccess)
         return fail(FLEXRT_E_OOM, "pinned allocation failed");
     CK(cudaEventCreateWithFlags(&ev_err_, cudaEventDisableTiming));
@@ -488,7 +497,6 @@ flexrt_status Engine::add_sim(const SimDev &proto, const double *n_H, int *slot_
             return fail(FLEXRT_E_INVALID, "members of one engine must use the same gamma_iters");
     const long long c0 = cell_alloc_.alloc(proto.ncell);
     if (c0 < 0) return fail(FLEXRT_E_CAPACITY, "cell arena full");
-    CK(cudaStreamSynchronize(st_));
     Slot &sl = slots_[s];
     sl = Slot();
     sl.used = true;
@@ -499,11 +507,22 @@ flexrt_status Engine::add_sim(const SimDev &proto, const double *n_H, int *slot_
     sl.h.step = 0;
     sl.h.active = 1;
     sl.cell0 = c0;
-    CK(cudaMemcpy(sims_ + s, &sl.h, sizeof(SimDev), cudaMemcpyHostToDevice));
-    CK(cudaMemset(acc_ + s, 0, sizeof(SimAcc)));
-    CK(cudaMemcpy(cells_.nH + c0, n_H, (size_t)proto.ncell * sizeof(double), cudaMemcpyHostToDevice));
+    // everything in stream order, behind the steps already enqueued (the
+    // member's cells may be those of a member retired before them): the host
+    // does not wait for the GPU
+    CK(cudaMemcpyAsync(sims_ + s, &sl.h, sizeof(SimDev), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemsetAsync(acc_ + s, 0, sizeof(SimAcc), st_));
+    const size_t nhb = (size_t)proto.ncell * sizeof(double);
+    if (h_nh_ && nhb <= (size_t)cfg_.max_grid * cfg_.max_grid * cfg_.max_grid * sizeof(double)) {
+        CK(cudaEventSynchronize(ev_nh_));            // the previous admission's upload is done
+        std::memcpy(h_nh_, n_H, nhb);
+        CK(cudaMemcpyAsync(cells_.nH + c0, h_nh_, nhb, cudaMemcpyHostToDevice, st_));
+        CK(cudaEventRecord(ev_nh_, st_));
+    } else {
+        CK(cudaMemcpyAsync(cells_.nH + c0, n_H, nhb, cudaMemcpyHostToDevice, st_));
+        CK(cudaStreamSynchronize(st_));              // n_H is the caller's pageable memory
+    }
     CK(launch_init_cells(sims_, s, cells_, proto.ncell, st_));
-    CK(cudaStreamSynchronize(st_));
     flexrt_status r = upload_lists();
     if (r != FLEXRT_OK) return r;
     *slot_out = s;
@@ -531,7 +550,6 @@ flexrt_status Engine::add_sources(int s, int32_t n, const int32_t *ijk, const do
         else { cell.push_back(make_int4(q[0], q[1], q[2], s)); rate.push_back(ndot[i]); }
     }
     const int ne = (int)cell.size();
-    CK(cudaStreamSynchronize(st_));
     if (ne > sl.em_n) {
         if (sl.em0 >= 0 && sl.em_n > 0) {
             // grow in place: only the single-simulation engine owns the whole table
@@ -559,11 +577,11 @@ flexrt_status Engine::add_sources(int s, int32_t n, const int32_t *ijk, const do
         if (mx > 0) {
             sl.h.nref = std::ldexp(1.0, (int)std::lround(std::log2(mx * MYR_S * sl.h.inv_ncast)));
             sl.nref_set = true;
-            CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, nref), &sl.h.nref, sizeof(double),
-                          cudaMemcpyHostToDevice));
+            CK(cudaMemcpyAsync((char *)(sims_ + s) + offsetof(SimDev, nref), &sl.h.nref, sizeof(double),
+                               cudaMemcpyHostToDevice, st_));
             sl.h.apn_f = atoms_per_nH(sl.h);
-            CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, apn_f), &sl.h.apn_f, sizeof(float),
-                          cudaMemcpyHostToDevice));
+            CK(cudaMemcpyAsync((char *)(sims_ + s) + offsetof(SimDev, apn_f), &sl.h.apn_f, sizeof(float),
+                               cudaMemcpyHostToDevice, st_));
             if (sl.h.dt > 0) {
                 const double dt = sl.h.dt;
                 sl.h.dt = 0.0;
@@ -575,9 +593,11 @@ flexrt_status Engine::add_sources(int s, int32_t n, const int32_t *ijk, const do
     }
     std::vector<int32_t> local(ne);
     for (int k = 0; k < ne; ++k) local[k] = k;
-    CK(cudaMemcpy(em_.cell + sl.em0, cell.data(), ne * sizeof(int4), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(em_.ndot + sl.em0, rate.data(), ne * sizeof(double), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(em_.local + sl.em0, local.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // pageable sources: each copy is staged before the call returns, and
+    // runs in stream order behind the steps already enqueued
+    CK(cudaMemcpyAsync(em_.cell + sl.em0, cell.data(), ne * sizeof(int4), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(em_.ndot + sl.em0, rate.data(), ne * sizeof(double), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(em_.local + sl.em0, local.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
     return upload_lists();
 }
 
@@ -601,23 +621,24 @@ flexrt_status Engine::upload_lists() {
         sim.push_back(s);
     }
     if ((long long)act.size() > em_cap_) return fail(FLEXRT_E_CAPACITY, "emitter list");
-    CK(cudaStreamSynchronize(st_));
+    // in stream order: the steps already enqueued read the old lists, the
+    // next ones the new (pageable sources, staged before each call returns)
     if (!act.empty()) {
-        CK(cudaMemcpy(em_.act, act.data(), act.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(em_.act_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(em_.act, act.data(), act.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
+        CK(cudaMemcpyAsync(em_.act_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, st_));
     }
     if (!sim.empty()) {
-        CK(cudaMemcpy(rg_.pref, pref.data(), pref.size() * sizeof(long long), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(rg_.cell0, cell0.data(), cell0.size() * sizeof(long long), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(rg_.sim, sim.data(), sim.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(rg_.pref, pref.data(), pref.size() * sizeof(long long), cudaMemcpyHostToDevice, st_));
+        CK(cudaMemcpyAsync(rg_.cell0, cell0.data(), cell0.size() * sizeof(long long), cudaMemcpyHostToDevice, st_));
+        CK(cudaMemcpyAsync(rg_.sim, sim.data(), sim.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st_));
     }
     const long long et = run;
     const int32_t na = (int32_t)act.size(), nr = (int32_t)sim.size();
     const long long nca = pref.back();
-    CK(cudaMemcpy((char *)ctl_ + offsetof(Ctl, emit_total), &et, sizeof(et), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy((char *)ctl_ + offsetof(Ctl, n_act_emit), &na, sizeof(na), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy((char *)ctl_ + offsetof(Ctl, n_ranges), &nr, sizeof(nr), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy((char *)ctl_ + offsetof(Ctl, ncell_active), &nca, sizeof(nca), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync((char *)ctl_ + offsetof(Ctl, emit_total), &et, sizeof(et), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync((char *)ctl_ + offsetof(Ctl, n_act_emit), &na, sizeof(na), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync((char *)ctl_ + offsetof(Ctl, n_ranges), &nr, sizeof(nr), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync((char *)ctl_ + offsetof(Ctl, ncell_active), &nca, sizeof(nca), cudaMemcpyHostToDevice, st_));
     return FLEXRT_OK;
 }
 
@@ -657,7 +678,9 @@ flexrt_status Engine::poll(bool wait) {
         return FLEXRT_OK;
     }
     err_pending_ = false;
-    const int32_t v = *h_err_;
+    static_assert(offsetof(Ctl, par) == 16 && offsetof(Ctl, err) == 20, "ctl layout");
+    const int32_t v = h_err_[5];
+    q_used_ = reinterpret_cast<const long long *>(h_err_)[h_err_[4] & 1];
     if (v) {
         latched_ = FLEXRT_E_CAPACITY;
         if (v & 1) err_ = "ray queue capacity exceeded; state kept at the last complete step";
@@ -772,7 +795,8 @@ flexrt_status Engine::step() {
         flexrt_status r = launch_step();
         if (r != FLEXRT_OK) return r;
     }
-    CK(cudaMemcpyAsync(h_err_, (char *)ctl_ + offsetof(Ctl, err), sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    // queue counts, parity and error word of the step, read when it completes
+    CK(cudaMemcpyAsync(h_err_, ctl_, offsetof(Ctl, err) + sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     CK(cudaEventRecord(ev_err_, st_));
     err_pending_ = true;
     ++steps_taken_;
@@ -799,7 +823,8 @@ flexrt_status Engine::step_stage(int stage) {
     mid_step_ = false;
     flexrt_status s = launch_stage(2);
     if (s != FLEXRT_OK) return s;
-    CK(cudaMemcpyAsync(h_err_, (char *)ctl_ + offsetof(Ctl, err), sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
+    // queue counts, parity and error word of the step, read when it completes
+    CK(cudaMemcpyAsync(h_err_, ctl_, offsetof(Ctl, err) + sizeof(int32_t), cudaMemcpyDeviceToHost, st_));
     CK(cudaEventRecord(ev_err_, st_));
     err_pending_ = true;
     ++steps_taken_;
@@ -815,12 +840,13 @@ flexrt_status Engine::sync() {
 
 flexrt_status Engine::retire(int s) {
     if (s < 0 || s >= (int)slots_.size() || !slots_[s].active) return fail(FLEXRT_E_INVALID, "bad slot");
-    CK(cudaStreamSynchronize(st_));
     Slot &sl = slots_[s];
     sl.active = false;
     sl.h.active = 0;
     const int32_t zero = 0;
-    CK(cudaMemcpy((char *)(sims_ + s) + offsetof(SimDev, active), &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    // stream-ordered: the steps already enqueued still advance the member
+    CK(cudaMemcpyAsync((char *)(sims_ + s) + offsetof(SimDev, active), &zero, sizeof(zero), cudaMemcpyHostToDevice,
+                       st_));
     cell_alloc_.release(sl.cell0, sl.h.ncell);
     sl.release_after = steps_taken_;   // its rays are dropped by the next step's march
     return upload_lists();
@@ -1098,11 +1124,11 @@ int Engine::free_slots() const {
 }
 
 flexrt_status Engine::queue_used(long long *n) {
-    CK(cudaStreamSynchronize(st_));
-    Ctl hc;
-    CK(cudaMemcpy(&hc, ctl_, sizeof(hc), cudaMemcpyDeviceToHost));
-    *n = hc.cnt[hc.par];
-    return FLEXRT_OK;
+    // the count after the last step seen complete (without waiting for the
+    // GPU); exact after sync()
+    flexrt_status r = poll(false);
+    *n = q_used_;
+    return r;
 }
 
 int Engine::active_count() const {

@@ -100,7 +100,7 @@ class Engine {
     flexrt_status kernel_times(double ms[4], int64_t launches[4], int64_t *rays);
     int active_count() const;
     int free_slots() const;
-    flexrt_status queue_used(long long *n);   // slots of the live ray queue (synchronises)
+    flexrt_status queue_used(long long *n);   // queue slots after the last step seen complete
     long long cells_free() const { return cell_alloc_.capacity() - cell_alloc_.used(); }
     long long emitters_free() const { return em_alloc_.capacity() - em_alloc_.used(); }
     const Slot *slot(int s) const { return (s >= 0 && s < (int)slots_.size() && slots_[s].used) ? &slots_[s] : nullptr; }
@@ -149,8 +149,11 @@ class Engine {
     int march_agg_ = 0, march_minb_ = 3, march_blocks_ = 1, march_threads_ = 256, march_slab_ = OUT_SLAB;
     int chem_blocks_ = 1, emit_blocks_ = 1, sm_count_ = 1;
 
-    int32_t *h_err_ = nullptr;
+    int32_t *h_err_ = nullptr;     // the last step's queue counts, parity and error word
     double *h_stage_ = nullptr;
+    double *h_nh_ = nullptr;       // pinned staging of a member's n_H (engines of several members)
+    cudaEvent_t ev_nh_ = nullptr;  // its upload has been consumed
+    long long q_used_ = 0;         // live rays after the last step the host has seen complete
     cudaEvent_t ev_err_ = nullptr, ev_stage_ = nullptr;
     bool err_pending_ = false;
 
