@@ -128,16 +128,17 @@ __device__ __forceinline__ uint64_t sm64(uint64_t z) {
 }
 constexpr uint64_t GOLD = 0x9E3779B97F4A7C15ULL;
 
-// num / den rounded half to even, for 0 < den <= 2^30 and |num / den| <= 2^24:
-// a single-precision estimate (within a few units) corrected exactly by the
-// remainder
-__device__ __forceinline__ int32_t div_round_even(long long num, long long den) {
-    long long q = __float2ll_rz(__fdividef((float)num, (float)den));
-    long long r = num - q * den;
+// num / den rounded half to even, for 0 < den <= 2^30 and |num / den| <= 2^24,
+// given rden, the single-precision reciprocal of den: an estimate within a
+// few units (three single-precision roundings of a quotient below 2^24)
+// corrected exactly by the remainder
+__device__ __forceinline__ int32_t div_round_even(long long num, int32_t den, float rden) {
+    int32_t q = __float2int_rz((float)num * rden);
+    long long r = num - (long long)q * den;
     for (int k = 0; k < 16 && r < 0; ++k) { --q; r += den; }
     for (int k = 0; k < 16 && r >= den; ++k) { ++q; r -= den; }
     if (2 * r > den || (2 * r == den && (q & 1))) ++q;
-    return (int32_t)q;
+    return q;
 }
 
 __device__ inline void rotation_rows(uint64_t seed, long long e, long long s, int rotate, int4 rows[3]) {
@@ -159,8 +160,9 @@ __device__ inline void rotation_rows(uint64_t seed, long long e, long long s, in
                             2 * (x * y + w * z), w * w - x * x + y * y - z * z, 2 * (y * z - w * x),
                             2 * (x * z - w * y), 2 * (y * z + w * x), w * w - x * x - y * y + z * z};
     int32_t q[9];
+    const float rn = __frcp_rn((float)n);          // one reciprocal for the nine entries
 #pragma unroll
-    for (int i = 0; i < 9; ++i) q[i] = div_round_even(Q[i] * (1LL << VQ_BITS), n);
+    for (int i = 0; i < 9; ++i) q[i] = div_round_even(Q[i] * (1LL << VQ_BITS), (int32_t)n, rn);
     for (int r = 0; r < 3; ++r) rows[r] = make_int4(q[3 * r], q[3 * r + 1], q[3 * r + 2], 0);
 }
 

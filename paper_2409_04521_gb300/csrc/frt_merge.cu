@@ -81,6 +81,7 @@ constexpr int SEL_STATE = 0, SEL_HIGH = 1, SEL_ABOVE = 2, SEL_T = 3, SEL_EXEMPT 
 constexpr uint32_t SEL_OFF = 0, SEL_PASS2 = 1, SEL_DONE = 2;
 constexpr int WBITS = 28;                    // merge weights below 2^28
 constexpr uint32_t NO_GROUP = 0xffffffffu;   // a queue slot that is in no group
+constexpr uint32_t NO_KEY = 0xffffffffu;     // one simulation: a slot not taking part (not a content)
 constexpr int GSUMS = 6;                     // integer sums: weight, weighted x, y, z, distance, level
 
 // num / den rounded to nearest, ties to even, for num < 2^62 and a
@@ -250,25 +251,32 @@ __global__ void __launch_bounds__(256) k_mhist1(MergeArgs A) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += (long long)gridDim.x * blockDim.x) {
         long long bin = -1;
         if (i < n) {
+            // the ray's words together (a single simulation needs no
+            // emitter lookup); bins past a member's own are zero
+            const uint32_t pl = q.pl[i];
+            const uint32_t e = A.nsims > 1 ? q.em[i] : 0u;
+            float ph[MAXB];
+#pragma unroll
+            for (int b = 0; b < MAXB; ++b) ph[b] = b < A.nbq ? q.ph[b][i] : 0.0f;
             int sim = -1;
             uint32_t key = 0;
-            const uint32_t pl = q.pl[i];
             if (pl != DEAD_RAY) {
-                const uint32_t e = q.em[i];
-                const int s = ray_sim(q, A.em, i, e);
-                const SimDev &S = A.sims[s];
-                if (merges(S, A.acc[s])) {
+                const int s = A.nsims > 1 ? ray_sim(q, A.em, i, e) : 0;
+                if (merges(A.sims[s], A.acc[s])) {
                     float T = 0.0f;
 #pragma unroll
-                    for (int b = 0; b < MAXB; ++b)
-                        if (b < S.nb) T += q.ph[b][i];
+                    for (int b = 0; b < MAXB; ++b) T += ph[b];
                     key = __float_as_uint(T);
                     sim = s;
                     bin = hist_row(A.w, s) + (key >> 16);
                 }
             }
-            A.w.tkey[i] = key;
-            A.w.tsim[i] = sim;
+            if (A.nsims > 1) {
+                A.w.tkey[i] = key;
+                A.w.tsim[i] = sim;
+            } else {
+                A.w.tkey[i] = sim >= 0 ? key : NO_KEY;   // one simulation: the key says it all
+            }
         }
         hist_add(A.w.hist, bin);
     }
@@ -383,6 +391,17 @@ __device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t *s_wofs, uint
     return r;
 }
 
+// the participating ray at slot i: its simulation (-1: none) and rank content
+__device__ __forceinline__ int slot_key(const MergeArgs &A, long long i, uint32_t &key) {
+    if (A.nsims > 1) {
+        const int sim = A.w.tsim[i];
+        key = sim >= 0 ? A.w.tkey[i] : 0u;
+        return sim;
+    }
+    key = A.w.tkey[i];
+    return key != NO_KEY ? 0 : -1;
+}
+
 // per ray in the selected upper bin: a histogram of the lower bits; and the
 // block's candidate list (the march writes a parent's children next to each
 // other, and the group pass combines the sums of neighbours in the list)
@@ -402,10 +421,9 @@ __global__ void __launch_bounds__(256) k_mhist2(MergeArgs A) {
         bool cand = false;
         uint32_t key = 0;
         if (i < b1) {
-            const int sim = A.w.tsim[i];
+            const int sim = slot_key(A, i, key);
             if (sim >= 0) {
                 const uint32_t *sel = A.w.sel + SEL_W * sim;
-                key = A.w.tkey[i];
                 if (sel[SEL_STATE] == SEL_PASS2) {
                     const uint32_t hi = key >> 16, high = sel[SEL_HIGH];
                     if (hi == high) bin = hist_row(A.w, sim) + (key & 0xffffu);
@@ -459,7 +477,7 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
         if (c < b1) {
             i = A.w.cand[c];
             key = A.w.ckey[c];
-            sim = A.w.tsim[i];
+            sim = A.nsims > 1 ? A.w.tsim[i] : 0;   // a candidate belongs to a merging simulation
         }
         if (sim >= 0) {
             const uint32_t *sel = A.w.sel + SEL_W * sim;
@@ -579,7 +597,7 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
         const bool leads = slot >= 0 && gm.z == ~(uint32_t)c;
         int sim = -1;
         if (slot >= 0) {
-            sim = A.w.tsim[qi];
+            sim = A.nsims > 1 ? A.w.tsim[qi] : 0;
             q.pl[qi] = DEAD_RAY;
         }
         unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
