@@ -667,7 +667,11 @@ def impl_merge(args, dist):
                 "config": {"workload": "merge: " + WORKLOAD_DESC + "; ray merging as Sec. 7.1",
                            "cases": [c[0] for c in cases], "timed_case": best},
                 "results": results, "clocks": clk,
-                "gpu_launches": args.steps * (1 + base.nsteps * 11)}
+                # per simulation: the cells' initialisation, then per RT step emission,
+                # march, chemistry and the budget's commit plus the merge's ten
+                # launches (rotations, content histogram, two radix-select passes of
+                # copy reduction and search, lower-bits histogram, group, weight, emit)
+                "gpu_launches": args.steps * (1 + base.nsteps * (4 + 10))}
         print(json.dumps(line), flush=True)
 
 
