@@ -16,20 +16,22 @@
 //               (those at most in T_ref's upper bin), so that the passes
 //               below run over candidates only, with whole warps;
 //   k_mgroup  : per non-exempt candidate, its end cell and merge pixel; a
-//               group slot per (cell, pixel) takes its photons and threshold
-//               (vector reductions), the largest member content and the ray's
-//               arrival rank: rank 0 leads the group, the others leave the
-//               queue (their slots become holes); the candidate's group slot,
-//               end point, distance and level are kept per candidate;
-//   k_mweight : per candidate in a group of two or more, its photon weight --
+//               group slot per (cell, pixel) counts its members and takes the
+//               largest member content and the leader (the member with the
+//               lowest list index); the candidate's group slot, end point,
+//               distance and level are kept per candidate;
+//   k_mweight : per candidate in a group of two or more, its photons and
+//               termination threshold (vector reductions; rays alone in their
+//               group never load them), its photon weight --
 //               the content on a grid of 2^-28 of the power of two above its
 //               group's largest content, truncated, at least 1 -- and the
 //               weighted end point, distance and level as exact 64-bit
 //               integer sums, so the photon-weighted means are exact quotients
 //               of sums that do not depend on the summation order, to 2^-27 of
-//               the group's brightest member; each group's leader leaves a
-//               hole too and takes the next entry of the merged-ray list; a
-//               ray alone in its group stays and clears the group;
+//               the group's brightest member; every member leaves a hole
+//               in the queue and each group's leader takes the next entry of
+//               the merged-ray list; a ray alone in its group stays and
+//               clears the group's word;
 //   k_memit   : per entry of that list, the merged ray (means rounded once),
 //               appended densely after the march's output, and the group
 //               cleared for the next step.
@@ -461,16 +463,12 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
     const Queue q = A.q[par ^ 1];
     const long long b0 = blockIdx.x * block_chunk(C->cnt[par ^ 1]);
     const long long b1 = b0 + A.w.bcnt[blockIdx.x];
-    const int ndir = A.w.ndir, gw = A.w.grp_w;
+    const int ndir = A.w.ndir;
     const int lane = lane_id();
     for (long long base = b0 + (threadIdx.x & ~31); base < b1; base += blockDim.x) {
         const long long c = base + lane;
         long long slot = -1;
         uint4 pack = make_uint4(NO_GROUP, 0u, 0u, 0u);
-        float f[MAXB + 4];
-#pragma unroll
-        for (int k = 0; k < MAXB + 4; ++k) f[k] = 0.0f;
-        int nbf = 0;
         int sim = -1;
         uint32_t key = 0;
         long long i = 0;
@@ -487,20 +485,14 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
                 const uint32_t e = q.em[i], pl = q.pl[i];
                 const int bi = q.bi[i];
                 const int dx = q.dx[i], dy = q.dy[i], dz = q.dz[i];
-                const int nbs = S.nb;
-#pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < nbs) f[b] = q.ph[b][i];
                 const int lev = (int)(pl >> LEVEL_SHIFT);
                 // end point of this step's march and the distance travelled
                 long long p[3];
                 int dist;
-                float thr;
                 if (e & MERGED_BIT) {
                     const long long k = S.step - bi;
                     p[0] = q.mx[i] + k * dx; p[1] = q.my[i] + k * dy; p[2] = q.mz[i] + k * dz;
                     dist = (int)(q.ma[i] & 0xffffu) + (int)k;
-                    thr = q.mthr[i];
                 } else {
                     const int4 ec = __ldg(&A.em.cell[e]);
                     const long long k = S.step - bi + 1;
@@ -508,7 +500,6 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
                     p[1] = ((2LL * ec.y + 1) << (FRAC_BITS - 1)) + k * dy;
                     p[2] = ((2LL * ec.z + 1) << (FRAC_BITS - 1)) + k * dz;
                     dist = (int)k;
-                    thr = S.eps_term * __ldg(&A.em.n0[e]) * pow2_neg(2 * (lev - S.l_src));
                 }
                 const long long cx = p[0] >> FRAC_BITS, cy = p[1] >> FRAC_BITS, cz = p[2] >> FRAC_BITS;
                 if (cx >= 0 && cy >= 0 && cz >= 0 && cx < S.nx && cy < S.ny && cz < S.nz) {
@@ -524,27 +515,18 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
                     const uint32_t ud = (uint32_t)min(dist, 65535);
                     pack = make_uint4((uint32_t)slot, ox | ((uint32_t)lev << 21), oy | ((ud & 0x7ffu) << 21),
                                       oz | ((ud >> 11) << 21));
-                    nbf = nbs;
-#pragma unroll
-                    for (int b = 0; b <= MAXB; ++b)
-                        if (b == nbs) f[b] = thr;
                 }
             }
         }
         if (c < b1) A.w.tgrp[c] = pack;
         // combine equal groups in the warp, then one set of reductions per group
         const unsigned peers = __match_any_sync(FULL, slot);
-        if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) peer_sum<MAXB + 4, float>(peers, f);
         const uint32_t kmax = __reduce_max_sync(peers, slot >= 0 ? key : 0u);
         if (slot >= 0 && (peers & ((1u << lane) - 1u)) == 0u) {
             uint4 *gc = A.w.gcm + slot;
             atomicAdd(&gc->x, (uint32_t)__popc(peers));
             atomicMax(&gc->y, kmax);
             atomicMax(&gc->z, ~(uint32_t)c);       // the lowest index of the peers is this lane's
-            float4 *gf = reinterpret_cast<float4 *>(A.w.grp + slot * gw + 2 * GSUMS);
-#pragma unroll
-            for (int b = 0; b <= MAXB; b += 4)
-                if (b <= nbf) red_add_v4(gf + b / 4, f[b], f[b + 1], f[b + 2], f[b + 3]);
         }
     }
 }
@@ -588,16 +570,32 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
         if (slot >= 0) gm = A.w.gcm[slot];
         if (slot >= 0 && gm.x < 2u) {
             // alone in its group: the ray stays as it is, and clears the
-            // group (no other ray touched it)
-            float4 *gz = reinterpret_cast<float4 *>(A.w.grp + slot * gw + 2 * GSUMS);
-            for (int b = 0; b < gw / 4 - GSUMS / 2; ++b) gz[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+            // group's word (no other ray touched the group)
             A.w.gcm[slot] = make_uint4(0u, 0u, 0u, 0u);
             slot = -1;
         }
         const bool leads = slot >= 0 && gm.z == ~(uint32_t)c;
         int sim = -1;
+        // a merging member's photons and termination threshold (only rays
+        // that merge load them)
+        float f[MAXB + 4];
+#pragma unroll
+        for (int k = 0; k < MAXB + 4; ++k) f[k] = 0.0f;
+        int nbf = 0;
         if (slot >= 0) {
             sim = A.nsims > 1 ? A.w.tsim[qi] : 0;
+            const SimDev &S = A.sims[sim];
+            const uint32_t e = q.em[qi];
+            nbf = S.nb;
+#pragma unroll
+            for (int b = 0; b < MAXB; ++b)
+                if (b < nbf) f[b] = q.ph[b][qi];
+            const int lev = (int)((pk.y >> 21) & 0xfu);
+            const float thr = (e & MERGED_BIT) ? q.mthr[qi]
+                                               : S.eps_term * __ldg(&A.em.n0[e]) * pow2_neg(2 * (lev - S.l_src));
+#pragma unroll
+            for (int b = 0; b <= MAXB; ++b)
+                if (b == nbf) f[b] = thr;
             q.pl[qi] = DEAD_RAY;
         }
         unsigned long long v[GSUMS] = {0, 0, 0, 0, 0, 0};
@@ -610,14 +608,21 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
             v[2] = qw * (unsigned long long)(pk.z & 0x1fffffu);
             v[3] = qw * (unsigned long long)(pk.w & 0x1fffffu);
             v[4] = qw * (unsigned long long)((pk.z >> 21) | ((pk.w >> 21) << 11));
-            v[5] = qw * (unsigned long long)(pk.y >> 21);
+            v[5] = qw * (unsigned long long)((pk.y >> 21) & 0xfu);
         }
         const unsigned peers = __match_any_sync(FULL, slot);
-        if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) peer_sum<GSUMS, unsigned long long>(peers, v);
+        if (__any_sync(FULL, slot >= 0 && __popc(peers) > 1)) {
+            peer_sum<GSUMS, unsigned long long>(peers, v);
+            peer_sum<MAXB + 4, float>(peers, f);
+        }
         if (slot >= 0 && (peers & ((1u << lane) - 1u)) == 0u) {
             unsigned long long *gs = reinterpret_cast<unsigned long long *>(A.w.grp + slot * gw);
 #pragma unroll
             for (int k = 0; k < GSUMS; ++k) atomicAdd(gs + k, v[k]);
+            float4 *gf = reinterpret_cast<float4 *>(A.w.grp + slot * gw + 2 * GSUMS);
+#pragma unroll
+            for (int b = 0; b <= MAXB; b += 4)
+                if (b <= nbf) red_add_v4(gf + b / 4, f[b], f[b + 1], f[b + 2], f[b + 3]);
         }
         // rays removed: every member of a merging group but one
         const int dsim = slot >= 0 && !leads ? sim : -1;
