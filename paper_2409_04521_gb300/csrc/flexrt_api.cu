@@ -496,7 +496,7 @@ extern "C" flexrt_status flexrt_probe_merge(const flexrt_merge_probe *p, int64_t
     w.grp_w = gw; w.hrep = 1; w.lead_slot = lead_slot.p; w.lead_sim = lead_sim.p;
     w.bcnt = bcnt.p; w.bled = bled.p; w.lead_cap = ml;
     MergeArgs a{dctl.p, dsim.p, dacc.p, 1, {q0, q1}, em, rg, tab, lt, w, nb, mq};
-    if (launch_merge(a, sms, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    if (launch_merge(a, sms, 0, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
         return free_fail(FLEXRT_E_CUDA, "probe_merge: kernels failed");
     Ctl hc;
     if (cudaMemcpy(&hc, dctl.p, sizeof(hc), cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -158,6 +158,9 @@ Engine::~Engine() {
     for (auto e : ev_pool_) cudaEventDestroy(e);
     for (auto &v : ev_k_)
         for (auto &p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    if (mside_.fork) cudaEventDestroy(mside_.fork);
+    if (mside_.join) cudaEventDestroy(mside_.join);
+    if (mside_.st) cudaStreamDestroy(mside_.st);
     if (own_stream_ && st_) cudaStreamDestroy(st_);
 }
 
@@ -273,6 +276,9 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
         for (size_t k = 0; k < sizeof(sz) / sizeof(sz[0]); ++k) { *dst[k] = p; p += (sz[k] + 255) & ~(size_t)255; }
         if (cap >= (1LL << 32)) return fail(FLEXRT_E_INVALID, "merging needs fewer than 2^32 queue slots");
         CK(cudaMemsetAsync(mwmem_, 0, tot, st_));
+        CK(cudaStreamCreateWithFlags(&mside_.st, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&mside_.fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&mside_.join, cudaEventDisableTiming));
     }
     if (cudaMallocHost(&h_err_, 64) != cudaSuccess) return fail(FLEXRT_E_OOM, "pinned allocation failed");
     if (ms > 1) {
@@ -751,7 +757,7 @@ flexrt_status Engine::launch_stage(int stage) {
     if (merge_built()) {
         MergeArgs ga{ctl_, sims_, acc_, ms, {q_[0], q_[1]}, em_, rg_, pixtab_, ltab_, mw_, cfg_.nb, qcap_};
         tic();
-        CK(launch_merge(ga, sm_count_, st_));
+        CK(launch_merge(ga, sm_count_, st_, &mside_));
         toc(3);
     }
     tic();

@@ -155,6 +155,7 @@ class Engine {
     cudaEvent_t ev_nh_ = nullptr;  // its upload has been consumed
     long long q_used_ = 0;         // live rays after the last step the host has seen complete
     cudaEvent_t ev_err_ = nullptr, ev_stage_ = nullptr;
+    MergeSide mside_{nullptr, nullptr, nullptr};   // merging engines: the rotation pass's stream
     bool err_pending_ = false;
 
     bool profiling_ = false;

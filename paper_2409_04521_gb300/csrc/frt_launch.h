@@ -76,7 +76,13 @@ cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_
 // between passes of the iteration: drop the march's output and the step's tallies (not emission)
 cudaError_t launch_iter_reset(Ctl *c, SimAcc *acc, int nsims, cudaStream_t st);
 // the merge step (Sec. 3.3) between the march and the chemistry
-cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st);
+// a second stream for the merge's independent rotation pass, with the events
+// that fork it from the step's stream and join it back
+struct MergeSide {
+    cudaStream_t st;
+    cudaEvent_t fork, join;
+};
+cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st, const MergeSide *side);
 cudaError_t launch_probe_merge_pixel(int level, long long n, const int32_t *d, const int32_t *Rq, bool per_ray,
                                      uint32_t *out, cudaStream_t st);
 cudaError_t launch_probe_pixvec(int level, long long p0, long long n, int32_t *out, cudaStream_t st);

@@ -109,6 +109,7 @@ __device__ __forceinline__ bool merges(const SimDev &S, const SimAcc &a) {
 
 // warp-aggregated histogram increment; bin < 0: nothing
 __device__ __forceinline__ void hist_add(uint32_t *hist, long long bin) {
+    if (!__any_sync(FULL, bin >= 0)) return;               // warp-uniform
     const unsigned peers = __match_any_sync(FULL, bin);
     const int lane = lane_id();
     if (bin >= 0 && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(hist + bin, (uint32_t)__popc(peers));
@@ -370,8 +371,10 @@ __device__ __forceinline__ long long block_chunk(long long n) {
 }
 
 // Exclusive positions, within a window of the block's 256 threads, of the
-// threads whose flag is set; *total gets the window's count.  Three barriers:
-// every thread of the block calls it.
+// threads whose flag is set; *total gets the window's count.  Two barriers:
+// every thread of the block calls it, with the two buffers of s_wofs taken in
+// turn by successive windows (a buffer is written again only two windows
+// later, after every thread has passed the next window's barriers).
 __device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t *s_wofs, uint32_t *total) {
     const int lane = lane_id(), wid = threadIdx.x >> 5;
     const unsigned m = __ballot_sync(FULL, flag);
@@ -389,7 +392,6 @@ __device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t *s_wofs, uint
     __syncthreads();
     const uint32_t r = s_wofs[wid] + (uint32_t)__popc(m & ((1u << lane) - 1u));
     *total = s_wofs[8];
-    __syncthreads();                               // the words are reused by the next window
     return r;
 }
 
@@ -408,7 +410,7 @@ __device__ __forceinline__ int slot_key(const MergeArgs &A, long long i, uint32_
 // block's candidate list (the march writes a parent's children next to each
 // other, and the group pass combines the sums of neighbours in the list)
 __global__ void __launch_bounds__(256) k_mhist2(MergeArgs A) {
-    __shared__ uint32_t s_wofs[9];
+    __shared__ uint32_t s_wofs[2][9];
     __shared__ int s_on;
     Ctl *C = A.ctl;
     if (!block_runs(C, false, &s_on)) return;
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(256) k_mhist2(MergeArgs A) {
         }
         hist_add(A.w.hist, bin);
         uint32_t tot;
-        const uint32_t r = block_rank(cand, s_wofs, &tot);
+        const uint32_t r = block_rank(cand, s_wofs[((w0 - b0) >> 8) & 1], &tot);
         if (cand) {
             A.w.cand[b0 + run + r] = (uint32_t)i;
             A.w.ckey[b0 + run + r] = key;
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(256, 4) k_mgroup(MergeArgs A) {
 // Every member of a group of two or more leaves the queue (its slot becomes a
 // hole); the leader lists the group in the block's merged-ray list.
 __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
-    __shared__ uint32_t s_wofs[9];
+    __shared__ uint32_t s_wofs[2][9];
     __shared__ int s_on;
     extern __shared__ uint32_t s_drop[];           // per simulation: rays removed
     for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) s_drop[k] = 0u;
@@ -558,13 +560,7 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
         const bool in = w0 + threadIdx.x < bc;
         uint4 pk = make_uint4(NO_GROUP, 0u, 0u, 0u);
         uint32_t key = 0, qi = 0;
-        if (in) {
-            pk = A.w.tgrp[c];
-            if (pk.x != NO_GROUP) {
-                key = A.w.ckey[c];
-                qi = A.w.cand[c];
-            }
-        }
+        if (in) pk = A.w.tgrp[c];
         long long slot = pk.x == NO_GROUP ? -1 : (long long)pk.x;
         uint4 gm = make_uint4(0u, 0u, 0u, 0u);
         if (slot >= 0) gm = A.w.gcm[slot];
@@ -573,6 +569,10 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
             // group's word (no other ray touched the group)
             A.w.gcm[slot] = make_uint4(0u, 0u, 0u, 0u);
             slot = -1;
+        }
+        if (slot >= 0) {
+            key = A.w.ckey[c];
+            qi = A.w.cand[c];
         }
         const bool leads = slot >= 0 && gm.z == ~(uint32_t)c;
         int sim = -1;
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
             if (dsim >= 0 && (dp & ((1u << lane) - 1u)) == 0u) atomicAdd(s_drop + dsim, (uint32_t)__popc(dp));
         }
         uint32_t tot;
-        const uint32_t r = block_rank(leads, s_wofs, &tot);
+        const uint32_t r = block_rank(leads, s_wofs[(w0 >> 8) & 1], &tot);
         if (leads) {
             A.w.lead_slot[b0 + run + r] = (uint32_t)slot;
             A.w.lead_sim[b0 + run + r] = sim;
@@ -751,16 +751,30 @@ __global__ void k_probe_merge_pixel(int level, long long n, const int32_t *d, co
     }
 }
 
-cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st) {
+cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st, const MergeSide *side) {
     const int rblocks = std::min(sm_count * 16, MERGE_MAX_BLOCKS);
     const size_t rng_sh = (size_t)(2 * a.nsims + 1) * sizeof(long long) + (size_t)a.nsims * sizeof(int);
-    k_mrot<<<rblocks, 256, rng_sh, st>>>(a);
+    // the merge spheres' rotations depend on no pass of the merge: with a
+    // side stream they are drawn (integer-bound) while the selection passes
+    // (memory-bound) run, and the group pass waits for both
+    cudaError_t e = cudaSuccess;
+    if (side) {
+        e = cudaEventRecord(side->fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side->st, side->fork, 0);
+        if (e != cudaSuccess) return e;
+        k_mrot<<<rblocks, 256, rng_sh, side->st>>>(a);
+        e = cudaEventRecord(side->join, side->st);
+        if (e != cudaSuccess) return e;
+    } else {
+        k_mrot<<<rblocks, 256, rng_sh, st>>>(a);
+    }
     k_mhist1<<<rblocks, 256, 0, st>>>(a);
     if (a.w.hrep > 1) k_mreduce<<<rblocks, 256, 0, st>>>(a, 1);
     k_mfind<<<a.nsims, 1024, 0, st>>>(a, 1);
     k_mhist2<<<rblocks, 256, 0, st>>>(a);
     if (a.w.hrep > 1) k_mreduce<<<rblocks, 256, 0, st>>>(a, 2);
     k_mfind<<<a.nsims, 1024, 0, st>>>(a, 2);
+    if (side && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
     k_mgroup<<<rblocks, 256, 0, st>>>(a);
     k_mweight<<<rblocks, 256, (size_t)a.nsims * sizeof(uint32_t), st>>>(a);
     k_memit<<<rblocks, 256, 0, st>>>(a);
