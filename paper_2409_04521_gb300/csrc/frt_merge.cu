@@ -406,9 +406,39 @@ __device__ __forceinline__ int slot_key(const MergeArgs &A, long long i, uint32_
     return key != NO_KEY ? 0 : -1;
 }
 
+// Exclusive prefix, over the block's 256 threads in order, of a per-thread
+// count; *total gets the block's sum.  Two barriers, the buffers of s_wofs in
+// turn as for block_rank.
+__device__ __forceinline__ uint32_t block_prefix(uint32_t c, uint32_t *s_wofs, uint32_t *total) {
+    const int lane = lane_id(), wid = threadIdx.x >> 5;
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_wofs[wid] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t v = s_wofs[k];
+            s_wofs[k] = t;
+            t += v;
+        }
+        s_wofs[8] = t;
+    }
+    __syncthreads();
+    *total = s_wofs[8];
+    return s_wofs[wid] + inc - c;
+}
+
 // per ray in the selected upper bin: a histogram of the lower bits; and the
 // block's candidate list (the march writes a parent's children next to each
-// other, and the group pass combines the sums of neighbours in the list)
+// other, and the group pass combines the sums of neighbours in the list).
+// Windows of 1024 slots, four consecutive slots a thread (a single
+// simulation's four keys in one 16-byte load), so that every thread has
+// several loads in flight between the window's barriers.
 __global__ void __launch_bounds__(256) k_mhist2(MergeArgs A) {
     __shared__ uint32_t s_wofs[2][9];
     __shared__ int s_on;
@@ -419,29 +449,49 @@ __global__ void __launch_bounds__(256) k_mhist2(MergeArgs A) {
     if (blockIdx.x == 0 && threadIdx.x == 0) C->mbase = n;
     const long long ch = block_chunk(n), b0 = blockIdx.x * ch, b1 = min(n, b0 + ch);
     uint32_t run = 0;                              // candidates listed so far (block-uniform)
-    for (long long w0 = b0; w0 < b1; w0 += 256) {
-        const long long i = w0 + threadIdx.x;
-        long long bin = -1;
-        bool cand = false;
-        uint32_t key = 0;
-        if (i < b1) {
-            const int sim = slot_key(A, i, key);
-            if (sim >= 0) {
-                const uint32_t *sel = A.w.sel + SEL_W * sim;
-                if (sel[SEL_STATE] == SEL_PASS2) {
-                    const uint32_t hi = key >> 16, high = sel[SEL_HIGH];
-                    if (hi == high) bin = hist_row(A.w, sim) + (key & 0xffffu);
-                    cand = !sel[SEL_EXEMPT] || hi <= high;
-                }
+    int wpar = 0;
+    for (long long w0 = b0; w0 < b1; w0 += 1024, wpar ^= 1) {
+        const long long i0 = w0 + 4 * threadIdx.x;  // a multiple of 4: b0 is one of 256
+        uint32_t key[4];
+        int sim[4];
+        if (A.nsims == 1 && i0 + 3 < b1) {
+            const uint4 k4 = *reinterpret_cast<const uint4 *>(A.w.tkey + i0);
+            key[0] = k4.x; key[1] = k4.y; key[2] = k4.z; key[3] = k4.w;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sim[j] = key[j] != NO_KEY ? 0 : -1;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                key[j] = 0u;
+                sim[j] = i0 + j < b1 ? slot_key(A, i0 + j, key[j]) : -1;
             }
         }
-        hist_add(A.w.hist, bin);
-        uint32_t tot;
-        const uint32_t r = block_rank(cand, s_wofs[((w0 - b0) >> 8) & 1], &tot);
-        if (cand) {
-            A.w.cand[b0 + run + r] = (uint32_t)i;
-            A.w.ckey[b0 + run + r] = key;
+        bool cand[4];
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            long long bin = -1;
+            cand[j] = false;
+            if (sim[j] >= 0) {
+                const uint32_t *sel = A.w.sel + SEL_W * sim[j];
+                if (sel[SEL_STATE] == SEL_PASS2) {
+                    const uint32_t hi = key[j] >> 16, high = sel[SEL_HIGH];
+                    if (hi == high) bin = hist_row(A.w, sim[j]) + (key[j] & 0xffffu);
+                    cand[j] = !sel[SEL_EXEMPT] || hi <= high;
+                }
+            }
+            hist_add(A.w.hist, bin);
+            c += cand[j] ? 1u : 0u;
         }
+        uint32_t tot;
+        uint32_t r = run + block_prefix(c, s_wofs[wpar], &tot);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (cand[j]) {
+                A.w.cand[b0 + r] = (uint32_t)(i0 + j);
+                A.w.ckey[b0 + r] = key[j];
+                ++r;
+            }
         run += tot;
     }
     if (threadIdx.x == 0) A.w.bcnt[blockIdx.x] = run;
