@@ -198,7 +198,8 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
 
     // ray queues: one allocation, structure of arrays, two buffers
     {
-        const size_t a = (size_t)cap * 4, per = ray_bytes(cfg_.nb, mrg) * (size_t)cap;
+        // each array starts on a 256-byte boundary (vector loads of the queue)
+        const size_t a = ((size_t)cap * 4 + 255) & ~(size_t)255, per = a * (ray_bytes(cfg_.nb, mrg) / 4);
         char *base = nullptr;
         if (dev_alloc((void **)&base, 2 * per + 256) != cudaSuccess) return fail(FLEXRT_E_OOM, "ray queue allocation failed");
         qmem_ = base;
