@@ -668,10 +668,11 @@ def impl_merge(args, dist):
                            "cases": [c[0] for c in cases], "timed_case": best},
                 "results": results, "clocks": clk,
                 # per simulation: the cells' initialisation, then per RT step emission,
-                # march, chemistry and the budget's commit plus the merge's ten
+                # march, chemistry and the budget's commit plus the merge's eleven
                 # launches (rotations, content histogram, two radix-select passes of
-                # copy reduction and search, lower-bits histogram, group, weight, emit)
-                "gpu_launches": args.steps * (1 + base.nsteps * (4 + 10))}
+                # copy reduction and search, lower-bits histogram, group, weight,
+                # placement scan, emit)
+                "gpu_launches": args.steps * (1 + base.nsteps * (4 + 11))}
         print(json.dumps(line), flush=True)
 
 

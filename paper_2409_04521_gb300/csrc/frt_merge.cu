@@ -32,6 +32,7 @@
 //               in the queue and each group's leader takes the next entry of
 //               the merged-ray list; a ray alone in its group stays and
 //               clears the group's word;
+//   k_mscan   : the blocks' places in the appended run of merged rays;
 //   k_memit   : per entry of that list, the merged ray (means rounded once),
 //               appended densely after the march's output, and the group
 //               cleared for the next step.
@@ -697,52 +698,66 @@ __global__ void __launch_bounds__(256, 4) k_mweight(MergeArgs A) {
 // ---------------------------------------------------------------------------
 // the merged rays, appended after the march's output
 // ---------------------------------------------------------------------------
+// the merged-ray lists' places in the appended run: an exclusive prefix of
+// the blocks' counts (written over the candidate counts, which the weight
+// pass was the last to read); the queue's new count; the rays the merge
+// removed.  One block of 1024 threads, four counts a thread.
+__global__ void __launch_bounds__(1024) k_mscan(MergeArgs A, int nblocks) {
+    __shared__ unsigned long long s_w[33];
+    __shared__ int s_on;
+    Ctl *C = A.ctl;
+    if (!block_runs(C, true, &s_on)) return;
+    const int lane = lane_id(), wid = threadIdx.x >> 5;
+    uint32_t v[4];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int k = 4 * threadIdx.x + j;
+        v[j] = k < nblocks ? A.w.bled[k] : 0u;
+        sum += v[j];
+    }
+    const unsigned long long inc = warp_incl_scan64(sum);
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const unsigned long long w = s_w[lane], wi = warp_incl_scan64(w);
+        __syncwarp();
+        s_w[lane] = wi - w;
+        if (lane == 31) s_w[32] = wi;
+    }
+    __syncthreads();
+    unsigned long long pre = s_w[wid] + inc - sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int k = 4 * threadIdx.x + j;
+        if (k < nblocks) A.w.bcnt[k] = (uint32_t)pre;
+        pre += v[j];
+    }
+    const unsigned long long tot = s_w[32];
+    const int par = C->par;
+    const long long mbase = C->mbase;
+    if ((long long)(mbase + tot) > A.cap) {
+        if (threadIdx.x == 0) atomicOr(&C->err, 1);
+        return;
+    }
+    if (threadIdx.x == 0) C->cnt[par ^ 1] = mbase + (long long)tot;
+    for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) {
+        uint32_t *d = A.w.sel + SEL_W * k + SEL_DROP;
+        if (*d) {
+            A.acc[k].p_rays_out -= (double)*d;
+            *d = 0u;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256, 4) k_memit(MergeArgs A) {
-    __shared__ unsigned long long s_sum[2][8];
     __shared__ int s_on;
     Ctl *C = A.ctl;
     if (!block_runs(C, true, &s_on)) return;
     const int par = C->par;
     const Queue q = A.q[par ^ 1];
     const long long mbase = C->mbase;
-    // this block's place in the appended run: the merged rays of the blocks
-    // before it; and the run's length
-    unsigned long long pre = 0, tot = 0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
-        const uint32_t v = A.w.bled[k];
-        tot += v;
-        if (k < (int)blockIdx.x) pre += v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        pre += __shfl_xor_sync(FULL, pre, o);
-        tot += __shfl_xor_sync(FULL, tot, o);
-    }
-    if (lane_id() == 0) {
-        s_sum[0][threadIdx.x >> 5] = pre;
-        s_sum[1][threadIdx.x >> 5] = tot;
-    }
-    __syncthreads();
-    pre = tot = 0;
-    for (int w = 0; w < 8; ++w) {
-        pre += s_sum[0][w];
-        tot += s_sum[1][w];
-    }
-    if ((long long)(mbase + tot) > A.cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&C->err, 1);
-        return;
-    }
-    if (blockIdx.x == 0) {
-        // no other thread of this kernel reads the count or the removals
-        if (threadIdx.x == 0) C->cnt[par ^ 1] = mbase + (long long)tot;
-        for (int k = threadIdx.x; k < A.nsims; k += blockDim.x) {
-            uint32_t *d = A.w.sel + SEL_W * k + SEL_DROP;
-            if (*d) {
-                A.acc[k].p_rays_out -= (double)*d;
-                *d = 0u;
-            }
-        }
-    }
+    const unsigned long long pre = A.w.bcnt[blockIdx.x];   // this block's place in the appended run
     const long long b0 = blockIdx.x * block_chunk(mbase);
     const uint32_t bl = A.w.bled[blockIdx.x];
     const int ndir = A.w.ndir, gw = A.w.grp_w, nbq = A.nbq;
@@ -827,6 +842,7 @@ cudaError_t launch_merge(const MergeArgs &a, int sm_count, cudaStream_t st, cons
     if (side && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
     k_mgroup<<<rblocks, 256, 0, st>>>(a);
     k_mweight<<<rblocks, 256, (size_t)a.nsims * sizeof(uint32_t), st>>>(a);
+    k_mscan<<<1, 1024, 0, st>>>(a, rblocks);
     k_memit<<<rblocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
