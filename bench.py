@@ -684,7 +684,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="flexrt", choices=["flexrt", "reference"])
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--rt-steps", type=int, default=100)
-    ap.add_argument("--capacity", type=int, default=400_000_000)
+    ap.add_argument("--capacity", type=int, default=200_000_000)
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

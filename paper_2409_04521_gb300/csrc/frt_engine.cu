@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 
 #include "frt_engine.h"
 
@@ -152,6 +153,7 @@ Engine::~Engine() {
     if (h_err_) cudaFreeHost(h_err_);
     if (h_stage_) cudaFreeHost(h_stage_);
     if (h_nh_) cudaFreeHost(h_nh_);
+    if (h_fields_) cudaFreeHost(h_fields_);
     if (ev_nh_) cudaEventDestroy(ev_nh_);
     if (ev_err_) cudaEventDestroy(ev_err_);
     if (ev_stage_) cudaEventDestroy(ev_stage_);
@@ -892,34 +894,57 @@ flexrt_status Engine::read_acc(int s, SimAcc &a) {
     return FLEXRT_OK;
 }
 
+// Runs fn(i0, i1) over [0, n) on up to eight host threads (one when n is
+// small): the read-back's conversions write the caller's arrays in parallel.
+template <typename F>
+static void host_parallel(size_t n, F fn) {
+    const size_t nt = n >= (1u << 20) ? 8 : 1;
+    if (nt == 1) { fn((size_t)0, n); return; }
+    std::vector<std::thread> th;
+    const size_t per = (n + nt - 1) / nt;
+    for (size_t k = 1; k < nt; ++k) {
+        const size_t i0 = std::min(n, k * per), i1 = std::min(n, (k + 1) * per);
+        th.emplace_back([=]() { fn(i0, i1); });
+    }
+    fn((size_t)0, std::min(n, per));
+    for (auto &t : th) t.join();
+}
+
 flexrt_status Engine::fields(int s, flexrt_fields *f) {
     const Slot *sl = slot(s);
     if (!sl || !f) return fail(FLEXRT_E_INVALID, "bad slot or fields");
-    CK(cudaStreamSynchronize(st_));
-    poll(true);
     const size_t n = (size_t)sl->h.ncell;
     const long long c0 = sl->cell0;
-    std::vector<double> y;
-    std::vector<float> t;
-    if (f->T || f->gamma_HI || f->x_HII) t.resize(n);
+    // the cells' words go to pinned staging in stream order (neutral
+    // fraction, n_H, then the single-precision x, T, Gamma), then the host
+    // converts them into the caller's double arrays
+    const size_t need = n * (2 * sizeof(double) + 3 * sizeof(float));
+    if (need > h_fields_bytes_) {
+        if (h_fields_) { CK(cudaStreamSynchronize(st_)); cudaFreeHost(h_fields_); h_fields_ = nullptr; h_fields_bytes_ = 0; }
+        if (cudaMallocHost(&h_fields_, need) != cudaSuccess) return fail(FLEXRT_E_OOM, "pinned allocation failed");
+        h_fields_bytes_ = need;
+    }
+    double *hy = static_cast<double *>(h_fields_), *hn = hy + n;
+    float *hx = reinterpret_cast<float *>(hn + n), *hT = hx + n, *hg = hT + n;
     if (f->n_HI) {
-        y.resize(n);
-        CK(cudaMemcpy(y.data(), cells_.y + c0, n * sizeof(double), cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(f->n_HI, cells_.nH + c0, n * sizeof(double), cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < n; ++i) f->n_HI[i] *= y[i];
+        CK(cudaMemcpyAsync(hy, cells_.y + c0, n * sizeof(double), cudaMemcpyDeviceToHost, st_));
+        CK(cudaMemcpyAsync(hn, cells_.nH + c0, n * sizeof(double), cudaMemcpyDeviceToHost, st_));
     }
-    if (f->x_HII) {
-        CK(cudaMemcpy(t.data(), cells_.x + c0, n * sizeof(float), cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < n; ++i) f->x_HII[i] = t[i];
-    }
-    if (f->T) {
-        CK(cudaMemcpy(t.data(), cells_.T + c0, n * sizeof(float), cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < n; ++i) f->T[i] = t[i];
-    }
-    if (f->gamma_HI) {
-        CK(cudaMemcpy(t.data(), cells_.gamma + c0, n * sizeof(float), cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < n; ++i) f->gamma_HI[i] = t[i];
-    }
+    if (f->x_HII) CK(cudaMemcpyAsync(hx, cells_.x + c0, n * sizeof(float), cudaMemcpyDeviceToHost, st_));
+    if (f->T) CK(cudaMemcpyAsync(hT, cells_.T + c0, n * sizeof(float), cudaMemcpyDeviceToHost, st_));
+    if (f->gamma_HI) CK(cudaMemcpyAsync(hg, cells_.gamma + c0, n * sizeof(float), cudaMemcpyDeviceToHost, st_));
+    CK(cudaStreamSynchronize(st_));
+    poll(true);                                   // latch a failed step's error (the state is kept)
+    host_parallel(n, [&](size_t i0, size_t i1) {
+        if (f->n_HI)
+            for (size_t i = i0; i < i1; ++i) f->n_HI[i] = hn[i] * hy[i];
+        if (f->x_HII)
+            for (size_t i = i0; i < i1; ++i) f->x_HII[i] = hx[i];
+        if (f->T)
+            for (size_t i = i0; i < i1; ++i) f->T[i] = hT[i];
+        if (f->gamma_HI)
+            for (size_t i = i0; i < i1; ++i) f->gamma_HI[i] = hg[i];
+    });
     return FLEXRT_OK;
 }
 

@@ -152,6 +152,8 @@ class Engine {
     int32_t *h_err_ = nullptr;     // the last step's queue counts, parity and error word
     double *h_stage_ = nullptr;
     double *h_nh_ = nullptr;       // pinned staging of a member's n_H (engines of several members)
+    void *h_fields_ = nullptr;     // pinned staging of the fields read-back, grown on demand
+    size_t h_fields_bytes_ = 0;
     cudaEvent_t ev_nh_ = nullptr;  // its upload has been consumed
     long long q_used_ = 0;         // live rays after the last step the host has seen complete
     cudaEvent_t ev_err_ = nullptr, ev_stage_ = nullptr;
