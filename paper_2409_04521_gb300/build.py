@@ -1,6 +1,6 @@
 """Build libflexrt.so (the C-ABI library of include/flexrt.h) for sm_103a.
 
-The two translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 ``paper_2409_04521_gb300/_build/libflexrt.so``.
 """
 from __future__ import annotations
@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libflexrt.so")
-SOURCES = ["flexrt_api.cu", "frt_engine.cu", "frt_kernels.cu", "frt_merge.cu", "frt_static.cu"]
+SOURCES = ["flexrt_api.cu", "frt_engine.cu", "frt_kernels.cu", "frt_merge.cu", "frt_march_gen.cu", "frt_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

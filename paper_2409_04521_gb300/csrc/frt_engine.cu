@@ -311,7 +311,7 @@ flexrt_status Engine::init(const EngineConfig &cfg) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device_);
     sm_count_ = std::max(sms, 1);
-    const bool ext = ext_variants();
+    const int ext = ext_variants();
     if (!march_variant_exists(cfg_.nb, march_agg_, march_minb_, ext)) { march_agg_ = 0; march_minb_ = 2; }
     CK(march_prepare(cfg_.nb, march_agg_, march_minb_, ms, ext));
     const int per_sm = march_max_blocks_per_sm(cfg_.nb, march_agg_, march_minb_, march_threads_, ms, ext);

@@ -88,8 +88,9 @@ class Engine {
     flexrt_status rays_merged(int slot, int64_t cap, int32_t *merged, int32_t *vertex, int32_t *dist, int64_t *pos,
                               double *thr, int64_t *n);
     bool merge_built() const { return cfg_.merge_l_max >= 0; }
-    // the march variants that carry merged rays and the moving screen
-    bool ext_variants() const { return merge_built() || cfg_.gen_capable; }
+    // the march variants: 0 plain, 1 with merged rays, 3 with merged rays
+    // and the moving screen (engines that may run Generalized members)
+    int ext_variants() const { return cfg_.gen_capable ? 3 : (merge_built() ? 1 : 0); }
     flexrt_status ionized_volume(int slot, double *x_ion);
     // checkpoint of a single-simulation engine (slot 0): bytes needed, save, load
     flexrt_status save_state(int slot, void *buf, int64_t cap, int64_t *bytes);

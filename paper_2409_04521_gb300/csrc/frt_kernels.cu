@@ -558,7 +558,8 @@ cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st) {
 // Kernel variants: every bin count with the default (AGG 0, 2 blocks/SM);
 // the bin counts of the standard spectra (1, 3, 4) with every aggregation
 // and register budget, for the autotuner.  The variants with merged rays
-// are built in frt_merge.cu.
+// are built in frt_merge.cu, those that also run Generalized members in
+// frt_march_gen.cu.
 static MarchFn march_fn_plain(int nb, int agg, int minb) {
 #define FRT_V(NB)                                                                   \
     if (nb == NB) {                                                                \
@@ -587,26 +588,31 @@ static MarchFn march_fn_plain(int nb, int agg, int minb) {
         default: return nullptr;
     }
 }
-static MarchFn march_fn(int nb, int agg, int minb, bool merge) {
-    return merge ? march_fn_merge(nb, agg, minb) : march_fn_plain(nb, agg, minb);
+static MarchFn march_fn(int nb, int agg, int minb, int ext) {
+    switch (ext) {
+        case 0: return march_fn_plain(nb, agg, minb);
+        case 1: return march_fn_merge(nb, agg, minb);
+        case 3: return march_fn_gen(nb, agg, minb);
+        default: return nullptr;
+    }
 }
-bool march_variant_exists(int nb, int agg, int minb, bool merge) { return march_fn(nb, agg, minb, merge) != nullptr; }
-cudaError_t march_prepare(int nb, int agg, int minb, int nsims, bool merge) {
-    MarchFn f = march_fn(nb, agg, minb, merge);
+bool march_variant_exists(int nb, int agg, int minb, int ext) { return march_fn(nb, agg, minb, ext) != nullptr; }
+cudaError_t march_prepare(int nb, int agg, int minb, int nsims, int ext) {
+    MarchFn f = march_fn(nb, agg, minb, ext);
     if (!f) return cudaErrorInvalidValue;
     const size_t sh = march_shared_bytes(nsims);
     if (sh > 48 * 1024) return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     return cudaSuccess;
 }
 cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st,
-                         bool merge) {
-    MarchFn f = march_fn(nb, agg, minb, merge);
+                         int ext) {
+    MarchFn f = march_fn(nb, agg, minb, ext);
     if (!f) return cudaErrorInvalidValue;
     f<<<blocks, threads, march_shared_bytes(a.nsims), st>>>(a);
     return cudaGetLastError();
 }
-int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims, bool merge) {
-    MarchFn f = march_fn(nb, agg, minb, merge);
+int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims, int ext) {
+    MarchFn f = march_fn(nb, agg, minb, ext);
     if (!f) return 0;
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, march_shared_bytes(nsims));

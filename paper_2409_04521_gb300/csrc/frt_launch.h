@@ -65,12 +65,15 @@ cudaError_t launch_emit(const EmitArgs &a, int blocks, cudaStream_t st);
 using MarchFn = void (*)(MarchArgs);
 // the march variant with merged rays (nullptr if not built)
 MarchFn march_fn_merge(int nb, int agg, int minb);
-bool march_variant_exists(int nb, int agg, int minb, bool merge);
+// the variant with merged rays and Generalized Opacity mode (nullptr if not built)
+MarchFn march_fn_gen(int nb, int agg, int minb);
+// ext: 0 plain, 1 merged rays, 3 merged rays and Generalized mode
+bool march_variant_exists(int nb, int agg, int minb, int ext);
 // opt the variant into the dynamic shared memory `nsims` slots need
-cudaError_t march_prepare(int nb, int agg, int minb, int nsims, bool merge);
+cudaError_t march_prepare(int nb, int agg, int minb, int nsims, int ext);
 cudaError_t launch_march(const MarchArgs &a, int nb, int agg, int minb, int blocks, int threads, cudaStream_t st,
-                         bool merge);
-int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims, bool merge);
+                         int ext);
+int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims, int ext);
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st);
 cudaError_t launch_end(Ctl *c, SimDev *sims, SimAcc *acc, int nsims, cudaStream_t st);
 // between passes of the iteration: drop the march's output and the step's tallies (not emission)

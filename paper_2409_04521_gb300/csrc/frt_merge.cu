@@ -1,5 +1,5 @@
 // frt_merge.cu -- ray merging at the end of a step (Sec. 3.3, Eq. 4) and the
-// march variants that carry merged rays.
+// march variants that carry merged rays (without Generalized Opacity mode).
 //
 // The step, per simulation that merges (it has more live rays than
 // K = floor(N_ex * N_RT)):
@@ -45,7 +45,7 @@
 namespace frt {
 
 // ---------------------------------------------------------------------------
-// march variants with merged rays
+// march variants with merged rays (engines without Generalized members)
 // ---------------------------------------------------------------------------
 MarchFn march_fn_merge(int nb, int agg, int minb) {
 #define FRT_V(NB)                                                                   \
