@@ -330,6 +330,11 @@ def impl_gpu(args, dist):
     ms = ev0.elapsed_time(ev1)
     kms, klaunch, krays = sim.kernel_times()
     sim.profile(False)
+    # Generalized mode: photons the moving screens absorbed beyond their atoms
+    # (ionising nothing) over those emitted, in the last timed simulation
+    screen_excess = None
+    if prob.options.gen_mode:
+        screen_excess = sim.screen_excess() / max(sim.budget()[0], 1e-300)
     sim.close()
 
     t_max = dist.max(ms)
@@ -424,6 +429,8 @@ def impl_gpu(args, dist):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_sim * args.steps,
                 "oracle_parity": parity, "batch": batch, "serve": serve_line}
+        if screen_excess is not None:
+            line["screen_excess_rel_of_emitted"] = screen_excess
         print(json.dumps(line), flush=True)
 
 

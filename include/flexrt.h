@@ -213,6 +213,13 @@ flexrt_status flexrt_get_fields(flexrt_ctx *ctx, flexrt_fields *f);
  * flight in live rays.  emitted = absorbed + escaped + in flight. */
 flexrt_status flexrt_get_budget(flexrt_ctx *ctx, double out[4]);
 
+/* Generalized Opacity mode (Sec. 4.2, Eq. 18): photons that moving screens
+ * absorbed beyond the neutral atoms their cells had, since creation/reset --
+ * part of out[1] of flexrt_get_budget that ionised nothing (a screen first
+ * reached in the step's last pass of the Gamma - <n_HI> iteration takes all
+ * that reaches it; more passes shrink it).  0 in Standard mode. */
+flexrt_status flexrt_get_screen_excess(flexrt_ctx *ctx, double *photons);
+
 /* Counters: out[0] live rays, out[1] ray-cell segments of the last step,
  * out[2] segments since creation/reset, out[3] steps taken, out[4] queue
  * capacity, out[5] rays marched in the last step. */
@@ -431,6 +438,7 @@ flexrt_status flexrt_batch_retire(flexrt_batch *b, int32_t slot);
 /* Per-member read-back, as the single-simulation getters. */
 flexrt_status flexrt_batch_get_fields(flexrt_batch *b, int32_t slot, flexrt_fields *f);
 flexrt_status flexrt_batch_get_budget(flexrt_batch *b, int32_t slot, double out[4]);
+flexrt_status flexrt_batch_get_screen_excess(flexrt_batch *b, int32_t slot, double *photons);
 flexrt_status flexrt_batch_get_counts(flexrt_batch *b, int32_t slot, int64_t out[6]);
 flexrt_status flexrt_batch_get_segment_counts(flexrt_batch *b, int32_t slot, int32_t *out);
 flexrt_status flexrt_batch_get_rays(flexrt_batch *b, int32_t slot, int64_t cap, int32_t *level,

@@ -125,6 +125,9 @@ extern "C" flexrt_status flexrt_get_fields(flexrt_ctx *c, flexrt_fields *f) {
 extern "C" flexrt_status flexrt_get_budget(flexrt_ctx *c, double out[4]) {
     return c ? c->eng.budget(c->slot, out) : FLEXRT_E_INVALID;
 }
+extern "C" flexrt_status flexrt_get_screen_excess(flexrt_ctx *c, double *photons) {
+    return c ? c->eng.screen_excess(c->slot, photons) : FLEXRT_E_INVALID;
+}
 extern "C" flexrt_status flexrt_get_counts(flexrt_ctx *c, int64_t out[6]) {
     return c ? c->eng.counts(c->slot, out) : FLEXRT_E_INVALID;
 }
@@ -253,6 +256,9 @@ extern "C" flexrt_status flexrt_batch_get_segment_counts(flexrt_batch *b, int32_
 }
 extern "C" flexrt_status flexrt_batch_get_budget(flexrt_batch *b, int32_t slot, double out[4]) {
     return b ? b->eng.budget(slot, out) : FLEXRT_E_INVALID;
+}
+extern "C" flexrt_status flexrt_batch_get_screen_excess(flexrt_batch *b, int32_t slot, double *photons) {
+    return b ? b->eng.screen_excess(slot, photons) : FLEXRT_E_INVALID;
 }
 extern "C" flexrt_status flexrt_batch_get_counts(flexrt_batch *b, int32_t slot, int64_t out[6]) {
     return b ? b->eng.counts(slot, out) : FLEXRT_E_INVALID;

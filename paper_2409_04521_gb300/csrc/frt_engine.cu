@@ -959,6 +959,16 @@ flexrt_status Engine::budget(int s, double out[4]) {
     return FLEXRT_OK;
 }
 
+flexrt_status Engine::screen_excess(int s, double *out) {
+    const Slot *sl = slot(s);
+    if (!sl || !out) return fail(FLEXRT_E_INVALID, "bad slot");
+    SimAcc a;
+    flexrt_status r = read_acc(s, a);
+    if (r != FLEXRT_OK) return r;
+    *out = a.lost * sl->h.nref;
+    return FLEXRT_OK;
+}
+
 flexrt_status Engine::counts(int s, int64_t out[6]) {
     const Slot *sl = slot(s);
     if (!sl || !out) return fail(FLEXRT_E_INVALID, "bad slot");

@@ -81,6 +81,7 @@ class Engine {
     flexrt_status reset_all();                // single-simulation reset
     flexrt_status fields(int slot, flexrt_fields *f);
     flexrt_status budget(int slot, double out[4]);
+    flexrt_status screen_excess(int slot, double *out);   // Generalized mode: photons absorbed beyond the atoms
     flexrt_status counts(int slot, int64_t out[6]);
     flexrt_status segment_counts(int slot, int32_t *out);
     flexrt_status rays(int slot, int64_t cap, int32_t *level, int64_t *pixel, int32_t *emitter, int32_t *birth,

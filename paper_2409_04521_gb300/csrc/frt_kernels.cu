@@ -227,9 +227,11 @@ __global__ void k_emit(EmitArgs A) {
 // chemistry
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
-    // per-simulation absorbed totals, then the active cell ranges
+    // per-simulation absorbed totals and screens' excess photons, then the
+    // active cell ranges
     extern __shared__ double sh_abs[];
-    long long *s_pref = reinterpret_cast<long long *>(sh_abs + A.nsims);
+    double *sh_lost = sh_abs + A.nsims;
+    long long *s_pref = reinterpret_cast<long long *>(sh_lost + A.nsims);
     long long *s_cell0 = s_pref + A.nsims + 1;
     int *s_sim = reinterpret_cast<int *>(s_cell0 + A.nsims);
     // Generalized mode: its flag and the atoms of a cell per unit n_H, in
@@ -240,6 +242,7 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
     const int nrng = C->n_ranges;
     for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) {
         sh_abs[i] = 0.0;
+        sh_lost[i] = 0.0;
         const SimDev &S = A.sims[i];
         s_apn[i] = S.apn_f;
         s_gen[i] = S.gen_mode;
@@ -313,6 +316,12 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
                     } else {
                         const float dxf = (fs.x + d.x) / Ac - alpha * nHf * xf * SG.dt_f;
                         const double x1 = fmin(fmax(x + (double)dxf, 0.0), 1.0);
+                        // a screen that absorbed more photons than its cell had
+                        // neutral atoms (one first reached in the last pass: its
+                        // share came from a pass it was not lit in): the excess
+                        // ionises nothing
+                        const float sx = fs.x - omx * Ac;
+                        if (sx > 0.0f) atomicAdd(&sh_lost[sim], (double)sx);
                         const float om1 = (float)(1.0 - x1), x1f = (float)x1;
                         A.cells.rho[g] = fs.y > om1 * Ac ? om1 * Ac / fs.y : 1.0f;
                         // the temperature moves with the start-of-step neutral
@@ -418,8 +427,10 @@ __global__ void __launch_bounds__(256) k_chem(ChemArgs A) {
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x)
+    for (int i = threadIdx.x; i < A.nsims; i += blockDim.x) {
         if (sh_abs[i] != 0.0) atomicAdd(&A.acc[i].p_abs, sh_abs[i]);
+        if (sh_lost[i] != 0.0) atomicAdd(&A.acc[i].p_lost, sh_lost[i]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -439,10 +450,11 @@ __global__ void k_end(Ctl *C, SimDev *sims, SimAcc *acc, int nsims) {
             a.rays_live = a.p_rays_out;
             a.rays_in_last = a.p_rays_in;
             a.rays_in_total += a.p_rays_in;
+            a.lost += a.p_lost;
             sims[j].step += 1;
         }
         a.p_emit = a.p_abs = a.p_esc = a.p_out = a.p_in = 0.0;
-        a.p_seg = a.p_rays_in = a.p_rays_out = 0.0;
+        a.p_seg = a.p_rays_in = a.p_rays_out = a.p_lost = 0.0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -467,7 +479,7 @@ __global__ void k_iter_reset(Ctl *C, SimAcc *acc, int nsims) {
         SimAcc &a = acc[j];
         a.rays_in_total += a.p_rays_in;
         a.p_abs = a.p_esc = a.p_out = a.p_in = 0.0;
-        a.p_seg = a.p_rays_in = a.p_rays_out = 0.0;
+        a.p_seg = a.p_rays_in = a.p_rays_out = a.p_lost = 0.0;
     }
     if (threadIdx.x == 0) C->cnt[C->par ^ 1] = 0;
 }
@@ -619,7 +631,7 @@ int march_max_blocks_per_sm(int nb, int agg, int minb, int threads, int nsims, i
     return n;
 }
 cudaError_t launch_chem(const ChemArgs &a, int blocks, cudaStream_t st) {
-    const size_t sh = (size_t)a.nsims * sizeof(double) + (size_t)(2 * a.nsims + 1) * sizeof(long long) +
+    const size_t sh = (size_t)a.nsims * 2 * sizeof(double) + (size_t)(2 * a.nsims + 1) * sizeof(long long) +
                       (size_t)a.nsims * (2 * sizeof(int) + sizeof(float));
     k_chem<<<blocks, 256, sh, st>>>(a);
     return cudaGetLastError();

@@ -82,7 +82,11 @@ struct SimAcc {
     double emitted, absorbed, escaped, in_flight;     // committed
     double p_emit, p_abs, p_esc, p_out, p_in;         // current step
     double p_seg, p_rays_in, p_rays_out;              // current step
-    double seg_last, seg_total, rays_live, rays_in_last, rays_in_total;
+    double seg_last, seg_total, rays_live, rays_in_last;
+    // Generalized mode: photons a screen absorbed beyond the atoms it had
+    // (ionising nothing), this step and committed
+    double p_lost, lost;
+    double rays_in_total;   // marched rays since creation (kept by a reset: last)
 };
 
 // Global control words of one engine.

@@ -105,6 +105,7 @@ def lib():
             L.flexrt_reset.argtypes = [vp]
             L.flexrt_get_fields.argtypes = [vp, P(Fields)]
             L.flexrt_get_budget.argtypes = [vp, P(C.c_double)]
+            L.flexrt_get_screen_excess.argtypes = [vp, P(C.c_double)]
             L.flexrt_get_counts.argtypes = [vp, P(C.c_int64)]
             L.flexrt_get_segment_counts.argtypes = [vp, P(C.c_int32)]
             L.flexrt_get_rays.argtypes = [vp, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32), P(C.c_int32),
@@ -132,6 +133,7 @@ def lib():
             L.flexrt_batch_retire.argtypes = [vp, C.c_int32]
             L.flexrt_batch_get_fields.argtypes = [vp, C.c_int32, P(Fields)]
             L.flexrt_batch_get_budget.argtypes = [vp, C.c_int32, P(C.c_double)]
+            L.flexrt_batch_get_screen_excess.argtypes = [vp, C.c_int32, P(C.c_double)]
             L.flexrt_batch_get_counts.argtypes = [vp, C.c_int32, P(C.c_int64)]
             L.flexrt_batch_get_segment_counts.argtypes = [vp, C.c_int32, P(C.c_int32)]
             L.flexrt_batch_get_rays.argtypes = [vp, C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int64), P(C.c_int32),
@@ -291,6 +293,11 @@ class Batch:
         self._check(lib().flexrt_batch_get_budget(self._h, int(slot), _p(b, C.c_double)))
         return b
 
+    def screen_excess(self, slot):
+        v = np.zeros(1)
+        self._check(lib().flexrt_batch_get_screen_excess(self._h, int(slot), _p(v, C.c_double)))
+        return float(v[0])
+
     def counts(self, slot):
         c = np.zeros(6, np.int64)
         self._check(lib().flexrt_batch_get_counts(self._h, int(slot), _p(c, C.c_int64)))
@@ -416,6 +423,13 @@ class Simulation:
         b = np.zeros(4)
         _check(lib().flexrt_get_budget(self._h, _p(b, C.c_double)), self._h)
         return b
+
+    def screen_excess(self):
+        """Photons the moving screens absorbed beyond their atoms (Generalized
+        mode; part of the absorbed photons that ionised nothing)."""
+        v = np.zeros(1)
+        _check(lib().flexrt_get_screen_excess(self._h, _p(v, C.c_double)), self._h)
+        return float(v[0])
 
     def counts(self):
         c = np.zeros(6, np.int64)

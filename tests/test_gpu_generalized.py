@@ -172,3 +172,51 @@ def test_generalized_subgrid_law_with_temperature():
     p = dc.replace(p, options=dc.replace(p.options, gen_mode=True, gamma_iters=4, chi=0.08, isothermal=False,
                                          T_init=100.0, t_reion=2e4))
     _run_gen_pair(p, x_atol=1e-4, vol_rtol=1e-5, bud_rtol=1e-6, g_rtol=1e-3, T_rtol=1e-3)
+
+
+def _oracle_lost(p):
+    """The oracle's photons absorbed that ionised nothing, over those emitted:
+    absorbed - (atoms ionised + recombinations in the ionised parts)."""
+    o = oracle.OracleSim(p)
+    V = p.dx_phys_cm ** 3
+    x0, a0, lost = np.zeros(p.ncell), 0.0, 0.0
+    for _ in range(p.nsteps):
+        o.step(p.dt)
+        x, _ = o.gen_state()
+        b = o.budget()
+        used = ((x - x0) * p.nH * V).sum() + (p.options.alpha_B_const * p.nH ** 2 * x0 * V * p.dt).sum()
+        lost += (b[1] - a0) - used
+        x0, a0 = x, b[1]
+    o.close()
+    return lost / b[0]
+
+
+def test_screen_excess_is_zero_in_standard_mode():
+    p = W.stromgren(n=16, nsteps=6)
+    g = F.Simulation(p, ray_capacity=1 << 20)
+    for _ in range(p.nsteps):
+        g.step(p.dt)
+    assert g.screen_excess() == 0.0
+    g.close()
+
+
+def test_screen_excess_against_oracle_loss():
+    # photons the screens absorbed beyond their cells' neutral atoms, on the
+    # first 40 steps of the 32^3 sphere: with 4 passes a measurable part of
+    # the oracle's photons that ionised nothing (absorbed minus ionisations
+    # and recombinations), with 6 passes iterated away on both sides
+    p = _gen_stromgren(40, iters=4)
+    g = F.Simulation(p, ray_capacity=1 << 22)
+    for _ in range(p.nsteps):
+        g.step(p.dt)
+    lg = g.screen_excess() / g.budget()[0]
+    g.close()
+    lo = _oracle_lost(p)
+    assert 1e-3 < lo < 1e-2
+    assert 0.5 * lo <= lg <= 1.05 * lo
+    p6 = _gen_stromgren(40, iters=6)
+    g = F.Simulation(p6, ray_capacity=1 << 22)
+    for _ in range(p6.nsteps):
+        g.step(p6.dt)
+    assert 0.0 <= g.screen_excess() / g.budget()[0] < 1e-6
+    g.close()
